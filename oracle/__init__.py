@@ -1,0 +1,27 @@
+"""Plain, slow FP64 CPU oracle for the ET-AIM hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the timed CPU
+baseline of the benchmark may import this package; the product path never calls
+it and shares no code, tables or constants with it.
+
+What it computes (each module cites the passage it follows):
+
+* ``rwg``        RWG spatial basis on a triangle mesh (Sec. 3, Eq. 3).
+* ``tbasis``     causal piecewise-polynomial interpolatory temporal basis, CPPIF
+                 (Sec. 3, Eq. 3).
+* ``quad``       triangle cubature rules.
+* ``singular``   closed-form integrals of 1/R and (r'-r)/R over a triangle, used
+                 for singularity extraction (Sec. 3.1 mentions singularity
+                 extraction; the formulas follow Wilton et al. 1984 / Graglia 1993).
+* ``efie``       envelope EFIE impedance matrices Z_m of ET-MOT (Eq. 4), the
+                 excitation vector V_l from the modulated Gaussian (Eq. 1), and the
+                 frequency-domain EFIE matrix used by the DC-identity pin.
+* ``aim``        the ET-AIM operator of Eq. 5: moment-matching anter/interpolation,
+                 grid Green-function envelopes, brute-force and FFT grid sums, and
+                 the pre-corrected near-zone matrices (Sec. 4, stages i-iv).
+* ``march``      time marching of Eq. 4 (direct ET-MOT) and Eq. 5 (ET-AIM).
+* ``mie``        Mie series for a PEC sphere (Sec. 5, reference [18]).
+
+Readings of passages the paper leaves open are listed in the design notes; the
+code states each one where it is used.
+"""

@@ -1,0 +1,242 @@
+"""Seeded synthetic inputs: surface meshes, excitation parameters and workload recipes.
+
+This module feeds both the CUDA path and the CPU oracle.  It holds geometry and
+bookkeeping only (meshes, pulse parameters, grid placement, random draws) and
+none of the method's arithmetic (no basis functions, kernels or matrices).
+
+Workloads follow the benchmark shapes of the paper: PEC spheres meshed with
+triangles, a cosine-modulated Gaussian plane wave (Sec. 2.2, Eq. 1) whose band
+is f_c +- 3/(2 pi sigma), a delay t_d = 8 sigma (Table I), time step
+dt = beta / f_bw with beta = 1/4 (Sec. 3, after Eq. 3) and an auxiliary grid that
+encloses the object (Sec. 4).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# meshes
+# ----------------------------------------------------------------------------
+
+
+def _orient_outward(v: np.ndarray, f: np.ndarray, center: np.ndarray) -> np.ndarray:
+    """Flip faces so that (b-a)x(c-a) points away from ``center`` (convex bodies)."""
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    n = np.cross(b - a, c - a)
+    out = np.einsum("ij,ij->i", n, (a + b + c) / 3.0 - center) < 0
+    f = f.copy()
+    f[out] = f[out][:, [0, 2, 1]]
+    return f
+
+
+def icosphere(sub: int, radius: float = 1.0, center=(0.0, 0.0, 0.0)):
+    """Icosahedron refined ``sub`` times (each triangle split in 4), projected on a sphere.
+
+    Returns ``(V[nv,3] float64, F[nt,3] int32)`` with faces counter-clockwise seen
+    from outside.  ``20 * 4**sub`` triangles, ``30 * 4**sub`` edges.
+    """
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, p, 0), (1, p, 0), (-1, -p, 0), (1, -p, 0),
+         (0, -1, p), (0, 1, p), (0, -1, -p), (0, 1, -p),
+         (p, 0, -1), (p, 0, 1), (-p, 0, -1), (-p, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+         (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+         (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+         (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.asarray(x, dtype=np.float64) / math.sqrt(1 + p * p) for x in v]
+    faces = list(f)
+    for _ in range(sub):
+        cache: dict[tuple[int, int], int] = {}
+
+        def mid(i, j):
+            key = (i, j) if i < j else (j, i)
+            if key not in cache:
+                m = verts[i] + verts[j]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+        faces = nf
+    V = np.asarray(verts) * radius + np.asarray(center, dtype=np.float64)
+    F = np.asarray(faces, dtype=np.int32)
+    F = _orient_outward(V, F, np.asarray(center, dtype=np.float64))
+    return V, F.astype(np.int32)
+
+
+def sphere_array(sub: int, radius: float, pitch: float, nx: int = 4, ny: int = 4):
+    """``nx x ny`` spheres in the z=0 plane, centred on the origin, at ``pitch``."""
+    Vs, Fs, off = [], [], 0
+    xs = (np.arange(nx) - (nx - 1) / 2.0) * pitch
+    ys = (np.arange(ny) - (ny - 1) / 2.0) * pitch
+    for y in ys:
+        for x in xs:
+            V, F = icosphere(sub, radius, (x, y, 0.0))
+            Vs.append(V)
+            Fs.append(F + off)
+            off += len(V)
+    return np.concatenate(Vs), np.concatenate(Fs).astype(np.int32)
+
+
+def ellipsoid_mesh(semi_axes=(1.0, 0.5, 0.25), n_points: int = 6668, seed: int = 3,
+                   jitter: float = 0.25):
+    """Closed ellipsoid surface from jittered Fibonacci-sphere samples.
+
+    The samples are mapped onto the ellipsoid and triangulated with a 3-D convex
+    hull (the surface Delaunay triangulation of a convex body).  Faces are oriented
+    outward.  ``E = 3 (V - 2)`` edges, i.e. about ``3 n_points`` RWG unknowns.
+    """
+    from scipy.spatial import ConvexHull
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    i = np.arange(n_points, dtype=np.float64) + 0.5
+    i = i + jitter * (rng.random(n_points) - 0.5)
+    z = 1.0 - 2.0 * i / n_points
+    phi = math.pi * (3.0 - math.sqrt(5.0)) * np.arange(n_points)
+    phi = phi + jitter * 0.5 * (rng.random(n_points) - 0.5)
+    r = np.sqrt(np.clip(1.0 - z * z, 0.0, None))
+    u = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    V = u * np.asarray(semi_axes, dtype=np.float64)
+    hull = ConvexHull(V)
+    F = _orient_outward(V, hull.simplices.astype(np.int32), np.zeros(3))
+    return V, F.astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# plane-wave draws
+# ----------------------------------------------------------------------------
+
+
+def random_plane_waves(nb: int, seed: int):
+    """``nb`` incidence directions uniform on the sphere with a random polarisation.
+
+    k = normalize(N(0, I3)); the polarisation angle psi ~ U[0, 2 pi) is measured in
+    the plane orthogonal to k from a fixed reference vector.  PCG64(seed).
+    Returns ``(khat[nb,3], phat[nb,3])``.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = rng.standard_normal((nb, 3))
+    k /= np.linalg.norm(k, axis=1, keepdims=True)
+    psi = rng.random(nb) * 2.0 * math.pi
+    ref = np.where(np.abs(k[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    e1 = np.cross(k, ref)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(k, e1)
+    p = np.cos(psi)[:, None] * e1 + np.sin(psi)[:, None] * e2
+    return k, p
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Workload:
+    """One benchmark configuration with every derived parameter written out."""
+
+    name: str
+    mesh: tuple            # (V, F)
+    f_c: float             # carrier (Hz)
+    band_frac: float       # band is f_c (1 +- band_frac)
+    n_t: int               # time steps
+    grid_n: int            # grid nodes per axis
+    h: float               # grid spacing (m)
+    origin: np.ndarray     # grid node (0,0,0) position
+    near_radius: float     # near-zone radius (m) between RWG edge midpoints
+    tol: float             # GMRES relative-residual tolerance
+    khat: np.ndarray       # [nb,3]
+    phat: np.ndarray       # [nb,3]
+    order: int = 2         # CPPIF order Q
+    precision: str = "c64"  # "c128" plain path, "c64" grid path with FP64 outer solve
+    beta: float = 0.25
+
+    @property
+    def f_bw(self) -> float:
+        return self.band_frac * self.f_c
+
+    @property
+    def sigma(self) -> float:
+        return 3.0 / (2.0 * math.pi * self.f_bw)
+
+    @property
+    def t_d(self) -> float:
+        return 8.0 * self.sigma
+
+    @property
+    def dt(self) -> float:
+        return self.beta / self.f_bw
+
+    @property
+    def chi(self) -> float:
+        return (self.f_c + self.f_bw) / self.f_bw
+
+    @property
+    def nb(self) -> int:
+        return int(self.khat.shape[0])
+
+
+def place_grid(V: np.ndarray, n: int, h: float | None = None):
+    """Cubic grid of ``n^3`` nodes centred on the mesh bounding box.
+
+    Without an explicit spacing, ``h = L_max / (n - 5)`` leaves two spare nodes per
+    side for a 4-point stencil.  Returns ``(h, origin[3])``.
+    """
+    lo, hi = V.min(axis=0), V.max(axis=0)
+    centre = 0.5 * (lo + hi)
+    if h is None:
+        h = float((hi - lo).max()) / (n - 5)
+    origin = centre - h * (n - 1) / 2.0
+    return float(h), origin
+
+
+def make_workload(name: str, **over) -> Workload:
+    """The named benchmark shapes (PEC spheres/ellipsoid/sphere array, EFIE, CPPIF Q=2)."""
+    if name == "sphere480":
+        V, F = icosphere(2, 1.0)
+        h, o = place_grid(V, 16, 0.15)
+        w = dict(mesh=(V, F), f_c=150e6, band_frac=0.5, n_t=200, grid_n=16, h=h, origin=o,
+                 near_radius=0.3, tol=1e-6, khat=np.array([[0.0, 0.0, 1.0]]),
+                 phat=np.array([[1.0, 0.0, 0.0]]), precision="c128")
+    elif name in ("sphere7680", "sphere7680_b64"):
+        V, F = icosphere(4, 1.0)
+        h, o = place_grid(V, 64)
+        if name == "sphere7680":
+            k, p = np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]])
+            w = dict(f_c=600e6, band_frac=0.3, n_t=400)
+        else:
+            k, p = random_plane_waves(64, 0)
+            w = dict(f_c=600e6, band_frac=0.1, n_t=300)
+        w.update(mesh=(V, F), grid_n=64, h=h, origin=o, near_radius=3 * h, tol=1e-6,
+                 khat=k, phat=p, precision="c64")
+    elif name == "ellipsoid20k":
+        V, F = ellipsoid_mesh()
+        h, o = place_grid(V, 96)
+        w = dict(mesh=(V, F), f_c=600e6, band_frac=0.3, n_t=500, grid_n=96, h=h, origin=o,
+                 near_radius=3 * h, tol=1e-6, khat=np.array([[0.0, 0.0, 1.0]]),
+                 phat=np.array([[1.0, 0.0, 0.0]]), precision="c64")
+    elif name == "array491k":
+        V, F = sphere_array(5, 0.5, 1.5)
+        h, o = place_grid(V, 384)
+        k, p = random_plane_waves(16, 4)
+        w = dict(mesh=(V, F), f_c=1e9, band_frac=0.05, n_t=1000, grid_n=384, h=h, origin=o,
+                 near_radius=3 * h, tol=1e-5, khat=k, phat=p, precision="c64")
+    elif name.startswith("sphere_sub"):
+        # small parity cases: sphere_sub<s>_n<N>  (radius 1 m, 600 MHz +-30 %)
+        s, n = name[len("sphere_sub"):].split("_n")
+        V, F = icosphere(int(s), 1.0)
+        h, o = place_grid(V, int(n))
+        w = dict(mesh=(V, F), f_c=over.pop("f_c", 300e6), band_frac=0.3, n_t=60, grid_n=int(n),
+                 h=h, origin=o, near_radius=3 * h, tol=1e-6,
+                 khat=np.array([[0.0, 0.0, 1.0]]), phat=np.array([[1.0, 0.0, 0.0]]),
+                 precision="c64")
+    else:
+        raise KeyError(name)
+    w.update(over)
+    return Workload(name=name, **w)
