@@ -1,0 +1,355 @@
+"""ET-AIM march benchmark: seconds per time step and per-kernel HBM roofline.
+
+A step is one time step of the march of Eq. 5 on the workload: excitation,
+delayed-interaction sum over the N_g history spectra (right-hand side), and the
+GMRES solve of the immediate system with the ET-AIM operator in every iteration.
+
+Default workload: PEC sphere r = 1 m, icosphere subdivision 4 (7680 RWG), 600 MHz
++-30 % band, 64^3 grid (128^3 padded FFT), complex64 grid path with FP64 outer
+solve, tol 1e-6, one plane wave.  Inputs are synthetic (seeded mesh and pulse).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl aim|reference]
+
+Under torchrun every rank marches its own plane wave (independent right-hand
+sides, no collective); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ET-AIM s/time-step (with AIM matvec HBM GB/s vs peak)"
+UNIT = "s/step"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
+    """Algorithmic HBM bytes of one launch of each kernel (each byte counted once)."""
+    L = 2 * N
+    slab = 4 * N * L * L * esz * nb           # [nb][4][N][L][L]
+    A = 4 * N * N * L * esz * nb              # [nb][4][N][N][L]
+    P = 4 * N * N * N * esz * nb              # [nb][4][N][N][N]
+    oct_ = (N + 1) ** 3 * esz                 # one kernel spectrum octant
+    lam = ns * 256 * (esz // 2)               # interpolation rows
+    csrT = 64 * ns * (4 + 2 * esz) + (N ** 3 + 1) * 4
+    near = nnz * (4 + 16) + (ns + 1) * 4
+    vec = ns * 16 * nb
+    return {
+        "anterp_xfft": csrT + vec + A,
+        "yfft_fwd": A + slab,
+        "zconv": 2 * slab + 2 * oct_,
+        "zrhs": ng * slab + slab + 2 * ng * oct_,
+        "yfft_inv": slab + A,
+        "xfft_inv": A + P,
+        "interp_near": P + lam + ns * 12 + near + 2 * vec,
+    }.get(kind)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nme)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_aim(args):
+    import torch
+
+    from paper_1408_7060_gb300 import AimContext
+    from paper_1408_7060_gb300.inputs import make_workload, random_plane_waves
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.init()
+    w = make_workload(args.workload)
+    if ws > 1:   # each rank marches its own plane wave (independent right-hand side)
+        k, p = random_plane_waves(ws, 100)
+        w.khat, w.phat = k[rank:rank + 1], p[rank:rank + 1]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = AimContext.from_workload(w, stream=stream.cuda_stream)
+    nb, ns = w.nb, ctx.ns
+    info = ctx.info
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    dev_out = torch.empty((1, nb, ns), dtype=torch.complex128, device="cuda")
+
+    def march_one(out):
+        return ctx.march_continue(w.khat, w.phat, w.sigma, w.t_d, 1, w.tol, out=out)
+
+    # warm-up: the first W steps of the march, from rest
+    ctx.march(w.khat, w.phat, w.sigma, w.t_d, max(args.warmup, 1), w.tol,
+              out=torch.empty((max(args.warmup, 1), nb, ns), dtype=torch.complex128, device="cuda"))
+    torch.cuda.synchronize()
+
+    def timed_steps(k, profile=False):
+        ctx.profile(profile)
+        evs = []
+        iters = []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)                      # L2 flush between timed steps (256 MB > 129 MB L2)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, st, rc = march_one(dev_out)
+            b.record(stream)
+            evs.append((a, b))
+            iters.append(st["total_iters"])
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        prof, launches = ctx.get_profile()
+        return ms, iters, prof, launches
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ms, iters, _, launches = timed_steps(args.steps, profile=False)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t_step = reduce_max(sum(ms) / len(ms) / 1e3, ws)
+
+    # the same steps with per-kernel events (device time per kernel)
+    ms_p, iters_p, prof, _ = timed_steps(args.steps, profile=True)
+
+    # end to end through the C ABI with host buffers (pinned output, host-side inputs)
+    host_out = torch.empty((1, nb, ns), dtype=torch.complex128).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        march_one(host_out)
+    torch.cuda.synchronize()
+    e2e = reduce_max((time.perf_counter() - t0) / args.steps, ws)
+
+    # roofline of the dominant kernel
+    hbm, src = load_peaks()
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_l, ms_l = prof[dom]
+    nbytes = kernel_bytes(dom, w.grid_n, ns, info["near_nnz"], info["n_delays"], nb)
+    per_launch_ms = ms_l / max(n_l, 1)
+    achieved = (nbytes / (per_launch_ms * 1e-3) / 1e9) if nbytes and per_launch_ms > 0 else None
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4),
+                   "share": round(v[1] / max(sum(x[1] for x in prof.values()), 1e-12), 4),
+                   "gbs": (round(kernel_bytes(k, w.grid_n, ns, info["near_nnz"], info["n_delays"], nb)
+                                 / (v[1] / v[0] * 1e-3) / 1e9, 1)
+                           if v[0] and v[1] > 0 and kernel_bytes(k, w.grid_n, ns, info["near_nnz"],
+                                                                 info["n_delays"], nb) else None)}
+               for k, v in prof.items() if v[0]}
+    line = {
+        "metric": METRIC, "value": t_step * 1.0, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 grid / f64 solve", "data": "synthetic",
+        "config": {"workload": w.name, "ns": ns, "grid": f"{w.grid_n}^3 -> {2 * w.grid_n}^3 FFT",
+                   "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "rhs_per_gpu": nb,
+                   "tol": w.tol, "chi": round(w.chi, 3), "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "independent plane waves per GPU" if ws > 1 else "single GPU"},
+        "gmres_iters_per_step": float(np.mean(iters)),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
+                     "peak": hbm, "peak_source": src, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4) if achieved else None, "traffic": None,
+                     "bytes_per_launch": nbytes, "ms_per_launch": round(per_launch_ms, 5)},
+        "kernels": kernels,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nb * 6 * 8,
+                "d2h_bytes_per_step": nb * ns * 16},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, samples=2, n_iter=float(np.mean(iters)))
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_setup(w):
+    from oracle import aim as oaim
+    from oracle import efie
+    from oracle.rwg import build_rwg
+
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    A.near_values()
+    return rwg, p, A
+
+
+def oracle_sample(A, rwg, rng):
+    """One sampled unit of a step: one delayed term of the right-hand side and one
+    operator application of the iterative solve (the oracle as it stands)."""
+    x = rng.standard_normal(rwg.ns) + 1j * rng.standard_normal(rwg.ns)
+    t0 = time.perf_counter()
+    A.matvec(1, x)
+    t1 = time.perf_counter()
+    A.matvec(0, x)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline(w, samples=2, n_iter=None):
+    rwg, p, A = oracle_setup(w)
+    rng = np.random.default_rng(0)
+    t_rhs, t_it = [], []
+    for _ in range(samples):
+        a, b = oracle_sample(A, rwg, rng)
+        t_rhs.append(a)
+        t_it.append(b)
+    ng = A.n_delays
+    n_iter = n_iter or 1.0
+    value = ng * np.mean(t_rhs) + n_iter * np.mean(t_it)
+    return {"value": float(value), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{samples} x (one delayed Z_m product + one Z_0 product) of the same workload, "
+                      f"scaled by N_g = {ng} delays and {n_iter:.1f} GMRES iterations per step"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    from oracle import march as omarch
+    from paper_1408_7060_gb300.inputs import make_workload
+
+    w = make_workload(args.workload)
+    rwg, p, A = oracle_setup(w)
+    # iteration count of the immediate system: the oracle's own GMRES on the first
+    # step (zero history), same tolerance
+    import scipy.sparse.linalg as spla
+
+    from oracle import efie
+
+    V = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, [int(round(w.t_d / w.dt))])[0, 0]
+    Aop = spla.LinearOperator((rwg.ns, rwg.ns), matvec=lambda x: A.matvec(0, x), dtype=complex)
+    cnt = [0]
+    spla.gmres(Aop, V, rtol=w.tol, atol=0.0, restart=50, maxiter=10, callback=lambda _: cnt.__setitem__(0, cnt[0] + 1),
+               callback_type="pr_norm")
+    n_iter = max(cnt[0], 1)
+    rng = np.random.default_rng(1)
+    for _ in range(args.warmup):
+        oracle_sample(A, rwg, rng)
+    t = []
+    for _ in range(args.steps):
+        a, b = oracle_sample(A, rwg, rng)
+        t.append(A.n_delays * a + n_iter * b)
+    value = float(np.mean(t))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "ns": rwg.ns, "grid": f"{w.grid_n}^3", "n_delays": A.n_delays},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
+                         "sample": f"per step: one delayed Z_m product x N_g={A.n_delays} + one Z_0 product x "
+                                   f"{n_iter} GMRES iterations (oracle GMRES count at the first pulse step)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    _ = omarch
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="aim", choices=["aim", "reference"])
+    ap.add_argument("--workload", default="sphere7680")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_aim(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * aim.h -- C ABI of the GB300 ET-AIM library (envelope-tracking adaptive integral
+ * method for the time-domain EFIE on PEC surfaces).
+ *
+ * The library marches the complex current envelopes of Eq. 5,
+ *
+ *   (Z~near_0 + Z~FFT_0) I_l = V_l - sum_{m=1..N_g} (Z~near_m + Z~FFT_m) I_{l-m},
+ *
+ * with Z~FFT_m = anterpolation -> 3-D FFT convolution with the delayed grid
+ * Green-function envelope -> interpolation (Sec. 4, stages i-iii), Z~near_m the
+ * pre-corrected near-zone matrices (stage iv) and a diagonally preconditioned GMRES
+ * for the immediate system (stage v; Sec. 5.1).  Unknowns are RWG current-envelope
+ * coefficients (Eq. 3) for a CPPIF temporal basis.
+ *
+ * Conventions
+ *  - Every call returns an int status (AIM_OK = 0, negative = error).  No C++
+ *    exception crosses the ABI.  aim_last_error() returns a message for the last
+ *    failing call on a context.
+ *  - Complex numbers are interleaved (re, im) doubles: aim_c128.
+ *  - Array arguments marked "host or device" may be either; the library
+ *    classifies the pointer with cudaPointerGetAttributes and copies host
+ *    arrays through internal staging buffers.  The caller owns every pointer it
+ *    passes; the context owns all device memory it allocates.
+ *  - A context is bound to one CUDA device and one stream (aim_opts.cuda_stream,
+ *    or a stream it creates).  It is not thread-safe.
+ *  - RWG ordering: edges sorted by (lower vertex, higher vertex); T+ is the face
+ *    whose counter-clockwise cycle runs along the edge from the lower to the
+ *    higher vertex.  aim_rwg_table() exports it.
+ *  - Grid nodes are indexed n = (iz * N + iy) * N + ix; each RWG owns the 4x4x4
+ *    stencil anchored at floor((x_e - origin)/h) - 1 (clamped to [0, N-4]) per
+ *    axis, x_e the midpoint of its edge.
+ */
+#ifndef AIM_GB300_H
+#define AIM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  AIM_OK = 0,
+  AIM_ERR_ARG = -1,      /* invalid argument (null pointer, size out of range)     */
+  AIM_ERR_MESH = -2,     /* boundary or non-manifold edge, inconsistent orientation */
+  AIM_ERR_CUDA = -3,     /* a CUDA runtime call failed (message in aim_last_error)  */
+  AIM_ERR_OOM = -4,      /* device allocation failed                               */
+  AIM_ERR_NOCONV = -5,   /* GMRES hit its iteration cap; stats->last_step is valid  */
+  AIM_ERR_TIMEOUT = -6,  /* a bounded device wait gave up                           */
+  AIM_WARN_UNSTABLE = 1  /* march finished, but the last |I_l| exceeds 1e3 x the
+                            largest |I_l| of the first half of the run (late-time growth) */
+};
+
+enum { AIM_C128 = 0,     /* plain path: every stage in complex128                  */
+       AIM_C64 = 1 };    /* grid stages (anterpolation, FFT, kernel multiply,
+                            interpolation) in complex64 with FP32 accumulation;
+                            near zone, residual and Krylov basis in FP64            */
+
+enum { AIM_CPPIF = 0 };  /* causal piecewise-polynomial interpolatory basis        */
+
+typedef struct aim_ctx aim_ctx;                 /* opaque */
+typedef struct { double re, im; } aim_c128;
+
+typedef struct {
+  int32_t nv, nt;
+  const double* v;       /* [nv][3] vertex positions (m), host                      */
+  const int32_t* tri;    /* [nt][3] vertex indices, counter-clockwise seen from
+                            outside, host                                           */
+} aim_mesh;
+
+typedef struct {
+  int32_t n;             /* nodes per axis (cubic grid N^3); padded FFT size 2N     */
+  double origin[3];      /* position of node (0,0,0) (m)                            */
+  double h;              /* node spacing (m)                                        */
+} aim_grid;
+
+typedef struct {
+  int32_t kind;          /* AIM_CPPIF                                               */
+  int32_t order;         /* Q (1..4); support (-1, Q] in units of dt                */
+} aim_tbasis;
+
+typedef struct {
+  double f_c;            /* carrier frequency (Hz); envelope x(t)=Re{x~ e^{j2pi f_c t}} */
+  int32_t precision;     /* AIM_C128 or AIM_C64                                     */
+  int32_t batch_max;     /* most right-hand sides marched together (>= 1)           */
+  int32_t gmres_restart; /* Krylov dimension before restart (default 50 if <= 0)    */
+  int32_t gmres_max_iter;/* iteration cap per step and RHS (default 500 if <= 0)    */
+  void* cuda_stream;     /* cudaStream_t to run on, or NULL for a private stream    */
+} aim_opts;
+
+typedef struct {
+  int32_t nb;            /* number of plane waves (<= batch_max)                    */
+  const double* khat;    /* [nb][3] unit propagation directions, host               */
+  const double* phat;    /* [nb][3] unit polarisations, host                        */
+  double sigma, t_d;     /* Gaussian width and delay of Eq. 1 (s)                   */
+} aim_excitation;
+
+typedef struct {
+  int32_t last_step;     /* last completed step l (1-based)                         */
+  int32_t total_iters;   /* GMRES iterations summed over steps and RHS              */
+  int32_t max_iters;     /* largest per-step iteration count                        */
+  double max_rel_res;    /* largest final relative residual over steps and RHS      */
+  double rhs_ms;         /* device time in right-hand-side work (all steps)         */
+  double solve_ms;       /* device time in the iterative solves (all steps)         */
+  int32_t* iters;        /* optional caller array [n_steps][nb] of iteration counts */
+} aim_stats;
+
+typedef struct {
+  int32_t ns;            /* RWG unknowns N_s                                        */
+  int32_t n_delays;      /* N_g: largest delay with a non-zero grid kernel entry    */
+  int32_t n_active;      /* grid nodes touched by some stencil                      */
+  int64_t near_nnz;      /* near-zone pairs (one CSR pattern shared by all delays)  */
+  int32_t grid_n;        /* N                                                       */
+  int32_t precision;
+  int64_t device_bytes;  /* device memory held by the context                       */
+} aim_info;
+
+/*
+ * aim_setup -- build every table of the method on the device (Sec. 4 and Eq. 5):
+ * RWG table, anterpolation coefficients by moment matching up to order 3 per
+ * axis (Sec. 5.1), grid kernels G^A_m = (D^2 T)(m - R/c dt) e^{-j k_c R}/R and
+ * G^phi_m = T(m - R/c dt) e^{-j k_c R}/R for m = 0..N_g (G(0) = 0) and their
+ * zero-padded FFT spectra, near-zone pairs (edge-midpoint distance <= near_radius;
+ * negative: none), the Galerkin near-zone entries Z_m (FP64, singularity
+ * extraction) minus their grid approximation, and the diagonal preconditioner.
+ *   mesh, grid, opts: host structs;  dt: time step (s);  out: receives the context.
+ * Errors: AIM_ERR_ARG, AIM_ERR_MESH, AIM_ERR_CUDA, AIM_ERR_OOM (nothing leaked).
+ */
+int aim_setup(const aim_mesh* mesh, const aim_grid* grid, double near_radius, double dt,
+              aim_tbasis tbasis, const aim_opts* opts, aim_ctx** out);
+
+/* Release every device allocation of the context.  Safe on NULL. */
+void aim_destroy(aim_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failed aim_setup if ctx is NULL). */
+const char* aim_last_error(const aim_ctx* ctx);
+
+int aim_get_info(const aim_ctx* ctx, aim_info* info);
+
+/* Kernels of the library, for aim_get_profile. */
+enum {
+  AIM_K_ANTERP_XFFT = 0, /* anterpolation gather + forward x-FFT                          */
+  AIM_K_YFFT_FWD,        /* forward y-FFT (pruned input)                                   */
+  AIM_K_ZCONV,           /* forward z-FFT, kernel product, inverse z-FFT (immediate term)  */
+  AIM_K_ZRHS,            /* forward z-FFTs, delay sum over N_g spectra, inverse z-FFT      */
+  AIM_K_YFFT_INV,        /* inverse y-FFT (pruned output)                                  */
+  AIM_K_XFFT_INV,        /* inverse x-FFT (pruned output)                                  */
+  AIM_K_INTERP_NEAR,     /* interpolation gather + near-zone CSR product                   */
+  AIM_K_EXCITATION,      /* excitation vector V_l                                          */
+  AIM_K_GMRES_DOT,       /* Krylov multi-dot products (two-stage reduction)                */
+  AIM_K_GMRES_UPDATE,    /* Gram-Schmidt update and norms                                  */
+  AIM_K_GMRES_SMALL,     /* Givens rotations, scaling, cycle bookkeeping                   */
+  AIM_K_COUNT
+};
+
+/*
+ * aim_profile -- reset the kernel counters; enable != 0 also records a CUDA event
+ * pair around every kernel launch on the context stream (device time per kernel).
+ * aim_get_profile -- launches[AIM_K_COUNT] and total device ms[AIM_K_COUNT] since
+ * the last reset (ms only while profiling was enabled), and the total number of
+ * kernel launches (always counted).  Host arrays; either may be NULL.
+ * aim_kernel_name -- a static name for a kernel id ("?" if out of range).
+ */
+int aim_profile(aim_ctx* ctx, int32_t enable);
+int aim_get_profile(aim_ctx* ctx, int64_t* launches, double* ms, int64_t* total_launches);
+const char* aim_kernel_name(int32_t id);
+
+/* N_s and N_g of the context. */
+int aim_num_unknowns(const aim_ctx* ctx, int32_t* ns, int32_t* n_delays);
+
+/*
+ * aim_rwg_table -- the RWG ordering used by every vector of the library.
+ *   edge [ns][2] (lower, higher vertex), tri [ns][2] (T+, T-), free_vertex [ns][2]
+ *   (vertex opposite the edge in T+, T-).  Host arrays supplied by the caller.
+ */
+int aim_rwg_table(const aim_ctx* ctx, int32_t* edge, int32_t* tri, int32_t* free_vertex);
+
+/*
+ * aim_matvec -- y = Z~AIM_m x = Z~FFT_m x + Z~near_m x (Eq. 5), for delay
+ * 0 <= m <= N_g and nb <= batch_max right-hand sides.
+ *   x, y: [nb][ns] aim_c128, host or device.  In AIM_C64 the grid part runs in
+ *   complex64 and the near part in FP64; y is accumulated in FP64.
+ */
+int aim_matvec(aim_ctx* ctx, int32_t delay_m, int32_t nb, const aim_c128* x, aim_c128* y);
+
+/*
+ * aim_rhs -- the delayed-interaction sum of Eq. 5 at step l:
+ *   rhs = sum_{m=1..N_g, l-m >= 1} Z~AIM_m I_{l-m}.
+ *   hist: [N_g][nb][ns] with hist[m-1] = I_{l-m} (entries with l - m < 1 are
+ *   ignored); rhs: [nb][ns].  Host or device.  The grid part is one spectral-domain
+ *   delay sum (one inverse transform for all delays).
+ */
+int aim_rhs(aim_ctx* ctx, int32_t step_l, int32_t nb, const aim_c128* hist, aim_c128* rhs);
+
+/*
+ * aim_excitation_vector -- V_l[k] = <S_k, D E~inc(., l dt)> for the modulated
+ * Gaussian plane waves of Eq. 1 (D = d/dt + j w_c), Cowper 7-point cubature.
+ *   out: [nb][ns], host or device.
+ */
+int aim_excitation_vector(aim_ctx* ctx, const aim_excitation* exc, int32_t step_l, aim_c128* out);
+
+/*
+ * aim_march -- solve Eq. 5 for l = 1..n_steps starting from rest (I_l = 0, l <= 0).
+ * Each step: excitation, delayed sum (spectral history ring), then GMRES on the
+ * immediate system to relative residual tol, warm-started from I_{l-1}.
+ *   currents: [n_steps][nb][ns] aim_c128, host or device (written step by step).
+ *   stats: optional.  Returns AIM_ERR_NOCONV if a solve hits gmres_max_iter (steps
+ *   up to stats->last_step are valid), AIM_WARN_UNSTABLE if the march completed
+ *   with late-time growth.
+ */
+int aim_march(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double tol,
+              aim_c128* currents, aim_stats* stats);
+
+/*
+ * aim_march_continue -- advance a march started by aim_march by n_steps more steps,
+ * using the history held in the context (the last N_g currents and their grid
+ * spectra).  exc must describe the same plane waves (same nb) as the aim_march
+ * call that started it.  currents: [n_steps][nb][ns], host or device.  Returns
+ * AIM_ERR_ARG if no march was started on this context.
+ */
+int aim_march_continue(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double tol,
+                       aim_c128* currents, aim_stats* stats);
+
+/*
+ * Parity access to the setup tables (host arrays supplied by the caller).
+ *   aim_get_anterp: anchor [ns][3] (int32), lam [ns][4][64] (x, y, z, div rows;
+ *     stencil node t = (dz*4 + dy)*4 + dx).
+ *   aim_get_near: rowptr [ns+1], col [nnz], val [(N_g+1)][nnz] aim_c128 (the
+ *     pre-corrected Z~near_m).
+ *   aim_get_kernel_spectrum: the stored octant [(N+1)^3] of the padded-grid
+ *     spectrum of G^A_m (kind 0) or G^phi_m (kind 1), including the folded constants
+ *     mu/(4 pi) or 1/(4 pi eps) and 1/(2N)^3.
+ */
+int aim_get_anterp(const aim_ctx* ctx, int32_t* anchor, double* lam);
+int aim_get_near(const aim_ctx* ctx, int32_t* rowptr, int32_t* col, aim_c128* val);
+int aim_get_kernel_spectrum(const aim_ctx* ctx, int32_t delay_m, int32_t kind, aim_c128* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIM_GB300_H */

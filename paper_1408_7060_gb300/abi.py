@@ -1,0 +1,374 @@
+"""ctypes binding of ``libaim_gb300.so`` (the C ABI in ``include/aim.h``).
+
+Argument marshalling only: every computation runs in the CUDA library.  Arrays may
+be numpy arrays (host) or torch tensors (host or CUDA); complex arrays are
+complex128 with shape ``[nb, ns]`` (``[steps, nb, ns]`` for histories and marches).
+Functions keep the C names (``aim_setup``, ``aim_matvec``, ...); ``AimContext`` is
+a convenience wrapper around them.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AIM_OK, AIM_ERR_ARG, AIM_ERR_MESH, AIM_ERR_CUDA, AIM_ERR_OOM, AIM_ERR_NOCONV, AIM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+AIM_WARN_UNSTABLE = 1
+AIM_C128, AIM_C64 = 0, 1
+AIM_CPPIF = 0
+
+_NAMES = {0: "AIM_OK", -1: "AIM_ERR_ARG", -2: "AIM_ERR_MESH", -3: "AIM_ERR_CUDA", -4: "AIM_ERR_OOM",
+          -5: "AIM_ERR_NOCONV", -6: "AIM_ERR_TIMEOUT", 1: "AIM_WARN_UNSTABLE"}
+
+
+class AimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class aim_mesh(ct.Structure):
+    _fields_ = [("nv", ct.c_int32), ("nt", ct.c_int32), ("v", ct.c_void_p), ("tri", ct.c_void_p)]
+
+
+class aim_grid(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("origin", ct.c_double * 3), ("h", ct.c_double)]
+
+
+class aim_tbasis(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("order", ct.c_int32)]
+
+
+class aim_opts(ct.Structure):
+    _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
+                ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p)]
+
+
+class aim_excitation(ct.Structure):
+    _fields_ = [("nb", ct.c_int32), ("khat", ct.c_void_p), ("phat", ct.c_void_p),
+                ("sigma", ct.c_double), ("t_d", ct.c_double)]
+
+
+class aim_stats(ct.Structure):
+    _fields_ = [("last_step", ct.c_int32), ("total_iters", ct.c_int32), ("max_iters", ct.c_int32),
+                ("max_rel_res", ct.c_double), ("rhs_ms", ct.c_double), ("solve_ms", ct.c_double),
+                ("iters", ct.c_void_p)]
+
+
+class aim_info(ct.Structure):
+    _fields_ = [("ns", ct.c_int32), ("n_delays", ct.c_int32), ("n_active", ct.c_int32),
+                ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
+                ("device_bytes", ct.c_int64)]
+
+
+EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
+           "aim_matvec", "aim_rhs", "aim_excitation_vector", "aim_march", "aim_march_continue", "aim_get_anterp",
+           "aim_get_near", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name"]
+AIM_K_COUNT = 11
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ct.CDLL:
+    """Load the CUDA library (building it in-tree first if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+    lib = ct.CDLL(_build.LIB)
+    P, I32, D = ct.c_void_p, ct.c_int32, ct.c_double
+    sig = {
+        "aim_setup": (ct.c_int, [ct.POINTER(aim_mesh), ct.POINTER(aim_grid), D, D, aim_tbasis,
+                                 ct.POINTER(aim_opts), ct.POINTER(P)]),
+        "aim_destroy": (None, [P]),
+        "aim_last_error": (ct.c_char_p, [P]),
+        "aim_get_info": (ct.c_int, [P, ct.POINTER(aim_info)]),
+        "aim_num_unknowns": (ct.c_int, [P, ct.POINTER(I32), ct.POINTER(I32)]),
+        "aim_rwg_table": (ct.c_int, [P, P, P, P]),
+        "aim_matvec": (ct.c_int, [P, I32, I32, P, P]),
+        "aim_rhs": (ct.c_int, [P, I32, I32, P, P]),
+        "aim_excitation_vector": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, P]),
+        "aim_march": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, D, P, ct.POINTER(aim_stats)]),
+        "aim_march_continue": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, D, P, ct.POINTER(aim_stats)]),
+        "aim_profile": (ct.c_int, [P, I32]),
+        "aim_get_profile": (ct.c_int, [P, P, P, P]),
+        "aim_kernel_name": (ct.c_char_p, [I32]),
+        "aim_get_anterp": (ct.c_int, [P, P, P]),
+        "aim_get_near": (ct.c_int, [P, P, P, P]),
+        "aim_get_kernel_spectrum": (ct.c_int, [P, I32, I32, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _like(x, shape):
+    """An output complex128 array of ``shape`` on the same side (numpy / torch device) as x."""
+    if isinstance(x, np.ndarray):
+        return np.empty(shape, dtype=np.complex128)
+    import torch
+
+    return torch.empty(shape, dtype=torch.complex128, device=x.device)
+
+
+def _check(lib, ctx, rc, what):
+    if rc < 0:
+        msg = lib.aim_last_error(ctx)
+        raise AimError(rc, f"{what}: {msg.decode() if msg else ''}")
+    return rc
+
+
+def _stream_handle():
+    try:
+        import torch
+
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
+              restart=50, max_iter=500, stream=None):
+    """Build a context; returns an opaque handle (int)."""
+    lib = load()
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    mesh = aim_mesh(len(V), len(F), V.ctypes.data, F.ctypes.data)
+    grid = aim_grid(int(grid_n), (ct.c_double * 3)(*[float(o) for o in origin]), float(h))
+    tb = aim_tbasis(AIM_CPPIF, int(order))
+    prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
+    opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
+                    stream if stream is not None else _stream_handle())
+    out = ct.c_void_p()
+    rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
+                       ct.byref(out))
+    _check(lib, None, rc, "aim_setup")
+    return out.value
+
+
+def aim_destroy(ctx):
+    load().aim_destroy(ctx)
+
+
+def aim_get_info(ctx) -> dict:
+    lib = load()
+    info = aim_info()
+    _check(lib, ctx, lib.aim_get_info(ctx, ct.byref(info)), "aim_get_info")
+    return {f: getattr(info, f) for f, _ in aim_info._fields_}
+
+
+def aim_num_unknowns(ctx):
+    lib = load()
+    ns, ng = ct.c_int32(), ct.c_int32()
+    _check(lib, ctx, lib.aim_num_unknowns(ctx, ct.byref(ns), ct.byref(ng)), "aim_num_unknowns")
+    return ns.value, ng.value
+
+
+def aim_rwg_table(ctx):
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    e, t, f = (np.empty((ns, 2), dtype=np.int32) for _ in range(3))
+    _check(lib, ctx, lib.aim_rwg_table(ctx, e.ctypes.data, t.ctypes.data, f.ctypes.data), "aim_rwg_table")
+    return e, t, f
+
+
+def aim_matvec(ctx, m, x, out=None):
+    """y = Z~AIM_m x for x[nb, ns] complex128 (numpy or torch)."""
+    lib = load()
+    y = _like(x, tuple(x.shape)) if out is None else out
+    _check(lib, ctx, lib.aim_matvec(ctx, int(m), int(x.shape[0]), _ptr(x), _ptr(y)), "aim_matvec")
+    return y
+
+
+def aim_rhs(ctx, step_l, hist, out=None):
+    """sum_{m>=1} Z~AIM_m I_{l-m} for hist[N_g, nb, ns] with hist[m-1] = I_{l-m}."""
+    lib = load()
+    y = _like(hist, tuple(hist.shape[1:])) if out is None else out
+    _check(lib, ctx, lib.aim_rhs(ctx, int(step_l), int(hist.shape[1]), _ptr(hist), _ptr(y)), "aim_rhs")
+    return y
+
+
+def _exc(khat, phat, sigma, t_d):
+    khat = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+    phat = np.ascontiguousarray(np.atleast_2d(phat), dtype=np.float64)
+    e = aim_excitation(len(khat), khat.ctypes.data, phat.ctypes.data, float(sigma), float(t_d))
+    return e, (khat, phat)
+
+
+def aim_excitation_vector(ctx, khat, phat, sigma, t_d, step_l, out=None):
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    e, keep = _exc(khat, phat, sigma, t_d)
+    y = np.empty((e.nb, ns), dtype=np.complex128) if out is None else out
+    _check(lib, ctx, lib.aim_excitation_vector(ctx, ct.byref(e), int(step_l), _ptr(y)), "aim_excitation_vector")
+    return y
+
+
+def aim_march(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
+    """March Eq. 5 for n_steps; returns (currents[n_steps, nb, ns], stats dict, status)."""
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    e, keep = _exc(khat, phat, sigma, t_d)
+    cur = np.empty((n_steps, e.nb, ns), dtype=np.complex128) if out is None else out
+    iters = np.zeros((n_steps, e.nb), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data)
+    rc = lib.aim_march(ctx, ct.byref(e), int(n_steps), float(tol), _ptr(cur), ct.byref(st))
+    _check(lib, ctx, rc, "aim_march")
+    stats = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
+    stats["iters"] = iters
+    return cur, stats, rc
+
+
+def aim_march_continue(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
+    """Advance the march started by aim_march on this context by n_steps."""
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    e, keep = _exc(khat, phat, sigma, t_d)
+    cur = np.empty((n_steps, e.nb, ns), dtype=np.complex128) if out is None else out
+    iters = np.zeros((n_steps, e.nb), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data)
+    rc = lib.aim_march_continue(ctx, ct.byref(e), int(n_steps), float(tol), _ptr(cur), ct.byref(st))
+    _check(lib, ctx, rc, "aim_march_continue")
+    stats = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
+    stats["iters"] = iters
+    return cur, stats, rc
+
+
+def aim_profile(ctx, enable=True):
+    lib = load()
+    _check(lib, ctx, lib.aim_profile(ctx, int(bool(enable))), "aim_profile")
+
+
+def aim_get_profile(ctx) -> dict:
+    """{kernel name: (launches, device ms)} and the total launch count."""
+    lib = load()
+    n = np.zeros(AIM_K_COUNT, dtype=np.int64)
+    ms = np.zeros(AIM_K_COUNT, dtype=np.float64)
+    tot = np.zeros(1, dtype=np.int64)
+    _check(lib, ctx, lib.aim_get_profile(ctx, n.ctypes.data, ms.ctypes.data, tot.ctypes.data), "aim_get_profile")
+    out = {lib.aim_kernel_name(i).decode(): (int(n[i]), float(ms[i])) for i in range(AIM_K_COUNT)}
+    return out, int(tot[0])
+
+
+def aim_get_anterp(ctx):
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    anchor = np.empty((ns, 3), dtype=np.int32)
+    lam = np.empty((ns, 4, 64), dtype=np.float64)
+    _check(lib, ctx, lib.aim_get_anterp(ctx, anchor.ctypes.data, lam.ctypes.data), "aim_get_anterp")
+    return anchor, lam
+
+
+def aim_get_near(ctx):
+    lib = load()
+    info = aim_get_info(ctx)
+    ns, nnz, ng = info["ns"], info["near_nnz"], info["n_delays"]
+    rowptr = np.empty(ns + 1, dtype=np.int32)
+    col = np.empty(max(nnz, 1), dtype=np.int32)
+    val = np.empty((ng + 1, max(nnz, 1)), dtype=np.complex128)
+    _check(lib, ctx, lib.aim_get_near(ctx, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data), "aim_get_near")
+    return rowptr, col[:nnz], val[:, :nnz]
+
+
+def aim_get_kernel_spectrum(ctx, m, kind):
+    lib = load()
+    n = aim_get_info(ctx)["grid_n"] + 1
+    out = np.empty((n, n, n), dtype=np.complex128)
+    _check(lib, ctx, lib.aim_get_kernel_spectrum(ctx, int(m), int(kind), out.ctypes.data), "aim_get_kernel_spectrum")
+    return out
+
+
+class AimContext:
+    """Owning wrapper: ``with AimContext.from_workload(w) as ctx: ctx.matvec(0, x)``."""
+
+    def __init__(self, **kw):
+        self.handle = aim_setup(**kw)
+        self.info = aim_get_info(self.handle)
+        self.ns = self.info["ns"]
+        self.n_delays = self.info["n_delays"]
+
+    @classmethod
+    def from_workload(cls, w, **over):
+        V, F = w.mesh
+        kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
+                  f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb)
+        kw.update(over)
+        return cls(**kw)
+
+    def matvec(self, m, x, out=None):
+        return aim_matvec(self.handle, m, x, out)
+
+    def rhs(self, step_l, hist, out=None):
+        return aim_rhs(self.handle, step_l, hist, out)
+
+    def excitation(self, khat, phat, sigma, t_d, step_l):
+        return aim_excitation_vector(self.handle, khat, phat, sigma, t_d, step_l)
+
+    def march(self, khat, phat, sigma, t_d, n_steps, tol, out=None):
+        return aim_march(self.handle, khat, phat, sigma, t_d, n_steps, tol, out)
+
+    def march_continue(self, khat, phat, sigma, t_d, n_steps, tol, out=None):
+        return aim_march_continue(self.handle, khat, phat, sigma, t_d, n_steps, tol, out)
+
+    def profile(self, enable=True):
+        aim_profile(self.handle, enable)
+
+    def get_profile(self):
+        return aim_get_profile(self.handle)
+
+    def rwg_table(self):
+        return aim_rwg_table(self.handle)
+
+    def anterp(self):
+        return aim_get_anterp(self.handle)
+
+    def near(self):
+        return aim_get_near(self.handle)
+
+    def kernel_spectrum(self, m, kind):
+        return aim_get_kernel_spectrum(self.handle, m, kind)
+
+    def close(self):
+        if self.handle:
+            aim_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

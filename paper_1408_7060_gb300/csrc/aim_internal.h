@@ -1,0 +1,176 @@
+// Internal state of an ET-AIM context and the helpers shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/aim.h"
+
+// free-space constants (Sec. 2.1: homogeneous medium, here vacuum)
+namespace aimc {
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4.0e-7 * kPi;
+constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+constexpr int kMaxDelays = 32;   // N_g + 1 <= kMaxDelays
+constexpr int kMaxOrder = 4;     // CPPIF order
+}  // namespace aimc
+
+struct AimError {
+  int code;
+  std::string msg;
+};
+
+#define AIM_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw AimError{AIM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};  \
+  } while (0)
+
+#define AIM_CHECK_LAUNCH() AIM_CUDA(cudaGetLastError())
+
+// one profiled kernel launch: AIM_KLAUNCH(ctx, AIM_K_..., kernel<<<...>>>(...))
+#define AIM_KLAUNCH(ctx, kid, ...)   \
+  do {                               \
+    KScope ks_(ctx, kid);            \
+    __VA_ARGS__;                     \
+    AIM_CHECK_LAUNCH();              \
+  } while (0)
+
+// CPPIF pieces: T on (j-1, j] is sum_p coef[j][p] u^p (Horner on device)
+struct TBasis {
+  int Q;
+  double coef[aimc::kMaxOrder + 1][aimc::kMaxOrder + 1];
+};
+
+// GMRES small state, one row of 64 per right-hand side (restart <= 63)
+struct GmresState {
+  double2* H = nullptr;      // [B][64][64] rotated Hessenberg (upper triangle)
+  double2* g = nullptr;      // [B][64]
+  double2* sn = nullptr;     // [B][64]
+  double* cs = nullptr;      // [B][64]
+  double2* y = nullptr;      // [B][64]
+  double2* h1 = nullptr;     // [B][64] first CGS pass
+  double2* h2 = nullptr;     // [B][64] second CGS pass
+  double* hn = nullptr;      // [B] ||w||
+  double* bn = nullptr;      // [B] ||b||
+  double* rn = nullptr;      // [B] ||r||
+  double* scale = nullptr;   // [B]
+  double* relres = nullptr;  // [B]
+  int* act = nullptr;        // [B] taking Arnoldi steps
+  int* done = nullptr;       // [B] 1 converged, 2 iteration cap
+  int* jc = nullptr;         // [B] columns in the current cycle
+  int* its = nullptr;        // [B] iterations of this solve
+  int* flag = nullptr;       // any active
+  double2* pc = nullptr;     // reduction partials
+  double* pr = nullptr;
+  unsigned* counter = nullptr;
+  int* h_flag = nullptr;     // pinned host mirrors
+  int* h_its = nullptr;
+  double* h_res = nullptr;
+  int* h_done = nullptr;
+};
+
+// per-kernel event timing (aim_profile / aim_get_profile); ids match AIM_K_* in aim.h
+struct ProfState {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Rec { int id; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  double ms[AIM_K_COUNT] = {0};
+  long long n[AIM_K_COUNT] = {0};
+  long long launches = 0;
+};
+
+struct aim_ctx {
+  // problem
+  int ns = 0, nt = 0, nv = 0;
+  int N = 0, L = 0;            // grid nodes per axis, padded length 2N
+  double h = 0, origin[3] = {0, 0, 0};
+  double dt = 0, f_c = 0, wc = 0, kc = 0, near_radius = 0;
+  TBasis tb{};
+  int precision = AIM_C64;
+  int batch_max = 1, restart = 50, max_iter = 500;
+  int n_delays = 0, n_active = 0;
+  long long nnz = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  // host copies of the RWG table (for aim_rwg_table)
+  std::vector<int> h_edge, h_tri, h_free;
+  std::vector<int> h_rowptr;
+
+  // ---- device tables (FP64 unless noted) ----
+  double* d_v = nullptr;       // [nv][3]
+  int* d_tri = nullptr;        // [nt][3]
+  int* d_rtri = nullptr;       // [ns][2]  T+, T-
+  int* d_rfree = nullptr;      // [ns][2]
+  double* d_len = nullptr;     // [ns]
+  double* d_area = nullptr;    // [nt]
+  int* d_tbk = nullptr;        // [nt][3] rwg of each edge slot of a face
+  double* d_tbs = nullptr;     // [nt][3] sign
+  int* d_tbf = nullptr;        // [nt][3] free vertex
+  double* d_qp = nullptr;      // [nt][7][3] cubature points
+  double* d_qw = nullptr;      // [nt][7] weights * area
+  double* d_cent = nullptr;    // [nt][3]
+  double mean_edge = 0;
+
+  int* d_anchor = nullptr;     // [ns][3]
+  double* d_lam = nullptr;     // [ns][4][64]  FP64 anterpolation rows
+  float* d_lamf = nullptr;     // [ns][4][64]  FP32 copy (C64 path)
+  int* d_nptr = nullptr;       // [N^3 + 1]    node-major CSR of the transpose
+  int* d_nidx = nullptr;       // [64 ns]
+  double4_32a* d_ncoef = nullptr;  // [64 ns]  (x, y, z, div) coefficients
+  float4* d_ncoeff = nullptr;  // [64 ns]  FP32 copy
+
+  double2* d_kspec = nullptr;  // [(N_g+1)][2][(N+1)^3] kernel spectra octant (FP64)
+  float2* d_kspecf = nullptr;  // FP32 copy
+  double2* d_tw = nullptr;     // [L] twiddles W_L^t (FP64)
+  float2* d_twf = nullptr;     // [L] FP32
+
+  int* d_rowptr = nullptr;     // [ns+1] near CSR
+  int* d_col = nullptr;        // [nnz]
+  double2* d_near = nullptr;   // [(N_g+1)][nnz]
+  double2* d_dinv = nullptr;   // [ns] 1 / Z_0[k,k]
+
+  // ---- work buffers (sized for batch_max) ----
+  void* d_A = nullptr;         // [B][4][N][N][L]   after the x pass
+  void* d_Bf = nullptr;        // [B][4][N][L][L]   after the y pass (z<N slab)
+  void* d_P = nullptr;         // [B][4][N][N][N]   potentials on the grid
+  void* d_ring = nullptr;      // [N_g][B][4][N][L][L] spectral history slabs
+  double2* d_iring = nullptr;  // [N_g][B][ns] current history (RWG space)
+  double2* d_x = nullptr;      // [B][ns] staging / solution
+  double2* d_y = nullptr;      // [B][ns]
+  double2* d_b = nullptr;      // [B][ns]
+  double2* d_r = nullptr;      // [B][ns]
+  double2* d_w = nullptr;      // [B][ns]
+  double2* d_V = nullptr;      // [restart+1][B][ns] Krylov basis
+  double2* d_hist = nullptr;   // [N_g][B][ns] staging for aim_rhs
+  double2* d_small = nullptr;  // GMRES small state (see gmres.cu)
+  double* d_partial = nullptr; // reduction partials
+  unsigned* d_counter = nullptr;
+  int* d_status = nullptr;
+  double* d_exc = nullptr;     // excitation parameters
+  size_t device_bytes = 0;
+
+  GmresState gs;
+  ProfState prof;
+  int l_done = 0, march_nb = 0;   // march state for aim_march_continue
+  std::vector<void*> allocs;
+};
+
+// helpers implemented in api.cu
+void* aim_alloc(aim_ctx* c, size_t bytes);
+
+// records events around one kernel launch when profiling is on; counts launches always
+struct KScope {
+  aim_ctx* c;
+  int id;
+  cudaEvent_t a = nullptr;
+  KScope(aim_ctx* c_, int id_);
+  ~KScope();
+};
+void prof_flush(aim_ctx* c);   // after a stream synchronisation

@@ -1,0 +1,531 @@
+// extern "C" entry points of the ET-AIM library (declared in include/aim.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "aim_internal.h"
+#include "gmres.h"
+#include "operator.h"
+#include "setup_gpu.h"
+#include "setup_host.h"
+
+namespace {
+
+thread_local std::string g_last_setup_error;
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class F>
+int guard(aim_ctx* c, F&& f) {
+  try {
+    return f();
+  } catch (const AimError& e) {
+    if (c) c->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return AIM_ERR_OOM;
+  } catch (...) {
+    if (c) c->err = "unexpected exception";
+    return AIM_ERR_ARG;
+  }
+}
+
+bool supported_n(int n) {
+  return n == 8 || n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 384;
+}
+
+template <class T>
+T* upload(aim_ctx* c, const std::vector<T>& v) {
+  T* d = (T*)aim_alloc(c, std::max<size_t>(1, v.size()) * sizeof(T));
+  if (!v.empty()) AIM_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return d;
+}
+
+size_t grid_elem(const aim_ctx* c) { return c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2); }
+
+void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double near_radius, double dt,
+                aim_tbasis tb, const aim_opts* opts) {
+  if (!mesh || !grid || !opts) throw AimError{AIM_ERR_ARG, "null argument"};
+  if (!supported_n(grid->n)) throw AimError{AIM_ERR_ARG, "grid n must be one of 8,16,32,64,96,128,384"};
+  if (!(grid->h > 0) || !(dt > 0) || !(opts->f_c > 0)) throw AimError{AIM_ERR_ARG, "h, dt and f_c must be > 0"};
+  if (tb.kind != AIM_CPPIF) throw AimError{AIM_ERR_ARG, "only the CPPIF temporal basis is built"};
+  if (opts->precision != AIM_C64 && opts->precision != AIM_C128) throw AimError{AIM_ERR_ARG, "precision"};
+  if (opts->batch_max < 1 || opts->batch_max > 4096) throw AimError{AIM_ERR_ARG, "batch_max out of range"};
+  c->N = grid->n;
+  c->L = 2 * grid->n;
+  c->h = grid->h;
+  for (int d = 0; d < 3; ++d) c->origin[d] = grid->origin[d];
+  c->dt = dt;
+  c->f_c = opts->f_c;
+  c->wc = 2.0 * aimc::kPi * opts->f_c;
+  c->kc = c->wc / aimc::kC0;
+  c->near_radius = near_radius;
+  c->precision = opts->precision;
+  c->batch_max = opts->batch_max;
+  c->restart = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 63) : 50;
+  c->max_iter = opts->gmres_max_iter > 0 ? opts->gmres_max_iter : 500;
+  if (opts->cuda_stream) {
+    c->stream = (cudaStream_t)opts->cuda_stream;
+  } else {
+    AIM_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  host_cppif(tb.order, c->tb);
+
+  HostMesh hm;
+  host_build_rwg(mesh, hm);
+  c->nv = hm.nv;
+  c->nt = hm.nt;
+  c->ns = hm.ns;
+  c->mean_edge = hm.mean_edge;
+  c->h_edge = hm.edge;
+  c->h_tri = hm.rtri;
+  c->h_free = hm.rfree;
+  std::vector<int> anchor;
+  host_anchors(hm, c->N, c->origin, c->h, anchor);
+
+  c->d_v = upload(c, hm.V);
+  c->d_tri = upload(c, hm.F);
+  c->d_rtri = upload(c, hm.rtri);
+  c->d_rfree = upload(c, hm.rfree);
+  c->d_len = upload(c, hm.len);
+  c->d_area = upload(c, hm.area);
+  c->d_cent = upload(c, hm.cent);
+  c->d_qp = upload(c, hm.qp);
+  c->d_qw = upload(c, hm.qw);
+  c->d_tbk = upload(c, hm.tbk);
+  c->d_tbs = upload(c, hm.tbs);
+  c->d_tbf = upload(c, hm.tbf);
+  c->d_anchor = upload(c, anchor);
+  c->d_lam = (double*)aim_alloc(c, (size_t)c->ns * 256 * sizeof(double));
+  c->d_lamf = (float*)aim_alloc(c, (size_t)c->ns * 256 * sizeof(float));
+  AIM_CUDA(cudaStreamSynchronize(c->stream));
+
+  setup_device_tables(c, hm, anchor);
+
+  // work buffers
+  const int B = c->batch_max, N = c->N, L = c->L, ns = c->ns, ng = c->n_delays;
+  const size_t es = grid_elem(c);
+  c->d_A = aim_alloc(c, (size_t)B * 4 * N * N * L * es);
+  c->d_Bf = aim_alloc(c, (size_t)B * 4 * N * L * L * es);
+  c->d_P = aim_alloc(c, (size_t)B * 4 * N * N * N * es);
+  c->d_ring = aim_alloc(c, (size_t)ng * op_slab_bytes(c, B));
+  const size_t vec = (size_t)B * ns * sizeof(double2);
+  c->d_iring = (double2*)aim_alloc(c, (size_t)ng * vec);
+  c->d_x = (double2*)aim_alloc(c, vec);
+  c->d_y = (double2*)aim_alloc(c, vec);
+  c->d_b = (double2*)aim_alloc(c, vec);
+  c->d_r = (double2*)aim_alloc(c, vec);
+  c->d_w = (double2*)aim_alloc(c, vec);
+  c->d_V = (double2*)aim_alloc(c, (size_t)(c->restart + 1) * vec);
+  c->d_hist = (double2*)aim_alloc(c, (size_t)ng * vec);
+  c->d_exc = (double*)aim_alloc(c, (size_t)B * 6 * sizeof(double));
+  gmres_alloc(c);
+  AIM_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// copy a caller array to device staging if it is a host pointer
+const double2* stage_in(aim_ctx* c, const aim_c128* p, size_t n, double2* staging) {
+  if (is_device_ptr(p)) return reinterpret_cast<const double2*>(p);
+  AIM_CUDA(cudaMemcpyAsync(staging, p, n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  return staging;
+}
+
+void upload_waves(aim_ctx* c, const aim_excitation* exc) {
+  if (!exc || !exc->khat || !exc->phat || exc->nb < 1 || exc->nb > c->batch_max)
+    throw AimError{AIM_ERR_ARG, "excitation: nb out of range or null directions"};
+  if (!(exc->sigma > 0)) throw AimError{AIM_ERR_ARG, "excitation: sigma must be > 0"};
+  std::vector<double> kp((size_t)exc->nb * 6);
+  for (int b = 0; b < exc->nb; ++b)
+    for (int d = 0; d < 3; ++d) {
+      kp[6 * b + d] = exc->khat[3 * b + d];
+      kp[6 * b + 3 + d] = exc->phat[3 * b + d];
+    }
+  AIM_CUDA(cudaMemcpyAsync(c->d_exc, kp.data(), kp.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  AIM_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace
+
+void* aim_alloc(aim_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw AimError{AIM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+  }
+  c->allocs.push_back(p);
+  c->device_bytes += bytes;
+  return p;
+}
+
+KScope::KScope(aim_ctx* c_, int id_) : c(c_), id(id_) {
+  c->prof.launches++;
+  c->prof.n[id]++;
+  if (c->prof.on) {
+    if (c->prof.pool.empty()) {
+      cudaEvent_t e;
+      AIM_CUDA(cudaEventCreate(&e));
+      c->prof.pool.push_back(e);
+    }
+    a = c->prof.pool.back();
+    c->prof.pool.pop_back();
+    cudaEventRecord(a, c->stream);
+  }
+}
+
+KScope::~KScope() {
+  if (!a) return;
+  cudaEvent_t b;
+  if (c->prof.pool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+  } else {
+    b = c->prof.pool.back();
+    c->prof.pool.pop_back();
+  }
+  cudaEventRecord(b, c->stream);
+  c->prof.pending.push_back({id, a, b});
+}
+
+void prof_flush(aim_ctx* c) {
+  for (auto& r : c->prof.pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) c->prof.ms[r.id] += ms;
+    c->prof.pool.push_back(r.a);
+    c->prof.pool.push_back(r.b);
+  }
+  c->prof.pending.clear();
+  cudaGetLastError();
+}
+
+static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, double tol, aim_c128* currents,
+                       aim_stats* stats);
+
+extern "C" {
+
+int aim_setup(const aim_mesh* mesh, const aim_grid* grid, double near_radius, double dt, aim_tbasis tbasis,
+              const aim_opts* opts, aim_ctx** out) {
+  if (!out) return AIM_ERR_ARG;
+  *out = nullptr;
+  aim_ctx* c = new (std::nothrow) aim_ctx;
+  if (!c) return AIM_ERR_OOM;
+  int rc = guard(c, [&] {
+    setup_impl(c, mesh, grid, near_radius, dt, tbasis, opts);
+    return AIM_OK;
+  });
+  if (rc != AIM_OK) {
+    g_last_setup_error = c->err;
+    aim_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return AIM_OK;
+}
+
+void aim_destroy(aim_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  for (auto& r : c->prof.pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->prof.pool) cudaEventDestroy(e);
+  gmres_free_host(c);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* aim_last_error(const aim_ctx* c) { return c ? c->err.c_str() : g_last_setup_error.c_str(); }
+
+int aim_get_info(const aim_ctx* c, aim_info* info) {
+  if (!c || !info) return AIM_ERR_ARG;
+  info->ns = c->ns;
+  info->n_delays = c->n_delays;
+  info->n_active = c->n_active;
+  info->near_nnz = c->nnz;
+  info->grid_n = c->N;
+  info->precision = c->precision;
+  info->device_bytes = (int64_t)c->device_bytes;
+  return AIM_OK;
+}
+
+int aim_num_unknowns(const aim_ctx* c, int32_t* ns, int32_t* n_delays) {
+  if (!c) return AIM_ERR_ARG;
+  if (ns) *ns = c->ns;
+  if (n_delays) *n_delays = c->n_delays;
+  return AIM_OK;
+}
+
+int aim_rwg_table(const aim_ctx* c, int32_t* edge, int32_t* tri, int32_t* free_vertex) {
+  if (!c) return AIM_ERR_ARG;
+  const size_t n = 2 * (size_t)c->ns;
+  if (edge) std::memcpy(edge, c->h_edge.data(), n * sizeof(int32_t));
+  if (tri) std::memcpy(tri, c->h_tri.data(), n * sizeof(int32_t));
+  if (free_vertex) std::memcpy(free_vertex, c->h_free.data(), n * sizeof(int32_t));
+  return AIM_OK;
+}
+
+int aim_matvec(aim_ctx* c, int32_t m, int32_t nb, const aim_c128* x, aim_c128* y) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!x || !y || nb < 1 || nb > c->batch_max || m < 0 || m > c->n_delays)
+      throw AimError{AIM_ERR_ARG, "aim_matvec: bad delay, batch or pointer"};
+    const size_t n = (size_t)nb * c->ns;
+    const double2* xs = stage_in(c, x, n, c->d_x);
+    const bool ydev = is_device_ptr(y);
+    double2* ys = ydev ? reinterpret_cast<double2*>(y) : c->d_y;
+    op_apply(c, m, nb, xs, nullptr, nullptr, 1.0, nullptr, ys);
+    if (!ydev) AIM_CUDA(cudaMemcpyAsync(y, ys, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    AIM_CUDA(cudaStreamSynchronize(c->stream));
+    return AIM_OK;
+  });
+}
+
+int aim_rhs(aim_ctx* c, int32_t l, int32_t nb, const aim_c128* hist, aim_c128* rhs) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!hist || !rhs || nb < 1 || nb > c->batch_max || l < 1)
+      throw AimError{AIM_ERR_ARG, "aim_rhs: bad step, batch or pointer"};
+    const int ng = c->n_delays;
+    const size_t n = (size_t)nb * c->ns;
+    const double2* hs = stage_in(c, hist, (size_t)ng * n, c->d_hist);
+    const size_t slab = op_slab_bytes(c, c->batch_max);
+    SlabList sl{};
+    NearList nl{};
+    for (int m = 1; m <= ng; ++m) {
+      if (l - m < 1) continue;
+      const double2* I = hs + (size_t)(m - 1) * n;
+      void* dst = (char*)c->d_ring + (size_t)(m - 1) * slab;
+      op_forward_slab(c, nb, I, dst);
+      sl.p[sl.n] = dst;
+      sl.m[sl.n] = m;
+      sl.n++;
+      if (c->nnz > 0) {
+        nl.val[nl.n] = c->d_near + (size_t)m * c->nnz;
+        nl.x[nl.n] = I;
+        nl.n++;
+      }
+    }
+    const bool ydev = is_device_ptr(rhs);
+    double2* ys = ydev ? reinterpret_cast<double2*>(rhs) : c->d_y;
+    op_apply_rhs(c, nb, sl, nl, nullptr, 1.0, ys);
+    if (!ydev) AIM_CUDA(cudaMemcpyAsync(rhs, ys, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    AIM_CUDA(cudaStreamSynchronize(c->stream));
+    return AIM_OK;
+  });
+}
+
+int aim_excitation_vector(aim_ctx* c, const aim_excitation* exc, int32_t l, aim_c128* out) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!out) throw AimError{AIM_ERR_ARG, "aim_excitation_vector: null output"};
+    upload_waves(c, exc);
+    const size_t n = (size_t)exc->nb * c->ns;
+    const bool dev = is_device_ptr(out);
+    double2* o = dev ? reinterpret_cast<double2*>(out) : c->d_y;
+    op_excitation(c, exc->nb, c->d_exc, exc->sigma, exc->t_d, l, o);
+    if (!dev) AIM_CUDA(cudaMemcpyAsync(out, o, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    AIM_CUDA(cudaStreamSynchronize(c->stream));
+    return AIM_OK;
+  });
+}
+
+int aim_march(aim_ctx* c, const aim_excitation* exc, int32_t n_steps, double tol, aim_c128* currents,
+              aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!currents || n_steps < 1 || !(tol > 0)) throw AimError{AIM_ERR_ARG, "aim_march: bad arguments"};
+    upload_waves(c, exc);
+    AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)exc->nb * c->ns * sizeof(double2), c->stream));
+    c->l_done = 0;
+    c->march_nb = exc->nb;
+    return march_steps(c, exc, n_steps, tol, currents, stats);
+  });
+}
+
+int aim_march_continue(aim_ctx* c, const aim_excitation* exc, int32_t n_steps, double tol, aim_c128* currents,
+                       aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!currents || n_steps < 1 || !(tol > 0)) throw AimError{AIM_ERR_ARG, "aim_march_continue: bad arguments"};
+    if (c->march_nb < 1 || !exc || exc->nb != c->march_nb)
+      throw AimError{AIM_ERR_ARG, "aim_march_continue: no march with this batch was started on the context"};
+    upload_waves(c, exc);
+    return march_steps(c, exc, n_steps, tol, currents, stats);
+  });
+}
+
+int aim_profile(aim_ctx* c, int32_t enable) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    AIM_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    for (int i = 0; i < AIM_K_COUNT; ++i) {
+      c->prof.ms[i] = 0;
+      c->prof.n[i] = 0;
+    }
+    c->prof.launches = 0;
+    c->prof.on = enable != 0;
+    return AIM_OK;
+  });
+}
+
+int aim_get_profile(aim_ctx* c, int64_t* launches, double* ms, int64_t* total) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    AIM_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    for (int i = 0; i < AIM_K_COUNT; ++i) {
+      if (launches) launches[i] = c->prof.n[i];
+      if (ms) ms[i] = c->prof.ms[i];
+    }
+    if (total) *total = c->prof.launches;
+    return AIM_OK;
+  });
+}
+
+const char* aim_kernel_name(int32_t id) {
+  static const char* names[AIM_K_COUNT] = {"anterp_xfft", "yfft_fwd", "zconv", "zrhs", "yfft_inv", "xfft_inv",
+                                          "interp_near", "excitation", "gmres_dot", "gmres_update", "gmres_small"};
+  return id >= 0 && id < AIM_K_COUNT ? names[id] : "?";
+}
+
+int aim_get_anterp(const aim_ctx* c, int32_t* anchor, double* lam) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(const_cast<aim_ctx*>(c), [&] {
+    if (anchor)
+      AIM_CUDA(cudaMemcpy(anchor, c->d_anchor, (size_t)c->ns * 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    if (lam) AIM_CUDA(cudaMemcpy(lam, c->d_lam, (size_t)c->ns * 256 * sizeof(double), cudaMemcpyDeviceToHost));
+    return AIM_OK;
+  });
+}
+
+int aim_get_near(const aim_ctx* c, int32_t* rowptr, int32_t* col, aim_c128* val) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(const_cast<aim_ctx*>(c), [&] {
+    if (rowptr) std::memcpy(rowptr, c->h_rowptr.data(), (c->ns + 1) * sizeof(int));
+    if (col && c->nnz) AIM_CUDA(cudaMemcpy(col, c->d_col, c->nnz * sizeof(int), cudaMemcpyDeviceToHost));
+    if (val && c->nnz)
+      AIM_CUDA(cudaMemcpy(val, c->d_near, (size_t)(c->n_delays + 1) * c->nnz * sizeof(double2),
+                          cudaMemcpyDeviceToHost));
+    return AIM_OK;
+  });
+}
+
+int aim_get_kernel_spectrum(const aim_ctx* c, int32_t m, int32_t kind, aim_c128* out) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(const_cast<aim_ctx*>(c), [&] {
+    if (!out || m < 0 || m > c->n_delays || kind < 0 || kind > 1)
+      throw AimError{AIM_ERR_ARG, "aim_get_kernel_spectrum: bad delay or kind"};
+    const size_t oct = (size_t)(c->N + 1) * (c->N + 1) * (c->N + 1);
+    AIM_CUDA(cudaMemcpy(out, c->d_kspec + ((size_t)m * 2 + kind) * oct, oct * sizeof(double2),
+                        cudaMemcpyDeviceToHost));
+    return AIM_OK;
+  });
+}
+
+}  // extern "C"
+
+static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, double tol, aim_c128* currents,
+                       aim_stats* stats) {
+    cudaStream_t st = c->stream;
+  const int nb = exc->nb, ns = c->ns, ng = c->n_delays, B = c->batch_max;
+  const size_t n = (size_t)nb * ns;
+  const size_t slab = op_slab_bytes(c, B);
+  const bool dev_out = is_device_ptr(currents);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) AIM_CUDA(cudaEventCreate(&e));
+  std::vector<int> its(nb);
+  std::vector<double> res(nb), norms;
+  double* d_nrm = c->gs.rn;  // reused after each solve
+  std::vector<double> h_nrm(nb);
+  if (stats) {
+    stats->last_step = 0;
+    stats->total_iters = 0;
+    stats->max_iters = 0;
+    stats->max_rel_res = 0;
+    stats->rhs_ms = 0;
+    stats->solve_ms = 0;
+  }
+  int rc = AIM_OK;
+  const int l0 = c->l_done;
+  for (int l = l0 + 1; l <= l0 + n_steps; ++l) {
+    AIM_CUDA(cudaEventRecord(ev[0], st));
+    op_excitation(c, nb, c->d_exc, exc->sigma, exc->t_d, l, c->d_b);
+    SlabList sl{};
+    NearList nl{};
+    for (int m = 1; m <= ng; ++m) {
+      if (l - m < 1) continue;
+      const int s = (l - m) % ng;
+      sl.p[sl.n] = (char*)c->d_ring + (size_t)s * slab;
+      sl.m[sl.n] = m;
+      sl.n++;
+      if (c->nnz > 0) {
+        nl.val[nl.n] = c->d_near + (size_t)m * c->nnz;
+        nl.x[nl.n] = c->d_iring + (size_t)s * B * ns;
+        nl.n++;
+      }
+    }
+    op_apply_rhs(c, nb, sl, nl, c->d_b, -1.0, c->d_b);  // b = V_l - sum_m Z_m I_{l-m}
+    AIM_CUDA(cudaEventRecord(ev[1], st));
+    int r = gmres_solve(c, nb, c->d_b, c->d_x, tol, its.data(), res.data());
+    AIM_CUDA(cudaEventRecord(ev[2], st));
+    // commit I_l: RWG-space history and its forward slab
+    const int s = l % ng;
+    AIM_CUDA(cudaMemcpyAsync(c->d_iring + (size_t)s * B * ns, c->d_x, n * sizeof(double2),
+                             cudaMemcpyDeviceToDevice, st));
+    op_forward_slab(c, nb, c->d_x, (char*)c->d_ring + (size_t)s * slab);
+    AIM_CUDA(cudaMemcpyAsync(currents + (size_t)(l - l0 - 1) * n, c->d_x, n * sizeof(double2),
+                             dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    gmres_norms(c, nb, c->d_x, d_nrm);
+    AIM_CUDA(cudaMemcpyAsync(h_nrm.data(), d_nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AIM_CUDA(cudaStreamSynchronize(st));
+    double mx = 0;
+    for (int b = 0; b < nb; ++b) mx = std::max(mx, h_nrm[b]);
+    norms.push_back(mx);
+    if (stats) {
+      float a = 0, b2 = 0;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b2, ev[1], ev[2]);
+      stats->rhs_ms += a;
+      stats->solve_ms += b2;
+      for (int b = 0; b < nb; ++b) {
+        stats->total_iters += its[b];
+        stats->max_iters = std::max(stats->max_iters, its[b]);
+        stats->max_rel_res = std::max(stats->max_rel_res, res[b]);
+        if (stats->iters) stats->iters[(size_t)(l - l0 - 1) * nb + b] = its[b];
+      }
+      stats->last_step = l;
+    }
+    c->l_done = l;
+    prof_flush(c);
+    if (r != AIM_OK) {
+      if (stats) stats->last_step = l - 1;
+      c->err = "GMRES reached its iteration cap at step " + std::to_string(l);
+      rc = r;
+      break;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc == AIM_OK && norms.size() >= 4) {
+    double early = 0;
+    for (size_t i = 0; i < norms.size() / 2; ++i) early = std::max(early, norms[i]);
+    if (norms.back() > 1e3 * early) rc = AIM_WARN_UNSTABLE;
+  }
+  return rc;
+}

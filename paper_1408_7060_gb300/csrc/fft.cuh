@@ -1,0 +1,143 @@
+// Shared-memory complex FFT of padded grid lines (length L = 2N), Stockham autosort.
+//
+// A line of length L = R_1 R_2 ... R_s is transformed in s radix-R passes.  Pass
+// with radix R and accumulated sub-length Ns reads v[r] = in[j + r L/R] for
+// j in [0, L/R), applies the twiddles W_{Ns R}^{r (j mod Ns)}, a length-R DFT, and
+// writes out[(j/Ns) Ns R + (j mod Ns) + r Ns]; the output is in natural order
+// after the last pass.  Twiddles come from a table W_L^t = exp(-2 pi i t / L)
+// computed on the host in FP64.  Forward uses exp(-...), inverse exp(+...), and
+// neither scales (the 1/L^3 of the inverse is folded into the kernel spectra).
+#pragma once
+#include "cplx.cuh"
+
+// radix plans: every supported padded length
+__host__ __device__ constexpr int plan_len(int L) {
+  return L == 16 ? 2 : L == 32 ? 2 : L == 64 ? 2 : L == 96 ? 3 : L == 128 ? 3 : L == 192 ? 3
+       : L == 256 ? 3 : L == 384 ? 4 : L == 512 ? 3 : L == 768 ? 4 : 0;
+}
+__host__ __device__ constexpr int plan_rad(int L, int s) {
+  return L == 16 ? 4
+       : L == 32 ? (s == 0 ? 8 : 4)
+       : L == 64 ? 8
+       : L == 96 ? (s == 0 ? 8 : s == 1 ? 4 : 3)
+       : L == 128 ? (s == 0 ? 8 : 4)
+       : L == 192 ? (s < 2 ? 8 : 3)
+       : L == 256 ? (s < 2 ? 8 : 4)
+       : L == 384 ? (s == 0 ? 8 : s < 3 ? 4 : 3)
+       : L == 512 ? 8
+       : L == 768 ? (s < 2 ? 8 : s == 2 ? 4 : 3)
+       : 0;
+}
+
+// ---------------------------------------------------------------- small DFTs
+template <bool INV, class C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a - b;
+  a = a + b;
+  b = t;
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ C rot_q(C a) {  // multiply by W_4 = -i (forward) / +i (inverse)
+  return INV ? mul_pi(a) : mul_mi(a);
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  C t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = rot_q<INV>(v1 - v3);
+  v0 = t0 + t2;
+  v2 = t0 - t2;
+  v1 = t1 + t3;
+  v3 = t1 - t3;
+}
+
+template <int R, bool INV, class C> struct DFT;
+
+template <bool INV, class C> struct DFT<2, INV, C> {
+  __device__ __forceinline__ static void run(C* v) { dft2<INV>(v[0], v[1]); }
+};
+template <bool INV, class C> struct DFT<4, INV, C> {
+  __device__ __forceinline__ static void run(C* v) { dft4<INV>(v[0], v[1], v[2], v[3]); }
+};
+template <bool INV, class C> struct DFT<8, INV, C> {
+  __device__ __forceinline__ static void run(C* v) {
+    using Rl = decltype(v[0].x);
+    const Rl h = (Rl)0.70710678118654752440;  // 1/sqrt(2)
+    dft4<INV>(v[0], v[2], v[4], v[6]);       // even samples -> E_q
+    dft4<INV>(v[1], v[3], v[5], v[7]);       // odd samples  -> O_q
+    // X_q = E_q + W_8^q O_q, X_{q+4} = E_q - W_8^q O_q
+    C o1 = v[3], o2 = v[5], o3 = v[7];
+    C w1 = INV ? mkc(h * (o1.x - o1.y), h * (o1.x + o1.y)) : mkc(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    C w2 = rot_q<INV>(o2);
+    C w3 = INV ? mkc(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : mkc(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = e0 + o0; v[4] = e0 - o0;
+    v[1] = e1 + w1; v[5] = e1 - w1;
+    v[2] = e2 + w2; v[6] = e2 - w2;
+    v[3] = e3 + w3; v[7] = e3 - w3;
+  }
+};
+template <bool INV, class C> struct DFT<3, INV, C> {
+  __device__ __forceinline__ static void run(C* v) {
+    using Rl = decltype(v[0].x);
+    const Rl s3 = (Rl)0.86602540378443864676;  // sqrt(3)/2
+    C s = v[1] + v[2], d = v[1] - v[2];
+    C t = mkc(v[0].x - (Rl)0.5 * s.x, v[0].y - (Rl)0.5 * s.y);
+    C jd = mkc(-s3 * d.y, s3 * d.x);  // i sqrt(3)/2 d
+    v[0] = v[0] + s;
+    v[1] = INV ? t + jd : t - jd;
+    v[2] = INV ? t - jd : t + jd;
+  }
+};
+
+// ---------------------------------------------------------------- one pass
+// nl lines; element i of line l sits at buf[l*ls + i*es].  LF: consecutive
+// threads walk consecutive lines (column tiles); else consecutive butterflies.
+template <int L, int R, int NS, bool INV, bool LF, class C>
+__device__ __forceinline__ void fft_pass(const C* __restrict__ in, C* __restrict__ out, int nl, int es,
+                                         int ls, const C* __restrict__ tw) {
+  constexpr int NB = L / R;
+  const int units = nl * NB;
+  for (int t = threadIdx.x; t < units; t += blockDim.x) {
+    int line, j;
+    if (LF) { line = t % nl; j = t / nl; } else { j = t % NB; line = t / NB; }
+    const C* src = in + line * ls;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * NB) * es];
+    if (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = tw[r * k * (L / (NS * R))];
+        v[r] = v[r] * (INV ? conjc(w) : w);
+      }
+    }
+    DFT<R, INV, C>::run(v);
+    const int base = (j / NS) * NS * R + (j % NS);
+    C* dst = out + line * ls;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(base + r * NS) * es] = v[r];
+  }
+}
+
+template <int L, int S, int NS, bool INV, bool LF, class C>
+__device__ __forceinline__ C* fft_passes(C* a, C* b, int nl, int es, int ls, const C* tw) {
+  if constexpr (S == plan_len(L)) {
+    return a;
+  } else {
+    constexpr int R = plan_rad(L, S);
+    fft_pass<L, R, NS, INV, LF, C>(a, b, nl, es, ls, tw);
+    __syncthreads();
+    return fft_passes<L, S + 1, NS * R, INV, LF, C>(b, a, nl, es, ls, tw);
+  }
+}
+
+// Transform nl lines held in a; b is scratch of the same size.  Returns the
+// buffer holding the result.  Must be called by every thread of the block, after
+// a __syncthreads() that publishes a.
+template <int L, bool INV, bool LF, class C>
+__device__ __forceinline__ C* block_fft(C* a, C* b, int nl, int es, int ls, const C* tw) {
+  static_assert(plan_len(L) > 0, "unsupported FFT length");
+  return fft_passes<L, 0, 1, INV, LF, C>(a, b, nl, es, ls, tw);
+}

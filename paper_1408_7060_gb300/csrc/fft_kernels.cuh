@@ -1,0 +1,74 @@
+// Batched line transforms over the padded grid, built on block_fft.
+//
+// k_rows:  contiguous lines (x direction).  Row r reads n_in elements at
+//          in + r*rs_in (the rest of the length-L line is zero: pruned zero
+//          padding) and writes the first n_out outputs at out + r*rs_out.
+// k_cols:  strided lines (y or z direction) processed as tiles of W adjacent
+//          x positions, so every global access is a contiguous run of W elements.
+//          Line (p2, p1, x) element i lives at base + p2*ps2 + p1*ps1 + x + i*es.
+#pragma once
+#include "fft.cuh"
+
+extern __shared__ __align__(16) unsigned char aim_smem[];
+
+template <class C>
+__device__ __forceinline__ void load_twiddles(C* tw, const C* __restrict__ twg, int L) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
+}
+
+template <int L, bool INV, class C>
+__global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __restrict__ out, int nrows,
+                                              int n_in, int n_out, long long rs_in, long long rs_out,
+                                              const C* __restrict__ twg, int rpb) {
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* b0 = tw + L;
+  C* b1 = b0 + rpb * L;
+  load_twiddles(tw, twg, L);
+  const int r0 = blockIdx.x * rpb;
+  const int nr = min(rpb, nrows - r0);
+  for (int t = threadIdx.x; t < rpb * L; t += blockDim.x) {
+    int rr = t / L, i = t % L;
+    C v = mkc((decltype(C().x))0, (decltype(C().x))0);
+    if (rr < nr && i < n_in) v = in[(long long)(r0 + rr) * rs_in + i];
+    b0[t] = v;
+  }
+  __syncthreads();
+  C* res = block_fft<L, INV, false, C>(b0, b1, rpb, 1, L, tw);
+  for (int t = threadIdx.x; t < rpb * L; t += blockDim.x) {
+    int rr = t / L, i = t % L;
+    if (rr < nr && i < n_out) out[(long long)(r0 + rr) * rs_out + i] = res[t];
+  }
+}
+
+template <int L, int W, bool INV, class C>
+__global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __restrict__ out, int n_in,
+                                              int n_out, long long es_in, long long es_out, int nx,
+                                              long long ps1_in, long long ps1_out, long long ps2_in,
+                                              long long ps2_out, const C* __restrict__ twg) {
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* b0 = tw + L;
+  C* b1 = b0 + L * W;
+  load_twiddles(tw, twg, L);
+  const int x0 = blockIdx.x * W;
+  const int nw = min(W, nx - x0);
+  const C* src = in + blockIdx.z * ps2_in + blockIdx.y * ps1_in + x0;
+  C* dst = out + blockIdx.z * ps2_out + blockIdx.y * ps1_out + x0;
+  for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
+    int i = t / W, l = t % W;
+    C v = mkc((decltype(C().x))0, (decltype(C().x))0);
+    if (i < n_in && l < nw) v = src[i * es_in + l];
+    b0[t] = v;
+  }
+  __syncthreads();
+  C* res = block_fft<L, INV, true, C>(b0, b1, W, W, 1, tw);
+  for (int t = threadIdx.x; t < n_out * W; t += blockDim.x) {
+    int i = t / W, l = t % W;
+    if (l < nw) dst[i * es_out + l] = res[t];
+  }
+}
+
+// tile width of a column pass: keep 2 (or 3) L x W buffers within ~160 KB
+template <int L, class C>
+constexpr int col_width() {
+  return (2 * L * 16 * (int)sizeof(C) <= 160 * 1024) ? 16 : (2 * L * 8 * (int)sizeof(C) <= 160 * 1024) ? 8 : 4;
+}

@@ -1,0 +1,9 @@
+// Batched GMRES for the immediate system of Eq. 5.
+#pragma once
+#include "aim_internal.h"
+
+void gmres_alloc(aim_ctx* c);
+void gmres_free_host(aim_ctx* c);
+int gmres_blocks(int ns);
+int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, int* iters, double* relres);
+void gmres_norms(aim_ctx* c, int nb, const double2* v, double* d_out);

@@ -1,0 +1,81 @@
+// Precision dispatch of the operator and the excitation kernel (Eq. 1).
+#include "aim_internal.h"
+#include "operator.h"
+
+template <class C>
+void body_apply(aim_ctx*, int, int, const double2*, const double2*, const double2*, double, const int*, double2*);
+template <class C>
+void body_forward_slab(aim_ctx*, int, const double2*, void*);
+template <class C>
+void body_apply_rhs(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double, double2*);
+
+void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
+              const int* active, double2* y) {
+  if (c->precision == AIM_C64)
+    body_apply<float2>(c, m, nb, v, dinv, base, sign, active, y);
+  else
+    body_apply<double2>(c, m, nb, v, dinv, base, sign, active, y);
+}
+
+void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst) {
+  if (c->precision == AIM_C64)
+    body_forward_slab<float2>(c, nb, v, dst);
+  else
+    body_forward_slab<double2>(c, nb, v, dst);
+}
+
+void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, const double2* base, double sign,
+                  double2* y) {
+  if (c->precision == AIM_C64)
+    body_apply_rhs<float2>(c, nb, sl, nl, base, sign, y);
+  else
+    body_apply_rhs<double2>(c, nb, sl, nl, base, sign, y);
+}
+
+size_t op_slab_bytes(const aim_ctx* c, int nb) {
+  return (size_t)nb * 4 * c->N * (size_t)c->L * c->L * (c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2));
+}
+
+// V_l[k] = <S_k, p (g'(tau) + j w g(tau)) e^{-j w (r.k/c + t_d)}>,  tau = l dt - r.k/c - t_d,
+// g = exp(-tau^2/(2 sigma^2)): the envelope of D E^inc for the plane wave of Eq. 1.
+__global__ void k_excitation(int ns, int nb, const int* __restrict__ rtri, const int* __restrict__ rfree,
+                             const double* __restrict__ len, const double* __restrict__ area,
+                             const double* __restrict__ V, const double* __restrict__ qp,
+                             const double* __restrict__ qw, const double* __restrict__ kp, double sigma, double t_d,
+                             double t, double wc, double c0, double2* __restrict__ out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ns * nb) return;
+  const int b = idx / ns, k = idx % ns;
+  const double* kh = kp + 6 * b;
+  const double* ph = kh + 3;
+  double2 acc = make_double2(0, 0);
+  for (int side = 0; side < 2; ++side) {
+    const int tr = rtri[2 * k + side];
+    const double* vf = V + 3 * rfree[2 * k + side];
+    const double cS = (side == 0 ? 1.0 : -1.0) * len[k] / (2.0 * area[tr]);
+    for (int q = 0; q < 7; ++q) {
+      const double* r = qp + 21 * tr + 3 * q;
+      const double delay = (r[0] * kh[0] + r[1] * kh[1] + r[2] * kh[2]) / c0;
+      const double tau = t - delay - t_d;
+      const double g = exp(-tau * tau / (2.0 * sigma * sigma));
+      double s, cph;
+      sincos(-wc * (delay + t_d), &s, &cph);
+      // (-tau/sigma^2 + j w) g e^{j phase}
+      const double ar = -tau / (sigma * sigma) * g, ai = wc * g;
+      const double sp = cS * ((r[0] - vf[0]) * ph[0] + (r[1] - vf[1]) * ph[1] + (r[2] - vf[2]) * ph[2]);
+      const double w = qw[7 * tr + q] * sp;
+      acc.x += w * (ar * cph - ai * s);
+      acc.y += w * (ar * s + ai * cph);
+    }
+  }
+  out[(size_t)b * ns + k] = acc;
+}
+
+void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double t_d, int step_l, double2* out) {
+  int n = c->ns * nb;
+  KScope ks(c, AIM_K_EXCITATION);
+  k_excitation<<<(n + 127) / 128, 128, 0, c->stream>>>(c->ns, nb, c->d_rtri, c->d_rfree, c->d_len, c->d_area,
+                                                      c->d_v, c->d_qp, c->d_qw, d_kp, sigma, t_d,
+                                                      step_l * c->dt, c->wc, aimc::kC0, out);
+  AIM_CHECK_LAUNCH();
+}

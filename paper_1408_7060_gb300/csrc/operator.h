@@ -1,0 +1,30 @@
+// Operator entry points shared by the API, the solver and the march.
+#pragma once
+#include "aim_internal.h"
+
+// near-zone terms summed by the interpolation kernel: sum_t Z~near_{m_t} x_t
+struct NearList {
+  const double2* val[aimc::kMaxDelays];  // [nnz] values of one delay
+  const double2* x[aimc::kMaxDelays];    // [nb][ns] vector it multiplies
+  const double2* dinv;                   // optional diagonal applied to every x (preconditioner)
+  int n;
+};
+
+// history slabs (forward x/y-transformed grids) and the delay each one carries
+struct SlabList {
+  const void* p[aimc::kMaxDelays];
+  int m[aimc::kMaxDelays];
+  int n;
+};
+
+// y = base + sign * Z~AIM_m (dinv .* v)     (dinv, base optional; m = delay)
+void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
+              const int* active, double2* y);
+// slab of one current vector (anterpolation + forward x and y passes) written to dst
+void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst);
+// y = base + sign * [ sum_s Z~FFT_{m_s} (slab_s) + near terms ]
+void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, const double2* base, double sign,
+                  double2* y);
+// V_l for the plane waves in exc (device parameter block [nb][6]: khat, phat)
+void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double t_d, int step_l, double2* out);
+size_t op_slab_bytes(const aim_ctx* c, int nb);

@@ -1,0 +1,59 @@
+// Precision-generic operator sequences, dispatched over the supported padded lengths.
+#pragma once
+#include "operator_impl.cuh"
+
+// supported padded lengths L = 2N (grid N in {8, 16, 32, 64, 96, 128, 384})
+#define AIM_DISPATCH_L(Lrt, ...)                                      \
+  switch (Lrt) {                                                       \
+    case 16: { constexpr int LL = 16; __VA_ARGS__; } break;                   \
+    case 32: { constexpr int LL = 32; __VA_ARGS__; } break;                   \
+    case 64: { constexpr int LL = 64; __VA_ARGS__; } break;                   \
+    case 128: { constexpr int LL = 128; __VA_ARGS__; } break;                 \
+    case 192: { constexpr int LL = 192; __VA_ARGS__; } break;                 \
+    case 256: { constexpr int LL = 256; __VA_ARGS__; } break;                 \
+    case 768: { constexpr int LL = 768; __VA_ARGS__; } break;                 \
+    default: throw AimError{AIM_ERR_ARG, "unsupported grid size"};     \
+  }
+
+template <class C>
+void body_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
+                const int* active, double2* y) {
+  NearList nl{};
+  nl.dinv = dinv;
+  nl.n = 0;
+  if (c->nnz > 0) {
+    nl.n = 1;
+    nl.val[0] = c->d_near + (size_t)m * c->nnz;
+    nl.x[0] = v;
+  }
+  AIM_DISPATCH_L(c->L, {
+    GridOps<LL, C>::forward_slab(c, nb, v, dinv, active, reinterpret_cast<C*>(c->d_Bf));
+    GridOps<LL, C>::zconv(c, nb, m, active);
+    GridOps<LL, C>::backward(c, nb, nl, base, sign, active, y);
+  });
+}
+
+template <class C>
+void body_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst) {
+  AIM_DISPATCH_L(c->L, { GridOps<LL, C>::forward_slab(c, nb, v, nullptr, nullptr, reinterpret_cast<C*>(dst)); });
+}
+
+template <class C>
+void body_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, const double2* base, double sign,
+                    double2* y) {
+  AIM_DISPATCH_L(c->L, {
+    if (sl.n > 0) {
+      GridOps<LL, C>::zrhs(c, nb, sl);
+      GridOps<LL, C>::backward(c, nb, nl, base, sign, nullptr, y);
+    } else {
+      GridOps<LL, C>::interp(c, nb, nullptr, nl, base, sign, nullptr, y);
+    }
+  });
+}
+
+#define AIM_INSTANTIATE_OPS(C)                                                                                   \
+  template void body_apply<C>(aim_ctx*, int, int, const double2*, const double2*, const double2*, double,       \
+                              const int*, double2*);                                                             \
+  template void body_forward_slab<C>(aim_ctx*, int, const double2*, void*);                                     \
+  template void body_apply_rhs<C>(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double,      \
+                                  double2*);

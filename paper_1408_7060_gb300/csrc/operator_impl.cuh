@@ -1,0 +1,337 @@
+// The ET-AIM operator on the device (Eq. 5, Sec. 4 stages i-iv), templated on the
+// complex type of the grid stages (float2: complex64 path, double2: plain path).
+//
+// Data layout per right-hand side b and component c (x, y, z, div), with L = 2N:
+//   A  [b][c][z<N][y<N][x<L]   after anterpolation + forward x-FFT
+//   Bf [b][c][z<N][y<L][x<L]   after the forward y-FFT (the z<N slab)
+//   P  [b][c][z<N][y<N][x<N]   potentials after the inverse passes
+// The forward z-FFT, the pointwise kernel product and the inverse z-FFT are one
+// kernel per column (k_zconv / k_zrhs), so the full (2N)^3 spectrum never reaches
+// memory.  Zero padding is pruned in every pass: forward passes read only the N
+// non-zero inputs, inverse passes write only the N needed outputs.
+#pragma once
+#include <algorithm>
+
+#include "aim_internal.h"
+#include "fft_kernels.cuh"
+#include "operator.h"
+
+template <class C> struct Real;
+template <> struct Real<float2> { using T = float; using F4 = float4; };
+template <> struct Real<double2> { using T = double; using F4 = double4_32a; };
+
+template <class C> __device__ __forceinline__ C cvt(double2 a);
+template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ double2 cvt<double2>(double2 a) { return a; }
+
+// ---------------------------------------------------------------- stage i + x pass
+// S_c[n] = sum_k L_c[n,k] x_k gathered node by node (the transpose of the
+// interpolation rows), then the forward x-FFT of each grid row.  One block holds
+// the 4 components of ypb consecutive rows (z, y).
+template <int L, class C>
+__global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ nptr, const int* __restrict__ nidx,
+                                                     const typename Real<C>::F4* __restrict__ ncoef,
+                                                     const double2* __restrict__ v, const double2* __restrict__ dinv,
+                                                     const int* __restrict__ active, int ns, int N, int ypb,
+                                                     C* __restrict__ A, const C* __restrict__ twg) {
+  using R = typename Real<C>::T;
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* b0 = tw + L;
+  C* b1 = b0 + 4 * ypb * L;
+  load_twiddles(tw, twg, L);
+  const int z = blockIdx.y, y0 = blockIdx.x * ypb;
+  const double2* vb = v + (size_t)b * ns;
+  for (int t = threadIdx.x; t < ypb * L; t += blockDim.x) {
+    const int yy = t / L, x = t % L, y = y0 + yy;
+    C a0{}, a1{}, a2{}, a3{};
+    if (x < N && y < N) {
+      const size_t n = ((size_t)z * N + y) * N + x;
+      for (int e = nptr[n]; e < nptr[n + 1]; ++e) {
+        const int k = nidx[e];
+        double2 xd = vb[k];
+        if (dinv) {
+          double2 d = dinv[k];
+          xd = make_double2(xd.x * d.x - xd.y * d.y, xd.x * d.y + xd.y * d.x);
+        }
+        const C xv = cvt<C>(xd);
+        const typename Real<C>::F4 w = ncoef[e];
+        a0 += (R)w.x * xv;
+        a1 += (R)w.y * xv;
+        a2 += (R)w.z * xv;
+        a3 += (R)w.w * xv;
+      }
+    }
+    b0[(0 * ypb + yy) * L + x] = a0;
+    b0[(1 * ypb + yy) * L + x] = a1;
+    b0[(2 * ypb + yy) * L + x] = a2;
+    b0[(3 * ypb + yy) * L + x] = a3;
+  }
+  __syncthreads();
+  C* res = block_fft<L, false, false, C>(b0, b1, 4 * ypb, 1, L, tw);
+  for (int t = threadIdx.x; t < 4 * ypb * L; t += blockDim.x) {
+    const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
+    if (y < N) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
+  }
+}
+
+// ---------------------------------------------------------------- z pass with the kernel
+__device__ __forceinline__ int fold(int k, int N) { return k <= N ? k : 2 * N - k; }
+
+// Forward z-FFT of the slab column, product with the kernel spectrum of delay m
+// (G^A for c = x,y,z; G^phi for c = div; even-symmetric octant), inverse z-FFT,
+// first N outputs written back in place.
+template <int L, int W, class C>
+__global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
+                                               const int* __restrict__ active, const C* __restrict__ twg) {
+  const int bc = blockIdx.z;
+  if (active && !active[bc >> 2]) return;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* b0 = tw + L;
+  C* b1 = b0 + L * W;
+  load_twiddles(tw, twg, L);
+  const int y = blockIdx.y, x0 = blockIdx.x * W;
+  const long long es = (long long)L * L;
+  C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
+  for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
+    const int i = t / W, l = t % W;
+    C v{};
+    if (i < N) v = col[i * es + l];
+    b0[t] = v;
+  }
+  __syncthreads();
+  C* f = block_fft<L, false, true, C>(b0, b1, W, W, 1, tw);
+  const int n1 = N + 1;
+  const C* G = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1;
+  const int fy = fold(y, N);
+  for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
+    const int i = t / W, l = t % W;
+    f[t] = f[t] * G[((size_t)fold(i, N) * n1 + fy) * n1 + fold(x0 + l, N)];
+  }
+  __syncthreads();
+  C* g = block_fft<L, true, true, C>(f, f == b0 ? b1 : b0, W, W, 1, tw);
+  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
+    const int i = t / W, l = t % W;
+    col[i * es + l] = g[t];
+  }
+}
+
+// Delay sum of the right-hand side in the spectral domain:
+//   P^_col = sum_i G^_{m_i} . FFT_z(slab_i column), then one inverse z-FFT.
+template <int L, int W, class C>
+__global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__ kspec_all, int N,
+                                              C* __restrict__ Bf, const C* __restrict__ twg) {
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* b0 = tw + L;
+  C* b1 = b0 + L * W;
+  C* acc = b1 + L * W;
+  load_twiddles(tw, twg, L);
+  const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
+  const long long es = (long long)L * L;
+  const int n1 = N + 1;
+  const size_t oct = (size_t)n1 * n1 * n1;
+  const int kind = (bc & 3) == 3 ? 1 : 0;
+  const int fy = fold(y, N);
+  for (int t = threadIdx.x; t < L * W; t += blockDim.x) acc[t] = C{};
+  for (int s = 0; s < sl.n; ++s) {
+    const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
+      const int i = t / W, l = t % W;
+      C v{};
+      if (i < N) v = col[i * es + l];
+      b0[t] = v;
+    }
+    __syncthreads();
+    C* f = block_fft<L, false, true, C>(b0, b1, W, W, 1, tw);
+    const C* G = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct;
+    for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
+      const int i = t / W, l = t % W;
+      acc[t] += f[t] * G[((size_t)fold(i, N) * n1 + fy) * n1 + fold(x0 + l, N)];
+    }
+  }
+  __syncthreads();
+  C* g = block_fft<L, true, true, C>(acc, b0, W, W, 1, tw);
+  C* out = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
+  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
+    const int i = t / W, l = t % W;
+    out[i * es + l] = g[t];
+  }
+}
+
+// ---------------------------------------------------------------- stage iii + iv
+// y_k = sign * ( sum_c sum_{n in stencil(k)} L_c[n,k] P_c[n]  +  sum_terms Z~near_m x_m ) + base_k
+// One warp per (b, k).  Grid part accumulated in the grid precision, near part in FP64.
+template <class C>
+__global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, const int* __restrict__ anchor,
+                                                     const typename Real<C>::T* __restrict__ lam, int N, int ns,
+                                                     int nb, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ col, NearList nl,
+                                                     const double2* __restrict__ base, double sign,
+                                                     const int* __restrict__ active, double2* __restrict__ y) {
+  using R = typename Real<C>::T;
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)nb * ns) return;
+  const int b = (int)(w / ns), k = (int)(w % ns);
+  if (active && !active[b]) return;
+  double2 tot = make_double2(0, 0);
+  if (P) {
+    const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
+    const R* lk = lam + (size_t)k * 256;
+    const size_t N3 = (size_t)N * N * N;
+    const C* Pb = P + (size_t)b * 4 * N3;
+    C g{};
+    for (int s = lane; s < 64; s += 32) {
+      const size_t n = ((size_t)(az + (s >> 4)) * N + (ay + ((s >> 2) & 3))) * N + (ax + (s & 3));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) g += lk[c * 64 + s] * Pb[c * N3 + n];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
+      g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
+    }
+    tot = make_double2((double)g.x, (double)g.y);
+  }
+  double2 nr = make_double2(0, 0);
+  for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 32) {
+    const int j = col[e];
+    for (int t = 0; t < nl.n; ++t) {
+      const double2 z = nl.val[t][e];
+      double2 xv = nl.x[t][(size_t)b * ns + j];
+      if (nl.dinv) {
+        const double2 d = nl.dinv[j];
+        xv = make_double2(xv.x * d.x - xv.y * d.y, xv.x * d.y + xv.y * d.x);
+      }
+      nr.x += z.x * xv.x - z.y * xv.y;
+      nr.y += z.x * xv.y + z.y * xv.x;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nr.x += __shfl_xor_sync(0xffffffffu, nr.x, o);
+    nr.y += __shfl_xor_sync(0xffffffffu, nr.y, o);
+  }
+  if (lane == 0) {
+    double2 r = make_double2(sign * (tot.x + nr.x), sign * (tot.y + nr.y));
+    if (base) {
+      const double2 bb = base[(size_t)b * ns + k];
+      r = make_double2(bb.x + r.x, bb.y + r.y);
+    }
+    y[(size_t)b * ns + k] = r;
+  }
+}
+
+// ---------------------------------------------------------------- launch helpers
+template <class K>
+static void smem_opt_in(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) AIM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+// precision selectors for the context tables
+inline const float2* sel_tw(aim_ctx* c, float2*) { return c->d_twf; }
+inline const double2* sel_tw(aim_ctx* c, double2*) { return c->d_tw; }
+inline const float2* sel_kspec(aim_ctx* c, float2*) { return c->d_kspecf; }
+inline const double2* sel_kspec(aim_ctx* c, double2*) { return c->d_kspec; }
+inline const float4* sel_ncoef(aim_ctx* c, float2*) { return c->d_ncoeff; }
+inline const double4_32a* sel_ncoef(aim_ctx* c, double2*) { return c->d_ncoef; }
+inline const float* sel_lam(aim_ctx* c, float2*) { return c->d_lamf; }
+inline const double* sel_lam(aim_ctx* c, double2*) { return c->d_lam; }
+
+template <int L, class C>
+struct GridOps {
+  static constexpr int W = col_width<L, C>();
+  static int ypb() { return std::max(1, 1024 / (4 * L)); }
+  static int rpb() { return std::max(1, 2048 / L); }
+
+  // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
+  static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab) {
+    const int N = c->N;
+    const C* tw = twiddles(c);
+    C* A = reinterpret_cast<C*>(c->d_A);
+    {
+      const int yp = ypb();
+      size_t sm = (L + 2 * 4 * yp * L) * sizeof(C);
+      smem_opt_in(k_anterp_rows<L, C>, sm);
+      dim3 grid((N + yp - 1) / yp, N, nb);
+      KScope ks(c, AIM_K_ANTERP_XFFT);
+      k_anterp_rows<L, C><<<grid, 256, sm, c->stream>>>(c->d_nptr, c->d_nidx, ncoef(c), v, dinv, active, c->ns, N,
+                                                        yp, A, tw);
+      AIM_CHECK_LAUNCH();
+    }
+    {
+      size_t sm = (L + 2 * L * W) * sizeof(C);
+      smem_opt_in(k_cols<L, W, false, C>, sm);
+      dim3 grid(L / W, N, nb * 4);
+      KScope ks(c, AIM_K_YFFT_FWD);
+      k_cols<L, W, false, C><<<grid, 256, sm, c->stream>>>(A, slab, N, L, L, L, L, (long long)N * L, (long long)L * L,
+                                                           (long long)N * N * L, (long long)N * L * L, tw);
+      AIM_CHECK_LAUNCH();
+    }
+  }
+
+  // inverse y and x passes: Bf slab -> P, then interpolation + near terms
+  static void backward(aim_ctx* c, int nb, const NearList& nl, const double2* base, double sign, const int* active,
+                       double2* y) {
+    const int N = c->N;
+    const C* tw = twiddles(c);
+    C* A = reinterpret_cast<C*>(c->d_A);
+    C* Bf = reinterpret_cast<C*>(c->d_Bf);
+    C* P = reinterpret_cast<C*>(c->d_P);
+    {
+      size_t sm = (L + 2 * L * W) * sizeof(C);
+      smem_opt_in(k_cols<L, W, true, C>, sm);
+      dim3 grid(L / W, N, nb * 4);
+      KScope ks(c, AIM_K_YFFT_INV);
+      k_cols<L, W, true, C><<<grid, 256, sm, c->stream>>>(Bf, A, L, N, L, L, L, (long long)L * L, (long long)N * L,
+                                                          (long long)N * L * L, (long long)N * N * L, tw);
+      AIM_CHECK_LAUNCH();
+    }
+    {
+      const int rp = rpb();
+      size_t sm = (L + 2 * rp * L) * sizeof(C);
+      smem_opt_in(k_rows<L, true, C>, sm);
+      const int nrows = nb * 4 * N * N;
+      KScope ks(c, AIM_K_XFFT_INV);
+      k_rows<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
+      AIM_CHECK_LAUNCH();
+    }
+    interp(c, nb, P, nl, base, sign, active, y);
+  }
+
+  static void interp(aim_ctx* c, int nb, const C* P, const NearList& nl, const double2* base, double sign,
+                     const int* active, double2* y) {
+    long long warps = (long long)nb * c->ns;
+    KScope ks(c, AIM_K_INTERP_NEAR);
+    k_interp_near<C><<<(int)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(
+        P, c->d_anchor, lam(c), c->N, c->ns, nb, c->d_rowptr, c->d_col, nl, base, sign, active, y);
+    AIM_CHECK_LAUNCH();
+  }
+
+  static void zconv(aim_ctx* c, int nb, int m, const int* active) {
+    const int N = c->N;
+    size_t sm = (L + 2 * L * W) * sizeof(C);
+    smem_opt_in(k_zconv<L, W, C>, sm);
+    dim3 grid(L / W, L, nb * 4);
+    const size_t oct = (size_t)(N + 1) * (N + 1) * (N + 1);
+    KScope ks(c, AIM_K_ZCONV);
+    k_zconv<L, W, C><<<grid, 256, sm, c->stream>>>(reinterpret_cast<C*>(c->d_Bf), kspec(c) + (size_t)m * 2 * oct, N,
+                                                   active, twiddles(c));
+    AIM_CHECK_LAUNCH();
+  }
+
+  static void zrhs(aim_ctx* c, int nb, const SlabList& sl) {
+    const int N = c->N;
+    size_t sm = (L + 3 * L * W) * sizeof(C);
+    smem_opt_in(k_zrhs<L, W, C>, sm);
+    dim3 grid(L / W, L, nb * 4);
+    KScope ks(c, AIM_K_ZRHS);
+    k_zrhs<L, W, C><<<grid, 256, sm, c->stream>>>(sl, kspec(c), N, reinterpret_cast<C*>(c->d_Bf), twiddles(c));
+    AIM_CHECK_LAUNCH();
+  }
+
+  static const C* twiddles(aim_ctx* c) { return sel_tw(c, (C*)nullptr); }
+  static const C* kspec(aim_ctx* c) { return sel_kspec(c, (C*)nullptr); }
+  static const typename Real<C>::F4* ncoef(aim_ctx* c) { return sel_ncoef(c, (C*)nullptr); }
+  static const typename Real<C>::T* lam(aim_ctx* c) { return sel_lam(c, (C*)nullptr); }
+};

@@ -1,0 +1,234 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Small cases (a 480-RWG sphere on a 16^3 grid, a 1920-RWG sphere on a 32^3 grid)
+span several FFT tiles and ragged stencil/near-zone rows; the 7680-RWG sphere on
+the 64^3 grid is the benchmark workload, compared on sampled outputs.
+
+Tolerances: complex128 path 1e-10 relative (FP64 rounding through the FFTs);
+complex64 grid path 1e-5 relative L2 per matvec and 1e-4 for marched currents;
+integer/index tables bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import aim as oaim
+from oracle import efie, march
+from oracle.rwg import build_rwg
+from paper_1408_7060_gb300.inputs import make_workload
+
+pytestmark = pytest.mark.gpu
+
+CASES = {}
+
+
+def case(name, **over):
+    key = (name, tuple(sorted(over.items())))
+    if key not in CASES:
+        w = make_workload(name, **over)
+        rwg = build_rwg(*w.mesh)
+        p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+        A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+        CASES[key] = (w, rwg, p, A)
+    return CASES[key]
+
+
+def ctx_for(w, **over):
+    from paper_1408_7060_gb300 import AimContext
+
+    return AimContext.from_workload(w, **over)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+@pytest.fixture(scope="module")
+def s480():
+    return case("sphere480")
+
+
+@pytest.fixture(scope="module")
+def s480_ctx(s480):
+    w = s480[0]
+    c = ctx_for(w, precision="c128")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def s480_ctx64(s480):
+    w = s480[0]
+    c = ctx_for(w, precision="c64")
+    yield c
+    c.close()
+
+
+# ------------------------------------------------------------------ setup tables
+
+def test_rwg_table_bit_exact(s480, s480_ctx):
+    w, rwg, p, A = s480
+    e, t, f = s480_ctx.rwg_table()
+    assert np.array_equal(e, rwg.edge) and np.array_equal(t, rwg.tri) and np.array_equal(f, rwg.free)
+
+
+def test_anterp_tables(s480, s480_ctx):
+    w, rwg, p, A = s480
+    anchor, lam = s480_ctx.anterp()
+    assert np.array_equal(anchor, A.anchor)
+    ref = np.transpose(A.lam, (1, 0, 2))               # [ns][4][64]
+    assert np.abs(lam - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_n_delays_and_active(s480, s480_ctx):
+    w, rwg, p, A = s480
+    assert s480_ctx.n_delays == A.n_delays
+    assert s480_ctx.info["n_active"] == len(A.active)
+
+
+def test_near_zone(s480, s480_ctx):
+    w, rwg, p, A = s480
+    rowptr, col, val = s480_ctx.near()
+    assert np.array_equal(col, A.pairs[:, 1]) and np.array_equal(np.diff(rowptr), np.bincount(A.pairs[:, 0], minlength=rwg.ns))
+    ref = A.near_values()
+    for m in range(A.n_delays + 1):
+        sc = np.abs(ref[0]).max()
+        assert np.abs(val[m] - ref[m]).max() < 1e-9 * sc, m
+
+
+def test_kernel_spectra(s480, s480_ctx):
+    w, rwg, p, A = s480
+    n = A.n
+    M = (2 * n) ** 3
+    for m in range(A.n_delays + 1):
+        for kind in (0, 1):
+            G = np.fft.fftn(A.kernel_grid(m, kind))[: n + 1, : n + 1, : n + 1]
+            G *= (oaim.CA if kind == 0 else oaim.CP) / M
+            got = s480_ctx.kernel_spectrum(m, kind)
+            assert np.abs(got - G).max() < 1e-12 * np.abs(G).max(), (m, kind)
+
+
+# ------------------------------------------------------------------ operator
+
+def test_matvec_c128(s480, s480_ctx):
+    w, rwg, p, A = s480
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((2, rwg.ns)) + 1j * rng.standard_normal((2, rwg.ns))
+    for m in range(A.n_delays + 1):
+        y = s480_ctx.matvec(m, x[:1])
+        assert rel(y[0], A.matvec(m, x[0])) < 1e-10, m
+
+
+def test_matvec_c128_device_pointers(s480, s480_ctx):
+    import torch
+
+    w, rwg, p, A = s480
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((1, rwg.ns)) + 1j * rng.standard_normal((1, rwg.ns))
+    y = s480_ctx.matvec(1, torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y[0], A.matvec(1, x[0])) < 1e-10
+
+
+def test_matvec_c64(s480, s480_ctx64):
+    w, rwg, p, A = s480
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((1, rwg.ns)) + 1j * rng.standard_normal((1, rwg.ns))
+    for m in range(A.n_delays + 1):
+        assert rel(s480_ctx64.matvec(m, x)[0], A.matvec(m, x[0])) < 1e-5, m
+
+
+def test_excitation(s480, s480_ctx):
+    w, rwg, p, A = s480
+    for l in (1, 10, 17, 30):
+        V = s480_ctx.excitation(w.khat, w.phat, w.sigma, w.t_d, l)
+        ref = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, [l])[0]
+        assert rel(V, ref) < 1e-12
+
+
+def test_rhs(s480, s480_ctx, s480_ctx64):
+    w, rwg, p, A = s480
+    ng = A.n_delays
+    rng = np.random.default_rng(11)
+    hist = rng.standard_normal((ng, 1, rwg.ns)) + 1j * rng.standard_normal((ng, 1, rwg.ns))
+    for l in (1, 2, ng, ng + 5):
+        ref = sum(A.matvec(m, hist[m - 1, 0]) for m in range(1, ng + 1) if l - m >= 1) if l > 1 else np.zeros(rwg.ns)
+        got = s480_ctx.rhs(l, hist)[0]
+        got64 = s480_ctx64.rhs(l, hist)[0]
+        if l == 1:
+            assert np.abs(got).max() == 0.0 and np.abs(got64).max() == 0.0
+        else:
+            assert rel(got, ref) < 1e-10
+            assert rel(got64, ref) < 1e-5
+
+
+# ------------------------------------------------------------------ march
+
+def test_march_c128_vs_oracle(s480, s480_ctx):
+    """The GPU march solves Eq. 5 with the oracle's operator: compare with the
+    oracle's LU march over the first 60 steps (the chi = 3 march grows later, as
+    Sec. 3.1.1 predicts for CPPIF; both grow identically)."""
+    w, rwg, p, A = s480
+    nt = 60
+    ZA = np.stack([A.dense(m) for m in range(A.n_delays + 1)])
+    V = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, np.arange(1, nt + 1))
+    ref = march.march_dense(ZA, V)
+    cur, stats, rc = s480_ctx.march(w.khat, w.phat, w.sigma, w.t_d, nt, 1e-10)
+    assert stats["last_step"] == nt
+    err = np.linalg.norm(cur - ref, axis=2) / np.linalg.norm(ref, axis=2).max(axis=0, keepdims=True)
+    assert err.max() < 1e-6, err.max()
+
+
+def test_march_c64_vs_oracle(s480, s480_ctx64):
+    w, rwg, p, A = s480
+    nt = 60
+    ZA = np.stack([A.dense(m) for m in range(A.n_delays + 1)])
+    V = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, np.arange(1, nt + 1))
+    ref = march.march_dense(ZA, V)
+    cur, stats, rc = s480_ctx64.march(w.khat, w.phat, w.sigma, w.t_d, nt, 1e-6)
+    err = np.linalg.norm(cur - ref) / np.linalg.norm(ref)
+    assert err < 1e-4, err
+
+
+# ------------------------------------------------------------------ a second size (32^3 grid, 1920 RWG)
+
+@pytest.fixture(scope="module")
+def s1920():
+    return case("sphere_sub3_n32")
+
+
+def test_matvec_sub3(s1920):
+    w, rwg, p, A = s1920
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((1, rwg.ns)) + 1j * rng.standard_normal((1, rwg.ns))
+    with ctx_for(w, precision="c128") as c128, ctx_for(w, precision="c64") as c64:
+        assert c128.n_delays == A.n_delays
+        for m in (0, 1, A.n_delays):
+            ref = A.matvec(m, x[0])
+            assert rel(c128.matvec(m, x)[0], ref) < 1e-10
+            assert rel(c64.matvec(m, x)[0], ref) < 1e-5
+
+
+# ------------------------------------------------------------------ benchmark workload, sampled rows
+
+def test_matvec_full_size_sampled():
+    """7680-RWG sphere on the 64^3 grid (complex64): sampled output rows against
+    direct grid sums and the oracle's near-zone entries for those rows."""
+    w = make_workload("sphere7680")
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((1, rwg.ns)) + 1j * rng.standard_normal((1, rwg.ns))
+    rows = np.sort(rng.choice(rwg.ns, 12, replace=False))
+    with ctx_for(w) as c:
+        assert c.n_delays == A.n_delays
+        for m in (0, 1):
+            y = c.matvec(m, x)[0]
+            ref = A.fft_part_rows(m, x[0], rows)
+            sel = np.isin(A.pairs[:, 0], rows)
+            pr = A.pairs[sel]
+            Zn = efie.fill_pairs(rwg, p, pr, m)[m] - A.fft_pairs(m, pr)
+            near = np.zeros(len(rows), dtype=complex)
+            for (k, kp), z in zip(pr, Zn):
+                near[np.searchsorted(rows, k)] += z * x[0, kp]
+            ref = ref + near
+            assert rel(y[rows], ref) < 1e-5, m
