@@ -103,14 +103,15 @@ class AimOracle:
     # ------------------------------------------------------------------ kernels
     def _n_delays_grid(self):
         """N_g = floor(R_max/(c dt) + Q), R_max the largest distance between two
-        stencil nodes (a reading of the N_g formula after Eq. 4)."""
-        ijk = self.node_ijk(self.active)
-        best = 0
+        stencil nodes (a reading of the N_g formula after Eq. 4).  The squared
+        integer distances |a|^2 + |b|^2 - 2 a.b are exact in FP64 for these grids."""
+        ijk = self.node_ijk(self.active).astype(np.float64)
+        sq = (ijk * ijk).sum(1)
+        best = 0.0
         for i in range(0, len(ijk), 4096):
-            d = ijk[i:i + 4096, None, :] - ijk[None, :, :]
-            d2 = d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1] + d[..., 2] * d[..., 2]
-            best = max(best, int(d2.max()))
-        rmax = self.h * math.sqrt(best)
+            d2 = sq[i:i + 4096, None] + sq[None, :] - 2.0 * (ijk[i:i + 4096] @ ijk.T)
+            best = max(best, float(d2.max()))
+        rmax = self.h * math.sqrt(int(round(best)))
         return int(math.floor(rmax / self.p.cdt + self.p.Q))
 
     def kernel_values(self, m: int, dijk: np.ndarray):
