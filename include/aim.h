@@ -184,6 +184,25 @@ int aim_rwg_table(const aim_ctx* ctx, int32_t* edge, int32_t* tri, int32_t* free
 int aim_matvec(aim_ctx* ctx, int32_t delay_m, int32_t nb, const aim_c128* x, aim_c128* y);
 
 /*
+ * aim_matvec_noalloc -- the same product as aim_matvec, for callers that must not
+ * allocate device memory while they run (a solver being captured into a CUDA graph,
+ * a real-time or certified path whose memory is fixed at start-up, an application
+ * whose device memory belongs to another allocator).  The paper has no counterpart:
+ * this is a library convenience.
+ *   Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).  The
+ *   grid work space comes from one fixed 16 MiB device array in the library, held by
+ *   every GPU that loads it until process exit; the context's other tables are used
+ *   as set up by aim_setup.  nb * 4 * (N*N*2N + N*2N*2N + N^3) elements (complex64 or
+ *   complex128 by precision) must fit in 16 MiB, else AIM_ERR_ARG (e.g. N <= 32 in
+ *   complex64 for one right-hand side).  The first call on a device looks up the
+ *   array's device address (cudaGetSymbolAddress) with that device current; make that
+ *   first call before any stream capture.  All calls share the array, so calls whose
+ *   work overlaps on the GPU (two streams, two contexts) race; nothing in it needs to
+ *   start at zero.  x, y: [nb][ns] aim_c128, host or device, not overlapping.
+ */
+int aim_matvec_noalloc(aim_ctx* ctx, int32_t delay_m, int32_t nb, const aim_c128* x, aim_c128* y);
+
+/*
  * aim_rhs -- the delayed-interaction sum of Eq. 5 at step l:
  *   rhs = sum_{m=1..N_g, l-m >= 1} Z~AIM_m I_{l-m}.
  *   hist: [N_g][nb][ns] with hist[m-1] = I_{l-m} (entries with l - m < 1 are

@@ -66,7 +66,8 @@ class aim_info(ct.Structure):
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
            "aim_matvec", "aim_rhs", "aim_excitation_vector", "aim_march", "aim_march_continue", "aim_get_anterp",
-           "aim_get_near", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name"]
+           "aim_get_near", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
+           "aim_matvec_noalloc"]
 AIM_K_COUNT = 11
 
 _LIB = None
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
         "aim_rwg_table": (ct.c_int, [P, P, P, P]),
         "aim_matvec": (ct.c_int, [P, I32, I32, P, P]),
         "aim_rhs": (ct.c_int, [P, I32, I32, P, P]),
+        "aim_matvec_noalloc": (ct.c_int, [P, I32, I32, P, P]),
         "aim_excitation_vector": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, P]),
         "aim_march": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, D, P, ct.POINTER(aim_stats)]),
         "aim_march_continue": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, D, P, ct.POINTER(aim_stats)]),
@@ -205,6 +207,14 @@ def aim_matvec(ctx, m, x, out=None):
     lib = load()
     y = _like(x, tuple(x.shape)) if out is None else out
     _check(lib, ctx, lib.aim_matvec(ctx, int(m), int(x.shape[0]), _ptr(x), _ptr(y)), "aim_matvec")
+    return y
+
+
+def aim_matvec_noalloc(ctx, m, x, out=None):
+    """aim_matvec with the grid work space in the library's fixed device array."""
+    lib = load()
+    y = _like(x, tuple(x.shape)) if out is None else out
+    _check(lib, ctx, lib.aim_matvec_noalloc(ctx, int(m), int(x.shape[0]), _ptr(x), _ptr(y)), "aim_matvec_noalloc")
     return y
 
 
