@@ -54,23 +54,34 @@ struct GmresState {
   double2* y = nullptr;      // [B][64]
   double2* h1 = nullptr;     // [B][64] first CGS pass
   double2* h2 = nullptr;     // [B][64] second CGS pass
-  double* hn = nullptr;      // [B] ||w||
+  double* sig = nullptr;     // [B][64] scales of the stored Krylov vectors
   double* bn = nullptr;      // [B] ||b||
-  double* rn = nullptr;      // [B] ||r||
-  double* scale = nullptr;   // [B]
   double* relres = nullptr;  // [B]
   int* act = nullptr;        // [B] taking Arnoldi steps
   int* done = nullptr;       // [B] 1 converged, 2 iteration cap
   int* jc = nullptr;         // [B] columns in the current cycle
   int* its = nullptr;        // [B] iterations of this solve
-  int* flag = nullptr;       // any active
-  double2* pc = nullptr;     // reduction partials
-  double* pr = nullptr;
-  unsigned* counter = nullptr;
+  int* jdev = nullptr;       // current Arnoldi column (shared by the batch)
+  int* flag = nullptr;       // [2] any active at cycle start / after a step
+  int* cnt = nullptr;        // [2] cycles and Arnoldi steps executed (launch accounting)
+  double2* pd = nullptr;     // multi-dot partials [B][64][S]
+  double* pu = nullptr;      // |w|^2 partials [B][U]
+  double* pr = nullptr;      // |r|^2 partials [B][P]
+  double* pbn = nullptr;     // |b|^2 partials [B][P]
+  double* nrm = nullptr;     // [B] norms for the march's growth check
   int* h_flag = nullptr;     // pinned host mirrors
   int* h_its = nullptr;
   double* h_res = nullptr;
   int* h_done = nullptr;
+  int* h_cnt = nullptr;
+  // captured solve (one graph with conditional loops), rebuilt when its inputs change
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int g_nb = 0;
+  double g_tol = 0;
+  const void* g_b = nullptr;
+  const void* g_x = nullptr;
+  bool graph_failed = false;
 };
 
 // per-kernel event timing (aim_profile / aim_get_profile); ids match AIM_K_* in aim.h
@@ -159,6 +170,8 @@ struct aim_ctx {
   GmresState gs;
   ProfState prof;
   int l_done = 0, march_nb = 0;   // march state for aim_march_continue
+  bool use_graphs = true;
+  std::string graph_error;
   std::vector<void*> allocs;
 };
 

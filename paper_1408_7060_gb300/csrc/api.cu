@@ -1,6 +1,7 @@
 // extern "C" entry points of the ET-AIM library (declared in include/aim.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -77,6 +78,10 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->batch_max = opts->batch_max;
   c->restart = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 63) : 50;
   c->max_iter = opts->gmres_max_iter > 0 ? opts->gmres_max_iter : 500;
+  {
+    const char* e = std::getenv("AIM_GB300_GRAPHS");  // "0": drive the solver from the host
+    c->use_graphs = !(e && e[0] == '0');
+  }
   if (opts->cuda_stream) {
     c->stream = (cudaStream_t)opts->cuda_stream;
   } else {
@@ -134,7 +139,21 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_hist = (double2*)aim_alloc(c, (size_t)ng * vec);
   c->d_exc = (double*)aim_alloc(c, (size_t)B * 6 * sizeof(double));
   gmres_alloc(c);
+  // run every operator kernel once outside any stream capture: sets the shared-memory
+  // attributes of each instantiation and surfaces launch errors at setup
+  AIM_CUDA(cudaMemsetAsync(c->d_x, 0, vec, c->stream));
+  op_apply(c, 0, 1, c->d_x, nullptr, nullptr, 1.0, nullptr, c->d_y);
+  op_forward_slab(c, 1, c->d_x, c->d_ring);
+  {
+    SlabList sl{};
+    sl.p[0] = c->d_ring;
+    sl.m[0] = 1;
+    sl.n = 1;
+    NearList nl{};
+    op_apply_rhs(c, 1, sl, nl, nullptr, 1.0, c->d_y);
+  }
   AIM_CUDA(cudaStreamSynchronize(c->stream));
+  c->prof = ProfState();
 }
 
 // copy a caller array to device staging if it is a host pointer
@@ -452,7 +471,7 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
   for (auto& e : ev) AIM_CUDA(cudaEventCreate(&e));
   std::vector<int> its(nb);
   std::vector<double> res(nb), norms;
-  double* d_nrm = c->gs.rn;  // reused after each solve
+  double* d_nrm = c->gs.nrm;
   std::vector<double> h_nrm(nb);
   if (stats) {
     stats->last_step = 0;

@@ -141,3 +141,126 @@ __device__ __forceinline__ C* block_fft(C* a, C* b, int nl, int es, int ls, cons
   static_assert(plan_len(L) > 0, "unsupported FFT length");
   return fft_passes<L, 0, 1, INV, LF, C>(a, b, nl, es, ls, tw);
 }
+
+// ---------------------------------------------------------------- radix-16 in registers
+// 16 = 4 x 4: four DFT4 over stride-4 samples, twiddles W_16^{n2 k1}, four DFT4 across.
+template <bool INV, class C> struct DFT<16, INV, C> {
+  __device__ __forceinline__ static C w16(C a, int q) {  // a * W_16^q (forward) or conj
+    using Rl = decltype(a.x);
+    const Rl c1 = (Rl)0.92387953251128675613, s1 = (Rl)0.38268343236508977173, h = (Rl)0.70710678118654752440;
+    Rl c, s;  // W_16^q = c - i s
+    switch (q) {
+      case 0: return a;
+      case 1: c = c1; s = s1; break;
+      case 2: c = h; s = h; break;
+      case 3: c = s1; s = c1; break;
+      case 4: c = 0; s = 1; break;
+      case 6: c = -h; s = h; break;
+      case 9: c = -c1; s = -s1; break;
+      default: c = 0; s = 0; break;
+    }
+    if (INV) s = -s;
+    return mkc(a.x * c + a.y * s, a.y * c - a.x * s);
+  }
+  __device__ __forceinline__ static void run(C* v) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // now v[4 k1 + n2] holds y[k1][n2]; twiddle then DFT4 over n2
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+      for (int n2 = 1; n2 < 4; ++n2) v[4 * k1 + n2] = w16(v[4 * k1 + n2], k1 * n2);
+    C t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C a0 = v[4 * k1], a1 = v[4 * k1 + 1], a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
+      dft4<INV>(a0, a1, a2, a3);
+      t[k1] = a0;
+      t[k1 + 4] = a1;
+      t[k1 + 8] = a2;
+      t[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = t[q];
+  }
+};
+
+// ---------------------------------------------------------------- two-step transform
+// For L = R1 R2 (powers of two): with n = R2 n1 + n2 and k = k1 + R1 k2,
+//   X[k1 + R1 k2] = sum_{n2} W_{R2}^{n2 k2} W_L^{n2 k1} sum_{n1} x[R2 n1 + n2] W_{R1}^{n1 k1}.
+// Step A: one radix-R1 DFT per (line, n2) and the twiddles W_L^{n2 k1};
+// step B: one radix-R2 DFT per (line, k1).  Each step reads and writes shared memory once.
+__host__ __device__ constexpr bool pow2_len(int L) { return L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512; }
+__host__ __device__ constexpr int split_r1(int L) {
+  return L == 16 ? 4 : L == 32 ? 8 : L == 64 ? 8 : L == 128 ? 8 : L == 256 ? 16 : L == 512 ? 16 : 0;
+}
+
+// Column tile: W lines, element i of line l at a[i*W + l].  Result in natural order in a.
+template <int L, bool INV, class C>
+__device__ __forceinline__ void col_fft2(C* a, C* tmp, int W, const C* __restrict__ tw) {
+  constexpr int R1 = split_r1(L), R2 = L / R1;
+  for (int u = threadIdx.x; u < W * R2; u += blockDim.x) {
+    const int l = u % W, n2 = u / W;
+    C v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = a[(R2 * n1 + n2) * W + l];
+    DFT<R1, INV, C>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C x = v[k1];
+      if (k1 && n2) {
+        C w = tw[n2 * k1];
+        x = x * (INV ? conjc(w) : w);
+      }
+      tmp[(k1 * R2 + n2) * W + l] = x;
+    }
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < W * R1; u += blockDim.x) {
+    const int l = u % W, k1 = u / W;
+    C v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = tmp[(k1 * R2 + n2) * W + l];
+    DFT<R2, INV, C>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) a[(k1 + R1 * k2) * W + l] = v[k2];
+  }
+  __syncthreads();
+}
+
+// Row tile: nl lines, element n of line r at a[r*L + n]; tmp holds nl * R1 * (R2 + 1)
+// elements (one padding slot per k1 row against bank conflicts).  Result in a.
+template <int L> __host__ __device__ constexpr int row_tmp_pitch() {
+  return split_r1(L) * (L / split_r1(L) + 1);
+}
+template <int L, bool INV, class C>
+__device__ __forceinline__ void row_fft2(C* a, C* tmp, int nl, const C* __restrict__ tw) {
+  constexpr int R1 = split_r1(L), R2 = L / R1, P = row_tmp_pitch<L>();
+  for (int u = threadIdx.x; u < nl * R2; u += blockDim.x) {
+    const int n2 = u % R2, r = u / R2;
+    C v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = a[r * L + R2 * n1 + n2];
+    DFT<R1, INV, C>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C x = v[k1];
+      if (k1 && n2) {
+        C w = tw[n2 * k1];
+        x = x * (INV ? conjc(w) : w);
+      }
+      tmp[r * P + k1 * (R2 + 1) + n2] = x;
+    }
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < nl * R1; u += blockDim.x) {
+    const int k1 = u % R1, r = u / R1;
+    C v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = tmp[r * P + k1 * (R2 + 1) + n2];
+    DFT<R2, INV, C>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) a[r * L + k1 + R1 * k2] = v[k2];
+  }
+  __syncthreads();
+}

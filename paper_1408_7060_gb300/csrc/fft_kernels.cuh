@@ -16,6 +16,33 @@ __device__ __forceinline__ void load_twiddles(C* tw, const C* __restrict__ twg, 
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = twg[i];
 }
 
+// Transform the lines of a tile (after a __syncthreads that publishes a); returns
+// the buffer holding the natural-order result.  Power-of-two lengths use the
+// two-step transform, lengths with a factor 3 the Stockham passes.
+template <int L, bool INV, class C>
+__device__ __forceinline__ C* line_fft_cols(C* a, C* b, int W, const C* tw) {
+  if constexpr (pow2_len(L)) {
+    col_fft2<L, INV, C>(a, b, W, tw);
+    return a;
+  } else {
+    return block_fft<L, INV, true, C>(a, b, W, W, 1, tw);
+  }
+}
+template <int L, bool INV, class C>
+__device__ __forceinline__ C* line_fft_rows(C* a, C* b, int nl, const C* tw) {
+  if constexpr (pow2_len(L)) {
+    row_fft2<L, INV, C>(a, b, nl, tw);
+    return a;
+  } else {
+    return block_fft<L, INV, false, C>(a, b, nl, 1, L, tw);
+  }
+}
+// scratch elements a row tile of nl lines needs beside the tile itself
+template <int L>
+__host__ __device__ constexpr int row_scratch(int nl) {
+  return pow2_len(L) ? nl * row_tmp_pitch<L>() : nl * L;
+}
+
 template <int L, bool INV, class C>
 __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __restrict__ out, int nrows,
                                               int n_in, int n_out, long long rs_in, long long rs_out,
@@ -25,6 +52,7 @@ __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __res
   C* b1 = b0 + rpb * L;
   load_twiddles(tw, twg, L);
   const int r0 = blockIdx.x * rpb;
+  (void)b1;
   const int nr = min(rpb, nrows - r0);
   for (int t = threadIdx.x; t < rpb * L; t += blockDim.x) {
     int rr = t / L, i = t % L;
@@ -33,7 +61,7 @@ __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __res
     b0[t] = v;
   }
   __syncthreads();
-  C* res = block_fft<L, INV, false, C>(b0, b1, rpb, 1, L, tw);
+  C* res = line_fft_rows<L, INV, C>(b0, b1, rpb, tw);
   for (int t = threadIdx.x; t < rpb * L; t += blockDim.x) {
     int rr = t / L, i = t % L;
     if (rr < nr && i < n_out) out[(long long)(r0 + rr) * rs_out + i] = res[t];
@@ -60,7 +88,7 @@ __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __res
     b0[t] = v;
   }
   __syncthreads();
-  C* res = block_fft<L, INV, true, C>(b0, b1, W, W, 1, tw);
+  C* res = line_fft_cols<L, INV, C>(b0, b1, W, tw);
   for (int t = threadIdx.x; t < n_out * W; t += blockDim.x) {
     int i = t / W, l = t % W;
     if (l < nw) dst[i * es_out + l] = res[t];

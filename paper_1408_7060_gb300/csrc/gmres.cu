@@ -2,11 +2,18 @@
 // system of Eq. 5 (Sec. 5.1: diagonally preconditioned GMRES, warm start from the
 // previous step).  Krylov basis, Hessenberg matrix, Givens rotations and residuals
 // are FP64; the operator is the ET-AIM matvec in the context's precision.
-// Orthogonalisation is classical Gram-Schmidt applied twice (CGS2), so each
-// Arnoldi step needs two multi-vector reductions instead of j sequential ones.
-// Every reduction is two-stage with a fixed summation order (bitwise reproducible).
+//
+// Layout: the Krylov vectors are stored unnormalised, v_i = sig_i * vt_i, with the
+// scales sig [B][64] kept beside the Hessenberg matrix.  The operator reads vt_j
+// (times sig_j and the preconditioner) and writes A v_j straight into slot j+1, which
+// classical Gram-Schmidt applied twice (CGS2) then orthogonalises in place -- no
+// copies, no normalisation pass.  Reductions are two-stage with a fixed summation
+// order (bitwise reproducible).  The column index j lives in device memory, so a
+// whole solve is one CUDA graph: an outer conditional WHILE over restart cycles and
+// an inner one over Arnoldi steps; kernels set the loop conditions.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <vector>
 
 #include "aim_internal.h"
@@ -16,6 +23,9 @@
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kDotChunk = 2048;  // elements per multi-dot block
+constexpr int kUpdN = 32;        // elements per update block (x 8 column groups)
+constexpr int kNormChunk = 256;  // elements per norm-partial block
 
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
@@ -24,279 +34,498 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// h[b][i] = sum_n conj(V_i[b][n]) w[b][n], i < J.  grid (nblk, nb).
-__global__ void k_dots(const double2* __restrict__ V, size_t vstride, int J, const double2* __restrict__ w, int ns,
-                       int nb, const int* __restrict__ act, double2* __restrict__ partial, unsigned* __restrict__ counter,
-                       double2* __restrict__ h) {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// raw partial dots pd[b][i][s] = sum_{n in chunk s} conj(vt_i[n]) w[n], w = slot j+1.
+// grid (64, S, nb); blocks with i > j return at once.
+__global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V, long long vstride,
+                                                   const int* __restrict__ jdev, int ns,
+                                                   const int* __restrict__ act, double2* __restrict__ pd) {
+  const int i = blockIdx.x, s = blockIdx.y, b = blockIdx.z;
+  const int j = *jdev;
+  if (i > j || !act[b]) return;
+  const double2* vi = V + i * vstride + (size_t)b * ns;
+  const double2* w = V + (j + 1) * vstride + (size_t)b * ns;
+  double re = 0, im = 0;
+  const int n1 = min(ns, (s + 1) * kDotChunk);
+  for (int n = s * kDotChunk + threadIdx.x; n < n1; n += kThreads) {
+    double2 p = cmulc(vi[n], w[n]);
+    re += p.x;
+    im += p.y;
+  }
+  __shared__ double red[2][kThreads / 32];
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = re;
+    red[1][threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int q = 0; q < kThreads / 32; ++q) {
+      a += red[0][q];
+      c += red[1][q];
+    }
+    pd[((size_t)b * 64 + i) * gridDim.y + s] = make_double2(a, c);
+  }
+}
+
+// Gram-Schmidt update of slot j+1: h_i = sig_i sum_s pd[b][i][s] (coefficients in the
+// normalised basis, written by block 0 to h), w -= sum_i vt_i (sig_i h_i); the block
+// also writes the partial sum of |w|^2 of its 32 elements to pn[b][blk].
+// grid (ceil(ns/32), nb), block (32, 8).
+__global__ void __launch_bounds__(kThreads) k_mupdate(double2* __restrict__ V, long long vstride,
+                                                      const int* __restrict__ jdev, int ns, int S,
+                                                      const int* __restrict__ act, const double* __restrict__ sig,
+                                                      const double2* __restrict__ pd, double2* __restrict__ h,
+                                                      double* __restrict__ pn) {
   const int b = blockIdx.y;
   if (!act[b]) return;
-  __shared__ double2 red[64][kThreads / 32];
-  __shared__ bool last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double2* wb = w + (size_t)b * ns;
-  for (int i = 0; i < J; ++i) {
-    const double2* vb = V + i * vstride + (size_t)b * ns;
-    double2 acc = make_double2(0, 0);
-    for (int n = blockIdx.x * kThreads + threadIdx.x; n < ns; n += gridDim.x * kThreads) {
-      double2 p = cmulc(vb[n], wb[n]);
+  const int j = *jdev, J = j + 1;
+  __shared__ double2 coef[64];
+  __shared__ double2 red[8][kUpdN];
+  const int tid = threadIdx.y * kUpdN + threadIdx.x;
+  if (tid < J) {
+    double2 t = make_double2(0, 0);
+    for (int q = 0; q < S; ++q) {
+      double2 v = pd[((size_t)b * 64 + tid) * S + q];
+      t.x += v.x;
+      t.y += v.y;
+    }
+    const double sg = sig[b * 64 + tid];
+    t = make_double2(sg * t.x, sg * t.y);  // h_i
+    if (blockIdx.x == 0) h[b * 64 + tid] = t;
+    coef[tid] = make_double2(sg * t.x, sg * t.y);  // sig_i h_i multiplies vt_i
+  }
+  __syncthreads();
+  const int n = blockIdx.x * kUpdN + threadIdx.x;
+  double2 acc = make_double2(0, 0);
+  if (n < ns) {
+    for (int i = threadIdx.y; i < J; i += 8) {
+      double2 p = cmul(V[i * vstride + (size_t)b * ns + n], coef[i]);
       acc.x += p.x;
       acc.y += p.y;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (lane == 0) red[i][warp] = acc;
   }
+  red[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
-  double2* pb = partial + ((size_t)b * gridDim.x + blockIdx.x) * 64;
-  if (threadIdx.x < J) {
-    double2 s = make_double2(0, 0);
-    for (int q = 0; q < kThreads / 32; ++q) {
-      s.x += red[threadIdx.x][q].x;
-      s.y += red[threadIdx.x][q].y;
-    }
-    pb[threadIdx.x] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&counter[b], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (last) {
-    if (threadIdx.x < J) {
-      double2 s = make_double2(0, 0);
-      for (int q = 0; q < (int)gridDim.x; ++q) {
-        double2 v = __ldcg(&partial[((size_t)b * gridDim.x + q) * 64 + threadIdx.x]);
-        s.x += v.x;
-        s.y += v.y;
+  if (threadIdx.y == 0) {
+    double nrm = 0;
+    if (n < ns) {
+      double2 t = make_double2(0, 0);
+      for (int q = 0; q < 8; ++q) {
+        t.x += red[q][threadIdx.x].x;
+        t.y += red[q][threadIdx.x].y;
       }
-      h[(size_t)b * 64 + threadIdx.x] = s;
+      double2* w = V + (J)*vstride + (size_t)b * ns + n;
+      double2 wv = *w;
+      wv = make_double2(wv.x - t.x, wv.y - t.y);
+      *w = wv;
+      nrm = wv.x * wv.x + wv.y * wv.y;
     }
-    if (threadIdx.x == 0) counter[b] = 0;
+    nrm = warp_sum(nrm);
+    if (threadIdx.x == 0) pn[(size_t)b * gridDim.x + blockIdx.x] = nrm;
   }
 }
 
-// w -= sum_{i<J} V_i h_i ; optionally ||w||^2 -> nrm[b] (two-stage).  grid (nblk, nb).
-__global__ void k_update(const double2* __restrict__ V, size_t vstride, int J, const double2* __restrict__ h,
-                         double2* __restrict__ w, int ns, const int* __restrict__ act, bool want_norm,
-                         double* __restrict__ partial, unsigned* __restrict__ counter, double* __restrict__ nrm) {
+// partial sums of |v_b|^2 over chunks of kNormChunk: grid (P, nb)
+__global__ void __launch_bounds__(kThreads) k_normpart(const double2* __restrict__ v, int ns,
+                                                       double* __restrict__ pn) {
   const int b = blockIdx.y;
-  if (!act[b]) return;
-  __shared__ double hs[2 * 64];
+  const int n = blockIdx.x * kNormChunk + threadIdx.x;
+  double a = 0;
+  if (n < ns) {
+    double2 x = v[(size_t)b * ns + n];
+    a = x.x * x.x + x.y * x.y;
+  }
   __shared__ double red[kThreads / 32];
-  __shared__ bool last;
-  for (int i = threadIdx.x; i < J; i += kThreads) {
-    hs[2 * i] = h[(size_t)b * 64 + i].x;
-    hs[2 * i + 1] = h[(size_t)b * 64 + i].y;
-  }
-  __syncthreads();
-  double acc = 0;
-  double2* wb = w + (size_t)b * ns;
-  for (int n = blockIdx.x * kThreads + threadIdx.x; n < ns; n += gridDim.x * kThreads) {
-    double2 s = wb[n];
-    for (int i = 0; i < J; ++i) {
-      double2 v = V[i * vstride + (size_t)b * ns + n];
-      double2 p = cmul(v, make_double2(hs[2 * i], hs[2 * i + 1]));
-      s.x -= p.x;
-      s.y -= p.y;
-    }
-    wb[n] = s;
-    acc += s.x * s.x + s.y * s.y;
-  }
-  if (!want_norm) return;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0;
     for (int q = 0; q < kThreads / 32; ++q) s += red[q];
-    partial[(size_t)b * gridDim.x + blockIdx.x] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&counter[b], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    double s = 0;
-    for (int q = 0; q < (int)gridDim.x; ++q) s += __ldcg(&partial[(size_t)b * gridDim.x + q]);
-    nrm[b] = sqrt(s);
-    counter[b] = 0;
+    pn[(size_t)b * gridDim.x + blockIdx.x] = s;
   }
 }
 
-// ||v_b|| for every b (two-stage).  grid (nblk, nb).
-__global__ void k_norms(const double2* __restrict__ v, int ns, double* __restrict__ partial,
-                        unsigned* __restrict__ counter, double* __restrict__ nrm) {
-  const int b = blockIdx.y;
-  __shared__ double red[kThreads / 32];
-  __shared__ bool last;
-  double acc = 0;
-  const double2* vb = v + (size_t)b * ns;
-  for (int n = blockIdx.x * kThreads + threadIdx.x; n < ns; n += gridDim.x * kThreads) {
-    double2 s = vb[n];
-    acc += s.x * s.x + s.y * s.y;
+// sum of P partials of row b by one warp in a fixed order
+__device__ __forceinline__ double warp_row_sum(const double* __restrict__ p, int P) {
+  const int lane = threadIdx.x & 31;
+  double s = 0;
+  for (int q = lane; q < P; q += 32) s += p[q];
+  return warp_sum(s);
+}
+
+struct CycleArgs {
+  int nb, restart, max_iter;
+  double tol;
+  const double* pb;   // partials of |b|^2   [nb][Pn]
+  const double* pr;   // partials of |r|^2   [nb][Pn]
+  int Pn;
+  int use_cond;
+  cudaGraphConditionalHandle outer, inner;
+};
+
+// cycle start: beta = |r| (explicit residual in slot 0), sig_0 = 1/beta, g = (beta, 0..),
+// activity, j = 0, and both loop conditions.  One block, one warp per right-hand side.
+__global__ void __launch_bounds__(kThreads) k_cycle_start(CycleArgs a, GmresState s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int b = warp; b < a.nb; b += nw) {
+    const double bn = sqrt(warp_row_sum(a.pb + (size_t)b * a.Pn, a.Pn));
+    const double beta = sqrt(warp_row_sum(a.pr + (size_t)b * a.Pn, a.Pn));
+    if (lane == 0) {
+      s.bn[b] = bn;
+      s.relres[b] = bn > 0 ? beta / bn : 0.0;
+      const bool conv = !(bn > 0) || beta <= a.tol * bn;
+      const bool cap = s.its[b] >= a.max_iter;
+      s.done[b] = conv ? 1 : (cap ? 2 : 0);
+      s.act[b] = s.done[b] == 0;
+      s.jc[b] = 0;
+      s.sig[b * 64] = beta > 0 ? 1.0 / beta : 0.0;
+      s.g[b * 64] = make_double2(beta, 0.0);
+      if (s.act[b]) atomicOr(&any, 1);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0;
-    for (int q = 0; q < kThreads / 32; ++q) s += red[q];
-    partial[(size_t)b * gridDim.x + blockIdx.x] = s;
+    *s.jdev = 0;
+    s.cnt[0] += 1;
+    s.flag[0] = any;
+    s.flag[1] = any;
+    if (a.use_cond) {
+      cudaGraphSetConditional(a.outer, any ? 1u : 0u);
+      cudaGraphSetConditional(a.inner, any ? 1u : 0u);
+    }
   }
-  __threadfence();
+}
+
+struct FinishArgs {
+  int nb, restart, max_iter;
+  double tol;
+  const double* pn;   // |w|^2 partials after the second update [nb][Pu]
+  int Pu;
+  int use_cond;
+  cudaGraphConditionalHandle inner;
+};
+
+// Arnoldi column j for every active RHS: H[0..j][j] = h1 + h2, H[j+1][j] = |w|,
+// previous rotations, a new complex Givens rotation, |g_{j+1}|, convergence / cap,
+// sig_{j+1} = 1/|w|; then j += 1 and the inner loop condition.  One warp per RHS:
+// the lanes stage the column and the rotations in shared memory, lane 0 applies the
+// rotations in order, the lanes write the column back.
+__global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int j = *s.jdev;
+  __shared__ int any;
+  __shared__ double2 col[kThreads / 32][65];
+  __shared__ double2 rsn[kThreads / 32][64];
+  __shared__ double rcs[kThreads / 32][64];
+  if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&counter[b], 1u) == gridDim.x - 1;
+  for (int b = warp; b < a.nb; b += nw) {
+    if (!s.act[b]) continue;
+    const double hn = sqrt(warp_row_sum(a.pn + (size_t)b * a.Pu, a.Pu));
+    for (int i = lane; i <= j; i += 32) {
+      const double2 x = s.h1[b * 64 + i], y = s.h2[b * 64 + i];
+      col[warp][i] = make_double2(x.x + y.x, x.y + y.y);
+      if (i < j) {
+        rcs[warp][i] = s.cs[b * 64 + i];
+        rsn[warp][i] = s.sn[b * 64 + i];
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      for (int i = 0; i < j; ++i) {  // G_i acts on rows (i, i+1)
+        const double c = rcs[warp][i];
+        const double2 sn = rsn[warp][i];
+        const double2 p = col[warp][i], q = col[warp][i + 1];
+        const double2 sq = cmul(sn, q);
+        const double2 csp = make_double2(sn.x * p.x + sn.y * p.y, sn.x * p.y - sn.y * p.x);  // conj(sn) p
+        col[warp][i] = make_double2(c * p.x + sq.x, c * p.y + sq.y);
+        col[warp][i + 1] = make_double2(c * q.x - csp.x, c * q.y - csp.y);
+      }
+      const double2 p = col[warp][j];
+      const double na = sqrt(p.x * p.x + p.y * p.y);
+      const double nd = hn;
+      const double r = sqrt(na * na + nd * nd);
+      double c;
+      double2 sn;
+      if (r == 0.0) {
+        c = 1.0;
+        sn = make_double2(0, 0);
+      } else if (na == 0.0) {
+        c = 0.0;
+        sn = make_double2(1.0, 0.0);
+      } else {
+        c = na / r;
+        sn = make_double2(p.x / na * (nd / r), p.y / na * (nd / r));  // (p/|p|) conj(hn)/r, hn real
+      }
+      s.cs[b * 64 + j] = c;
+      s.sn[b * 64 + j] = sn;
+      col[warp][j] = make_double2(c * p.x + sn.x * nd, c * p.y + sn.y * nd);
+      const double2 gj = s.g[b * 64 + j];
+      s.g[b * 64 + j] = make_double2(c * gj.x, c * gj.y);
+      const double2 gn = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(sn) g_j
+      s.g[b * 64 + j + 1] = gn;
+      const double res = sqrt(gn.x * gn.x + gn.y * gn.y);
+      s.relres[b] = res / s.bn[b];
+      s.jc[b] = j + 1;
+      s.its[b] += 1;
+      s.sig[b * 64 + j + 1] = hn > 0 ? 1.0 / hn : 0.0;
+      const bool stop = res <= a.tol * s.bn[b] || !(hn > 0) || s.its[b] >= a.max_iter || j + 1 >= a.restart;
+      if (stop)
+        s.act[b] = 0;
+      else
+        atomicOr(&any, 1);
+    }
+    __syncwarp();
+    double2* H = s.H + (size_t)b * 64 * 64;  // H[i][j] at i*64 + j
+    for (int i = lane; i <= j; i += 32) H[i * 64 + j] = col[warp][i];
+  }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    double s = 0;
-    for (int q = 0; q < (int)gridDim.x; ++q) s += __ldcg(&partial[(size_t)b * gridDim.x + q]);
-    nrm[b] = sqrt(s);
-    counter[b] = 0;
+  if (threadIdx.x == 0) {
+    *s.jdev = j + 1;
+    s.cnt[1] += 1;
+    s.flag[1] = any;
+    if (a.use_cond) cudaGraphSetConditional(a.inner, any ? 1u : 0u);
   }
 }
 
-// start of a cycle: beta = ||r||, V_0 = r/beta, g = (beta, 0, ...), activity from the
-// explicit residual.  One thread per b (small state only); scaling in k_scale.
-__global__ void k_cycle_start(int nb, int restart, double tol, int max_iter, const double* __restrict__ rn,
-                              const double* __restrict__ bn, GmresState s) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  const double beta = rn[b];
-  s.relres[b] = bn[b] > 0 ? beta / bn[b] : 0.0;
-  const bool conv = !(bn[b] > 0) || beta <= tol * bn[b];
-  const bool cap = s.its[b] >= max_iter;
-  s.done[b] = conv ? 1 : (cap ? 2 : 0);
-  s.act[b] = s.done[b] == 0;
-  s.jc[b] = 0;
-  s.scale[b] = beta > 0 ? 1.0 / beta : 0.0;
-  for (int i = 0; i <= restart; ++i) s.g[(size_t)b * 64 + i] = make_double2(i == 0 ? beta : 0.0, 0.0);
-}
-
-// v_out[b] = v_in[b] * scale[b] for active b.  grid (nblk, nb).
-__global__ void k_scale(const double2* __restrict__ in, double2* __restrict__ out, int ns,
-                        const int* __restrict__ act, const double* __restrict__ scale) {
-  const int b = blockIdx.y;
-  if (!act[b]) return;
-  const double sc = scale[b];
-  for (int n = blockIdx.x * kThreads + threadIdx.x; n < ns; n += gridDim.x * kThreads) {
-    double2 v = in[(size_t)b * ns + n];
-    out[(size_t)b * ns + n] = make_double2(sc * v.x, sc * v.y);
-  }
-}
-
-// Arnoldi column j: H[0..j][j] = h1 + h2, H[j+1][j] = ||w||; previous rotations,
-// a new complex Givens rotation, residual estimate |g_{j+1}|, convergence / cap.
-__global__ void k_arnoldi_finish(int nb, int j, int restart, double tol, int max_iter, const double2* __restrict__ h1,
-                                 const double2* __restrict__ h2, const double* __restrict__ hn,
-                                 const double* __restrict__ bn, GmresState s) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb || !s.act[b]) return;
-  double2* H = s.H + (size_t)b * 64 * 64;  // H[i][j] at i*64 + j
-  double2 col[65];
-  for (int i = 0; i <= j; ++i) {
-    double2 a = h1[(size_t)b * 64 + i], c = h2[(size_t)b * 64 + i];
-    col[i] = make_double2(a.x + c.x, a.y + c.y);
-  }
-  col[j + 1] = make_double2(hn[b], 0.0);
-  for (int i = 0; i < j; ++i) {  // apply G_i: [c s; -conj(s) c]
-    double c = s.cs[(size_t)b * 64 + i];
-    double2 sn = s.sn[(size_t)b * 64 + i];
-    double2 a = col[i], d = col[i + 1];
-    double2 sd = cmul(sn, d);
-    double2 csa = make_double2(sn.x * a.x + sn.y * a.y, sn.x * a.y - sn.y * a.x);  // conj(sn) a
-    col[i] = make_double2(c * a.x + sd.x, c * a.y + sd.y);
-    col[i + 1] = make_double2(c * d.x - csa.x, c * d.y - csa.y);
-  }
-  double2 a = col[j], d = col[j + 1];
-  double na = sqrt(a.x * a.x + a.y * a.y), nd = sqrt(d.x * d.x + d.y * d.y);
-  double r = sqrt(na * na + nd * nd);
-  double c;
-  double2 sn;
-  if (r == 0.0) {
-    c = 1.0;
-    sn = make_double2(0, 0);
-  } else if (na == 0.0) {
-    c = 0.0;
-    sn = make_double2(d.x / nd, -d.y / nd);
-  } else {
-    c = na / r;
-    double2 ph = make_double2(a.x / na, a.y / na);
-    sn = cmul(ph, make_double2(d.x / r, -d.y / r));  // (a/|a|) conj(d)/r
-  }
-  s.cs[(size_t)b * 64 + j] = c;
-  s.sn[(size_t)b * 64 + j] = sn;
-  col[j] = make_double2(c * a.x + (sn.x * d.x - sn.y * d.y), c * a.y + (sn.x * d.y + sn.y * d.x));
-  col[j + 1] = make_double2(0, 0);
-  for (int i = 0; i <= j; ++i) H[i * 64 + j] = col[i];
-  double2 gj = s.g[(size_t)b * 64 + j];
-  s.g[(size_t)b * 64 + j] = make_double2(c * gj.x, c * gj.y);
-  double2 gn = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(sn) g_j
-  s.g[(size_t)b * 64 + j + 1] = gn;
-  s.jc[b] = j + 1;
-  s.its[b] += 1;
-  const double res = sqrt(gn.x * gn.x + gn.y * gn.y);
-  s.relres[b] = res / bn[b];
-  s.scale[b] = hn[b] > 0 ? 1.0 / hn[b] : 0.0;
-  if (res <= tol * bn[b] || !(hn[b] > 0) || s.its[b] >= max_iter || j + 1 >= restart) s.act[b] = 0;
-}
-
-// y = H^{-1} g on the jc x jc triangle, per b
-__global__ void k_cycle_solve(int nb, GmresState s) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+// y = H^{-1} g on the jc x jc triangle (one block per b; H staged in shared memory,
+// back-substitution by one warp); the scales sig_i are folded into y.
+__global__ void __launch_bounds__(kThreads) k_cycle_solve(int nb, GmresState s) {
+  extern __shared__ double2 hs[];  // [64][64]
+  __shared__ double2 ys[64];
+  const int b = blockIdx.x;
   const int n = s.jc[b];
+  if (n == 0) return;
   const double2* H = s.H + (size_t)b * 64 * 64;
-  double2* y = s.y + (size_t)b * 64;
-  for (int i = n - 1; i >= 0; --i) {
-    double2 t = s.g[(size_t)b * 64 + i];
-    for (int k = i + 1; k < n; ++k) {
-      double2 p = cmul(H[i * 64 + k], y[k]);
-      t.x -= p.x;
-      t.y -= p.y;
+  for (int t = threadIdx.x; t < n * 64; t += blockDim.x) hs[t] = H[t];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = n - 1; i >= 0; --i) {
+      double re = 0, im = 0;
+      for (int k = i + 1 + lane; k < n; k += 32) {
+        const double2 p = cmul(hs[i * 64 + k], ys[k]);
+        re += p.x;
+        im += p.y;
+      }
+      re = warp_sum(re);
+      im = warp_sum(im);
+      if (lane == 0) {
+        const double2 g = s.g[b * 64 + i];
+        const double2 t = make_double2(g.x - re, g.y - im);
+        const double2 d = hs[i * 64 + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        ys[i] = dd > 0 ? make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd)
+                       : make_double2(0, 0);
+      }
+      __syncwarp();
     }
-    double2 d = H[i * 64 + i];
-    double dd = d.x * d.x + d.y * d.y;
-    y[i] = dd > 0 ? make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd) : make_double2(0, 0);
+    for (int i = lane; i < n; i += 32) {
+      const double sg = s.sig[b * 64 + i];
+      s.y[b * 64 + i] = make_double2(sg * ys[i].x, sg * ys[i].y);
+    }
   }
 }
 
-// x += dinv .* (V y)
-__global__ void k_xupdate(const double2* __restrict__ V, size_t vstride, int ns, const double2* __restrict__ dinv,
-                          GmresState s, double2* __restrict__ x) {
+// x += dinv .* sum_i vt_i (sig_i y_i);  grid (ceil(ns/32), nb), block (32, 8)
+__global__ void __launch_bounds__(kThreads) k_xupdate(const double2* __restrict__ V, long long vstride, int ns,
+                                                      const double2* __restrict__ dinv, GmresState s,
+                                                      double2* __restrict__ x) {
   const int b = blockIdx.y;
-  const int n_cols = s.jc[b];
-  if (n_cols == 0) return;
-  for (int n = blockIdx.x * kThreads + threadIdx.x; n < ns; n += gridDim.x * kThreads) {
-    double2 u = make_double2(0, 0);
-    for (int i = 0; i < n_cols; ++i) {
-      double2 p = cmul(V[i * vstride + (size_t)b * ns + n], s.y[(size_t)b * 64 + i]);
+  const int J = s.jc[b];
+  if (J == 0) return;
+  __shared__ double2 red[8][kUpdN];
+  const int n = blockIdx.x * kUpdN + threadIdx.x;
+  double2 u = make_double2(0, 0);
+  if (n < ns)
+    for (int i = threadIdx.y; i < J; i += 8) {
+      double2 p = cmul(V[i * vstride + (size_t)b * ns + n], s.y[b * 64 + i]);
       u.x += p.x;
       u.y += p.y;
     }
-    double2 d = dinv[n];
-    double2 du = cmul(d, u);
+  red[threadIdx.y][threadIdx.x] = u;
+  __syncthreads();
+  if (threadIdx.y == 0 && n < ns) {
+    double2 t = make_double2(0, 0);
+    for (int q = 0; q < 8; ++q) {
+      t.x += red[q][threadIdx.x].x;
+      t.y += red[q][threadIdx.x].y;
+    }
+    const double2 du = cmul(dinv[n], t);
     double2 xv = x[(size_t)b * ns + n];
     x[(size_t)b * ns + n] = make_double2(xv.x + du.x, xv.y + du.y);
   }
 }
 
-__global__ void k_any(int nb, const int* __restrict__ act, int* __restrict__ flag) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    int a = 0;
-    for (int b = 0; b < nb; ++b) a |= act[b];
-    *flag = a;
+// |v_b| for every b into out[b]
+__global__ void __launch_bounds__(kThreads) k_norm_finish(int nb, const double* __restrict__ pn, int P, double* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = warp; b < nb; b += nw) {
+    double v = sqrt(warp_row_sum(pn + (size_t)b * P, P));
+    if ((threadIdx.x & 31) == 0) out[b] = v;
   }
+}
+
+int n_dot_chunks(int ns) { return (ns + kDotChunk - 1) / kDotChunk; }
+int n_upd_blocks(int ns) { return (ns + kUpdN - 1) / kUpdN; }
+int n_norm_blocks(int ns) { return (ns + kNormChunk - 1) / kNormChunk; }
+
+// ---------------------------------------------------------------- launch sequences
+
+// explicit residual into slot 0 and the cycle start
+void cycle_prologue(aim_ctx* c, int nb, const double2* b, double2* x, double tol, bool use_cond,
+                    cudaGraphConditionalHandle outer, cudaGraphConditionalHandle inner) {
+  GmresState& s = c->gs;
+  cudaStream_t st = c->stream;
+  const int ns = c->ns;
+  op_apply(c, 0, nb, x, nullptr, b, -1.0, nullptr, c->d_V);  // slot 0 = b - Z_0 x
+  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
+              k_normpart<<<dim3(n_norm_blocks(ns), nb), kThreads, 0, st>>>(c->d_V, ns, s.pr));
+  CycleArgs a{nb, c->restart, c->max_iter, tol, s.pbn, s.pr, n_norm_blocks(ns), use_cond ? 1 : 0, outer, inner};
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_start<<<1, kThreads, 0, st>>>(a, s));
+}
+
+// one Arnoldi step for every active RHS (column j from device memory)
+void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle inner) {
+  GmresState& s = c->gs;
+  cudaStream_t st = c->stream;
+  const int ns = c->ns;
+  const long long vstride = (long long)c->batch_max * ns;
+  VecSel vin;
+  vin.sel = s.jdev;
+  vin.stride = vstride;
+  vin.off = 0;
+  vin.scale = s.sig;
+  VecSel vout;
+  vout.sel = s.jdev;
+  vout.stride = vstride;
+  vout.off = 1;
+  // slot j+1 = Z_0 (dinv .* v_j)
+  op_apply(c, 0, nb, c->d_V, c->d_dinv, nullptr, 1.0, s.act, c->d_V, vin, vout);
+  const int S = n_dot_chunks(ns), U = n_upd_blocks(ns);
+  for (int pass = 0; pass < 2; ++pass) {
+    AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
+                k_mdot<<<dim3(64, S, nb), kThreads, 0, st>>>(c->d_V, vstride, s.jdev, ns, s.act, s.pd));
+    AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
+                k_mupdate<<<dim3(U, nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, s.jdev, ns, S, s.act, s.sig,
+                                                                   s.pd, pass == 0 ? s.h1 : s.h2, s.pu));
+  }
+  FinishArgs f{nb, c->restart, c->max_iter, tol, s.pu, U, use_cond ? 1 : 0, inner};
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_finish<<<1, kThreads, 0, st>>>(f, s));
+}
+
+void cycle_epilogue(aim_ctx* c, int nb, double2* x) {
+  GmresState& s = c->gs;
+  cudaStream_t st = c->stream;
+  const int ns = c->ns;
+  const long long vstride = (long long)c->batch_max * ns;
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_solve<<<nb, kThreads, 64 * 64 * sizeof(double2), st>>>(nb, s));
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
+              k_xupdate<<<dim3(n_upd_blocks(ns), nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, ns, c->d_dinv, s, x));
+}
+
+// ---------------------------------------------------------------- graph of one solve
+
+cudaGraphNode_t leaf_of(cudaGraph_t g) {
+  size_t n = 0;
+  AIM_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  AIM_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+  for (auto nd : nodes) {
+    size_t out = 0;
+    AIM_CUDA(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &out));
+    if (out == 0) return nd;
+  }
+  throw AimError{AIM_ERR_CUDA, "graph without a leaf node"};
+}
+
+void capture_into(aim_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                  const std::function<void()>& body) {
+  AIM_CUDA(cudaStreamBeginCaptureToGraph(c->stream, g, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal));
+  try {
+    body();
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(c->stream, &dummy);
+    cudaGetLastError();
+    throw;
+  }
+  cudaGraph_t out;
+  AIM_CUDA(cudaStreamEndCapture(c->stream, &out));
+}
+
+cudaGraphNode_t add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, cudaGraphConditionalHandle h,
+                          cudaGraph_t* body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  AIM_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
+  *body = p.conditional.phGraph_out[0];
+  return node;
+}
+
+void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double tol) {
+  GmresState& s = c->gs;
+  cudaGraph_t g;
+  AIM_CUDA(cudaGraphCreate(&g, 0));
+  const ProfState saved = c->prof;  // capture-time launches are not executions
+  c->prof.on = false;                // no event records inside a captured graph
+  try {
+    // |b|^2 partials, then WHILE(cycles) { prologue; WHILE(arnoldi) { step }; epilogue }
+    capture_into(c, g, nullptr, 0, [&] {
+      AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
+                  k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, c->stream>>>(b, c->ns, s.pbn));
+    });
+    cudaGraphNode_t pre = leaf_of(g);
+    cudaGraphConditionalHandle outer, inner;
+    AIM_CUDA(cudaGraphConditionalHandleCreate(&outer, g, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t obody;
+    add_while(g, &pre, 1, outer, &obody);
+    AIM_CUDA(cudaGraphConditionalHandleCreate(&inner, obody, 0, cudaGraphCondAssignDefault));
+    capture_into(c, obody, nullptr, 0, [&] { cycle_prologue(c, nb, b, x, tol, true, outer, inner); });
+    cudaGraphNode_t pro = leaf_of(obody);
+    cudaGraph_t ibody;
+    cudaGraphNode_t wn = add_while(obody, &pro, 1, inner, &ibody);
+    capture_into(c, ibody, nullptr, 0, [&] { arnoldi_step(c, nb, tol, true, inner); });
+    capture_into(c, obody, &wn, 1, [&] { cycle_epilogue(c, nb, x); });
+    cudaGraphExec_t ex;
+    AIM_CUDA(cudaGraphInstantiate(&ex, g, 0));
+    if (s.graph_exec) cudaGraphExecDestroy(s.graph_exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    s.graph = g;
+    s.graph_exec = ex;
+    s.g_nb = nb;
+    s.g_tol = tol;
+    s.g_b = b;
+    s.g_x = x;
+  } catch (...) {
+    c->prof = saved;
+    cudaGraphDestroy(g);
+    throw;
+  }
+  c->prof = saved;
 }
 
 }  // namespace
 
-int gmres_blocks(int ns) { return std::max(1, std::min(64, (ns + kThreads * 4 - 1) / (kThreads * 4))); }
-
 void gmres_alloc(aim_ctx* c) {
-  const int B = c->batch_max;
+  const int B = c->batch_max, ns = c->ns;
   GmresState& s = c->gs;
-  const size_t nblk = gmres_blocks(c->ns);
   s.H = (double2*)aim_alloc(c, (size_t)B * 64 * 64 * sizeof(double2));
   s.g = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.sn = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
@@ -304,21 +533,25 @@ void gmres_alloc(aim_ctx* c) {
   s.y = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.h1 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.h2 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
-  s.hn = (double*)aim_alloc(c, B * sizeof(double));
+  s.sig = (double*)aim_alloc(c, (size_t)B * 64 * sizeof(double));
   s.bn = (double*)aim_alloc(c, B * sizeof(double));
-  s.rn = (double*)aim_alloc(c, B * sizeof(double));
-  s.scale = (double*)aim_alloc(c, B * sizeof(double));
   s.relres = (double*)aim_alloc(c, B * sizeof(double));
   s.act = (int*)aim_alloc(c, B * sizeof(int));
   s.done = (int*)aim_alloc(c, B * sizeof(int));
   s.jc = (int*)aim_alloc(c, B * sizeof(int));
   s.its = (int*)aim_alloc(c, B * sizeof(int));
-  s.flag = (int*)aim_alloc(c, sizeof(int));
-  s.pc = (double2*)aim_alloc(c, (size_t)B * nblk * 64 * sizeof(double2));
-  s.pr = (double*)aim_alloc(c, (size_t)B * nblk * sizeof(double));
-  s.counter = (unsigned*)aim_alloc(c, B * sizeof(unsigned));
-  AIM_CUDA(cudaMemsetAsync(s.counter, 0, B * sizeof(unsigned), c->stream));
-  AIM_CUDA(cudaMallocHost(&s.h_flag, sizeof(int)));
+  s.jdev = (int*)aim_alloc(c, sizeof(int));
+  s.flag = (int*)aim_alloc(c, 2 * sizeof(int));
+  s.pd = (double2*)aim_alloc(c, (size_t)B * 64 * n_dot_chunks(ns) * sizeof(double2));
+  s.pu = (double*)aim_alloc(c, (size_t)B * n_upd_blocks(ns) * sizeof(double));
+  s.pr = (double*)aim_alloc(c, (size_t)B * n_norm_blocks(ns) * sizeof(double));
+  s.pbn = (double*)aim_alloc(c, (size_t)B * n_norm_blocks(ns) * sizeof(double));
+  s.nrm = (double*)aim_alloc(c, B * sizeof(double));
+  s.cnt = (int*)aim_alloc(c, 2 * sizeof(int));
+  AIM_CUDA(cudaMallocHost(&s.h_cnt, 2 * sizeof(int)));
+  AIM_CUDA(cudaFuncSetAttribute(k_cycle_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(64 * 64 * sizeof(double2))));
+  AIM_CUDA(cudaMallocHost(&s.h_flag, 2 * sizeof(int)));
   AIM_CUDA(cudaMallocHost(&s.h_its, B * sizeof(int)));
   AIM_CUDA(cudaMallocHost(&s.h_res, B * sizeof(double)));
   AIM_CUDA(cudaMallocHost(&s.h_done, B * sizeof(int)));
@@ -326,10 +559,16 @@ void gmres_alloc(aim_ctx* c) {
 
 void gmres_free_host(aim_ctx* c) {
   GmresState& s = c->gs;
+  if (s.graph_exec) cudaGraphExecDestroy(s.graph_exec);
+  if (s.graph) cudaGraphDestroy(s.graph);
+  s.graph_exec = nullptr;
+  s.graph = nullptr;
   if (s.h_flag) cudaFreeHost(s.h_flag);
   if (s.h_its) cudaFreeHost(s.h_its);
   if (s.h_res) cudaFreeHost(s.h_res);
   if (s.h_done) cudaFreeHost(s.h_done);
+  if (s.h_cnt) cudaFreeHost(s.h_cnt);
+  s.h_cnt = nullptr;
   s.h_flag = nullptr;
   s.h_its = nullptr;
   s.h_res = nullptr;
@@ -342,54 +581,50 @@ void gmres_free_host(aim_ctx* c) {
 int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, int* iters, double* relres) {
   GmresState& s = c->gs;
   cudaStream_t st = c->stream;
-  const int ns = c->ns, R = c->restart;
-  const int nblk = gmres_blocks(ns);
-  const size_t vstride = (size_t)c->batch_max * ns;
-  dim3 vg(nblk, nb);
-  const int sb = (nb + 63) / 64;
   AIM_CUDA(cudaMemsetAsync(s.its, 0, nb * sizeof(int), st));
-  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE, k_norms<<<vg, kThreads, 0, st>>>(b, ns, s.pr, s.counter, s.bn));
-  for (int cycle = 0;; ++cycle) {
-    // explicit residual r = b - Z_0 x (FP64 vectors; operator in the context precision)
-    op_apply(c, 0, nb, x, nullptr, b, -1.0, nullptr, c->d_r);
-    AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE, k_norms<<<vg, kThreads, 0, st>>>(c->d_r, ns, s.pr, s.counter, s.rn));
-    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_start<<<sb, 64, 0, st>>>(nb, R, tol, c->max_iter, s.rn, s.bn, s));
-    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_scale<<<vg, kThreads, 0, st>>>(c->d_r, c->d_V, ns, s.act, s.scale));
-    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_any<<<1, 32, 0, st>>>(nb, s.act, s.flag));
-    AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    AIM_CUDA(cudaStreamSynchronize(st));
-    if (!*s.h_flag) break;
-    for (int j = 0; j < R; ++j) {
-      double2* vj = c->d_V + (size_t)j * vstride;
-      double2* vn = c->d_V + (size_t)(j + 1) * vstride;
-      // w = Z_0 (dinv .* v_j), then CGS2 against v_0..v_j
-      op_apply(c, 0, nb, vj, c->d_dinv, nullptr, 1.0, s.act, c->d_w);
-      AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
-                  k_dots<<<vg, kThreads, 0, st>>>(c->d_V, vstride, j + 1, c->d_w, ns, nb, s.act, s.pc, s.counter, s.h1));
-      AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-                  k_update<<<vg, kThreads, 0, st>>>(c->d_V, vstride, j + 1, s.h1, c->d_w, ns, s.act, false, s.pr,
-                                                    s.counter, s.hn));
-      AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
-                  k_dots<<<vg, kThreads, 0, st>>>(c->d_V, vstride, j + 1, c->d_w, ns, nb, s.act, s.pc, s.counter, s.h2));
-      AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-                  k_update<<<vg, kThreads, 0, st>>>(c->d_V, vstride, j + 1, s.h2, c->d_w, ns, s.act, true, s.pr,
-                                                    s.counter, s.hn));
-      AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
-                  k_arnoldi_finish<<<sb, 64, 0, st>>>(nb, j, R, tol, c->max_iter, s.h1, s.h2, s.hn, s.bn, s));
-      AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_scale<<<vg, kThreads, 0, st>>>(c->d_w, vn, ns, s.act, s.scale));
-      AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_any<<<1, 32, 0, st>>>(nb, s.act, s.flag));
-      AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-      AIM_CUDA(cudaStreamSynchronize(st));
-      if (!*s.h_flag) break;
+  AIM_CUDA(cudaMemsetAsync(s.cnt, 0, 2 * sizeof(int), st));
+  bool graphed = false;
+  // per-kernel event timing needs host-side launches: profiling runs the host-driven loop
+  if (c->use_graphs && !s.graph_failed && !c->prof.on) {
+    try {
+      if (!s.graph_exec || s.g_nb != nb || s.g_tol != tol || s.g_b != b || s.g_x != x)
+        build_solve_graph(c, nb, b, x, tol);
+      AIM_CUDA(cudaGraphLaunch(s.graph_exec, st));
+      graphed = true;
+    } catch (const AimError& e) {
+      s.graph_failed = true;
+      c->graph_error = e.msg;
+      cudaGetLastError();
     }
-    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_solve<<<sb, 64, 0, st>>>(nb, s));
-    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_xupdate<<<vg, kThreads, 0, st>>>(c->d_V, vstride, ns, c->d_dinv, s, x));
-    if (cycle > 4 * (c->max_iter / std::max(1, R) + 2)) break;
+  }
+  if (!graphed) {
+    // the same kernels driven from the host (one synchronisation per Arnoldi step)
+    AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
+                k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, st>>>(b, c->ns, s.pbn));
+    for (int cycle = 0;; ++cycle) {
+      cycle_prologue(c, nb, b, x, tol, false, 0, 0);
+      AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      AIM_CUDA(cudaStreamSynchronize(st));
+      if (!s.h_flag[0]) break;
+      for (;;) {
+        arnoldi_step(c, nb, tol, false, 0);
+        AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        AIM_CUDA(cudaStreamSynchronize(st));
+        if (!s.h_flag[1]) break;
+      }
+      cycle_epilogue(c, nb, x);
+      if (cycle > 4 * (c->max_iter / std::max(1, c->restart) + 2)) break;
+    }
   }
   AIM_CUDA(cudaMemcpyAsync(s.h_its, s.its, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaMemcpyAsync(s.h_res, s.relres, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaMemcpyAsync(s.h_done, s.done, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  AIM_CUDA(cudaMemcpyAsync(s.h_cnt, s.cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaStreamSynchronize(st));
+  if (graphed) {
+    // kernels the graph executed: 1 + cycles * (prologue 8 + epilogue 2) + steps * 11
+    c->prof.launches += 1 + 10LL * s.h_cnt[0] + 11LL * s.h_cnt[1];
+  }
   int rc = AIM_OK;
   for (int i = 0; i < nb; ++i) {
     if (iters) iters[i] = s.h_its[i];
@@ -399,7 +634,10 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
   return rc;
 }
 
+int gmres_blocks(int ns) { return n_norm_blocks(ns); }
+
 void gmres_norms(aim_ctx* c, int nb, const double2* v, double* d_out) {
-  dim3 vg(gmres_blocks(c->ns), nb);
-  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE, k_norms<<<vg, kThreads, 0, c->stream>>>(v, c->ns, c->gs.pr, c->gs.counter, d_out));
+  const int P = n_norm_blocks(c->ns);
+  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE, k_normpart<<<dim3(P, nb), kThreads, 0, c->stream>>>(v, c->ns, c->gs.pr));
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_norm_finish<<<1, kThreads, 0, c->stream>>>(nb, c->gs.pr, P, d_out));
 }

@@ -3,18 +3,19 @@
 #include "operator.h"
 
 template <class C>
-void body_apply(aim_ctx*, int, int, const double2*, const double2*, const double2*, double, const int*, double2*);
+void body_apply(aim_ctx*, int, int, const double2*, const double2*, const double2*, double, const int*, double2*,
+                VecSel, VecSel);
 template <class C>
 void body_forward_slab(aim_ctx*, int, const double2*, void*);
 template <class C>
 void body_apply_rhs(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double, double2*);
 
 void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
-              const int* active, double2* y) {
+              const int* active, double2* y, VecSel vin, VecSel yout) {
   if (c->precision == AIM_C64)
-    body_apply<float2>(c, m, nb, v, dinv, base, sign, active, y);
+    body_apply<float2>(c, m, nb, v, dinv, base, sign, active, y, vin, yout);
   else
-    body_apply<double2>(c, m, nb, v, dinv, base, sign, active, y);
+    body_apply<double2>(c, m, nb, v, dinv, base, sign, active, y, vin, yout);
 }
 
 void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst) {

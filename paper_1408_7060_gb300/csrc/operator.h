@@ -2,11 +2,22 @@
 #pragma once
 #include "aim_internal.h"
 
+// Optional device-side selection of vector j of a Krylov-style array [j][B][ns]:
+// address = base + (*sel + off) * stride; scale (if set) multiplies input b by
+// scale[b * 64 + *sel + off].  A null sel means "base itself" (off, stride unused).
+struct VecSel {
+  const int* sel = nullptr;
+  long long stride = 0;
+  int off = 0;
+  const double* scale = nullptr;
+};
+
 // near-zone terms summed by the interpolation kernel: sum_t Z~near_{m_t} x_t
 struct NearList {
   const double2* val[aimc::kMaxDelays];  // [nnz] values of one delay
   const double2* x[aimc::kMaxDelays];    // [nb][ns] vector it multiplies
   const double2* dinv;                   // optional diagonal applied to every x (preconditioner)
+  VecSel xsel;                           // selection applied to every x
   int n;
 };
 
@@ -19,7 +30,7 @@ struct SlabList {
 
 // y = base + sign * Z~AIM_m (dinv .* v)     (dinv, base optional; m = delay)
 void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
-              const int* active, double2* y);
+              const int* active, double2* y, VecSel vin = VecSel(), VecSel yout = VecSel());
 // slab of one current vector (anterpolation + forward x and y passes) written to dst
 void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst);
 // y = base + sign * [ sum_s Z~FFT_{m_s} (slab_s) + near terms ]

@@ -17,9 +17,10 @@
 
 template <class C>
 void body_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
-                const int* active, double2* y) {
+                const int* active, double2* y, VecSel vin, VecSel yout) {
   NearList nl{};
   nl.dinv = dinv;
+  nl.xsel = vin;
   nl.n = 0;
   if (c->nnz > 0) {
     nl.n = 1;
@@ -27,9 +28,9 @@ void body_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv
     nl.x[0] = v;
   }
   AIM_DISPATCH_L(c->L, {
-    GridOps<LL, C>::forward_slab(c, nb, v, dinv, active, reinterpret_cast<C*>(c->d_Bf));
+    GridOps<LL, C>::forward_slab(c, nb, v, dinv, active, reinterpret_cast<C*>(c->d_Bf), vin);
     GridOps<LL, C>::zconv(c, nb, m, active);
-    GridOps<LL, C>::backward(c, nb, nl, base, sign, active, y);
+    GridOps<LL, C>::backward(c, nb, nl, base, sign, active, y, yout);
   });
 }
 
@@ -53,7 +54,7 @@ void body_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, 
 
 #define AIM_INSTANTIATE_OPS(C)                                                                                   \
   template void body_apply<C>(aim_ctx*, int, int, const double2*, const double2*, const double2*, double,       \
-                              const int*, double2*);                                                             \
+                              const int*, double2*, VecSel, VecSel);                                             \
   template void body_forward_slab<C>(aim_ctx*, int, const double2*, void*);                                     \
   template void body_apply_rhs<C>(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double,      \
                                   double2*);

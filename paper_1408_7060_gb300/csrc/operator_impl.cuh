@@ -32,8 +32,8 @@ template <int L, class C>
 __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ nptr, const int* __restrict__ nidx,
                                                      const typename Real<C>::F4* __restrict__ ncoef,
                                                      const double2* __restrict__ v, const double2* __restrict__ dinv,
-                                                     const int* __restrict__ active, int ns, int N, int ypb,
-                                                     C* __restrict__ A, const C* __restrict__ twg) {
+                                                     VecSel vs, const int* __restrict__ active, int ns, int N,
+                                                     int ypb, C* __restrict__ A, const C* __restrict__ twg) {
   using R = typename Real<C>::T;
   const int b = blockIdx.z;
   if (active && !active[b]) return;
@@ -42,21 +42,30 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
   C* b1 = b0 + 4 * ypb * L;
   load_twiddles(tw, twg, L);
   const int z = blockIdx.y, y0 = blockIdx.x * ypb;
+  double vscale = 1.0;
+  if (vs.sel) {
+    const int j = *vs.sel + vs.off;
+    v += j * vs.stride;
+    if (vs.scale) vscale = vs.scale[b * 64 + j];
+  }
   const double2* vb = v + (size_t)b * ns;
-  for (int t = threadIdx.x; t < ypb * L; t += blockDim.x) {
-    const int yy = t / L, x = t % L, y = y0 + yy;
+  // gather the N nodes of each row (all threads busy), zero the padding half
+  for (int t = threadIdx.x; t < ypb * N; t += blockDim.x) {
+    const int yy = t / N, x = t % N, y = y0 + yy;
     C a0{}, a1{}, a2{}, a3{};
-    if (x < N && y < N) {
+    if (y < N) {
       const size_t n = ((size_t)z * N + y) * N + x;
-      for (int e = nptr[n]; e < nptr[n + 1]; ++e) {
+      const int e1 = nptr[n + 1];
+      for (int e = nptr[n]; e < e1; ++e) {
         const int k = nidx[e];
+        const typename Real<C>::F4 w = ncoef[e];
         double2 xd = vb[k];
+        xd = make_double2(vscale * xd.x, vscale * xd.y);
         if (dinv) {
           double2 d = dinv[k];
           xd = make_double2(xd.x * d.x - xd.y * d.y, xd.x * d.y + xd.y * d.x);
         }
         const C xv = cvt<C>(xd);
-        const typename Real<C>::F4 w = ncoef[e];
         a0 += (R)w.x * xv;
         a1 += (R)w.y * xv;
         a2 += (R)w.z * xv;
@@ -68,8 +77,12 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
     b0[(2 * ypb + yy) * L + x] = a2;
     b0[(3 * ypb + yy) * L + x] = a3;
   }
+  for (int t = threadIdx.x; t < 4 * ypb * (L - N); t += blockDim.x) {
+    const int row = t / (L - N), x = N + t % (L - N);
+    b0[row * L + x] = C{};
+  }
   __syncthreads();
-  C* res = block_fft<L, false, false, C>(b0, b1, 4 * ypb, 1, L, tw);
+  C* res = line_fft_rows<L, false, C>(b0, b1, 4 * ypb, tw);
   for (int t = threadIdx.x; t < 4 * ypb * L; t += blockDim.x) {
     const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
     if (y < N) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
@@ -101,7 +114,7 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
     b0[t] = v;
   }
   __syncthreads();
-  C* f = block_fft<L, false, true, C>(b0, b1, W, W, 1, tw);
+  C* f = line_fft_cols<L, false, C>(b0, b1, W, tw);
   const int n1 = N + 1;
   const C* G = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1;
   const int fy = fold(y, N);
@@ -110,7 +123,7 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
     f[t] = f[t] * G[((size_t)fold(i, N) * n1 + fy) * n1 + fold(x0 + l, N)];
   }
   __syncthreads();
-  C* g = block_fft<L, true, true, C>(f, f == b0 ? b1 : b0, W, W, 1, tw);
+  C* g = line_fft_cols<L, true, C>(f, f == b0 ? b1 : b0, W, tw);
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int i = t / W, l = t % W;
     col[i * es + l] = g[t];
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
       b0[t] = v;
     }
     __syncthreads();
-    C* f = block_fft<L, false, true, C>(b0, b1, W, W, 1, tw);
+    C* f = line_fft_cols<L, false, C>(b0, b1, W, tw);
     const C* G = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct;
     for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
       const int i = t / W, l = t % W;
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
     }
   }
   __syncthreads();
-  C* g = block_fft<L, true, true, C>(acc, b0, W, W, 1, tw);
+  C* g = line_fft_cols<L, true, C>(acc, b0, W, tw);
   C* out = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int i = t / W, l = t % W;
@@ -169,7 +182,8 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
                                                      int nb, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col, NearList nl,
                                                      const double2* __restrict__ base, double sign,
-                                                     const int* __restrict__ active, double2* __restrict__ y) {
+                                                     const int* __restrict__ active, double2* __restrict__ y,
+                                                     VecSel ys) {
   using R = typename Real<C>::T;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -195,11 +209,19 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
     tot = make_double2((double)g.x, (double)g.y);
   }
   double2 nr = make_double2(0, 0);
+  long long xoff = 0;
+  double xscale = 1.0;
+  if (nl.xsel.sel) {
+    const int jj = *nl.xsel.sel + nl.xsel.off;
+    xoff = jj * nl.xsel.stride;
+    if (nl.xsel.scale) xscale = nl.xsel.scale[b * 64 + jj];
+  }
   for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 32) {
     const int j = col[e];
     for (int t = 0; t < nl.n; ++t) {
       const double2 z = nl.val[t][e];
-      double2 xv = nl.x[t][(size_t)b * ns + j];
+      double2 xv = nl.x[t][xoff + (size_t)b * ns + j];
+      xv = make_double2(xscale * xv.x, xscale * xv.y);
       if (nl.dinv) {
         const double2 d = nl.dinv[j];
         xv = make_double2(xv.x * d.x - xv.y * d.y, xv.x * d.y + xv.y * d.x);
@@ -213,6 +235,7 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
     nr.y += __shfl_xor_sync(0xffffffffu, nr.y, o);
   }
   if (lane == 0) {
+    if (ys.sel) y += (*ys.sel + ys.off) * ys.stride;
     double2 r = make_double2(sign * (tot.x + nr.x), sign * (tot.y + nr.y));
     if (base) {
       const double2 bb = base[(size_t)b * ns + k];
@@ -241,22 +264,23 @@ inline const double* sel_lam(aim_ctx* c, double2*) { return c->d_lam; }
 template <int L, class C>
 struct GridOps {
   static constexpr int W = col_width<L, C>();
-  static int ypb() { return std::max(1, 1024 / (4 * L)); }
+  static int ypb() { return std::max(1, 256 / (L / 2)); }
   static int rpb() { return std::max(1, 2048 / L); }
 
   // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
-  static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab) {
+  static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab,
+                           VecSel vs = VecSel()) {
     const int N = c->N;
     const C* tw = twiddles(c);
     C* A = reinterpret_cast<C*>(c->d_A);
     {
       const int yp = ypb();
-      size_t sm = (L + 2 * 4 * yp * L) * sizeof(C);
+      size_t sm = (L + 4 * yp * L + row_scratch<L>(4 * yp)) * sizeof(C);
       smem_opt_in(k_anterp_rows<L, C>, sm);
       dim3 grid((N + yp - 1) / yp, N, nb);
       KScope ks(c, AIM_K_ANTERP_XFFT);
-      k_anterp_rows<L, C><<<grid, 256, sm, c->stream>>>(c->d_nptr, c->d_nidx, ncoef(c), v, dinv, active, c->ns, N,
-                                                        yp, A, tw);
+      k_anterp_rows<L, C><<<grid, 256, sm, c->stream>>>(c->d_nptr, c->d_nidx, ncoef(c), v, dinv, vs, active, c->ns,
+                                                        N, yp, A, tw);
       AIM_CHECK_LAUNCH();
     }
     {
@@ -272,7 +296,7 @@ struct GridOps {
 
   // inverse y and x passes: Bf slab -> P, then interpolation + near terms
   static void backward(aim_ctx* c, int nb, const NearList& nl, const double2* base, double sign, const int* active,
-                       double2* y) {
+                       double2* y, VecSel ys = VecSel()) {
     const int N = c->N;
     const C* tw = twiddles(c);
     C* A = reinterpret_cast<C*>(c->d_A);
@@ -289,22 +313,22 @@ struct GridOps {
     }
     {
       const int rp = rpb();
-      size_t sm = (L + 2 * rp * L) * sizeof(C);
+      size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(C);
       smem_opt_in(k_rows<L, true, C>, sm);
       const int nrows = nb * 4 * N * N;
       KScope ks(c, AIM_K_XFFT_INV);
       k_rows<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
       AIM_CHECK_LAUNCH();
     }
-    interp(c, nb, P, nl, base, sign, active, y);
+    interp(c, nb, P, nl, base, sign, active, y, ys);
   }
 
   static void interp(aim_ctx* c, int nb, const C* P, const NearList& nl, const double2* base, double sign,
-                     const int* active, double2* y) {
+                     const int* active, double2* y, VecSel ys = VecSel()) {
     long long warps = (long long)nb * c->ns;
     KScope ks(c, AIM_K_INTERP_NEAR);
     k_interp_near<C><<<(int)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(
-        P, c->d_anchor, lam(c), c->N, c->ns, nb, c->d_rowptr, c->d_col, nl, base, sign, active, y);
+        P, c->d_anchor, lam(c), c->N, c->ns, nb, c->d_rowptr, c->d_col, nl, base, sign, active, y, ys);
     AIM_CHECK_LAUNCH();
   }
 

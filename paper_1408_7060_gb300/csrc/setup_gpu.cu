@@ -604,7 +604,7 @@ static void fft3d_full_L(aim_ctx* c, double2* G) {
   cudaStream_t st = c->stream;
   const double2* tw = c->d_tw;
   const int rp = std::max(1, 2048 / L);
-  size_t sm = (L + 2 * rp * L) * sizeof(double2);
+  size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(double2);
   smem_opt_in(k_rows<L, false, double2>, sm);
   k_rows<L, false, double2><<<(L * L + rp - 1) / rp, 256, sm, st>>>(G, G, L * L, L, L, L, L, tw, rp);
   AIM_CHECK_LAUNCH();

@@ -232,3 +232,34 @@ def test_matvec_full_size_sampled():
                 near[np.searchsorted(rows, k)] += z * x[0, kp]
             ref = ref + near
             assert rel(y[rows], ref) < 1e-5, m
+
+
+# ------------------------------------------------------------------ solver modes, resume
+
+def test_graph_solver_matches_host_loop(s480):
+    """The captured solve (conditional WHILE graph) runs the same kernels in the same
+    order as the host-driven loop: identical currents."""
+    import os
+
+    w = s480[0]
+    os.environ["AIM_GB300_GRAPHS"] = "0"
+    try:
+        with ctx_for(w, precision="c64") as c0:
+            a, sa, _ = c0.march(w.khat, w.phat, w.sigma, w.t_d, 25, 1e-6)
+    finally:
+        del os.environ["AIM_GB300_GRAPHS"]
+    with ctx_for(w, precision="c64") as c1:
+        b, sb, _ = c1.march(w.khat, w.phat, w.sigma, w.t_d, 25, 1e-6)
+    assert sa["total_iters"] == sb["total_iters"]
+    assert np.array_equal(a, b)
+
+
+def test_march_continue_resumes_exactly(s480):
+    """march(n1) + march_continue(n2) == march(n1 + n2): the context holds the whole
+    state of the march (the last N_g currents and their spectra)."""
+    w = s480[0]
+    with ctx_for(w, precision="c64") as c:
+        full, _, _ = c.march(w.khat, w.phat, w.sigma, w.t_d, 30, 1e-6)
+        a, _, _ = c.march(w.khat, w.phat, w.sigma, w.t_d, 12, 1e-6)
+        b, _, _ = c.march_continue(w.khat, w.phat, w.sigma, w.t_d, 18, 1e-6)
+    assert np.array_equal(np.concatenate([a, b]), full)
