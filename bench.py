@@ -53,7 +53,8 @@ def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
     near = nnz * (4 + 16) + (ns + 1) * 4
     vec = ns * 16 * nb
     return {
-        "anterp_xfft": csrT + vec + A,
+        "prep": vec + ns * 16 + ns * (esz + 16) * nb,
+        "anterp_xfft": csrT + ns * esz * nb + A,
         "yfft_fwd": A + slab,
         "zconv": 2 * slab + 2 * oct_,
         "zrhs": ng * slab + slab + 2 * ng * oct_,

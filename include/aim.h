@@ -150,6 +150,7 @@ enum {
   AIM_K_GMRES_DOT,       /* Krylov multi-dot products (two-stage reduction)                */
   AIM_K_GMRES_UPDATE,    /* Gram-Schmidt update and norms                                  */
   AIM_K_GMRES_SMALL,     /* Givens rotations, scaling, cycle bookkeeping                   */
+  AIM_K_PREP,            /* operator input: selection, Krylov scale, preconditioner, cast  */
   AIM_K_COUNT
 };
 
@@ -239,6 +240,46 @@ int aim_march(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double t
  */
 int aim_march_continue(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double tol,
                        aim_c128* currents, aim_stats* stats);
+
+/*
+ * Gradients (not in the paper: the linear maps around the march of Eq. 5, used to
+ * differentiate a far-field objective with respect to the incident envelope).
+ *
+ * aim_march_source -- march Eq. 5 from rest with explicit right-hand sides S_l in
+ * place of the plane-wave excitation: sum_m Z_m I_{l-m} = S_l (transpose = 0), or with
+ * every Z_m replaced by its transpose Z_m^T (transpose = 1; the grid part is symmetric,
+ * the near-zone values are transposed).  The adjoint march M^H lam = G is the
+ * transposed march of conj(G) in reversed time, conjugated.
+ *   src, currents: [n_steps][nb][ns], host or device.
+ *
+ * aim_excitation_samples -- V_l[k], l = 1..n_steps, for the incident envelope
+ * e(tau) = sum_i a_i T(tau/dt - i) (the CPPIF interpolant of envelope samples
+ * a_i, i = i0..i0+n_samp-1) of a plane wave (khat, phat: host [3]):
+ *   V_l[k] = sum_i a_i <S_k, phat (DT)(l - i - r.khat/(c dt)) e^{-j k_c r.khat}>,
+ *   (DT)(u) = T'(u)/dt + j w_c T(u)  (Eq. 1 and Eq. 4 with a sampled envelope).
+ *   a: [n_samp], V: [n_steps][ns]; host or device.
+ * aim_excitation_samples_adjoint -- its adjoint: grad_i = sum_l sum_k conj(B_{l-i}[k])
+ *   lam_l[k] for lam [n_steps][ns] -> grad [n_samp].
+ *
+ * aim_farfield -- far-field envelope in nd directions rhat [nd][3] with transverse
+ * unit vectors e1, e2 [nd][3] (host), n = n0..n0+n_out-1:
+ *   F[n][d][q] = -mu/(4 pi) sum_l sum_k I_l[k] int S_k.e_q (DT)(n - l + rhat.r'/(c dt))
+ *                e^{+j k_c rhat.r'} dS',   I: [n_steps][ns], F: [n_out][nd][2].
+ * aim_farfield_adjoint -- G_l[k] = sum_n sum_{d,q} conj(coefficient of I_l[k] in
+ *   F[n][d][q]) F[n][d][q] for the given F -> G [n_steps][ns] (= dJ/d conj(I) for
+ *   J = sum |F|^2).
+ * All cubatures use the 7-point rule; errors: AIM_ERR_ARG on null pointers or sizes.
+ */
+int aim_march_source(aim_ctx* ctx, int32_t transpose, int32_t nb, int32_t n_steps, const aim_c128* src,
+                     double tol, aim_c128* currents, aim_stats* stats);
+int aim_excitation_samples(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                           const aim_c128* a, int32_t n_steps, aim_c128* V);
+int aim_excitation_samples_adjoint(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0,
+                                   int32_t n_samp, int32_t n_steps, const aim_c128* lam, aim_c128* grad);
+int aim_farfield(aim_ctx* ctx, int32_t nd, const double* rhat, const double* e1, const double* e2,
+                 int32_t n_steps, const aim_c128* I, int32_t n0, int32_t n_out, aim_c128* F);
+int aim_farfield_adjoint(aim_ctx* ctx, int32_t nd, const double* rhat, const double* e1, const double* e2,
+                         int32_t n_steps, int32_t n0, int32_t n_out, const aim_c128* F, aim_c128* G);
 
 /*
  * Parity access to the setup tables (host arrays supplied by the caller).

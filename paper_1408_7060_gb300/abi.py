@@ -67,8 +67,9 @@ class aim_info(ct.Structure):
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
            "aim_matvec", "aim_rhs", "aim_excitation_vector", "aim_march", "aim_march_continue", "aim_get_anterp",
            "aim_get_near", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
-           "aim_matvec_noalloc"]
-AIM_K_COUNT = 11
+           "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
+           "aim_farfield", "aim_farfield_adjoint"]
+AIM_K_COUNT = 12
 
 _LIB = None
 
@@ -105,6 +106,11 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
         "aim_profile": (ct.c_int, [P, I32]),
         "aim_get_profile": (ct.c_int, [P, P, P, P]),
         "aim_kernel_name": (ct.c_char_p, [I32]),
+        "aim_march_source": (ct.c_int, [P, I32, I32, I32, P, D, P, ct.POINTER(aim_stats)]),
+        "aim_excitation_samples": (ct.c_int, [P, P, P, I32, I32, P, I32, P]),
+        "aim_excitation_samples_adjoint": (ct.c_int, [P, P, P, I32, I32, I32, P, P]),
+        "aim_farfield": (ct.c_int, [P, I32, P, P, P, I32, P, I32, I32, P]),
+        "aim_farfield_adjoint": (ct.c_int, [P, I32, P, P, P, I32, I32, I32, P, P]),
         "aim_get_anterp": (ct.c_int, [P, P, P]),
         "aim_get_near": (ct.c_int, [P, P, P, P]),
         "aim_get_kernel_spectrum": (ct.c_int, [P, I32, I32, P]),
@@ -286,6 +292,66 @@ def aim_get_profile(ctx) -> dict:
     _check(lib, ctx, lib.aim_get_profile(ctx, n.ctypes.data, ms.ctypes.data, tot.ctypes.data), "aim_get_profile")
     out = {lib.aim_kernel_name(i).decode(): (int(n[i]), float(ms[i])) for i in range(AIM_K_COUNT)}
     return out, int(tot[0])
+
+
+def _vec3(x, n=None):
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    return x
+
+
+def aim_march_source(ctx, src, tol, transpose=False, out=None):
+    """March from rest with explicit right-hand sides src[n_steps, nb, ns]."""
+    lib = load()
+    n_steps, nb, ns = src.shape
+    cur = _like(src, tuple(src.shape)) if out is None else out
+    iters = np.zeros((n_steps, nb), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data)
+    rc = lib.aim_march_source(ctx, int(bool(transpose)), int(nb), int(n_steps), _ptr(src), float(tol), _ptr(cur),
+                              ct.byref(st))
+    _check(lib, ctx, rc, "aim_march_source")
+    stats = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
+    stats["iters"] = iters
+    return cur, stats, rc
+
+
+def aim_excitation_samples(ctx, khat, phat, i0, a, n_steps, out=None):
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    k, p = _vec3(khat), _vec3(phat)
+    V = _like(a, (int(n_steps), ns)) if out is None else out
+    _check(lib, ctx, lib.aim_excitation_samples(ctx, k.ctypes.data, p.ctypes.data, int(i0), int(a.shape[0]), _ptr(a),
+                                                int(n_steps), _ptr(V)), "aim_excitation_samples")
+    return V
+
+
+def aim_excitation_samples_adjoint(ctx, khat, phat, i0, n_samp, lam, out=None):
+    lib = load()
+    k, p = _vec3(khat), _vec3(phat)
+    g = _like(lam, (int(n_samp),)) if out is None else out
+    _check(lib, ctx, lib.aim_excitation_samples_adjoint(ctx, k.ctypes.data, p.ctypes.data, int(i0), int(n_samp),
+                                                        int(lam.shape[0]), _ptr(lam), _ptr(g)),
+           "aim_excitation_samples_adjoint")
+    return g
+
+
+def aim_farfield(ctx, rhat, e1, e2, I, n0, n_out, out=None):
+    lib = load()
+    r, a, b = _vec3(rhat), _vec3(e1), _vec3(e2)
+    F = _like(I, (int(n_out), len(r), 2)) if out is None else out
+    _check(lib, ctx, lib.aim_farfield(ctx, len(r), r.ctypes.data, a.ctypes.data, b.ctypes.data, int(I.shape[0]),
+                                      _ptr(I), int(n0), int(n_out), _ptr(F)), "aim_farfield")
+    return F
+
+
+def aim_farfield_adjoint(ctx, rhat, e1, e2, n_steps, n0, F, out=None):
+    lib = load()
+    r, a, b = _vec3(rhat), _vec3(e1), _vec3(e2)
+    ns, _ = aim_num_unknowns(ctx)
+    G = _like(F, (int(n_steps), ns)) if out is None else out
+    _check(lib, ctx, lib.aim_farfield_adjoint(ctx, len(r), r.ctypes.data, a.ctypes.data, b.ctypes.data,
+                                              int(n_steps), int(n0), int(F.shape[0]), _ptr(F), _ptr(G)),
+           "aim_farfield_adjoint")
+    return G
 
 
 def aim_get_anterp(ctx):

@@ -81,6 +81,7 @@ struct GmresState {
   double g_tol = 0;
   const void* g_b = nullptr;
   const void* g_x = nullptr;
+  const void* g_near = nullptr;
   bool graph_failed = false;
 };
 
@@ -112,7 +113,7 @@ struct aim_ctx {
 
   // host copies of the RWG table (for aim_rwg_table)
   std::vector<int> h_edge, h_tri, h_free;
-  std::vector<int> h_rowptr;
+  std::vector<int> h_rowptr, h_col;
 
   // ---- device tables (FP64 unless noted) ----
   double* d_v = nullptr;       // [nv][3]
@@ -146,12 +147,15 @@ struct aim_ctx {
   int* d_col = nullptr;        // [nnz]
   double2* d_near = nullptr;   // [(N_g+1)][nnz]
   double2* d_dinv = nullptr;   // [ns] 1 / Z_0[k,k]
+  double2* d_nearT = nullptr;  // [(N_g+1)][nnz] values of the transposed near matrices (lazy)
 
   // ---- work buffers (sized for batch_max) ----
   void* d_A = nullptr;         // [B][4][N][N][L]   after the x pass
   void* d_Bf = nullptr;        // [B][4][N][L][L]   after the y pass (z<N slab)
   void* d_P = nullptr;         // [B][4][N][N][N]   potentials on the grid
   void* d_ring = nullptr;      // [N_g][B][4][N][L][L] spectral history slabs
+  void* d_xs = nullptr;        // [B][ns] prepared operator input, grid precision
+  double2* d_xd = nullptr;     // [B][ns] prepared operator input, FP64 (near zone)
   double2* d_iring = nullptr;  // [N_g][B][ns] current history (RWG space)
   double2* d_x = nullptr;      // [B][ns] staging / solution
   double2* d_y = nullptr;      // [B][ns]
@@ -168,6 +172,8 @@ struct aim_ctx {
   size_t device_bytes = 0;
 
   GmresState gs;
+  double2* adj_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // adjoint-helper staging
+  size_t adj_cap[5] = {0, 0, 0, 0, 0};
   ProfState prof;
   int l_done = 0, march_nb = 0;   // march state for aim_march_continue
   bool use_graphs = true;

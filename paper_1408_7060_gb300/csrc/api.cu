@@ -127,6 +127,8 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_A = aim_alloc(c, (size_t)B * 4 * N * N * L * es);
   c->d_Bf = aim_alloc(c, (size_t)B * 4 * N * L * L * es);
   c->d_P = aim_alloc(c, (size_t)B * 4 * N * N * N * es);
+  c->d_xs = aim_alloc(c, (size_t)B * ns * es);
+  c->d_xd = (double2*)aim_alloc(c, (size_t)B * ns * sizeof(double2));
   c->d_ring = aim_alloc(c, (size_t)ng * op_slab_bytes(c, B));
   const size_t vec = (size_t)B * ns * sizeof(double2);
   c->d_iring = (double2*)aim_alloc(c, (size_t)ng * vec);
@@ -232,7 +234,17 @@ void prof_flush(aim_ctx* c) {
 }
 
 static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, double tol, aim_c128* currents,
-                       aim_stats* stats);
+                       aim_stats* stats, int nb_src = 0, const aim_c128* src = nullptr);
+
+void adj_excitation_samples(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
+                            const double2* a, int n_steps, double2* V);
+void adj_excitation_samples_adjoint(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
+                                    int n_steps, const double2* lam, double2* grad);
+void adj_farfield(aim_ctx* c, int nd, const double* d_dirs, int n_steps, const double2* I, int n0, int n_out,
+                  double2* F);
+void adj_farfield_adjoint(aim_ctx* c, int nd, const double* d_dirs, int n_steps, int n0, int n_out,
+                          const double2* F, double2* G);
+void adj_ensure_near_transpose(aim_ctx* c);
 
 extern "C" {
 
@@ -420,8 +432,128 @@ int aim_get_profile(aim_ctx* c, int64_t* launches, double* ms, int64_t* total) {
 
 const char* aim_kernel_name(int32_t id) {
   static const char* names[AIM_K_COUNT] = {"anterp_xfft", "yfft_fwd", "zconv", "zrhs", "yfft_inv", "xfft_inv",
-                                          "interp_near", "excitation", "gmres_dot", "gmres_update", "gmres_small"};
+                                          "interp_near", "excitation", "gmres_dot", "gmres_update", "gmres_small", "prep"};
   return id >= 0 && id < AIM_K_COUNT ? names[id] : "?";
+}
+
+int aim_march_source(aim_ctx* c, int32_t transpose, int32_t nb, int32_t n_steps, const aim_c128* src, double tol,
+                     aim_c128* currents, aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!src || !currents || n_steps < 1 || nb < 1 || nb > c->batch_max || !(tol > 0))
+      throw AimError{AIM_ERR_ARG, "aim_march_source: bad arguments"};
+    double2* fwd = c->d_near;
+    if (transpose) {
+      adj_ensure_near_transpose(c);
+      if (c->nnz) c->d_near = c->d_nearT;
+    }
+    struct Restore {
+      aim_ctx* c;
+      double2* p;
+      ~Restore() { c->d_near = p; }
+    } restore{c, fwd};
+    AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)nb * c->ns * sizeof(double2), c->stream));
+    c->l_done = 0;
+    c->march_nb = 0;  // a source march cannot be continued with aim_march_continue
+    return march_steps(c, nullptr, n_steps, tol, currents, stats, nb, src);
+  });
+}
+
+namespace {
+// host or device array of n doubles -> device pointer (staged through a scratch buffer)
+const double2* dev_in(aim_ctx* c, const aim_c128* p, size_t n, double2* staging) {
+  if (is_device_ptr(p)) return reinterpret_cast<const double2*>(p);
+  AIM_CUDA(cudaMemcpyAsync(staging, p, n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  return staging;
+}
+double2* scratch(aim_ctx* c, size_t n, int slot) {
+  if (c->adj_cap[slot] < n) {
+    c->adj_buf[slot] = (double2*)aim_alloc(c, n * sizeof(double2));
+    c->adj_cap[slot] = n;
+  }
+  return c->adj_buf[slot];
+}
+void finish_out(aim_ctx* c, aim_c128* out, const double2* d, size_t n, bool dev) {
+  if (!dev) AIM_CUDA(cudaMemcpyAsync(out, d, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+  AIM_CUDA(cudaStreamSynchronize(c->stream));
+}
+const double* upload_dirs(aim_ctx* c, int nd, const double* rhat, const double* e1, const double* e2) {
+  std::vector<double> h((size_t)9 * nd);
+  for (int i = 0; i < 3 * nd; ++i) {
+    h[i] = rhat[i];
+    h[3 * nd + i] = e1[i];
+    h[6 * nd + i] = e2[i];
+  }
+  double* d = reinterpret_cast<double*>(scratch(c, (size_t)(9 * nd + 1) / 2 + 1, 4));
+  AIM_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return d;
+}
+}  // namespace
+
+int aim_excitation_samples(aim_ctx* c, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                           const aim_c128* a, int32_t n_steps, aim_c128* V) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!khat || !phat || !a || !V || n_samp < 1 || n_steps < 1)
+      throw AimError{AIM_ERR_ARG, "aim_excitation_samples: bad arguments"};
+    const size_t n = (size_t)n_steps * c->ns;
+    const double2* da = dev_in(c, a, n_samp, scratch(c, n_samp, 0));
+    const bool dev = is_device_ptr(V);
+    double2* out = dev ? reinterpret_cast<double2*>(V) : scratch(c, n, 1);
+    adj_excitation_samples(c, khat, phat, i0, n_samp, da, n_steps, out);
+    finish_out(c, V, out, n, dev);
+    return AIM_OK;
+  });
+}
+
+int aim_excitation_samples_adjoint(aim_ctx* c, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                                   int32_t n_steps, const aim_c128* lam, aim_c128* grad) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!khat || !phat || !lam || !grad || n_samp < 1 || n_steps < 1)
+      throw AimError{AIM_ERR_ARG, "aim_excitation_samples_adjoint: bad arguments"};
+    const size_t n = (size_t)n_steps * c->ns;
+    const double2* dl = dev_in(c, lam, n, scratch(c, n, 1));
+    const bool dev = is_device_ptr(grad);
+    double2* out = dev ? reinterpret_cast<double2*>(grad) : scratch(c, n_samp, 0);
+    adj_excitation_samples_adjoint(c, khat, phat, i0, n_samp, n_steps, dl, out);
+    finish_out(c, grad, out, n_samp, dev);
+    return AIM_OK;
+  });
+}
+
+int aim_farfield(aim_ctx* c, int32_t nd, const double* rhat, const double* e1, const double* e2, int32_t n_steps,
+                 const aim_c128* I, int32_t n0, int32_t n_out, aim_c128* F) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (nd < 1 || !rhat || !e1 || !e2 || !I || !F || n_steps < 1 || n_out < 1)
+      throw AimError{AIM_ERR_ARG, "aim_farfield: bad arguments"};
+    const size_t n = (size_t)n_steps * c->ns, nf = (size_t)n_out * nd * 2;
+    const double* dd = upload_dirs(c, nd, rhat, e1, e2);
+    const double2* dI = dev_in(c, I, n, scratch(c, n, 1));
+    const bool dev = is_device_ptr(F);
+    double2* out = dev ? reinterpret_cast<double2*>(F) : scratch(c, nf, 2);
+    adj_farfield(c, nd, dd, n_steps, dI, n0, n_out, out);
+    finish_out(c, F, out, nf, dev);
+    return AIM_OK;
+  });
+}
+
+int aim_farfield_adjoint(aim_ctx* c, int32_t nd, const double* rhat, const double* e1, const double* e2,
+                         int32_t n_steps, int32_t n0, int32_t n_out, const aim_c128* F, aim_c128* G) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (nd < 1 || !rhat || !e1 || !e2 || !F || !G || n_steps < 1 || n_out < 1)
+      throw AimError{AIM_ERR_ARG, "aim_farfield_adjoint: bad arguments"};
+    const size_t n = (size_t)n_steps * c->ns, nf = (size_t)n_out * nd * 2;
+    const double* dd = upload_dirs(c, nd, rhat, e1, e2);
+    const double2* dF = dev_in(c, F, nf, scratch(c, nf, 2));
+    const bool dev = is_device_ptr(G);
+    double2* out = dev ? reinterpret_cast<double2*>(G) : scratch(c, n, 3);
+    adj_farfield_adjoint(c, nd, dd, n_steps, n0, n_out, dF, out);
+    finish_out(c, G, out, n, dev);
+    return AIM_OK;
+  });
 }
 
 int aim_get_anterp(const aim_ctx* c, int32_t* anchor, double* lam) {
@@ -461,9 +593,10 @@ int aim_get_kernel_spectrum(const aim_ctx* c, int32_t m, int32_t kind, aim_c128*
 }  // extern "C"
 
 static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, double tol, aim_c128* currents,
-                       aim_stats* stats) {
-    cudaStream_t st = c->stream;
-  const int nb = exc->nb, ns = c->ns, ng = c->n_delays, B = c->batch_max;
+                       aim_stats* stats, int nb_src, const aim_c128* src) {
+  cudaStream_t st = c->stream;
+  const int nb = src ? nb_src : exc->nb, ns = c->ns, ng = c->n_delays, B = c->batch_max;
+  const bool src_dev = src && is_device_ptr(src);
   const size_t n = (size_t)nb * ns;
   const size_t slab = op_slab_bytes(c, B);
   const bool dev_out = is_device_ptr(currents);
@@ -485,7 +618,11 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
   const int l0 = c->l_done;
   for (int l = l0 + 1; l <= l0 + n_steps; ++l) {
     AIM_CUDA(cudaEventRecord(ev[0], st));
-    op_excitation(c, nb, c->d_exc, exc->sigma, exc->t_d, l, c->d_b);
+    if (src)  // explicit right-hand side samples S_l
+      AIM_CUDA(cudaMemcpyAsync(c->d_b, src + (size_t)(l - l0 - 1) * n, n * sizeof(double2),
+                               src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    else
+      op_excitation(c, nb, c->d_exc, exc->sigma, exc->t_d, l, c->d_b);
     SlabList sl{};
     NearList nl{};
     for (int m = 1; m <= ng; ++m) {

@@ -196,8 +196,8 @@ __host__ __device__ constexpr int split_r1(int L) {
 }
 
 // Column tile: W lines, element i of line l at a[i*W + l].  Result in natural order in a.
-template <int L, bool INV, class C>
-__device__ __forceinline__ void col_fft2(C* a, C* tmp, int W, const C* __restrict__ tw) {
+template <int L, int W, bool INV, class C>
+__device__ __forceinline__ void col_fft2(C* a, C* tmp, const C* __restrict__ tw) {
   constexpr int R1 = split_r1(L), R2 = L / R1;
   for (int u = threadIdx.x; u < W * R2; u += blockDim.x) {
     const int l = u % W, n2 = u / W;

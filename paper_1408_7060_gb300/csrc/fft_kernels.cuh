@@ -19,10 +19,10 @@ __device__ __forceinline__ void load_twiddles(C* tw, const C* __restrict__ twg, 
 // Transform the lines of a tile (after a __syncthreads that publishes a); returns
 // the buffer holding the natural-order result.  Power-of-two lengths use the
 // two-step transform, lengths with a factor 3 the Stockham passes.
-template <int L, bool INV, class C>
-__device__ __forceinline__ C* line_fft_cols(C* a, C* b, int W, const C* tw) {
+template <int L, int W, bool INV, class C>
+__device__ __forceinline__ C* line_fft_cols(C* a, C* b, const C* tw) {
   if constexpr (pow2_len(L)) {
-    col_fft2<L, INV, C>(a, b, W, tw);
+    col_fft2<L, W, INV, C>(a, b, tw);
     return a;
   } else {
     return block_fft<L, INV, true, C>(a, b, W, W, 1, tw);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __res
     b0[t] = v;
   }
   __syncthreads();
-  C* res = line_fft_cols<L, INV, C>(b0, b1, W, tw);
+  C* res = line_fft_cols<L, W, INV, C>(b0, b1, tw);
   for (int t = threadIdx.x; t < n_out * W; t += blockDim.x) {
     int i = t / W, l = t % W;
     if (l < nw) dst[i * es_out + l] = res[t];

@@ -19,16 +19,15 @@ template <class C>
 void body_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
                 const int* active, double2* y, VecSel vin, VecSel yout) {
   NearList nl{};
-  nl.dinv = dinv;
-  nl.xsel = vin;
+  nl.dinv = nullptr;
   nl.n = 0;
-  if (c->nnz > 0) {
+  if (c->nnz > 0) {  // the near term multiplies the prepared FP64 input
     nl.n = 1;
     nl.val[0] = c->d_near + (size_t)m * c->nnz;
-    nl.x[0] = v;
+    nl.x[0] = c->d_xd;
   }
   AIM_DISPATCH_L(c->L, {
-    GridOps<LL, C>::forward_slab(c, nb, v, dinv, active, reinterpret_cast<C*>(c->d_Bf), vin);
+    GridOps<LL, C>::forward_slab(c, nb, v, dinv, active, reinterpret_cast<C*>(c->d_Bf), vin, true);
     GridOps<LL, C>::zconv(c, nb, m, active);
     GridOps<LL, C>::backward(c, nb, nl, base, sign, active, y, yout);
   });

@@ -31,9 +31,9 @@ template <> __device__ __forceinline__ double2 cvt<double2>(double2 a) { return 
 template <int L, class C>
 __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ nptr, const int* __restrict__ nidx,
                                                      const typename Real<C>::F4* __restrict__ ncoef,
-                                                     const double2* __restrict__ v, const double2* __restrict__ dinv,
-                                                     VecSel vs, const int* __restrict__ active, int ns, int N,
-                                                     int ypb, C* __restrict__ A, const C* __restrict__ twg) {
+                                                     const C* __restrict__ xs, const int* __restrict__ active,
+                                                     int ns, int N, int ypb, C* __restrict__ A,
+                                                     const C* __restrict__ twg) {
   using R = typename Real<C>::T;
   const int b = blockIdx.z;
   if (active && !active[b]) return;
@@ -42,13 +42,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
   C* b1 = b0 + 4 * ypb * L;
   load_twiddles(tw, twg, L);
   const int z = blockIdx.y, y0 = blockIdx.x * ypb;
-  double vscale = 1.0;
-  if (vs.sel) {
-    const int j = *vs.sel + vs.off;
-    v += j * vs.stride;
-    if (vs.scale) vscale = vs.scale[b * 64 + j];
-  }
-  const double2* vb = v + (size_t)b * ns;
+  const C* vb = xs + (size_t)b * ns;
   // gather the N nodes of each row (all threads busy), zero the padding half
   for (int t = threadIdx.x; t < ypb * N; t += blockDim.x) {
     const int yy = t / N, x = t % N, y = y0 + yy;
@@ -59,13 +53,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
       for (int e = nptr[n]; e < e1; ++e) {
         const int k = nidx[e];
         const typename Real<C>::F4 w = ncoef[e];
-        double2 xd = vb[k];
-        xd = make_double2(vscale * xd.x, vscale * xd.y);
-        if (dinv) {
-          double2 d = dinv[k];
-          xd = make_double2(xd.x * d.x - xd.y * d.y, xd.x * d.y + xd.y * d.x);
-        }
-        const C xv = cvt<C>(xd);
+        const C xv = vb[k];
         a0 += (R)w.x * xv;
         a1 += (R)w.y * xv;
         a2 += (R)w.z * xv;
@@ -87,6 +75,33 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
     const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
     if (y < N) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
   }
+}
+
+// Operator input: x_b = scale_b(j) * dinv .* v_b (selection, Krylov scale and
+// preconditioner applied once), in the grid precision for the anterpolation gather
+// and in FP64 for the near-zone product.
+template <class C>
+__global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, const double2* __restrict__ dinv,
+                                              VecSel vs, const int* __restrict__ active, int ns, int nb,
+                                              C* __restrict__ xs, double2* __restrict__ xd) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nb * ns) return;
+  const int b = (int)(idx / ns), k = (int)(idx % ns);
+  if (active && !active[b]) return;
+  double sc = 1.0;
+  if (vs.sel) {
+    const int j = *vs.sel + vs.off;
+    v += j * vs.stride;
+    if (vs.scale) sc = vs.scale[b * 64 + j];
+  }
+  double2 x = v[idx];
+  x = make_double2(sc * x.x, sc * x.y);
+  if (dinv) {
+    const double2 d = dinv[k];
+    x = make_double2(x.x * d.x - x.y * d.y, x.x * d.y + x.y * d.x);
+  }
+  xs[idx] = cvt<C>(x);
+  if (xd) xd[idx] = x;
 }
 
 // ---------------------------------------------------------------- z pass with the kernel
@@ -114,16 +129,18 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
     b0[t] = v;
   }
   __syncthreads();
-  C* f = line_fft_cols<L, false, C>(b0, b1, W, tw);
+  C* f = line_fft_cols<L, W, false, C>(b0, b1, tw);
   const int n1 = N + 1;
   const C* G = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1;
   const int fy = fold(y, N);
-  for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
-    const int i = t / W, l = t % W;
-    f[t] = f[t] * G[((size_t)fold(i, N) * n1 + fy) * n1 + fold(x0 + l, N)];
+  {
+    static_assert(256 % W == 0, "tile width must divide the block");
+    const int l = threadIdx.x % W;
+    const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
+    for (int i = threadIdx.x / W; i < L; i += 256 / W) f[i * W + l] = f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
   }
   __syncthreads();
-  C* g = line_fft_cols<L, true, C>(f, f == b0 ? b1 : b0, W, tw);
+  C* g = line_fft_cols<L, W, true, C>(f, f == b0 ? b1 : b0, tw);
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int i = t / W, l = t % W;
     col[i * es + l] = g[t];
@@ -157,15 +174,16 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
       b0[t] = v;
     }
     __syncthreads();
-    C* f = line_fft_cols<L, false, C>(b0, b1, W, tw);
+    C* f = line_fft_cols<L, W, false, C>(b0, b1, tw);
     const C* G = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct;
-    for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
-      const int i = t / W, l = t % W;
-      acc[t] += f[t] * G[((size_t)fold(i, N) * n1 + fy) * n1 + fold(x0 + l, N)];
+    {
+      const int l = threadIdx.x % W;
+      const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
+      for (int i = threadIdx.x / W; i < L; i += 256 / W) acc[i * W + l] += f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
     }
   }
   __syncthreads();
-  C* g = line_fft_cols<L, true, C>(acc, b0, W, tw);
+  C* g = line_fft_cols<L, W, true, C>(acc, b0, tw);
   C* out = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     const int i = t / W, l = t % W;
@@ -192,15 +210,21 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
   if (active && !active[b]) return;
   double2 tot = make_double2(0, 0);
   if (P) {
+    // lane -> (component c, stencil row (dz, dy)): the row's 4 nodes are consecutive in
+    // x and its 4 coefficients one aligned 4-vector of the interpolation row
     const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
-    const R* lk = lam + (size_t)k * 256;
     const size_t N3 = (size_t)N * N * N;
     const C* Pb = P + (size_t)b * 4 * N3;
     C g{};
-    for (int s = lane; s < 64; s += 32) {
-      const size_t n = ((size_t)(az + (s >> 4)) * N + (ay + ((s >> 2) & 3))) * N + (ax + (s & 3));
-#pragma unroll
-      for (int c = 0; c < 4; ++c) g += lk[c * 64 + s] * Pb[c * N3 + n];
+    for (int q = lane; q < 64; q += 32) {
+      const int c = q >> 4, row = q & 15;
+      const int dz = row >> 2, dy = row & 3;
+      const typename Real<C>::F4 w = reinterpret_cast<const typename Real<C>::F4*>(lam + (size_t)k * 256 + c * 64)[row];
+      const C* pr = Pb + c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N + ax;
+      g += w.x * pr[0];
+      g += w.y * pr[1];
+      g += w.z * pr[2];
+      g += w.w * pr[3];
     }
     for (int o = 16; o > 0; o >>= 1) {
       g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
@@ -268,19 +292,31 @@ struct GridOps {
   static int rpb() { return std::max(1, 2048 / L); }
 
   // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
+  static void prep(aim_ctx* c, int nb, const double2* v, const double2* dinv, VecSel vs, const int* active,
+                   bool want_fp64) {
+    const long long n = (long long)nb * c->ns;
+    KScope ks(c, AIM_K_PREP);
+    k_prep<C><<<(int)((n + 255) / 256), 256, 0, c->stream>>>(v, dinv, vs, active, c->ns, nb,
+                                                            reinterpret_cast<C*>(c->d_xs),
+                                                            want_fp64 ? c->d_xd : nullptr);
+    AIM_CHECK_LAUNCH();
+  }
+
   static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab,
-                           VecSel vs = VecSel()) {
+                           VecSel vs = VecSel(), bool want_fp64 = false) {
     const int N = c->N;
     const C* tw = twiddles(c);
     C* A = reinterpret_cast<C*>(c->d_A);
+    prep(c, nb, v, dinv, vs, active, want_fp64);
     {
       const int yp = ypb();
       size_t sm = (L + 4 * yp * L + row_scratch<L>(4 * yp)) * sizeof(C);
       smem_opt_in(k_anterp_rows<L, C>, sm);
       dim3 grid((N + yp - 1) / yp, N, nb);
       KScope ks(c, AIM_K_ANTERP_XFFT);
-      k_anterp_rows<L, C><<<grid, 256, sm, c->stream>>>(c->d_nptr, c->d_nidx, ncoef(c), v, dinv, vs, active, c->ns,
-                                                        N, yp, A, tw);
+      k_anterp_rows<L, C><<<grid, 256, sm, c->stream>>>(c->d_nptr, c->d_nidx, ncoef(c),
+                                                        reinterpret_cast<const C*>(c->d_xs), active, c->ns, N, yp,
+                                                        A, tw);
       AIM_CHECK_LAUNCH();
     }
     {

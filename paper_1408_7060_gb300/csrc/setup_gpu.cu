@@ -18,22 +18,9 @@
 #include "fft_kernels.cuh"
 #include "setup_host.h"
 #include "setup_gpu.h"
+#include "tbasis.cuh"
 
 // ------------------------------------------------------------------ temporal basis
-
-__device__ __forceinline__ void cppif_eval(const TBasis& tb, double v, double T[4]) {
-  T[0] = T[1] = T[2] = T[3] = 0.0;
-  double jr = ceil(v);
-  if (jr < 0.0 || jr > (double)tb.Q) return;
-  const double* c = tb.coef[(int)jr];
-  const int Q = tb.Q;
-  double p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-  for (int p = Q; p >= 0; --p) p0 = p0 * v + c[p];
-  for (int p = Q; p >= 1; --p) p1 = p1 * v + p * c[p];
-  for (int p = Q; p >= 2; --p) p2 = p2 * v + p * (p - 1) * c[p];
-  for (int p = Q; p >= 3; --p) p3 = p3 * v + p * (p - 1) * (p - 2) * c[p];
-  T[0] = p0; T[1] = p1; T[2] = p2; T[3] = p3;
-}
 
 // f^A_m(R) = (D^2 T)(m - R/c dt) e^{-j k R},  f^phi_m(R) = T(m - R/c dt) e^{-j k R}
 // with (D^2 T)(u) = T''/dt^2 + 2 j w T'/dt - w^2 T (envelope derivative D = d/dt + j w)
@@ -592,6 +579,7 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
     }
     AIM_CUDA(cudaStreamSynchronize(st));
     c->h_rowptr = rowptr;
+    c->h_col = col;
   }
 }
 

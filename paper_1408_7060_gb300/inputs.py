@@ -85,15 +85,18 @@ def sphere_array(sub: int, radius: float, pitch: float, nx: int = 4, ny: int = 4
 
 
 def ellipsoid_mesh(semi_axes=(1.0, 0.5, 0.25), n_points: int = 6668, seed: int = 3,
-                   jitter: float = 0.25):
+                   jitter: float = 0.25, relax_iters: int = 60):
     """Closed ellipsoid surface from jittered Fibonacci-sphere samples.
 
-    The samples are mapped onto the ellipsoid and triangulated with a 3-D convex
-    hull (the surface Delaunay triangulation of a convex body).  Faces are oriented
+    The samples are mapped onto the ellipsoid, spread evenly by a short repulsion
+    relaxation on the surface (each point pushed away from its nearest neighbours,
+    then scaled back onto the ellipsoid), and triangulated with a 3-D convex hull
+    (the surface Delaunay triangulation of a convex body).  Faces are oriented
     outward.  ``E = 3 (V - 2)`` edges, i.e. about ``3 n_points`` RWG unknowns.
     """
-    from scipy.spatial import ConvexHull
+    from scipy.spatial import ConvexHull, cKDTree
 
+    ax = np.asarray(semi_axes, dtype=np.float64)
     rng = np.random.Generator(np.random.PCG64(seed))
     i = np.arange(n_points, dtype=np.float64) + 0.5
     i = i + jitter * (rng.random(n_points) - 0.5)
@@ -102,7 +105,19 @@ def ellipsoid_mesh(semi_axes=(1.0, 0.5, 0.25), n_points: int = 6668, seed: int =
     phi = phi + jitter * 0.5 * (rng.random(n_points) - 0.5)
     r = np.sqrt(np.clip(1.0 - z * z, 0.0, None))
     u = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
-    V = u * np.asarray(semi_axes, dtype=np.float64)
+    V = u * ax
+
+    def onto(P):
+        return P / np.sqrt(((P / ax) ** 2).sum(axis=1, keepdims=True))
+
+    for _ in range(relax_iters):
+        d, nb = cKDTree(V).query(V, k=7)
+        h = d[:, 1:].mean()
+        diff = V[:, None, :] - V[nb[:, 1:]]
+        dist = np.maximum(d[:, 1:, None], 1e-12)
+        push = (diff / dist ** 3).sum(axis=1)
+        step = 0.05 * h ** 3 * push
+        V = onto(V + step)
     hull = ConvexHull(V)
     F = _orient_outward(V, hull.simplices.astype(np.int32), np.zeros(3))
     return V, F.astype(np.int32)

@@ -263,3 +263,26 @@ def test_march_continue_resumes_exactly(s480):
         a, _, _ = c.march(w.khat, w.phat, w.sigma, w.t_d, 12, 1e-6)
         b, _, _ = c.march_continue(w.khat, w.phat, w.sigma, w.t_d, 18, 1e-6)
     assert np.array_equal(np.concatenate([a, b]), full)
+
+
+def test_matvec_n96_sampled():
+    """96^3 grid (padded length 192 = 8*8*3: the radix-3 passes) on the 1920-RWG
+    sphere, both precisions, sampled rows against direct grid sums."""
+    w = make_workload("sphere_sub3_n96")
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((1, rwg.ns)) + 1j * rng.standard_normal((1, rwg.ns))
+    rows = np.sort(rng.choice(rwg.ns, 10, replace=False))
+    for m in (0, 1):
+        ref = A.fft_part_rows(m, x[0], rows)
+        sel = np.isin(A.pairs[:, 0], rows)
+        pr = A.pairs[sel]
+        Zn = efie.fill_pairs(rwg, p, pr, m)[m] - A.fft_pairs(m, pr)
+        for (k, kp), z in zip(pr, Zn):
+            ref[np.searchsorted(rows, k)] += z * x[0, kp]
+        for prec, tol in (("c128", 1e-10), ("c64", 1e-5)):
+            with ctx_for(w, precision=prec) as c:
+                assert c.n_delays == A.n_delays
+                assert rel(c.matvec(m, x)[0][rows], ref) < tol, (m, prec)
