@@ -67,7 +67,7 @@ class AimOracle:
         ijk = self.anchor[:, None, :] + off[None]
         return (ijk[..., 2] * n + ijk[..., 1]) * n + ijk[..., 0]
 
-    def _moment_matching(self, nq: int = 8):
+    def _moment_matching(self, nq: int = 8, chunk: int = 8192):
         rwg = self.rwg
         bary, w = quad.collapsed_gauss(nq)
         d = np.arange(4)
@@ -76,19 +76,21 @@ class AimOracle:
         # Vandermonde V[a, n] = prod xi_n^a with xi_n in {0..3}^3 (same ordering)
         Vm = np.prod(alpha[None, :, :].astype(float) ** alpha[:, None, :], axis=2)  # [a, n]
         lam = np.zeros((4, rwg.ns, 64))
-        for side, sign in ((0, 1.0), (1, -1.0)):
-            t = rwg.tri[:, side]
-            P = quad.points(rwg.V, rwg.F[t], bary)                  # [ns,nq,3]
-            W = w[None, :] * rwg.area[t][:, None]
-            vf = rwg.V[rwg.free[:, side]]
-            S = sign * (rwg.length / (2 * rwg.area[t]))[:, None, None] * (P - vf[:, None, :])
-            div = sign * rwg.length / rwg.area[t]
-            r_a = self.origin[None, :] + self.h * self.anchor             # [ns,3]
-            xi = (P - r_a[:, None, :]) / self.h                           # [ns,nq,3]
-            mono = np.prod(xi[:, :, None, :] ** alpha[None, None], axis=3)  # [ns,nq,64]
-            for c in range(3):
-                lam[c] += np.einsum("kq,kq,kqa->ka", W, S[..., c], mono)
-            lam[3] += np.einsum("kq,k,kqa->ka", W, div, mono)
+        for k0 in range(0, rwg.ns, chunk):
+            ks = slice(k0, min(rwg.ns, k0 + chunk))
+            for side, sign in ((0, 1.0), (1, -1.0)):
+                t = rwg.tri[ks, side]
+                P = quad.points(rwg.V, rwg.F[t], bary)                  # [nk,nq,3]
+                W = w[None, :] * rwg.area[t][:, None]
+                vf = rwg.V[rwg.free[ks, side]]
+                S = sign * (rwg.length[ks] / (2 * rwg.area[t]))[:, None, None] * (P - vf[:, None, :])
+                div = sign * rwg.length[ks] / rwg.area[t]
+                r_a = self.origin[None, :] + self.h * self.anchor[ks]     # [nk,3]
+                xi = (P - r_a[:, None, :]) / self.h                       # [nk,nq,3]
+                mono = np.prod(xi[:, :, None, :] ** alpha[None, None], axis=3)  # [nk,nq,64]
+                for c in range(3):
+                    lam[c, ks] += np.einsum("kq,kq,kqa->ka", W, S[..., c], mono)
+                lam[3, ks] += np.einsum("kq,k,kqa->ka", W, div, mono)
         # solve V lam = moments per RWG and component
         sol = np.linalg.solve(Vm, lam.reshape(-1, 64).T).T
         return sol.reshape(4, rwg.ns, 64)
@@ -103,9 +105,17 @@ class AimOracle:
     # ------------------------------------------------------------------ kernels
     def _n_delays_grid(self):
         """N_g = floor(R_max/(c dt) + Q), R_max the largest distance between two
-        stencil nodes (a reading of the N_g formula after Eq. 4).  The squared
-        integer distances |a|^2 + |b|^2 - 2 a.b are exact in FP64 for these grids."""
+        stencil nodes (a reading of the N_g formula after Eq. 4).  The farthest pair
+        of a point set lies on its convex hull, so large sets are first reduced to the
+        hull's vertices (scipy); squared integer distances are exact in FP64."""
         ijk = self.node_ijk(self.active).astype(np.float64)
+        if len(ijk) > 20000:
+            from scipy.spatial import ConvexHull
+
+            try:
+                ijk = ijk[ConvexHull(ijk).vertices]
+            except Exception:
+                pass
         sq = (ijk * ijk).sum(1)
         best = 0.0
         for i in range(0, len(ijk), 4096):
@@ -132,17 +142,40 @@ class AimOracle:
     def conv_direct(self, m: int, src: np.ndarray, kind: int, targets=None, chunk: int = 2048):
         """P[n] = sum_{n'} G_m(n - n') src[n'] over source nodes where src != 0.
         ``src`` is [N^3]; ``kind`` 0 = G^A, 1 = G^phi.  Returns P at ``targets``
-        (default: every node)."""
+        (default: every node).  G depends on |D_x|, |D_y|, |D_z| only; large grids
+        look it up in a table of those offsets."""
         srcn = np.nonzero(src)[0]
         sv = src[srcn]
         sijk = self.node_ijk(srcn)
         tgt = np.arange(self.n ** 3) if targets is None else np.asarray(targets)
         tijk = self.node_ijk(tgt)
         out = np.zeros(len(tgt), dtype=complex)
+        tab = self._kernel_table(m, kind) if self.n > 64 else None
+        schunk = max(1, (1 << 24) // max(1, min(chunk, len(tgt))))
         for i in range(0, len(tgt), chunk):
-            G = self.kernel_values(m, tijk[i:i + chunk, None, :] - sijk[None, :, :])[kind]
-            out[i:i + chunk] = G @ sv
+            for j in range(0, len(srcn), schunk):
+                d = tijk[i:i + chunk, None, :] - sijk[None, j:j + schunk, :]
+                if tab is None:
+                    G = self.kernel_values(m, d)[kind]
+                else:
+                    d = np.abs(d)
+                    G = tab[d[..., 2], d[..., 1], d[..., 0]]
+                out[i:i + chunk] += G @ sv[j:j + schunk]
         return out
+
+    def _kernel_table(self, m: int, kind: int) -> np.ndarray:
+        key = (m, kind)
+        if not hasattr(self, "_tabs"):
+            self._tabs = {}
+        if key not in self._tabs:
+            r = np.arange(self.n)
+            tab = np.empty((self.n, self.n, self.n), dtype=complex)
+            for z in range(self.n):
+                ty, tx = np.meshgrid(r, r, indexing="ij")
+                off = np.stack([tx, ty, np.full_like(tx, z)], axis=-1)
+                tab[z] = self.kernel_values(m, off)[kind]
+            self._tabs[key] = tab
+        return self._tabs[key]
 
     def kernel_grid(self, m: int, kind: int) -> np.ndarray:
         """G_m embedded even-symmetrically in the (2N)^3 padded grid (index N unused)."""
@@ -230,17 +263,29 @@ class AimOracle:
 
     # ------------------------------------------------------------------ near zone
     def _near_pairs(self):
+        """Pairs with |x_e(k) - x_e(k')|^2 <= r^2 (inclusive), sorted by (k, k').
+        Large meshes take candidates from a k-d tree with a slightly larger radius; the
+        decision is always the same squared-distance comparison."""
         xe = self.rwg.midpoint()
         if self.near_radius < 0:
             return np.zeros((0, 2), dtype=np.int64)
         r2 = self.near_radius * self.near_radius
-        out = []
-        for i in range(0, len(xe), 1024):
-            d = xe[i:i + 1024, None, :] - xe[None, :, :]
-            d2 = d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1] + d[..., 2] * d[..., 2]
-            a, b = np.nonzero(d2 <= r2)
-            out.append(np.stack([a + i, b], axis=1))
-        pr = np.concatenate(out) if out else np.zeros((0, 2), dtype=np.int64)
+        if len(xe) > 20000:
+            from scipy.spatial import cKDTree
+
+            cand = cKDTree(xe).query_pairs(self.near_radius * (1 + 1e-6) + 1e-12, output_type="ndarray")
+            cand = np.concatenate([cand, cand[:, ::-1], np.stack([np.arange(len(xe))] * 2, axis=1)])
+            d = xe[cand[:, 0]] - xe[cand[:, 1]]
+            d2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+            pr = cand[d2 <= r2].astype(np.int64)
+        else:
+            out = []
+            for i in range(0, len(xe), 1024):
+                d = xe[i:i + 1024, None, :] - xe[None, :, :]
+                d2 = d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1] + d[..., 2] * d[..., 2]
+                a, b = np.nonzero(d2 <= r2)
+                out.append(np.stack([a + i, b], axis=1))
+            pr = np.concatenate(out) if out else np.zeros((0, 2), dtype=np.int64)
         order = np.lexsort((pr[:, 1], pr[:, 0]))
         return pr[order]
 

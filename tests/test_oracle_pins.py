@@ -379,3 +379,22 @@ def test_n_delays(s480_aim, s480):
     # the active set of a sphere spans its bounding box diagonal or less
     assert A.n_delays <= math.floor(A.h * np.linalg.norm(hi - lo) / (C0 * w.dt) + 2)
     assert A.n_delays >= math.floor(A.h * (hi - lo).max() / (C0 * w.dt) + 2)
+
+
+def test_direct_sum_offset_table_large_grid():
+    """On grids above 64^3 the direct sum looks G up by |offset|; it must equal the
+    kernel evaluated at the signed offsets."""
+    w = make_workload("sphere_sub1_n96", f_c=150e6)
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=2)
+    A = aim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    rng = np.random.default_rng(4)
+    src = np.zeros(A.n ** 3, dtype=complex)
+    idx = rng.choice(A.n ** 3, 200, replace=False)
+    src[idx] = rng.standard_normal(200) + 1j * rng.standard_normal(200)
+    tg = rng.choice(A.n ** 3, 50, replace=False)
+    for kind in (0, 1):
+        got = A.conv_direct(1, src, kind, targets=tg)
+        d = A.node_ijk(tg)[:, None, :] - A.node_ijk(idx)[None, :, :]
+        ref = A.kernel_values(1, d)[kind] @ src[idx]
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
