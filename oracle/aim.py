@@ -103,13 +103,13 @@ class AimOracle:
         return sp.csr_matrix((self.lam[c].ravel(), (rows, cols)), shape=(self.n ** 3, ns))
 
     # ------------------------------------------------------------------ kernels
-    def _n_delays_grid(self):
+    def _n_delays_grid(self, hull_above: int = 20000):
         """N_g = floor(R_max/(c dt) + Q), R_max the largest distance between two
         stencil nodes (a reading of the N_g formula after Eq. 4).  The farthest pair
         of a point set lies on its convex hull, so large sets are first reduced to the
         hull's vertices (scipy); squared integer distances are exact in FP64."""
         ijk = self.node_ijk(self.active).astype(np.float64)
-        if len(ijk) > 20000:
+        if len(ijk) > hull_above:
             from scipy.spatial import ConvexHull
 
             try:
@@ -262,7 +262,7 @@ class AimOracle:
         return out
 
     # ------------------------------------------------------------------ near zone
-    def _near_pairs(self):
+    def _near_pairs(self, tree_above: int = 20000):
         """Pairs with |x_e(k) - x_e(k')|^2 <= r^2 (inclusive), sorted by (k, k').
         Large meshes take candidates from a k-d tree with a slightly larger radius; the
         decision is always the same squared-distance comparison."""
@@ -270,7 +270,7 @@ class AimOracle:
         if self.near_radius < 0:
             return np.zeros((0, 2), dtype=np.int64)
         r2 = self.near_radius * self.near_radius
-        if len(xe) > 20000:
+        if len(xe) > tree_above:
             from scipy.spatial import cKDTree
 
             cand = cKDTree(xe).query_pairs(self.near_radius * (1 + 1e-6) + 1e-12, output_type="ndarray")

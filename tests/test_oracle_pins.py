@@ -398,3 +398,11 @@ def test_direct_sum_offset_table_large_grid():
         d = A.node_ijk(tg)[:, None, :] - A.node_ijk(idx)[None, :, :]
         ref = A.kernel_values(1, d)[kind] @ src[idx]
         assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_setup_shortcuts_match_plain(s480_aim):
+    """The convex-hull reduction for N_g and the k-d tree prefilter of the near pairs
+    (taken on large meshes) give what the plain all-pairs scans give."""
+    A = s480_aim
+    assert A._n_delays_grid(hull_above=0) == A._n_delays_grid(hull_above=10 ** 9)
+    assert np.array_equal(A._near_pairs(tree_above=0), A._near_pairs(tree_above=10 ** 9))
