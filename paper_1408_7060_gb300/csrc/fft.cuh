@@ -196,14 +196,16 @@ __host__ __device__ constexpr int split_r1(int L) {
 }
 
 // Column tile: W lines, element i of line l at a[i*W + l].  Result in natural order in a.
-template <int L, int W, bool INV, class C>
+// HALF_IN: only the first L/2 samples are nonzero (zero padding), so step A reads
+// n1 < R1/2 and the zero half is folded out of the radix-R1 butterfly.
+template <int L, int W, bool INV, class C, bool HALF_IN = false>
 __device__ __forceinline__ void col_fft2(C* a, C* tmp, const C* __restrict__ tw) {
   constexpr int R1 = split_r1(L), R2 = L / R1;
   for (int u = threadIdx.x; u < W * R2; u += blockDim.x) {
     const int l = u % W, n2 = u / W;
     C v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = a[(R2 * n1 + n2) * W + l];
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = (HALF_IN && n1 >= R1 / 2) ? C{} : a[(R2 * n1 + n2) * W + l];
     DFT<R1, INV, C>::run(v);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
@@ -233,14 +235,14 @@ __device__ __forceinline__ void col_fft2(C* a, C* tmp, const C* __restrict__ tw)
 template <int L> __host__ __device__ constexpr int row_tmp_pitch() {
   return split_r1(L) * (L / split_r1(L) + 1);
 }
-template <int L, bool INV, class C>
+template <int L, bool INV, class C, bool HALF_IN = false>
 __device__ __forceinline__ void row_fft2(C* a, C* tmp, int nl, const C* __restrict__ tw) {
   constexpr int R1 = split_r1(L), R2 = L / R1, P = row_tmp_pitch<L>();
   for (int u = threadIdx.x; u < nl * R2; u += blockDim.x) {
     const int n2 = u % R2, r = u / R2;
     C v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = a[r * L + R2 * n1 + n2];
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = (HALF_IN && n1 >= R1 / 2) ? C{} : a[r * L + R2 * n1 + n2];
     DFT<R1, INV, C>::run(v);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {

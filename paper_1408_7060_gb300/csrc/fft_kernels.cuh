@@ -68,7 +68,60 @@ __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __res
   }
 }
 
-template <int L, int W, bool INV, class C>
+// Power-of-two L = R1 * R2 rows without staging copies: thread (r, n2) reads inputs
+// R2 n1 + n2 < n_in of row r straight from memory, radix-R1 butterfly, twiddle, one
+// exchange through the padded tile; thread (r, k1) runs the radix-R2 butterfly and
+// stores outputs k1 + R1 k2 < n_out straight to memory.  256 threads, rpb rows.
+template <int L, bool INV, class C>
+__global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __restrict__ out, int nrows,
+                                                 int n_in, int n_out, long long rs_in, long long rs_out,
+                                                 const C* __restrict__ twg, int rpb) {
+  constexpr int R1 = split_r1(L), R2 = L / R1, P = row_tmp_pitch<L>();
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* t = tw + L;
+  load_twiddles(tw, twg, L);
+  __syncthreads();
+  const int r0 = blockIdx.x * rpb;
+  const int nr = min(rpb, nrows - r0);
+  for (int u = threadIdx.x; u < nr * R2; u += 256) {
+    const int n2 = u % R2, r = u / R2;
+    const C* src = in + (long long)(r0 + r) * rs_in;
+    C v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int i = R2 * n1 + n2;
+      v[n1] = i < n_in ? src[i] : C{};
+    }
+    DFT<R1, INV, C>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C x = v[k1];
+      if (k1 && n2) {
+        const C w = tw[n2 * k1];
+        x = x * (INV ? conjc(w) : w);
+      }
+      t[r * P + k1 * (R2 + 1) + n2] = x;
+    }
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < nr * R1; u += 256) {
+    const int k1 = u % R1, r = u / R1;
+    C* dst = out + (long long)(r0 + r) * rs_out;
+    C v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[r * P + k1 * (R2 + 1) + n2];
+    DFT<R2, INV, C>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = k1 + R1 * k2;
+      if (k < n_out) dst[k] = v[k2];
+    }
+  }
+}
+
+// HALF: the input is the first L/2 samples (pruned zero padding, n_in = L/2), read
+// without the zero half.
+template <int L, int W, bool INV, class C, bool HALF = false>
 __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __restrict__ out, int n_in,
                                               int n_out, long long es_in, long long es_out, int nx,
                                               long long ps1_in, long long ps1_out, long long ps2_in,
@@ -81,18 +134,85 @@ __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __res
   const int nw = min(W, nx - x0);
   const C* src = in + blockIdx.z * ps2_in + blockIdx.y * ps1_in + x0;
   C* dst = out + blockIdx.z * ps2_out + blockIdx.y * ps1_out + x0;
-  for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
+  constexpr bool half = HALF && pow2_len(L);
+  const int rows = half ? L / 2 : L;
+  for (int t = threadIdx.x; t < rows * W; t += blockDim.x) {
     int i = t / W, l = t % W;
     C v = mkc((decltype(C().x))0, (decltype(C().x))0);
     if (i < n_in && l < nw) v = src[i * es_in + l];
     b0[t] = v;
   }
   __syncthreads();
-  C* res = line_fft_cols<L, W, INV, C>(b0, b1, tw);
+  C* res;
+  if constexpr (half) {
+    col_fft2<L, W, INV, C, true>(b0, b1, tw);
+    res = b0;
+  } else {
+    res = line_fft_cols<L, W, INV, C>(b0, b1, tw);
+  }
   for (int t = threadIdx.x; t < n_out * W; t += blockDim.x) {
     int i = t / W, l = t % W;
     if (l < nw) dst[i * es_out + l] = res[t];
   }
+}
+
+// Power-of-two L = R1 * R2 without staging copies: thread (l, n2) reads its R1 inputs
+// i = R2 n1 + n2 straight from memory (HALF: n1 < R1/2 only), radix-R1 butterfly,
+// twiddle, one exchange through t[(k1 R2 + n2) W + l]; thread (l, k1) runs the
+// radix-R2 butterfly and stores the outputs k1 + R1 k2 < n_out straight to memory.
+// 256 threads; tile t of L x W elements after the L twiddles.
+template <int L, int W, bool INV, class C, bool HALF = false>
+__global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __restrict__ out, int n_in,
+                                                 int n_out, long long es_in, long long es_out, int nx,
+                                                 long long ps1_in, long long ps1_out, long long ps2_in,
+                                                 long long ps2_out, const C* __restrict__ twg) {
+  constexpr int R1 = split_r1(L), R2 = L / R1;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* t = tw + L;
+  load_twiddles(tw, twg, L);
+  __syncthreads();
+  const int x0 = blockIdx.x * W;
+  const int nw = min(W, nx - x0);
+  const C* src = in + blockIdx.z * ps2_in + blockIdx.y * ps1_in + x0;
+  C* dst = out + blockIdx.z * ps2_out + blockIdx.y * ps1_out + x0;
+  for (int u = threadIdx.x; u < W * R2; u += 256) {
+    const int l = u % W, n2 = u / W;
+    C v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int i = R2 * n1 + n2;
+      v[n1] = ((!HALF || n1 < R1 / 2) && i < n_in && l < nw) ? src[(long long)i * es_in + l] : C{};
+    }
+    DFT<R1, INV, C>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C x = v[k1];
+      if (k1 && n2) {
+        const C w = tw[n2 * k1];
+        x = x * (INV ? conjc(w) : w);
+      }
+      t[(k1 * R2 + n2) * W + l] = x;
+    }
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < W * R1; u += 256) {
+    const int l = u % W, k1 = u / W;
+    C v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[(k1 * R2 + n2) * W + l];
+    DFT<R2, INV, C>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = k1 + R1 * k2;
+      if (k < n_out && l < nw) dst[(long long)k * es_out + l] = v[k2];
+    }
+  }
+}
+
+// tile width of the direct power-of-two column passes (one L x W tile)
+template <int L, class C>
+constexpr int col_width_p2() {
+  return (int)sizeof(C) == 8 ? (L < 32 ? L : 32) : (L < 16 ? L : 16);
 }
 
 // tile width of a column pass: keep 2 (or 3) L x W buffers within ~160 KB

@@ -65,12 +65,19 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
     b0[(2 * ypb + yy) * L + x] = a2;
     b0[(3 * ypb + yy) * L + x] = a3;
   }
-  for (int t = threadIdx.x; t < 4 * ypb * (L - N); t += blockDim.x) {
-    const int row = t / (L - N), x = N + t % (L - N);
-    b0[row * L + x] = C{};
+  C* res;
+  if constexpr (pow2_len(L)) {  // the padding half is never read
+    __syncthreads();
+    row_fft2<L, false, C, true>(b0, b1, 4 * ypb, tw);
+    res = b0;
+  } else {
+    for (int t = threadIdx.x; t < 4 * ypb * (L - N); t += blockDim.x) {
+      const int row = t / (L - N), x = N + t % (L - N);
+      b0[row * L + x] = C{};
+    }
+    __syncthreads();
+    res = line_fft_rows<L, false, C>(b0, b1, 4 * ypb, tw);
   }
-  __syncthreads();
-  C* res = line_fft_rows<L, false, C>(b0, b1, 4 * ypb, tw);
   for (int t = threadIdx.x; t < 4 * ypb * L; t += blockDim.x) {
     const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
     if (y < N) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
@@ -107,9 +114,123 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
 // ---------------------------------------------------------------- z pass with the kernel
 __device__ __forceinline__ int fold(int k, int N) { return k <= N ? k : 2 * N - k; }
 
+// Power-of-two L = R1 * R2, one tile of W adjacent z-columns per block, a single
+// shared exchange tile t[(k1 R2 + n2) W + l]:
+//   A  thread (l, n2): the N = L/2 nonzero samples z = R2 n1 + n2 (n1 < R1/2) come
+//      straight from memory, radix-R1 butterfly, twiddle W_L^{n2 k1}, into t;
+//   B  thread (l, k1): its R2 values of t, radix-R2 butterfly -> X[k1 + R1 k2] in
+//      registers; product with the kernel spectrum; inverse radix-R2 butterfly,
+//      twiddle W_L^{-k1 n2}, back into the same slots of t (a thread reads and writes
+//      only its own (k1, l) slice, so B needs no barrier inside);
+//   C  thread (l, n2): inverse radix-R1 butterfly over k1, the outputs
+//      z = n2 + R2 n1 < N stored straight to memory.
+// A column's data cross shared memory twice instead of once per pass.
+// radix split of the z pass: for L = 128 the 16 x 8 split keeps the step-B registers
+// (operands and spectrum slice) at 8 complex values each
+template <int L>
+constexpr int zsplit_r1() {
+  return L == 128 ? 16 : split_r1(L);
+}
+template <int L, class C>
+constexpr int zcol_width() {
+  return (int)sizeof(C) == 8 ? (L < 32 ? L : 32) : (L < 16 ? L : 16);
+}
+constexpr int kZThreads = 256;
+
+template <int L, int W, class C>
+__device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long es, C* t, const C* tw) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+  for (int u = threadIdx.x; u < W * R2; u += kZThreads) {
+    const int l = u % W, n2 = u / W;
+    C v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = n1 < R1 / 2 ? col[(long long)(R2 * n1 + n2) * es + l] : C{};
+    DFT<R1, false, C>::run(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C x = v[k1];
+      if (k1 && n2) x = x * tw[n2 * k1];
+      t[(k1 * R2 + n2) * W + l] = x;
+    }
+  }
+}
+
+// the spectrum X[k1 + R1 k2] of column l from t (after step A and a barrier)
+template <int L, int W, class C>
+__device__ __forceinline__ void zcol_step_b_fwd(const C* t, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[(k1 * R2 + n2) * W + l];
+  DFT<R2, false, C>::run(v);
+  (void)R1;
+}
+
+// inverse radix-R2 butterfly of a spectrum slice, twiddled back into t
+template <int L, int W, class C>
+__device__ __forceinline__ void zcol_step_b_inv(C* t, const C* tw, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+  DFT<R2, true, C>::run(v);
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    C x = v[n2];
+    if (k1 && n2) x = x * conjc(tw[n2 * k1]);
+    t[(k1 * R2 + n2) * W + l] = x;
+  }
+  (void)R1;
+}
+
+template <int L, int W, class C>
+__device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restrict__ col, long long es) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+  for (int u = threadIdx.x; u < W * R2; u += kZThreads) {
+    const int l = u % W, n2 = u / W;
+    C v[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = t[(k1 * R2 + n2) * W + l];
+    DFT<R1, true, C>::run(v);
+#pragma unroll
+    for (int n1 = 0; n1 < R1 / 2; ++n1) col[(long long)(n2 + R2 * n1) * es + l] = v[n1];
+  }
+  (void)tw;
+}
+
 // Forward z-FFT of the slab column, product with the kernel spectrum of delay m
 // (G^A for c = x,y,z; G^phi for c = div; even-symmetric octant), inverse z-FFT,
 // first N outputs written back in place.
+template <int L, int W, class C>
+__global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
+                                                        const int* __restrict__ active,
+                                                        const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+  const int bc = blockIdx.z;
+  if (active && !active[bc >> 2]) return;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* t = tw + L;
+  load_twiddles(tw, twg, L);
+  __syncthreads();
+  const int y = blockIdx.y, x0 = blockIdx.x * W;
+  const long long es = (long long)L * L;
+  C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
+  const int n1 = N + 1;
+  const C* Gy = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1 + (size_t)fold(y, N) * n1;
+  zcol_step_a<L, W, C>(col, es, t, tw);
+  __syncthreads();
+  for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
+    const int l = u % W, k1 = u / W;
+    const C* G = Gy + fold(x0 + l, N);
+    C g[R2], v[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
+    zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = v[k2] * g[k2];
+    zcol_step_b_inv<L, W, C>(t, tw, k1, l, v);
+  }
+  __syncthreads();
+  zcol_step_c<L, W, C>(t, tw, col, es);
+}
+
+// Lengths with a factor 3: staged tile, Stockham passes, separate product loop.
 template <int L, int W, class C>
 __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
                                                const int* __restrict__ active, const C* __restrict__ twg) {
@@ -122,6 +243,8 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
   const int y = blockIdx.y, x0 = blockIdx.x * W;
   const long long es = (long long)L * L;
   C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
+  const int n1 = N + 1;
+  const C* G = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1;
   for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
     const int i = t / W, l = t % W;
     C v{};
@@ -130,11 +253,8 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
   }
   __syncthreads();
   C* f = line_fft_cols<L, W, false, C>(b0, b1, tw);
-  const int n1 = N + 1;
-  const C* G = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1;
   const int fy = fold(y, N);
   {
-    static_assert(256 % W == 0, "tile width must divide the block");
     const int l = threadIdx.x % W;
     const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
     for (int i = threadIdx.x / W; i < L; i += 256 / W) f[i * W + l] = f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
@@ -149,6 +269,58 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
 
 // Delay sum of the right-hand side in the spectral domain:
 //   P^_col = sum_i G^_{m_i} . FFT_z(slab_i column), then one inverse z-FFT.
+// Power-of-two L: steps A and B per slab, the sum kept in registers of the step-B
+// threads, then one inverse (B, C).
+template <int L, int W, class C>
+__global__ void __launch_bounds__(kZThreads) k_zrhs_p2(SlabList sl, const C* __restrict__ kspec_all, int N,
+                                                       C* __restrict__ Bf, const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* t = tw + L;
+  load_twiddles(tw, twg, L);
+  const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
+  const long long es = (long long)L * L;
+  const int n1 = N + 1;
+  const size_t oct = (size_t)n1 * n1 * n1;
+  const int kind = (bc & 3) == 3 ? 1 : 0;
+  const int fy = fold(y, N);
+  C acc[U][R2];
+#pragma unroll
+  for (int j = 0; j < U; ++j)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
+  for (int s = 0; s < sl.n; ++s) {
+    const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
+    const C* Gy = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct + (size_t)fy * n1;
+    __syncthreads();  // twiddles published; the previous slab's step B is done with t
+    zcol_step_a<L, W, C>(col, es, t, tw);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = threadIdx.x + j * kZThreads;
+      if (u < W * R1) {
+        const int l = u % W, k1 = u / W;
+        const C* G = Gy + fold(x0 + l, N);
+        C g[R2], v[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
+        zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * g[k2];
+      }
+    }
+  }
+  __syncthreads();  // every step-B read of t is done (also orders the sl.n == 0 case)
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int u = threadIdx.x + j * kZThreads;
+    if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
+  }
+  __syncthreads();
+  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
+}
+
+// Lengths with a factor 3.
 template <int L, int W, class C>
 __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__ kspec_all, int N,
                                               C* __restrict__ Bf, const C* __restrict__ twg) {
@@ -166,6 +338,7 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
   for (int t = threadIdx.x; t < L * W; t += blockDim.x) acc[t] = C{};
   for (int s = 0; s < sl.n; ++s) {
     const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
+    const C* G = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct;
     __syncthreads();
     for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
       const int i = t / W, l = t % W;
@@ -175,12 +348,9 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
     }
     __syncthreads();
     C* f = line_fft_cols<L, W, false, C>(b0, b1, tw);
-    const C* G = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct;
-    {
-      const int l = threadIdx.x % W;
-      const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
-      for (int i = threadIdx.x / W; i < L; i += 256 / W) acc[i * W + l] += f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
-    }
+    const int l = threadIdx.x % W;
+    const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
+    for (int i = threadIdx.x / W; i < L; i += 256 / W) acc[i * W + l] += f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
   }
   __syncthreads();
   C* g = line_fft_cols<L, W, true, C>(acc, b0, tw);
@@ -210,21 +380,19 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
   if (active && !active[b]) return;
   double2 tot = make_double2(0, 0);
   if (P) {
-    // lane -> (component c, stencil row (dz, dy)): the row's 4 nodes are consecutive in
-    // x and its 4 coefficients one aligned 4-vector of the interpolation row
+    // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node) terms
+    // of an RWG take 8 warp loads of 8 rows x 32 B each, coefficients contiguous
     const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
     const size_t N3 = (size_t)N * N * N;
-    const C* Pb = P + (size_t)b * 4 * N3;
+    const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
+    const R* lk = lam + (size_t)k * 256 + lane;
     C g{};
-    for (int q = lane; q < 64; q += 32) {
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int q = it * 8 + (lane >> 2);  // (component, row) pair, 0..63
       const int c = q >> 4, row = q & 15;
       const int dz = row >> 2, dy = row & 3;
-      const typename Real<C>::F4 w = reinterpret_cast<const typename Real<C>::F4*>(lam + (size_t)k * 256 + c * 64)[row];
-      const C* pr = Pb + c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N + ax;
-      g += w.x * pr[0];
-      g += w.y * pr[1];
-      g += w.z * pr[2];
-      g += w.w * pr[3];
+      g += lk[it * 32] * Pb[c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N];
     }
     for (int o = 16; o > 0; o >>= 1) {
       g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
@@ -320,12 +488,19 @@ struct GridOps {
       AIM_CHECK_LAUNCH();
     }
     {
-      size_t sm = (L + 2 * L * W) * sizeof(C);
-      smem_opt_in(k_cols<L, W, false, C>, sm);
-      dim3 grid(L / W, N, nb * 4);
       KScope ks(c, AIM_K_YFFT_FWD);
-      k_cols<L, W, false, C><<<grid, 256, sm, c->stream>>>(A, slab, N, L, L, L, L, (long long)N * L, (long long)L * L,
-                                                           (long long)N * N * L, (long long)N * L * L, tw);
+      if constexpr (pow2_len(L)) {
+        constexpr int CW = col_width_p2<L, C>();
+        const size_t sm = (L + L * CW) * sizeof(C);
+        smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
+        k_cols_p2<L, CW, false, C, true><<<dim3(L / CW, N, nb * 4), 256, sm, c->stream>>>(
+            A, slab, N, L, L, L, L, (long long)N * L, (long long)L * L, (long long)N * N * L, (long long)N * L * L, tw);
+      } else {
+        const size_t sm = (L + 2 * L * W) * sizeof(C);
+        smem_opt_in(k_cols<L, W, false, C, true>, sm);
+        k_cols<L, W, false, C, true><<<dim3(L / W, N, nb * 4), 256, sm, c->stream>>>(
+            A, slab, N, L, L, L, L, (long long)N * L, (long long)L * L, (long long)N * N * L, (long long)N * L * L, tw);
+      }
       AIM_CHECK_LAUNCH();
     }
   }
@@ -339,21 +514,35 @@ struct GridOps {
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     C* P = reinterpret_cast<C*>(c->d_P);
     {
-      size_t sm = (L + 2 * L * W) * sizeof(C);
-      smem_opt_in(k_cols<L, W, true, C>, sm);
-      dim3 grid(L / W, N, nb * 4);
       KScope ks(c, AIM_K_YFFT_INV);
-      k_cols<L, W, true, C><<<grid, 256, sm, c->stream>>>(Bf, A, L, N, L, L, L, (long long)L * L, (long long)N * L,
-                                                          (long long)N * L * L, (long long)N * N * L, tw);
+      if constexpr (pow2_len(L)) {
+        constexpr int CW = col_width_p2<L, C>();
+        const size_t sm = (L + L * CW) * sizeof(C);
+        smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
+        k_cols_p2<L, CW, true, C><<<dim3(L / CW, N, nb * 4), 256, sm, c->stream>>>(
+            Bf, A, L, N, L, L, L, (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, tw);
+      } else {
+        const size_t sm = (L + 2 * L * W) * sizeof(C);
+        smem_opt_in(k_cols<L, W, true, C>, sm);
+        k_cols<L, W, true, C><<<dim3(L / W, N, nb * 4), 256, sm, c->stream>>>(
+            Bf, A, L, N, L, L, L, (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, tw);
+      }
       AIM_CHECK_LAUNCH();
     }
     {
-      const int rp = rpb();
-      size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(C);
-      smem_opt_in(k_rows<L, true, C>, sm);
       const int nrows = nb * 4 * N * N;
       KScope ks(c, AIM_K_XFFT_INV);
-      k_rows<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
+      if constexpr (pow2_len(L)) {
+        const int rp = std::max(1, 4096 / L);
+        const size_t sm = (L + rp * row_tmp_pitch<L>()) * sizeof(C);
+        smem_opt_in(k_rows_p2<L, true, C>, sm);
+        k_rows_p2<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
+      } else {
+        const int rp = rpb();
+        const size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(C);
+        smem_opt_in(k_rows<L, true, C>, sm);
+        k_rows<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
+      }
       AIM_CHECK_LAUNCH();
     }
     interp(c, nb, P, nl, base, sign, active, y, ys);
@@ -370,23 +559,37 @@ struct GridOps {
 
   static void zconv(aim_ctx* c, int nb, int m, const int* active) {
     const int N = c->N;
-    size_t sm = (L + 2 * L * W) * sizeof(C);
-    smem_opt_in(k_zconv<L, W, C>, sm);
-    dim3 grid(L / W, L, nb * 4);
     const size_t oct = (size_t)(N + 1) * (N + 1) * (N + 1);
+    C* Bf = reinterpret_cast<C*>(c->d_Bf);
+    const C* G = kspec(c) + (size_t)m * 2 * oct;
     KScope ks(c, AIM_K_ZCONV);
-    k_zconv<L, W, C><<<grid, 256, sm, c->stream>>>(reinterpret_cast<C*>(c->d_Bf), kspec(c) + (size_t)m * 2 * oct, N,
-                                                   active, twiddles(c));
+    if constexpr (pow2_len(L)) {
+      constexpr int ZW = zcol_width<L, C>();
+      const size_t sm = (L + L * ZW) * sizeof(C);
+      smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
+      k_zconv_p2<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(Bf, G, N, active, twiddles(c));
+    } else {
+      const size_t sm = (L + 2 * L * W) * sizeof(C);
+      smem_opt_in(k_zconv<L, W, C>, sm);
+      k_zconv<L, W, C><<<dim3(L / W, L, nb * 4), 256, sm, c->stream>>>(Bf, G, N, active, twiddles(c));
+    }
     AIM_CHECK_LAUNCH();
   }
 
   static void zrhs(aim_ctx* c, int nb, const SlabList& sl) {
     const int N = c->N;
-    size_t sm = (L + 3 * L * W) * sizeof(C);
-    smem_opt_in(k_zrhs<L, W, C>, sm);
-    dim3 grid(L / W, L, nb * 4);
+    C* Bf = reinterpret_cast<C*>(c->d_Bf);
     KScope ks(c, AIM_K_ZRHS);
-    k_zrhs<L, W, C><<<grid, 256, sm, c->stream>>>(sl, kspec(c), N, reinterpret_cast<C*>(c->d_Bf), twiddles(c));
+    if constexpr (pow2_len(L)) {
+      constexpr int ZW = zcol_width<L, C>();
+      const size_t sm = (L + L * ZW) * sizeof(C);
+      smem_opt_in(k_zrhs_p2<L, ZW, C>, sm);
+      k_zrhs_p2<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+    } else {
+      const size_t sm = (L + 3 * L * W) * sizeof(C);
+      smem_opt_in(k_zrhs<L, W, C>, sm);
+      k_zrhs<L, W, C><<<dim3(L / W, L, nb * 4), 256, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+    }
     AIM_CHECK_LAUNCH();
   }
 

@@ -286,3 +286,65 @@ def test_matvec_n96_sampled():
             with ctx_for(w, precision=prec) as c:
                 assert c.n_delays == A.n_delays
                 assert rel(c.matvec(m, x)[0][rows], ref) < tol, (m, prec)
+
+
+def test_batched_march_vs_oracle(s480):
+    """Several plane waves marched together (per-RHS GMRES masks inside one graph)
+    give each wave's own march."""
+    from paper_1408_7060_gb300.inputs import random_plane_waves
+
+    w, rwg, p, A = s480
+    k, pp = random_plane_waves(3, 0)
+    nt = 30
+    ZA = np.stack([A.dense(m) for m in range(A.n_delays + 1)])
+    V = efie.excitation(rwg, p, k, pp, w.sigma, w.t_d, np.arange(1, nt + 1))
+    ref = march.march_dense(ZA, V)
+    with ctx_for(w, precision="c128", batch_max=3) as c:
+        cur, stats, _ = c.march(k, pp, w.sigma, w.t_d, nt, 1e-10)
+    assert stats["iters"].shape == (nt, 3)
+    for b in range(3):
+        err = np.linalg.norm(cur[:, b] - ref[:, b]) / np.linalg.norm(ref[:, b])
+        assert err < 1e-6, (b, err)
+
+
+# ------------------------------------------------------------------ smallest and largest power-of-two z pass
+
+def _oracle_rows(A, rwg, p, m, x, rows):
+    """Rows of Z~AIM_m x from direct grid sums plus the oracle's near-zone entries."""
+    ref = A.fft_part_rows(m, x, rows)
+    pr = A.pairs[np.isin(A.pairs[:, 0], rows)]
+    Zn = efie.fill_pairs(rwg, p, pr, m)[m] - A.fft_pairs(m, pr)
+    for (k, kp), z in zip(pr, Zn):
+        ref[np.searchsorted(rows, k)] += z * x[kp]
+    return ref
+
+
+@pytest.mark.parametrize("name", ["sphere_sub2_n8", "array_sub2_n128"])
+def test_pow2_lengths_matvec_and_rhs(name):
+    """Padded lengths 16 and 256 (8^3 grid, 480-RWG sphere; 128^3 grid, 4x4 array of
+    480-RWG spheres): sampled rows of the operator product and of the spectral-domain
+    delay sum, both precisions.  The near zone is one grid step wide so that the grid
+    part carries most interactions.  (An RWG many grid steps long makes the order-3
+    moment matching ill-conditioned -- large grid sources of alternating sign whose
+    sum cancels -- so both meshes keep edges within a few grid steps.)"""
+    w = make_workload(name)
+    w = make_workload(name, near_radius=1.0 * w.h)
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    ng = A.n_delays
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(rwg.ns) + 1j * rng.standard_normal(rwg.ns)
+    rows = np.sort(rng.choice(rwg.ns, 6, replace=False))
+    used = sorted({1, ng})
+    hist = np.zeros((ng, 1, rwg.ns), dtype=complex)
+    for m in used:
+        hist[m - 1, 0] = rng.standard_normal(rwg.ns) + 1j * rng.standard_normal(rwg.ns)
+    ref_mv = {m: _oracle_rows(A, rwg, p, m, x, rows) for m in (0, 1)}
+    ref_rhs = sum(_oracle_rows(A, rwg, p, m, hist[m - 1, 0], rows) for m in used)
+    for prec, tol in (("c128", 1e-10), ("c64", 1e-5)):
+        with ctx_for(w, precision=prec) as c:
+            assert c.n_delays == ng
+            for m in (0, 1):
+                assert rel(c.matvec(m, x[None])[0][rows], ref_mv[m]) < tol, (m, prec)
+            assert rel(c.rhs(ng + 2, hist)[0][rows], ref_rhs) < tol, prec
