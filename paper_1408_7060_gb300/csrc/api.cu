@@ -129,7 +129,6 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_P = aim_alloc(c, (size_t)B * 4 * N * N * N * es);
   c->d_xs = aim_alloc(c, (size_t)B * ns * es);
   c->d_xd = (double2*)aim_alloc(c, (size_t)B * ns * sizeof(double2));
-  c->d_ring = aim_alloc(c, (size_t)ng * op_slab_bytes(c, B));
   const size_t vec = (size_t)B * ns * sizeof(double2);
   c->d_iring = (double2*)aim_alloc(c, (size_t)ng * vec);
   c->d_x = (double2*)aim_alloc(c, vec);
@@ -145,10 +144,10 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   // attributes of each instantiation and surfaces launch errors at setup
   AIM_CUDA(cudaMemsetAsync(c->d_x, 0, vec, c->stream));
   op_apply(c, 0, 1, c->d_x, nullptr, nullptr, 1.0, nullptr, c->d_y);
-  op_forward_slab(c, 1, c->d_x, c->d_ring);
+  op_forward_slab(c, 1, c->d_x, c->d_Bf);
   {
     SlabList sl{};
-    sl.p[0] = c->d_ring;
+    sl.p[0] = c->d_Bf;
     sl.m[0] = 1;
     sl.n = 1;
     NearList nl{};
@@ -156,6 +155,12 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   }
   AIM_CUDA(cudaStreamSynchronize(c->stream));
   c->prof = ProfState();
+}
+
+// the spectral history ring (N_g forward slabs per right-hand side) is the largest
+// buffer; it is allocated on the first call that needs it
+void ensure_ring(aim_ctx* c) {
+  if (!c->d_ring) c->d_ring = aim_alloc(c, (size_t)c->n_delays * op_slab_bytes(c, c->batch_max));
 }
 
 // copy a caller array to device staging if it is a host pointer
@@ -335,6 +340,7 @@ int aim_rhs(aim_ctx* c, int32_t l, int32_t nb, const aim_c128* hist, aim_c128* r
     const int ng = c->n_delays;
     const size_t n = (size_t)nb * c->ns;
     const double2* hs = stage_in(c, hist, (size_t)ng * n, c->d_hist);
+    ensure_ring(c);
     const size_t slab = op_slab_bytes(c, c->batch_max);
     SlabList sl{};
     NearList nl{};
@@ -600,6 +606,7 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
   const size_t n = (size_t)nb * ns;
   const size_t slab = op_slab_bytes(c, B);
   const bool dev_out = is_device_ptr(currents);
+  ensure_ring(c);
   cudaEvent_t ev[3];
   for (auto& e : ev) AIM_CUDA(cudaEventCreate(&e));
   std::vector<int> its(nb);

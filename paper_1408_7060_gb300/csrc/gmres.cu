@@ -50,10 +50,20 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V
   if (i > j || !act[b]) return;
   const double2* vi = V + i * vstride + (size_t)b * ns;
   const double2* w = V + (j + 1) * vstride + (size_t)b * ns;
+  // all loads of the chunk in flight before the (ordered) sum
+  constexpr int T = kDotChunk / kThreads;
+  const int base = s * kDotChunk + threadIdx.x;
+  double2 av[T], wv[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int n = base + t * kThreads;
+    av[t] = n < ns ? vi[n] : make_double2(0, 0);
+    wv[t] = n < ns ? w[n] : make_double2(0, 0);
+  }
   double re = 0, im = 0;
-  const int n1 = min(ns, (s + 1) * kDotChunk);
-  for (int n = s * kDotChunk + threadIdx.x; n < n1; n += kThreads) {
-    double2 p = cmulc(vi[n], w[n]);
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const double2 p = cmulc(av[t], wv[t]);
     re += p.x;
     im += p.y;
   }
@@ -158,7 +168,16 @@ __global__ void __launch_bounds__(kThreads) k_normpart(const double2* __restrict
 __device__ __forceinline__ double warp_row_sum(const double* __restrict__ p, int P) {
   const int lane = threadIdx.x & 31;
   double s = 0;
-  for (int q = lane; q < P; q += 32) s += p[q];
+  for (int q0 = 0; q0 < P; q0 += 256) {  // 8 loads per lane in flight, summed in order
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int q = q0 + 32 * t + lane;
+      v[t] = q < P ? p[q] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s += v[t];
+  }
   return warp_sum(s);
 }
 
@@ -217,64 +236,117 @@ struct FinishArgs {
   cudaGraphConditionalHandle inner;
 };
 
-// Arnoldi column j for every active RHS: H[0..j][j] = h1 + h2, H[j+1][j] = |w|,
+// affine map x -> a x + b on complex numbers; compose(earlier, later) = later o earlier
+struct Aff {
+  double2 a, b;
+};
+__device__ __forceinline__ Aff aff_then(Aff e, Aff l) {  // l o e
+  return Aff{cmul(l.a, e.a), make_double2(cmul(l.a, e.b).x + l.b.x, cmul(l.a, e.b).y + l.b.y)};
+}
+__device__ __forceinline__ Aff shfl_up_aff(Aff v, int d) {
+  Aff r;
+  r.a.x = __shfl_up_sync(0xffffffffu, v.a.x, d);
+  r.a.y = __shfl_up_sync(0xffffffffu, v.a.y, d);
+  r.b.x = __shfl_up_sync(0xffffffffu, v.b.x, d);
+  r.b.y = __shfl_up_sync(0xffffffffu, v.b.y, d);
+  return r;
+}
+
+// Arnoldi column j for every active RHS: H[0..j][j] = h1 + h2, H[j+1][j] = |w|, the
 // previous rotations, a new complex Givens rotation, |g_{j+1}|, convergence / cap,
-// sig_{j+1} = 1/|w|; then j += 1 and the inner loop condition.  One warp per RHS:
-// the lanes stage the column and the rotations in shared memory, lane 0 applies the
-// rotations in order, the lanes write the column back.
+// sig_{j+1} = 1/|w|; then j += 1 and the inner loop condition.  One warp per RHS.
+// Applying G_0..G_{j-1} to the column is the recurrence p_0 = h_0,
+// p_{i+1} = -conj(s_i) p_i + c_i h_{i+1}, with rotated entries c_i p_i + s_i h_{i+1}:
+// a composition of affine maps, evaluated by a warp-wide inclusive scan (2 entries
+// per lane) instead of a j-long dependent chain of FP64 operations.
 __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int j = *s.jdev;
   __shared__ int any;
-  __shared__ double2 col[kThreads / 32][65];
-  __shared__ double2 rsn[kThreads / 32][64];
-  __shared__ double rcs[kThreads / 32][64];
-  if (threadIdx.x == 0) any = 0;
+  if (tid == 0) any = 0;
   __syncthreads();
   for (int b = warp; b < a.nb; b += nw) {
     if (!s.act[b]) continue;
     const double hn = sqrt(warp_row_sum(a.pn + (size_t)b * a.Pu, a.Pu));
-    for (int i = lane; i <= j; i += 32) {
-      const double2 x = s.h1[b * 64 + i], y = s.h2[b * 64 + i];
-      col[warp][i] = make_double2(x.x + y.x, x.y + y.y);
-      if (i < j) {
-        rcs[warp][i] = s.cs[b * 64 + i];
-        rsn[warp][i] = s.sn[b * 64 + i];
+    // entries i = 2 lane, 2 lane + 1 of the column and the rotations that act on them
+    double2 h[2], sn[2];
+    double cs[2];
+    Aff m[2];
+    for (int t = 0; t < 2; ++t) {
+      const int i = 2 * lane + t;
+      h[t] = make_double2(0, 0);
+      if (i <= j) {
+        const double2 x = s.h1[b * 64 + i], y = s.h2[b * 64 + i];
+        h[t] = make_double2(x.x + y.x, x.y + y.y);
       }
     }
-    __syncwarp();
-    if (lane == 0) {
-      for (int i = 0; i < j; ++i) {  // G_i acts on rows (i, i+1)
-        const double c = rcs[warp][i];
-        const double2 sn = rsn[warp][i];
-        const double2 p = col[warp][i], q = col[warp][i + 1];
-        const double2 sq = cmul(sn, q);
-        const double2 csp = make_double2(sn.x * p.x + sn.y * p.y, sn.x * p.y - sn.y * p.x);  // conj(sn) p
-        col[warp][i] = make_double2(c * p.x + sq.x, c * p.y + sq.y);
-        col[warp][i + 1] = make_double2(c * q.x - csp.x, c * q.y - csp.y);
+    // h_{i+1} for the rotation G_i held by this lane (i = 2 lane + t)
+    const double2 hn0 = h[1];
+    double2 hn1 = make_double2(__shfl_down_sync(0xffffffffu, h[0].x, 1), __shfl_down_sync(0xffffffffu, h[0].y, 1));
+    const double2 hnext[2] = {hn0, hn1};
+    for (int t = 0; t < 2; ++t) {
+      const int i = 2 * lane + t;
+      if (i < j) {
+        cs[t] = s.cs[b * 64 + i];
+        sn[t] = s.sn[b * 64 + i];
+        m[t] = Aff{make_double2(-sn[t].x, sn[t].y), make_double2(cs[t] * hnext[t].x, cs[t] * hnext[t].y)};
+      } else {
+        cs[t] = 1.0;
+        sn[t] = make_double2(0, 0);
+        m[t] = Aff{make_double2(1, 0), make_double2(0, 0)};  // identity
       }
-      const double2 p = col[warp][j];
-      const double na = sqrt(p.x * p.x + p.y * p.y);
+    }
+    // inclusive scan over i of the compositions M_i o ... o M_0
+    Aff inc1 = aff_then(m[0], m[1]);  // lane aggregate (entry 2 lane + 1)
+    Aff agg = inc1;
+    for (int d = 1; d < 32; d <<= 1) {
+      Aff o = shfl_up_aff(agg, d);
+      if (lane >= d) agg = aff_then(o, agg);
+    }
+    Aff excl = shfl_up_aff(agg, 1);
+    if (lane == 0) excl = Aff{make_double2(1, 0), make_double2(0, 0)};
+    const double2 h0 = make_double2(__shfl_sync(0xffffffffu, h[0].x, 0), __shfl_sync(0xffffffffu, h[0].y, 0));
+    // p_i for i = 2 lane (= excl(h0)) and i = 2 lane + 1 (= (M_{2 lane} o excl)(h0))
+    const Aff c0 = excl, c1 = aff_then(excl, m[0]);
+    double2 p[2];
+    p[0] = make_double2(cmul(c0.a, h0).x + c0.b.x, cmul(c0.a, h0).y + c0.b.y);
+    p[1] = make_double2(cmul(c1.a, h0).x + c1.b.x, cmul(c1.a, h0).y + c1.b.y);
+    double2* H = s.H + (size_t)b * 64 * 64;  // H[i][j] at i*64 + j
+    double2 pj = make_double2(0, 0);
+    for (int t = 0; t < 2; ++t) {
+      const int i = 2 * lane + t;
+      if (i < j) {
+        const double2 sq = cmul(sn[t], hnext[t]);
+        H[i * 64 + j] = make_double2(cs[t] * p[t].x + sq.x, cs[t] * p[t].y + sq.y);
+      } else if (i == j) {
+        pj = p[t];
+      }
+    }
+    // the new rotation (lane holding entry j)
+    if (2 * lane == j || 2 * lane + 1 == j) {
+      const double2 pp = pj;
+      const double na = sqrt(pp.x * pp.x + pp.y * pp.y);
       const double nd = hn;
       const double r = sqrt(na * na + nd * nd);
       double c;
-      double2 sn;
+      double2 snew;
       if (r == 0.0) {
         c = 1.0;
-        sn = make_double2(0, 0);
+        snew = make_double2(0, 0);
       } else if (na == 0.0) {
         c = 0.0;
-        sn = make_double2(1.0, 0.0);
+        snew = make_double2(1.0, 0.0);
       } else {
         c = na / r;
-        sn = make_double2(p.x / na * (nd / r), p.y / na * (nd / r));  // (p/|p|) conj(hn)/r, hn real
+        snew = make_double2(pp.x / na * (nd / r), pp.y / na * (nd / r));  // (p/|p|) hn/r, hn real
       }
       s.cs[b * 64 + j] = c;
-      s.sn[b * 64 + j] = sn;
-      col[warp][j] = make_double2(c * p.x + sn.x * nd, c * p.y + sn.y * nd);
+      s.sn[b * 64 + j] = snew;
+      H[j * 64 + j] = make_double2(c * pp.x + snew.x * nd, c * pp.y + snew.y * nd);
       const double2 gj = s.g[b * 64 + j];
       s.g[b * 64 + j] = make_double2(c * gj.x, c * gj.y);
-      const double2 gn = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));  // -conj(sn) g_j
+      const double2 gn = make_double2(-(snew.x * gj.x + snew.y * gj.y), -(snew.x * gj.y - snew.y * gj.x));
       s.g[b * 64 + j + 1] = gn;
       const double res = sqrt(gn.x * gn.x + gn.y * gn.y);
       s.relres[b] = res / s.bn[b];
@@ -287,18 +359,16 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s)
       else
         atomicOr(&any, 1);
     }
-    __syncwarp();
-    double2* H = s.H + (size_t)b * 64 * 64;  // H[i][j] at i*64 + j
-    for (int i = lane; i <= j; i += 32) H[i * 64 + j] = col[warp][i];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     *s.jdev = j + 1;
     s.cnt[1] += 1;
     s.flag[1] = any;
     if (a.use_cond) cudaGraphSetConditional(a.inner, any ? 1u : 0u);
   }
 }
+
 
 // y = H^{-1} g on the jc x jc triangle (one block per b; H staged in shared memory,
 // back-substitution by one warp); the scales sig_i are folded into y.
@@ -397,10 +467,9 @@ void cycle_prologue(aim_ctx* c, int nb, const double2* b, double2* x, double tol
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_start<<<1, kThreads, 0, st>>>(a, s));
 }
 
-// one Arnoldi step for every active RHS (column j from device memory)
-void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle inner) {
+// slot j+1 = Z_0 (dinv .* v_j) for every active RHS (column j from device memory)
+void arnoldi_operator(aim_ctx* c, int nb) {
   GmresState& s = c->gs;
-  cudaStream_t st = c->stream;
   const int ns = c->ns;
   const long long vstride = (long long)c->batch_max * ns;
   VecSel vin;
@@ -412,8 +481,16 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
   vout.sel = s.jdev;
   vout.stride = vstride;
   vout.off = 1;
-  // slot j+1 = Z_0 (dinv .* v_j)
   op_apply(c, 0, nb, c->d_V, c->d_dinv, nullptr, 1.0, s.act, c->d_V, vin, vout);
+}
+
+// one Arnoldi step for every active RHS: operator into slot j+1, CGS2, column finish
+void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle inner) {
+  GmresState& s = c->gs;
+  cudaStream_t st = c->stream;
+  const int ns = c->ns;
+  const long long vstride = (long long)c->batch_max * ns;
+  arnoldi_operator(c, nb);
   const int S = n_dot_chunks(ns), U = n_upd_blocks(ns);
   for (int pass = 0; pass < 2; ++pass) {
     AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
@@ -466,12 +543,12 @@ void capture_into(aim_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t
   AIM_CUDA(cudaStreamEndCapture(c->stream, &out));
 }
 
-cudaGraphNode_t add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, cudaGraphConditionalHandle h,
-                          cudaGraph_t* body) {
+cudaGraphNode_t add_cond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, cudaGraphConditionalHandle h,
+                         cudaGraphConditionalNodeType type, cudaGraph_t* body) {
   cudaGraphNodeParams p = {};
   p.type = cudaGraphNodeTypeConditional;
   p.conditional.handle = h;
-  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.type = type;
   p.conditional.size = 1;
   cudaGraphNode_t node;
   AIM_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
@@ -495,12 +572,12 @@ void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double 
     cudaGraphConditionalHandle outer, inner;
     AIM_CUDA(cudaGraphConditionalHandleCreate(&outer, g, 1, cudaGraphCondAssignDefault));
     cudaGraph_t obody;
-    add_while(g, &pre, 1, outer, &obody);
+    add_cond(g, &pre, 1, outer, cudaGraphCondTypeWhile, &obody);
     AIM_CUDA(cudaGraphConditionalHandleCreate(&inner, obody, 0, cudaGraphCondAssignDefault));
     capture_into(c, obody, nullptr, 0, [&] { cycle_prologue(c, nb, b, x, tol, true, outer, inner); });
     cudaGraphNode_t pro = leaf_of(obody);
     cudaGraph_t ibody;
-    cudaGraphNode_t wn = add_while(obody, &pro, 1, inner, &ibody);
+    cudaGraphNode_t wn = add_cond(obody, &pro, 1, inner, cudaGraphCondTypeWhile, &ibody);
     capture_into(c, ibody, nullptr, 0, [&] { arnoldi_step(c, nb, tol, true, inner); });
     capture_into(c, obody, &wn, 1, [&] { cycle_epilogue(c, nb, x); });
     cudaGraphExec_t ex;
@@ -623,9 +700,10 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
   AIM_CUDA(cudaMemcpyAsync(s.h_cnt, s.cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaStreamSynchronize(st));
   if (graphed) {
-    // kernels the graph executed: 1 + cycles * (prologue 9 + epilogue 2) + steps * 12
-    // (operator: prep, anterp+x, y, z, y^-1, x^-1, interp = 7)
-    c->prof.launches += 1 + 11LL * s.h_cnt[0] + 12LL * s.h_cnt[1];
+    // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2)
+    // + steps * (operator + 2 x (dot, update) + finish)
+    const long long op = op_kernel_count(c);
+    c->prof.launches += 1 + (op + 4) * s.h_cnt[0] + (op + 5) * s.h_cnt[1];
   }
   int rc = AIM_OK;
   for (int i = 0; i < nb; ++i) {

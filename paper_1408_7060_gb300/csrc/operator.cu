@@ -33,6 +33,9 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
     body_apply_rhs<double2>(c, nb, sl, nl, base, sign, y);
 }
 
+// kernels one operator application launches: prep, anterp + x, y, z, y^-1, x^-1, interp
+int op_kernel_count(const aim_ctx*) { return 7; }
+
 size_t op_slab_bytes(const aim_ctx* c, int nb) {
   return (size_t)nb * 4 * c->N * (size_t)c->L * c->L * (c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2));
 }

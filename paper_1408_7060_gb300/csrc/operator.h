@@ -38,4 +38,5 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
                   double2* y);
 // V_l for the plane waves in exc (device parameter block [nb][6]: khat, phat)
 void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double t_d, int step_l, double2* out);
+int op_kernel_count(const aim_ctx* c);
 size_t op_slab_bytes(const aim_ctx* c, int nb);
