@@ -85,27 +85,32 @@ def sphere_array(sub: int, radius: float, pitch: float, nx: int = 4, ny: int = 4
 
 
 def ellipsoid_mesh(semi_axes=(1.0, 0.5, 0.25), n_points: int = 6668, seed: int = 3,
-                   jitter: float = 0.25, relax_iters: int = 60):
-    """Closed ellipsoid surface from jittered Fibonacci-sphere samples.
+                   relax_iters: int = 150):
+    """Closed ellipsoid surface with nearly uniform point spacing.
 
-    The samples are mapped onto the ellipsoid, spread evenly by a short repulsion
-    relaxation on the surface (each point pushed away from its nearest neighbours,
-    then scaled back onto the ellipsoid), and triangulated with a 3-D convex hull
-    (the surface Delaunay triangulation of a convex body).  Faces are oriented
+    Seeded samples uniform on the unit sphere are mapped onto the ellipsoid and kept
+    with probability proportional to the local area scale of that map,
+    abc |(u_x/a, u_y/b, u_z/c)| (so the kept points are uniform in ellipsoid area),
+    then spread evenly by a repulsion relaxation on the surface (each point pushed away
+    from its nearest neighbours and scaled back onto the ellipsoid), triangulated with a
+    3-D convex hull and made Delaunay on the surface by edge flips.  Faces are oriented
     outward.  ``E = 3 (V - 2)`` edges, i.e. about ``3 n_points`` RWG unknowns.
     """
     from scipy.spatial import ConvexHull, cKDTree
 
     ax = np.asarray(semi_axes, dtype=np.float64)
     rng = np.random.Generator(np.random.PCG64(seed))
-    i = np.arange(n_points, dtype=np.float64) + 0.5
-    i = i + jitter * (rng.random(n_points) - 0.5)
-    z = 1.0 - 2.0 * i / n_points
-    phi = math.pi * (3.0 - math.sqrt(5.0)) * np.arange(n_points)
-    phi = phi + jitter * 0.5 * (rng.random(n_points) - 0.5)
-    r = np.sqrt(np.clip(1.0 - z * z, 0.0, None))
-    u = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
-    V = u * ax
+    pts = []
+    got = 0
+    fmax = ax.prod() * np.linalg.norm(1.0 / ax)
+    while got < n_points:
+        u = rng.standard_normal((4 * n_points, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        f = ax.prod() * np.linalg.norm(u / ax, axis=1)
+        keep = rng.random(len(u)) < f / fmax
+        pts.append(u[keep])
+        got += int(keep.sum())
+    V = np.concatenate(pts)[:n_points] * ax
 
     def onto(P):
         return P / np.sqrt(((P / ax) ** 2).sum(axis=1, keepdims=True))
@@ -120,7 +125,63 @@ def ellipsoid_mesh(semi_axes=(1.0, 0.5, 0.25), n_points: int = 6668, seed: int =
         V = onto(V + step)
     hull = ConvexHull(V)
     F = _orient_outward(V, hull.simplices.astype(np.int32), np.zeros(3))
-    return V, F.astype(np.int32)
+    return V, _delaunay_flips(V, F).astype(np.int32)
+
+
+def _delaunay_flips(V, F, max_pass: int = 100):
+    """Lawson edge flips on a closed, consistently oriented triangle surface: an edge
+    whose two opposite angles sum to more than pi is replaced by the other diagonal of
+    its two triangles, until no such edge is left.  The convex hull of points on an
+    ellipsoid is the Delaunay triangulation of the points mapped to the unit sphere
+    (hulls are affine invariant), i.e. anisotropic on the ellipsoid itself; the flips
+    make it Delaunay in the surface's own angles.  Each pass flips a set of edges that
+    share no triangle, largest angle excess first; a flip that would duplicate an
+    existing edge is skipped.  Orientation is kept."""
+    F = np.array(F, dtype=np.int64)
+    nv, nf = len(V), len(F)
+    for _ in range(max_pass):
+        a = F.reshape(-1)
+        b = F[:, [1, 2, 0]].reshape(-1)
+        c = F[:, [2, 0, 1]].reshape(-1)
+        fi = np.repeat(np.arange(nf), 3)
+        key = a * nv + b
+        order = np.argsort(key, kind="stable")
+        twin = order[np.searchsorted(key[order], b * nv + a)]
+        h = np.nonzero(a < b)[0]
+        g = twin[h]
+        d = c[g]
+
+        def angle_at(p, q, r):  # angle at r of triangle (p, q, r)
+            u = V[p] - V[r]
+            v = V[q] - V[r]
+            cosv = (u * v).sum(1) / (np.linalg.norm(u, axis=1) * np.linalg.norm(v, axis=1))
+            return np.arccos(np.clip(cosv, -1.0, 1.0))
+
+        excess = angle_at(a[h], b[h], c[h]) + angle_at(a[h], b[h], d) - np.pi
+        cand = np.nonzero(excess > 1e-12)[0]
+        if len(cand) == 0:
+            break
+        cand = cand[np.argsort(-excess[cand], kind="stable")]
+        edges = set((key[a < b]).tolist())
+        used = np.zeros(nf, dtype=bool)
+        flips = 0
+        for j in cand:
+            hh, gg = h[j], g[j]
+            f1, f2 = fi[hh], fi[gg]
+            if used[f1] or used[f2]:
+                continue
+            ea, eb, ec, ed = int(a[hh]), int(b[hh]), int(c[hh]), int(d[j])
+            if ec == ed or min(ec, ed) * nv + max(ec, ed) in edges:
+                continue
+            F[f1] = (ec, ed, eb)
+            F[f2] = (ed, ec, ea)
+            used[f1] = used[f2] = True
+            edges.discard(min(ea, eb) * nv + max(ea, eb))
+            edges.add(min(ec, ed) * nv + max(ec, ed))
+            flips += 1
+        if flips == 0:
+            break
+    return F
 
 
 # ----------------------------------------------------------------------------
@@ -234,7 +295,7 @@ def make_workload(name: str, **over) -> Workload:
         V, F = ellipsoid_mesh()
         h, o = place_grid(V, 96)
         w = dict(mesh=(V, F), f_c=600e6, band_frac=0.3, n_t=500, grid_n=96, h=h, origin=o,
-                 near_radius=3 * h, tol=1e-6, khat=np.array([[0.0, 0.0, 1.0]]),
+                 near_radius=3 * h, tol=1e-5, khat=np.array([[0.0, 0.0, 1.0]]),
                  phat=np.array([[1.0, 0.0, 0.0]]), precision="c64")
     elif name == "array491k":
         V, F = sphere_array(5, 0.5, 1.5)
@@ -242,6 +303,14 @@ def make_workload(name: str, **over) -> Workload:
         k, p = random_plane_waves(16, 4)
         w = dict(mesh=(V, F), f_c=1e9, band_frac=0.05, n_t=1000, grid_n=384, h=h, origin=o,
                  near_radius=3 * h, tol=1e-5, khat=k, phat=p, precision="c64")
+    elif name.startswith("array_sub"):
+        # smaller sphere arrays on the large grid: array_sub<s>_n<N> (4x4 spheres r = 0.5 m)
+        s_, n = name[len("array_sub"):].split("_n")
+        V, F = sphere_array(int(s_), 0.5, 1.5)
+        h, o = place_grid(V, int(n))
+        w = dict(mesh=(V, F), f_c=1e9, band_frac=0.05, n_t=50, grid_n=int(n), h=h, origin=o,
+                 near_radius=3 * h, tol=1e-5, khat=np.array([[0.0, 0.0, 1.0]]),
+                 phat=np.array([[1.0, 0.0, 0.0]]), precision="c64")
     elif name.startswith("sphere_sub"):
         # small parity cases: sphere_sub<s>_n<N>  (radius 1 m, 600 MHz +-30 %)
         s, n = name[len("sphere_sub"):].split("_n")
