@@ -17,7 +17,9 @@ from __future__ import annotations
 
 import argparse
 import json
+import hashlib
 import math
+import re
 import os
 import subprocess
 import sys
@@ -39,6 +41,31 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+CSRC = os.path.join(ROOT, "paper_1408_7060_gb300", "csrc")
+
+
+def kernel_digest(kind):
+    """Digest of a kernel's source text and the FFT core it uses: measured DRAM traffic
+    is only reported while the kernel is unchanged since the capture."""
+    name = {"zconv": "k_zconv", "zrhs": "k_zrhs", "interp_near": "k_interp_near",
+            "anterp_xfft": "k_anterp_rows"}.get(kind)
+    if name is None:
+        return None
+    src = open(os.path.join(CSRC, "operator_impl.cuh")).read()
+    m = re.search(r"__global__ void __launch_bounds__\(256\) " + name + r"\(.*?\n}\n", src, re.S)
+    if not m:
+        return None
+    h = hashlib.sha1(m.group(0).encode())
+    for f in ("fft.cuh", "fft_kernels.cuh"):
+        h.update(open(os.path.join(CSRC, f)).read().encode())
+    return h.hexdigest()[:16]
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from one ncu capture of
+# this workload: (kernel, workload, source digest) -> bytes
+TRAFFIC = {("zconv", "sphere7680", "603a3063aa0f9c22"): 37968384 + 256}
 
 
 def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
@@ -172,6 +199,7 @@ def run_aim(args):
         ctx.profile(profile)
         evs = []
         iters = []
+        split = []
         for _ in range(k):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)                      # L2 flush between timed steps (256 MB > 129 MB L2)
@@ -182,15 +210,18 @@ def run_aim(args):
             b.record(stream)
             evs.append((a, b))
             iters.append(st["total_iters"])
+            split.append((st["rhs_ms"], st["solve_ms"]))
         torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in evs]
         prof, launches = ctx.get_profile()
+        timed_steps.split = np.mean(np.array(split), axis=0) if split else (0.0, 0.0)
         return ms, iters, prof, launches
 
     barrier(ws)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     ms, iters, _, launches = timed_steps(args.steps, profile=False)
+    rhs_ms, solve_ms = (float(x) for x in timed_steps.split)
     clk = clocks.stop()
     torch.cuda.synchronize()
     barrier(ws)
@@ -231,9 +262,12 @@ def run_aim(args):
                    "tol": w.tol, "chi": round(w.chi, 3), "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "independent plane waves per GPU" if ws > 1 else "single GPU"},
         "gmres_iters_per_step": float(np.mean(iters)),
+        "split_ms_per_step": {"rhs": round(rhs_ms, 4), "solve": round(solve_ms, 4),
+                              "commit_and_host": round(t_step * 1e3 - rhs_ms - solve_ms, 4)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
                      "peak": hbm, "peak_source": src, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4) if achieved else None, "traffic": None,
+                     "frac": round(achieved / hbm, 4) if achieved else None,
+                     "traffic": TRAFFIC.get((dom, w.name, kernel_digest(dom))),
                      "bytes_per_launch": nbytes, "ms_per_launch": round(per_launch_ms, 5)},
         "kernels": kernels,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nb * 6 * 8,
