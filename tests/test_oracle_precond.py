@@ -1,0 +1,92 @@
+"""Pins of the oracle's near-zone sparse approximate inverse (oracle/precond.py).
+
+It is pinned to what fixes it independently of its per-column solves: the diagonal
+special case, the exact inverse when the near zone covers every pair, the defining
+identity evaluated through a sparse matrix product, and its effect on GMRES."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import aim, efie
+from oracle.precond import near_sai
+from oracle.rwg import build_rwg
+from paper_1408_7060_gb300.inputs import icosphere, make_workload
+
+
+def _case(V, F, dt, f_c, radius):
+    rwg = build_rwg(V, F)
+    p = efie.Params(dt=dt, f_c=f_c, Q=2)
+    xe = rwg.midpoint()
+    d2 = ((xe[:, None, :] - xe[None, :, :]) ** 2).sum(-1)
+    r, c = np.nonzero(d2 <= radius * radius)
+    pairs = np.stack([r, c], axis=1)
+    pairs = pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))]
+    z0 = efie.fill_pairs(rwg, p, pairs, 0)[0]
+    return rwg, p, pairs, z0
+
+
+def test_self_pairs_give_the_diagonal_preconditioner():
+    w = make_workload("sphere480")
+    rwg, p, pairs, z0 = _case(*w.mesh, w.dt, w.f_c, 1e-9)
+    assert np.array_equal(pairs[:, 0], pairs[:, 1])
+    m = near_sai(rwg.ns, pairs, z0)
+    assert np.abs(m * z0 - 1).max() < 1e-14
+
+
+def test_full_near_zone_gives_the_inverse():
+    V, F = icosphere(1, 1.0)
+    rwg, p, pairs, z0 = _case(V, F, 3.33e-9, 150e6, 10.0)
+    assert len(pairs) == rwg.ns ** 2
+    Z = np.zeros((rwg.ns, rwg.ns), dtype=complex)
+    Z[pairs[:, 0], pairs[:, 1]] = z0
+    m = near_sai(rwg.ns, pairs, z0)
+    M = np.zeros_like(Z)
+    M[pairs[:, 0], pairs[:, 1]] = m
+    Zi = np.linalg.inv(Z)
+    assert np.abs(M - Zi).max() < 1e-10 * np.abs(Zi).max()
+
+
+@pytest.fixture(scope="module")
+def s480_near():
+    w = make_workload("sphere480")
+    rwg, p, pairs, z0 = _case(*w.mesh, w.dt, w.f_c, w.near_radius)
+    return w, rwg, p, pairs, z0, near_sai(rwg.ns, pairs, z0)
+
+
+def test_defining_identity_through_sparse_product(s480_near):
+    """(Zn M)[i, k] = delta_ik on every near pair (i, k): column k of M inverts the near
+    block around k.  Evaluated by a sparse matrix product, not by the solves."""
+    w, rwg, p, pairs, z0, m = s480_near
+    ns = rwg.ns
+    Zn = sp.csr_matrix((z0, (pairs[:, 0], pairs[:, 1])), shape=(ns, ns))
+    M = sp.csr_matrix((m, (pairs[:, 0], pairs[:, 1])), shape=(ns, ns))
+    P = (Zn @ M).toarray()
+    got = P[pairs[:, 0], pairs[:, 1]]
+    want = (pairs[:, 0] == pairs[:, 1]).astype(float)
+    assert np.abs(got - want).max() < 1e-10
+
+
+def test_sai_cuts_gmres_iterations(s480_near):
+    """On the oracle's immediate AIM operator of the 480-RWG sphere, right
+    preconditioning with M needs fewer GMRES iterations than the diagonal (68 -> 38
+    here; the gain grows with the share of Z_0's support inside the near zone)."""
+    w, rwg, p, pairs, z0, m = s480_near
+    A = aim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    Z0 = A.dense(0)
+    ns = rwg.ns
+    M = sp.csr_matrix((m, (pairs[:, 0], pairs[:, 1])), shape=(ns, ns))
+    d = np.diag(Z0)
+    b = np.random.default_rng(0).standard_normal(ns) + 0j
+
+    def iters(apply):
+        n = [0]
+        op = spla.LinearOperator((ns, ns), matvec=lambda x: Z0 @ apply(x), dtype=complex)
+        _, info = spla.gmres(op, b, rtol=1e-8, restart=50, maxiter=400,
+                             callback=lambda r: n.__setitem__(0, n[0] + 1), callback_type="pr_norm")
+        assert info == 0
+        return n[0]
+
+    it_diag = iters(lambda x: x / d)
+    it_sai = iters(lambda x: M @ x)
+    assert it_sai <= 0.7 * it_diag, (it_sai, it_diag)
