@@ -175,7 +175,7 @@ def run_aim(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.init()
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, precond=args.precond)
     if ws > 1:   # each rank marches its own plane wave (independent right-hand side)
         k, p = random_plane_waves(ws, 100)
         w.khat, w.phat = k[rank:rank + 1], p[rank:rank + 1]
@@ -259,7 +259,8 @@ def run_aim(args):
         "vs_baseline": None, "dtype": "c64 grid / f64 solve", "data": "synthetic",
         "config": {"workload": w.name, "ns": ns, "grid": f"{w.grid_n}^3 -> {2 * w.grid_n}^3 FFT",
                    "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "rhs_per_gpu": nb,
-                   "tol": w.tol, "chi": round(w.chi, 3), "l2": "flushed between timed steps (256 MB write)",
+                   "tol": w.tol, "chi": round(w.chi, 3), "precond": w.precond,
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "independent plane waves per GPU" if ws > 1 else "single GPU"},
         "gmres_iters_per_step": float(np.mean(iters)),
         "split_ms_per_step": {"rhs": round(rhs_ms, 4), "solve": round(solve_ms, 4),
@@ -277,8 +278,13 @@ def run_aim(args):
     }
     if not args.no_plain:
         line["plain_c128"] = plain_comparison(w, ctx, stream, args)
+        if w.precond != "diag":
+            line["diag_precond"] = diag_comparison(w, ctx, stream, args)
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, samples=2, n_iter=float(np.mean(iters)))
+        # the oracle's method is the paper's (diagonal preconditioner): its iteration count
+        n_or = float(np.mean(iters)) if w.precond == "diag" else \
+            line.get("diag_precond", {}).get("gmres_iters_per_step", ITERS_PER_STEP.get(w.name, 50.0))
+        line["cpu_baseline"] = cpu_baseline(w, samples=2, n_iter=n_or)
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
@@ -286,6 +292,37 @@ def run_aim(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def diag_comparison(w, ctx, stream, args):
+    """The same march with the paper's diagonal preconditioner: its s/step and GMRES
+    iterations over the same steps, and the relative difference of the two marches
+    (both from rest, both converged to the workload's tolerance)."""
+    import torch
+
+    from paper_1408_7060_gb300 import AimContext
+
+    n = args.warmup + args.steps
+    with torch.cuda.stream(stream):
+        cd = AimContext.from_workload(w, precond="diag", stream=stream.cuda_stream)
+    outd = torch.empty((n, w.nb, cd.ns), dtype=torch.complex128, device="cuda")
+    outs = torch.empty_like(outd)
+    cd.march(w.khat, w.phat, w.sigma, w.t_d, args.warmup, w.tol, out=outd[: args.warmup])
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    _, st, _ = cd.march_continue(w.khat, w.phat, w.sigma, w.t_d, args.steps, w.tol, out=outd[args.warmup:])
+    e.record(stream)
+    torch.cuda.synchronize()
+    td = a.elapsed_time(e) / args.steps / 1e3
+    ctx.march(w.khat, w.phat, w.sigma, w.t_d, n, w.tol, out=outs)
+    torch.cuda.synchronize()
+    num = torch.linalg.vector_norm(outs - outd).item()
+    den = torch.linalg.vector_norm(outd).item()
+    cd.close()
+    return {"s_per_step": td, "gmres_iters_per_step": st["total_iters"] / args.steps,
+            "rel_diff_vs_this_march": num / den, "steps_compared": n}
 
 
 def plain_comparison(w, ctx64, stream, args):
@@ -409,6 +446,8 @@ def main():
     ap.add_argument("--workload", default="sphere7680")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
+    ap.add_argument("--precond", default="sai", choices=["sai", "diag"],
+                    help="GMRES right preconditioner (near-zone SAI, or the paper's diagonal)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -44,7 +44,8 @@ class aim_tbasis(ct.Structure):
 
 class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
-                ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p)]
+                ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
+                ("preconditioner", ct.c_int32)]
 
 
 class aim_excitation(ct.Structure):
@@ -61,12 +62,12 @@ class aim_stats(ct.Structure):
 class aim_info(ct.Structure):
     _fields_ = [("ns", ct.c_int32), ("n_delays", ct.c_int32), ("n_active", ct.c_int32),
                 ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
-                ("device_bytes", ct.c_int64)]
+                ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
            "aim_matvec", "aim_rhs", "aim_excitation_vector", "aim_march", "aim_march_continue", "aim_get_anterp",
-           "aim_get_near", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
+           "aim_get_near", "aim_get_preconditioner", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
            "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
            "aim_farfield", "aim_farfield_adjoint"]
 AIM_K_COUNT = 12
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
         "aim_farfield_adjoint": (ct.c_int, [P, I32, P, P, P, I32, I32, I32, P, P]),
         "aim_get_anterp": (ct.c_int, [P, P, P]),
         "aim_get_near": (ct.c_int, [P, P, P, P]),
+        "aim_get_preconditioner": (ct.c_int, [P, P]),
         "aim_get_kernel_spectrum": (ct.c_int, [P, I32, I32, P]),
     }
     for name, (res, args) in sig.items():
@@ -163,9 +165,13 @@ def _stream_handle():
     return None
 
 
+PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
+
+
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
-              restart=50, max_iter=500, stream=None):
-    """Build a context; returns an opaque handle (int)."""
+              restart=50, max_iter=500, stream=None, precond="diag"):
+    """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
+    diagonal preconditioner) or "sai" (near-zone sparse approximate inverse)."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -174,7 +180,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     tb = aim_tbasis(AIM_CPPIF, int(order))
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
-                    stream if stream is not None else _stream_handle())
+                    stream if stream is not None else _stream_handle(), PRECOND[precond])
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -374,6 +380,15 @@ def aim_get_near(ctx):
     return rowptr, col[:nnz], val[:, :nnz]
 
 
+def aim_get_preconditioner(ctx):
+    """The right preconditioner M on the near-zone CSR pattern: val[e] = M[row, col[e]]."""
+    lib = load()
+    nnz = aim_get_info(ctx)["near_nnz"]
+    val = np.empty(max(nnz, 1), dtype=np.complex128)
+    _check(lib, ctx, lib.aim_get_preconditioner(ctx, val.ctypes.data), "aim_get_preconditioner")
+    return val[:nnz]
+
+
 def aim_get_kernel_spectrum(ctx, m, kind):
     lib = load()
     n = aim_get_info(ctx)["grid_n"] + 1
@@ -395,7 +410,7 @@ class AimContext:
     def from_workload(cls, w, **over):
         V, F = w.mesh
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
-                  f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb)
+                  f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond)
         kw.update(over)
         return cls(**kw)
 
@@ -428,6 +443,9 @@ class AimContext:
 
     def near(self):
         return aim_get_near(self.handle)
+
+    def preconditioner(self):
+        return aim_get_preconditioner(self.handle)
 
     def kernel_spectrum(self, m, kind):
         return aim_get_kernel_spectrum(self.handle, m, kind)

@@ -147,6 +147,9 @@ struct aim_ctx {
   int* d_col = nullptr;        // [nnz]
   double2* d_near = nullptr;   // [(N_g+1)][nnz]
   double2* d_dinv = nullptr;   // [ns] 1 / Z_0[k,k]
+  int precond = 0;             // AIM_PRECOND_*
+  double2* d_sai = nullptr;    // [nnz] near-zone SAI on the near CSR pattern (AIM_PRECOND_NEAR_SAI)
+  double2* d_u = nullptr;      // [B][ns] Krylov combination before the preconditioner (SAI)
   double2* d_nearT = nullptr;  // [(N_g+1)][nnz] values of the transposed near matrices (lazy)
 
   // ---- work buffers (sized for batch_max) ----

@@ -78,6 +78,11 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->batch_max = opts->batch_max;
   c->restart = opts->gmres_restart > 0 ? std::min(opts->gmres_restart, 63) : 50;
   c->max_iter = opts->gmres_max_iter > 0 ? opts->gmres_max_iter : 500;
+  if (opts->preconditioner != AIM_PRECOND_DIAG && opts->preconditioner != AIM_PRECOND_NEAR_SAI)
+    throw AimError{AIM_ERR_ARG, "aim_setup: unknown preconditioner"};
+  if (opts->preconditioner == AIM_PRECOND_NEAR_SAI && near_radius < 0)
+    throw AimError{AIM_ERR_ARG, "aim_setup: the near-zone SAI preconditioner needs a near zone"};
+  c->precond = opts->preconditioner;
   {
     const char* e = std::getenv("AIM_GB300_GRAPHS");  // "0": drive the solver from the host
     c->use_graphs = !(e && e[0] == '0');
@@ -136,6 +141,7 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_b = (double2*)aim_alloc(c, vec);
   c->d_r = (double2*)aim_alloc(c, vec);
   c->d_w = (double2*)aim_alloc(c, vec);
+  if (c->d_sai) c->d_u = (double2*)aim_alloc(c, vec);
   c->d_V = (double2*)aim_alloc(c, (size_t)(c->restart + 1) * vec);
   c->d_hist = (double2*)aim_alloc(c, (size_t)ng * vec);
   c->d_exc = (double*)aim_alloc(c, (size_t)B * 6 * sizeof(double));
@@ -297,6 +303,7 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   info->grid_n = c->N;
   info->precision = c->precision;
   info->device_bytes = (int64_t)c->device_bytes;
+  info->preconditioner = c->precond;
   return AIM_OK;
 }
 
@@ -580,6 +587,26 @@ int aim_get_near(const aim_ctx* c, int32_t* rowptr, int32_t* col, aim_c128* val)
     if (val && c->nnz)
       AIM_CUDA(cudaMemcpy(val, c->d_near, (size_t)(c->n_delays + 1) * c->nnz * sizeof(double2),
                           cudaMemcpyDeviceToHost));
+    return AIM_OK;
+  });
+}
+
+int aim_get_preconditioner(const aim_ctx* c, aim_c128* val) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(const_cast<aim_ctx*>(c), [&] {
+    if (!val || c->nnz == 0) throw AimError{AIM_ERR_ARG, "aim_get_preconditioner: no near zone"};
+    if (c->d_sai) {
+      AIM_CUDA(cudaMemcpy(val, c->d_sai, c->nnz * sizeof(double2), cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<double2> dinv(c->ns);
+      std::vector<int> col(c->nnz);
+      AIM_CUDA(cudaMemcpy(dinv.data(), c->d_dinv, c->ns * sizeof(double2), cudaMemcpyDeviceToHost));
+      AIM_CUDA(cudaMemcpy(col.data(), c->d_col, c->nnz * sizeof(int), cudaMemcpyDeviceToHost));
+      double2* out = reinterpret_cast<double2*>(val);
+      for (int k = 0; k < c->ns; ++k)
+        for (int e = c->h_rowptr[k]; e < c->h_rowptr[k + 1]; ++e)
+          out[e] = col[e] == k ? dinv[k] : make_double2(0, 0);
+    }
     return AIM_OK;
   });
 }

@@ -410,9 +410,10 @@ __global__ void __launch_bounds__(kThreads) k_cycle_solve(int nb, GmresState s) 
 }
 
 // x += dinv .* sum_i vt_i (sig_i y_i);  grid (ceil(ns/32), nb), block (32, 8)
+// (with u non-null: u = sum_i vt_i (sig_i y_i) is stored instead, for the SAI below)
 __global__ void __launch_bounds__(kThreads) k_xupdate(const double2* __restrict__ V, long long vstride, int ns,
                                                       const double2* __restrict__ dinv, GmresState s,
-                                                      double2* __restrict__ x) {
+                                                      double2* __restrict__ x, double2* __restrict__ u_out) {
   const int b = blockIdx.y;
   const int J = s.jc[b];
   if (J == 0) return;
@@ -433,9 +434,38 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(const double2* __restrict_
       t.x += red[q][threadIdx.x].x;
       t.y += red[q][threadIdx.x].y;
     }
+    if (u_out) {
+      u_out[(size_t)b * ns + n] = t;
+      return;
+    }
     const double2 du = cmul(dinv[n], t);
     double2 xv = x[(size_t)b * ns + n];
     x[(size_t)b * ns + n] = make_double2(xv.x + du.x, xv.y + du.y);
+  }
+}
+
+// x_b += M u_b with the near-zone SAI (one warp per row, fixed-order warp sum); RHS with
+// an empty cycle (jc = 0) are left alone.
+__global__ void __launch_bounds__(kThreads) k_sai_xupdate(const double2* __restrict__ sai,
+                                                          const int* __restrict__ rowptr,
+                                                          const int* __restrict__ col, const double2* __restrict__ u,
+                                                          int ns, int nb, GmresState s, double2* __restrict__ x) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)nb * ns) return;
+  const int b = (int)(w / ns), k = (int)(w % ns);
+  if (s.jc[b] == 0) return;
+  const double2* ub = u + (size_t)b * ns;
+  double2 t = make_double2(0, 0);
+  for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 32) {
+    const double2 p = cmul(sai[e], ub[col[e]]);
+    t.x += p.x;
+    t.y += p.y;
+  }
+  t = make_double2(warp_sum(t.x), warp_sum(t.y));
+  if (lane == 0) {
+    double2 xv = x[(size_t)b * ns + k];
+    x[(size_t)b * ns + k] = make_double2(xv.x + t.x, xv.y + t.y);
   }
 }
 
@@ -510,7 +540,14 @@ void cycle_epilogue(aim_ctx* c, int nb, double2* x) {
   const long long vstride = (long long)c->batch_max * ns;
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_solve<<<nb, kThreads, 64 * 64 * sizeof(double2), st>>>(nb, s));
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
-              k_xupdate<<<dim3(n_upd_blocks(ns), nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, ns, c->d_dinv, s, x));
+              k_xupdate<<<dim3(n_upd_blocks(ns), nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, ns, c->d_dinv, s, x,
+                                                                                c->d_sai ? c->d_u : nullptr));
+  if (c->d_sai) {
+    const long long warps = (long long)nb * ns;
+    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
+                k_sai_xupdate<<<(int)((warps * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+                    c->d_sai, c->d_rowptr, c->d_col, c->d_u, ns, nb, s, x));
+  }
 }
 
 // ---------------------------------------------------------------- graph of one solve
@@ -700,10 +737,10 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
   AIM_CUDA(cudaMemcpyAsync(s.h_cnt, s.cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaStreamSynchronize(st));
   if (graphed) {
-    // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2)
-    // + steps * (operator + 2 x (dot, update) + finish)
+    // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2, + 1
+    // with the SAI) + steps * (operator + 2 x (dot, update) + finish)
     const long long op = op_kernel_count(c);
-    c->prof.launches += 1 + (op + 4) * s.h_cnt[0] + (op + 5) * s.h_cnt[1];
+    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 5) * s.h_cnt[1];
   }
   int rc = AIM_OK;
   for (int i = 0; i < nb; ++i) {

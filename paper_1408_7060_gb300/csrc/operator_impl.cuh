@@ -111,6 +111,44 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
   if (xd) xd[idx] = x;
 }
 
+// The same with the near-zone SAI as the preconditioner: x_b[k] = scale_b(j) *
+// sum_e M[k, col_e] v_b[col_e] over CSR row k (one warp per row, lanes over the row,
+// fixed-order warp sum).
+template <class C>
+__global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v, const double2* __restrict__ sai,
+                                                  const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                  VecSel vs, const int* __restrict__ active, int ns, int nb,
+                                                  C* __restrict__ xs, double2* __restrict__ xd) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)nb * ns) return;
+  const int b = (int)(w / ns), k = (int)(w % ns);
+  if (active && !active[b]) return;
+  double sc = 1.0;
+  if (vs.sel) {
+    const int j = *vs.sel + vs.off;
+    v += j * vs.stride;
+    if (vs.scale) sc = vs.scale[b * 64 + j];
+  }
+  const double2* vb = v + (size_t)b * ns;
+  double2 x = make_double2(0, 0);
+  for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 32) {
+    const double2 m = sai[e], u = vb[col[e]];
+    x.x += m.x * u.x - m.y * u.y;
+    x.y += m.x * u.y + m.y * u.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
+    x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+  }
+  if (lane == 0) {
+    x = make_double2(sc * x.x, sc * x.y);
+    const size_t idx = (size_t)b * ns + k;
+    xs[idx] = cvt<C>(x);
+    if (xd) xd[idx] = x;
+  }
+}
+
 // ---------------------------------------------------------------- z pass with the kernel
 __device__ __forceinline__ int fold(int k, int N) { return k <= N ? k : 2 * N - k; }
 
@@ -460,13 +498,20 @@ struct GridOps {
   static int rpb() { return std::max(1, 2048 / L); }
 
   // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
+  // dinv non-null asks for the context's right preconditioner: the diagonal dinv, or the
+  // near-zone SAI when the context built one
   static void prep(aim_ctx* c, int nb, const double2* v, const double2* dinv, VecSel vs, const int* active,
                    bool want_fp64) {
     const long long n = (long long)nb * c->ns;
     KScope ks(c, AIM_K_PREP);
-    k_prep<C><<<(int)((n + 255) / 256), 256, 0, c->stream>>>(v, dinv, vs, active, c->ns, nb,
-                                                            reinterpret_cast<C*>(c->d_xs),
-                                                            want_fp64 ? c->d_xd : nullptr);
+    if (dinv && c->d_sai)
+      k_prep_sai<C><<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(
+          v, c->d_sai, c->d_rowptr, c->d_col, vs, active, c->ns, nb, reinterpret_cast<C*>(c->d_xs),
+          want_fp64 ? c->d_xd : nullptr);
+    else
+      k_prep<C><<<(int)((n + 255) / 256), 256, 0, c->stream>>>(v, dinv, vs, active, c->ns, nb,
+                                                              reinterpret_cast<C*>(c->d_xs),
+                                                              want_fp64 ? c->d_xd : nullptr);
     AIM_CHECK_LAUNCH();
   }
 

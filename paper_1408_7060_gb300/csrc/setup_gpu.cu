@@ -370,6 +370,123 @@ __global__ void k_diag_inverse(int ns, int nnz, const int* __restrict__ rowptr, 
   dinv[k] = n > 0 ? make_double2(d.x / n, -d.y / n) : make_double2(1.0, 0.0);
 }
 
+// position of column k in the sorted CSR row [e0, e1), or -1
+__device__ __forceinline__ int csr_find(const int* __restrict__ col, int e0, int e1, int k) {
+  while (e0 < e1) {
+    const int mid = (e0 + e1) >> 1;
+    const int v = col[mid];
+    if (v == k) return mid;
+    if (v < k) e0 = mid + 1;
+    else e1 = mid;
+  }
+  return -1;
+}
+
+// Near-zone sparse approximate inverse (right preconditioner, no counterpart in the
+// paper): column k of M solves A m = e_p, A[i][j] = Z_0[S_i, S_j] on near pairs (0 off
+// the pattern), S the near set of k (CSR row k), p the position of k in S.  One block
+// per k: Gaussian elimination with partial pivoting (largest |a|, lowest row on ties)
+// of the augmented n x (n+1) system in shared memory, FP64; back substitution by one
+// warp; m scattered to M[S_i, k] (the entry of column k in CSR row S_i).  A zero pivot
+// sets *status and leaves the column zero.
+constexpr int kSaiThreads = 128;
+__global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                          const double2* __restrict__ z0, double2* __restrict__ M,
+                                                          int* __restrict__ status) {
+  extern __shared__ double2 a[];  // row i at a[i * (n + 1)], column n = right-hand side
+  __shared__ int piv;
+  __shared__ double pbest;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const int e0 = rowptr[k], n = rowptr[k + 1] - e0, ld = n + 1;
+  const int* S = col + e0;
+  for (int t = tid; t < n * n; t += kSaiThreads) {
+    const int i = t / n, j = t % n, r = S[i];
+    const int e = csr_find(col, rowptr[r], rowptr[r + 1], S[j]);
+    a[i * ld + j] = e >= 0 ? z0[e] : make_double2(0, 0);
+  }
+  for (int i = tid; i < n; i += kSaiThreads) a[i * ld + n] = make_double2(S[i] == k ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = c;
+      for (int r = c + tid; r < n; r += 32) {
+        const double2 v = a[r * ld + c];
+        const double m2 = v.x * v.x + v.y * v.y;
+        if (m2 > best) {
+          best = m2;
+          bi = r;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        piv = bi;
+        pbest = best;
+      }
+    }
+    __syncthreads();
+    if (!(pbest > 0.0)) {
+      if (tid == 0) atomicExch(status, 1);
+      for (int i = tid; i < n; i += kSaiThreads) a[i * ld + n] = make_double2(0, 0);
+      __syncthreads();
+      break;
+    }
+    if (piv != c)
+      for (int j = c + tid; j <= n; j += kSaiThreads) {
+        const double2 t = a[c * ld + j];
+        a[c * ld + j] = a[piv * ld + j];
+        a[piv * ld + j] = t;
+      }
+    __syncthreads();
+    const double2 d = a[c * ld + c];
+    const double dn = d.x * d.x + d.y * d.y;
+    const int w = n - c;  // columns c+1 .. n
+    for (int t = tid; t < (n - c - 1) * w; t += kSaiThreads) {
+      const int r = c + 1 + t / w, j = c + 1 + t % w;
+      const double2 q = a[r * ld + c];
+      const double2 f = make_double2((q.x * d.x + q.y * d.y) / dn, (q.y * d.x - q.x * d.y) / dn);  // q / d
+      const double2 u = a[c * ld + j];
+      a[r * ld + j] = make_double2(a[r * ld + j].x - (f.x * u.x - f.y * u.y), a[r * ld + j].y - (f.x * u.y + f.y * u.x));
+    }
+    __syncthreads();
+  }
+  if (tid < 32) {
+    for (int r = n - 1; r >= 0; --r) {
+      double sx = 0, sy = 0;
+      for (int j = r + 1 + tid; j < n; j += 32) {
+        const double2 u = a[r * ld + j], x = a[j * ld + n];
+        sx += u.x * x.x - u.y * x.y;
+        sy += u.x * x.y + u.y * x.x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (tid == 0) {
+        const double2 d = a[r * ld + r], b = a[r * ld + n];
+        const double dn = d.x * d.x + d.y * d.y;
+        const double2 t = make_double2(b.x - sx, b.y - sy);
+        a[r * ld + n] = dn > 0 ? make_double2((t.x * d.x + t.y * d.y) / dn, (t.y * d.x - t.x * d.y) / dn)
+                               : make_double2(0, 0);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += kSaiThreads) {
+    const int r = S[i];
+    const int e = csr_find(col, rowptr[r], rowptr[r + 1], k);
+    if (e >= 0) M[e] = a[i * ld + n];
+  }
+}
+
 // ------------------------------------------------------------------ host driver
 
 static int launch_blocks(long long work, int threads) {
@@ -576,6 +693,25 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
       k_precorrect<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(nnz, nm, d_prow, d_pcol, c->d_anchor, c->d_lam,
                                                                    tab, D, c->d_near);
       AIM_CHECK_LAUNCH();
+    }
+    // near-zone SAI from the direct immediate entries Z_0 on the near pairs
+    if (c->precond == AIM_PRECOND_NEAR_SAI) {
+      int nmax = 0;
+      for (int k = 0; k < ns; ++k) nmax = std::max(nmax, rowptr[k + 1] - rowptr[k]);
+      if (nmax > 112) throw AimError{AIM_ERR_ARG, "near-zone SAI: a near set has more than 112 RWGs"};
+      const size_t sm = (size_t)nmax * (nmax + 1) * sizeof(double2);
+      if (sm > 48 * 1024)
+        AIM_CUDA(cudaFuncSetAttribute(k_near_sai, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      c->d_sai = (double2*)aim_alloc(c, (size_t)nnz * sizeof(double2));
+      int* d_status = (int*)aim_alloc(c, sizeof(int));
+      AIM_CUDA(cudaMemsetAsync(c->d_sai, 0, (size_t)nnz * sizeof(double2), st));
+      AIM_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+      k_near_sai<<<ns, kSaiThreads, sm, st>>>(c->d_rowptr, c->d_col, zdir, c->d_sai, d_status);
+      AIM_CHECK_LAUNCH();
+      int h_status = 0;
+      AIM_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      AIM_CUDA(cudaStreamSynchronize(st));
+      if (h_status) throw AimError{AIM_ERR_ARG, "near-zone SAI: a singular near block"};
     }
     AIM_CUDA(cudaStreamSynchronize(st));
     c->h_rowptr = rowptr;

@@ -232,6 +232,7 @@ class Workload:
     order: int = 2         # CPPIF order Q
     precision: str = "c64"  # "c128" plain path, "c64" grid path with FP64 outer solve
     beta: float = 0.25
+    precond: str = "diag"  # GMRES right preconditioner: "diag" (Sec. 5.1) or "sai" (near zone)
 
     @property
     def f_bw(self) -> float:
