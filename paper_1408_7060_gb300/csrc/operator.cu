@@ -42,43 +42,49 @@ size_t op_slab_bytes(const aim_ctx* c, int nb) {
 
 // V_l[k] = <S_k, p (g'(tau) + j w g(tau)) e^{-j w (r.k/c + t_d)}>,  tau = l dt - r.k/c - t_d,
 // g = exp(-tau^2/(2 sigma^2)): the envelope of D E^inc for the plane wave of Eq. 1.
-__global__ void k_excitation(int ns, int nb, const int* __restrict__ rtri, const int* __restrict__ rfree,
-                             const double* __restrict__ len, const double* __restrict__ area,
-                             const double* __restrict__ V, const double* __restrict__ qp,
-                             const double* __restrict__ qw, const double* __restrict__ kp, double sigma, double t_d,
-                             double t, double wc, double c0, double2* __restrict__ out) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= ns * nb) return;
-  const int b = idx / ns, k = idx % ns;
+// 16 lanes per (b, k): lane l < 14 takes quadrature point q = l % 7 of side l / 7; the
+// 16 contributions are summed by a fixed xor-butterfly.
+__global__ void __launch_bounds__(128) k_excitation(int ns, int nb, const int* __restrict__ rtri,
+                                                    const int* __restrict__ rfree, const double* __restrict__ len,
+                                                    const double* __restrict__ area, const double* __restrict__ V,
+                                                    const double* __restrict__ qp, const double* __restrict__ qw,
+                                                    const double* __restrict__ kp, double sigma, double t_d, double t,
+                                                    double wc, double c0, double2* __restrict__ out) {
+  const long long g16 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+  const int l = threadIdx.x & 15;
+  const bool valid = g16 < (long long)ns * nb;  // both groups of a warp join the shuffles
+  const int b = valid ? (int)(g16 / ns) : 0, k = valid ? (int)(g16 % ns) : 0;
   const double* kh = kp + 6 * b;
   const double* ph = kh + 3;
   double2 acc = make_double2(0, 0);
-  for (int side = 0; side < 2; ++side) {
+  if (valid && l < 14) {
+    const int side = l / 7, q = l % 7;
     const int tr = rtri[2 * k + side];
     const double* vf = V + 3 * rfree[2 * k + side];
     const double cS = (side == 0 ? 1.0 : -1.0) * len[k] / (2.0 * area[tr]);
-    for (int q = 0; q < 7; ++q) {
-      const double* r = qp + 21 * tr + 3 * q;
-      const double delay = (r[0] * kh[0] + r[1] * kh[1] + r[2] * kh[2]) / c0;
-      const double tau = t - delay - t_d;
-      const double g = exp(-tau * tau / (2.0 * sigma * sigma));
-      double s, cph;
-      sincos(-wc * (delay + t_d), &s, &cph);
-      // (-tau/sigma^2 + j w) g e^{j phase}
-      const double ar = -tau / (sigma * sigma) * g, ai = wc * g;
-      const double sp = cS * ((r[0] - vf[0]) * ph[0] + (r[1] - vf[1]) * ph[1] + (r[2] - vf[2]) * ph[2]);
-      const double w = qw[7 * tr + q] * sp;
-      acc.x += w * (ar * cph - ai * s);
-      acc.y += w * (ar * s + ai * cph);
-    }
+    const double* r = qp + 21 * tr + 3 * q;
+    const double delay = (r[0] * kh[0] + r[1] * kh[1] + r[2] * kh[2]) / c0;
+    const double tau = t - delay - t_d;
+    const double g = exp(-tau * tau / (2.0 * sigma * sigma));
+    double sn, cph;
+    sincos(-wc * (delay + t_d), &sn, &cph);
+    // (-tau/sigma^2 + j w) g e^{j phase}
+    const double ar = -tau / (sigma * sigma) * g, ai = wc * g;
+    const double sp = cS * ((r[0] - vf[0]) * ph[0] + (r[1] - vf[1]) * ph[1] + (r[2] - vf[2]) * ph[2]);
+    const double w = qw[7 * tr + q] * sp;
+    acc = make_double2(w * (ar * cph - ai * sn), w * (ar * sn + ai * cph));
   }
-  out[(size_t)b * ns + k] = acc;
+  for (int o = 8; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (valid && l == 0) out[(size_t)b * ns + k] = acc;
 }
 
 void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double t_d, int step_l, double2* out) {
-  int n = c->ns * nb;
+  const long long n = (long long)c->ns * nb * 16;
   KScope ks(c, AIM_K_EXCITATION);
-  k_excitation<<<(n + 127) / 128, 128, 0, c->stream>>>(c->ns, nb, c->d_rtri, c->d_rfree, c->d_len, c->d_area,
+  k_excitation<<<(int)((n + 127) / 128), 128, 0, c->stream>>>(c->ns, nb, c->d_rtri, c->d_rfree, c->d_len, c->d_area,
                                                       c->d_v, c->d_qp, c->d_qw, d_kp, sigma, t_d,
                                                       step_l * c->dt, c->wc, aimc::kC0, out);
   AIM_CHECK_LAUNCH();

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
 // Power-of-two L: steps A and B per slab, the sum kept in registers of the step-B
 // threads, then one inverse (B, C).
 template <int L, int W, class C>
-__global__ void __launch_bounds__(kZThreads) k_zrhs_p2(SlabList sl, const C* __restrict__ kspec_all, int N,
+__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_p2(SlabList sl, const C* __restrict__ kspec_all, int N,
                                                        C* __restrict__ Bf, const C* __restrict__ twg) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
@@ -626,7 +626,9 @@ struct GridOps {
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     KScope ks(c, AIM_K_ZRHS);
     if constexpr (pow2_len(L)) {
-      constexpr int ZW = zcol_width<L, C>();
+      // 16 columns per tile: one step-B item per thread, so the delay sum held in
+      // registers stays at one radix-R2 slice
+      constexpr int ZW = L < 16 ? L : 16;
       const size_t sm = (L + L * ZW) * sizeof(C);
       smem_opt_in(k_zrhs_p2<L, ZW, C>, sm);
       k_zrhs_p2<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
