@@ -61,10 +61,10 @@ enum { AIM_CPPIF = 0 };  /* causal piecewise-polynomial interpolatory basis     
 /* Right preconditioner of the immediate system (x = M y, solve Z_0 M y = b). */
 enum { AIM_PRECOND_DIAG = 0,      /* M = diag(1 / Z_0[k,k]) (Sec. 5.1)                  */
        AIM_PRECOND_NEAR_SAI = 1 };/* no counterpart in the paper: M on the near-zone
-                                     pattern, column k = column k of the inverse of the
-                                     near block Z_0[S_k, S_k] around RWG k (S_k its near
-                                     set, Z_0 kept on near pairs only).  Needs a near
-                                     zone; a near set wider than 112 RWGs is rejected.  */
+                                     pattern, column k minimising ||Zn[:, S_k] m - e_k||
+                                     (S_k the near set of RWG k, Zn = Z_0 kept on near
+                                     pairs only).  Needs a near zone; a near set wider
+                                     than 112 RWGs is rejected.                          */
 
 typedef struct aim_ctx aim_ctx;                 /* opaque */
 typedef struct { double re, im; } aim_c128;

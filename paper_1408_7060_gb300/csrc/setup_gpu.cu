@@ -383,12 +383,15 @@ __device__ __forceinline__ int csr_find(const int* __restrict__ col, int e0, int
 }
 
 // Near-zone sparse approximate inverse (right preconditioner, no counterpart in the
-// paper): column k of M solves A m = e_p, A[i][j] = Z_0[S_i, S_j] on near pairs (0 off
-// the pattern), S the near set of k (CSR row k), p the position of k in S.  One block
-// per k: Gaussian elimination with partial pivoting (largest |a|, lowest row on ties)
-// of the augmented n x (n+1) system in shared memory, FP64; back substitution by one
-// warp; m scattered to M[S_i, k] (the entry of column k in CSR row S_i).  A zero pivot
-// sets *status and leaves the column zero.
+// paper): column k of M minimises || Zn[:, S] m - e_k ||_2, Zn = Z_0 on near pairs (0 off
+// the pattern), S the near set of k (CSR row k).  Normal equations G m = g with
+//   G[i][j] = sum_r conj(Zn[r, S_i]) Zn[r, S_j]   (r over the near sets of S_i and S_j,
+//             merged from their sorted CSR rows),   g[i] = conj(Zn[k, S_i]).
+// One block per k: G (Hermitian; upper triangle computed, lower mirrored) in shared
+// memory, Gaussian elimination with partial pivoting (largest |a|, lowest row on ties)
+// of the augmented n x (n+1) system, FP64; back substitution by one warp; m scattered to
+// M[S_i, k] (the entry of column k in CSR row S_i).  A zero pivot sets *status and
+// leaves the column zero.
 constexpr int kSaiThreads = 128;
 __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict__ rowptr, const int* __restrict__ col,
                                                           const double2* __restrict__ z0, double2* __restrict__ M,
@@ -400,11 +403,38 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
   const int e0 = rowptr[k], n = rowptr[k + 1] - e0, ld = n + 1;
   const int* S = col + e0;
   for (int t = tid; t < n * n; t += kSaiThreads) {
-    const int i = t / n, j = t % n, r = S[i];
-    const int e = csr_find(col, rowptr[r], rowptr[r + 1], S[j]);
-    a[i * ld + j] = e >= 0 ? z0[e] : make_double2(0, 0);
+    const int i = t / n, j = t % n;
+    if (i > j) continue;
+    const int si = S[i], sj = S[j];
+    int p = rowptr[si], q = rowptr[sj];
+    const int pe = rowptr[si + 1], qe = rowptr[sj + 1];
+    double gx = 0, gy = 0;
+    while (p < pe && q < qe) {  // r in near(S_i) and near(S_j), ascending
+      const int rp = col[p], rq = col[q];
+      if (rp < rq) {
+        ++p;
+      } else if (rq < rp) {
+        ++q;
+      } else {
+        const int r0 = rowptr[rp], r1 = rowptr[rp + 1];
+        const double2 zi = z0[csr_find(col, r0, r1, si)], zj = z0[csr_find(col, r0, r1, sj)];
+        gx += zi.x * zj.x + zi.y * zj.y;  // conj(zi) zj
+        gy += zi.x * zj.y - zi.y * zj.x;
+        ++p;
+        ++q;
+      }
+    }
+    a[i * ld + j] = make_double2(gx, gy);
   }
-  for (int i = tid; i < n; i += kSaiThreads) a[i * ld + n] = make_double2(S[i] == k ? 1.0 : 0.0, 0.0);
+  for (int i = tid; i < n; i += kSaiThreads) {
+    const double2 z = z0[e0 + i];  // Zn[k, S_i]
+    a[i * ld + n] = make_double2(z.x, -z.y);
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += kSaiThreads) {
+    const int i = t / n, j = t % n;
+    if (i > j) a[i * ld + j] = make_double2(a[j * ld + i].x, -a[j * ld + i].y);
+  }
   __syncthreads();
   for (int c = 0; c < n; ++c) {
     if (tid < 32) {
