@@ -49,23 +49,30 @@ CSRC = os.path.join(ROOT, "paper_1408_7060_gb300", "csrc")
 def kernel_digest(kind):
     """Digest of a kernel's source text and the FFT core it uses: measured DRAM traffic
     is only reported while the kernel is unchanged since the capture."""
-    name = {"zconv": "k_zconv", "zrhs": "k_zrhs", "interp_near": "k_interp_near",
-            "anterp_xfft": "k_anterp_rows"}.get(kind)
-    if name is None:
-        return None
     src = open(os.path.join(CSRC, "operator_impl.cuh")).read()
-    m = re.search(r"__global__ void __launch_bounds__\(256\) " + name + r"\(.*?\n}\n", src, re.S)
-    if not m:
-        return None
-    h = hashlib.sha1(m.group(0).encode())
+    if kind == "zconv":  # the power-of-two z pass: its helpers and k_zconv_p2
+        a = src.find("// Power-of-two L = R1 * R2, one tile of W adjacent z-columns per block")
+        b = src.find("// Lengths with a factor 3: staged tile")
+        if a < 0 or b < 0:
+            return None
+        text = src[a:b]
+    else:
+        name = {"interp_near": "k_interp_near", "anterp_xfft": "k_anterp_rows"}.get(kind)
+        if name is None:
+            return None
+        m = re.search(r"__global__ void __launch_bounds__\(256\) " + name + r"\(.*?\n}\n", src, re.S)
+        if not m:
+            return None
+        text = m.group(0)
+    h = hashlib.sha1(text.encode())
     for f in ("fft.cuh", "fft_kernels.cuh"):
         h.update(open(os.path.join(CSRC, f)).read().encode())
     return h.hexdigest()[:16]
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from one ncu capture of
-# this workload: (kernel, workload, source digest) -> bytes
-TRAFFIC = {("zconv", "sphere7680", "603a3063aa0f9c22"): 37968384 + 256}
+# DRAM bytes (read + write) of one launch from an ncu --set full capture (cold caches),
+# keyed by (kernel, workload, kernel_digest): profiles/zconv_sphere7680_ncu.md.
+TRAFFIC = {("zconv", "sphere7680", "d536617904978c8d"): 37967616 + 1280}
 
 
 def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):

@@ -84,7 +84,8 @@ def test_array491k_full_size():
 
 
 def test_ellipsoid_adjoint_at_scale():
-    """Ellipsoid (19 998 RWG, 96^3 grid, complex64 grid path), 40-step march.
+    """Ellipsoid (19 998 RWG, 96^3 grid, complex64 grid path, near-zone SAI
+    preconditioner with near sets of up to 83 RWGs), 40-step march.
 
     The march solves each step only to the GMRES tolerance, so the map from incident
     samples a to far field F(a) is linear only up to solver error, and the adjoint
@@ -118,7 +119,7 @@ def test_ellipsoid_adjoint_at_scale():
         d = np.fft.ifft(np.fft.fft(z) * np.exp(-0.5 * (2 * np.pi * f * w.sigma) ** 2))
         return d / np.linalg.norm(d)
 
-    with AimContext.from_workload(w, precision="c64", max_iter=2000, restart=63) as c:
+    with AimContext.from_workload(w, precision="c64", max_iter=2000, restart=63, precond="sai") as c:
         h = c.handle
 
         def F(a, tol):
