@@ -183,6 +183,7 @@ def run_aim(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.init()
     w = make_workload(args.workload, precond=args.precond)
+    w.precond_radius = args.precond_scale * w.near_radius if w.precond == "sai" else 0.0
     if ws > 1:   # each rank marches its own plane wave (independent right-hand side)
         k, p = random_plane_waves(ws, 100)
         w.khat, w.phat = k[rank:rank + 1], p[rank:rank + 1]
@@ -267,6 +268,7 @@ def run_aim(args):
         "config": {"workload": w.name, "ns": ns, "grid": f"{w.grid_n}^3 -> {2 * w.grid_n}^3 FFT",
                    "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "rhs_per_gpu": nb,
                    "tol": w.tol, "chi": round(w.chi, 3), "precond": w.precond,
+                   "precond_radius_m": round(w.precond_radius, 6), "precond_nnz": info["precond_nnz"],
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "independent plane waves per GPU" if ws > 1 else "single GPU"},
         "gmres_iters_per_step": float(np.mean(iters)),
@@ -454,7 +456,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--precond", default="sai", choices=["sai", "diag"],
-                    help="GMRES right preconditioner (near-zone SAI, or the paper's diagonal)")
+                    help="GMRES right preconditioner (sparse approximate inverse, or the paper's diagonal)")
+    ap.add_argument("--precond-scale", type=float, default=2.0,
+                    help="SAI pattern radius in units of the near-zone radius")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -60,11 +60,11 @@ enum { AIM_CPPIF = 0 };  /* causal piecewise-polynomial interpolatory basis     
 
 /* Right preconditioner of the immediate system (x = M y, solve Z_0 M y = b). */
 enum { AIM_PRECOND_DIAG = 0,      /* M = diag(1 / Z_0[k,k]) (Sec. 5.1)                  */
-       AIM_PRECOND_NEAR_SAI = 1 };/* no counterpart in the paper: M on the near-zone
-                                     pattern, column k minimising ||Zn[:, S_k] m - e_k||
-                                     (S_k the near set of RWG k, Zn = Z_0 kept on near
-                                     pairs only).  Needs a near zone; a near set wider
-                                     than 112 RWGs is rejected.                          */
+       AIM_PRECOND_NEAR_SAI = 1 };/* no counterpart in the paper: M on the pattern of
+                                     the RWG pairs within precond_radius (edge
+                                     midpoints), column k minimising ||Zp[:, S_k] m - e_k||
+                                     (S_k the pattern set of RWG k, Zp = Z_0 kept on the
+                                     pattern).  A set wider than 112 RWGs is rejected.   */
 
 typedef struct aim_ctx aim_ctx;                 /* opaque */
 typedef struct { double re, im; } aim_c128;
@@ -95,6 +95,7 @@ typedef struct {
   int32_t gmres_max_iter;/* iteration cap per step and RHS (default 500 if <= 0)    */
   void* cuda_stream;     /* cudaStream_t to run on, or NULL for a private stream    */
   int32_t preconditioner;/* AIM_PRECOND_DIAG (0, the paper's) or AIM_PRECOND_NEAR_SAI */
+  double precond_radius; /* SAI pattern radius (m); <= 0: the near radius             */
 } aim_opts;
 
 typedef struct {
@@ -123,6 +124,7 @@ typedef struct {
   int32_t precision;
   int64_t device_bytes;  /* device memory held by the context                       */
   int32_t preconditioner;/* AIM_PRECOND_*                                           */
+  int64_t precond_nnz;   /* entries of the preconditioner's sparsity pattern          */
 } aim_info;
 
 /*
@@ -300,13 +302,13 @@ int aim_farfield_adjoint(aim_ctx* ctx, int32_t nd, const double* rhat, const dou
  *   aim_get_kernel_spectrum: the stored octant [(N+1)^3] of the padded-grid
  *     spectrum of G^A_m (kind 0) or G^phi_m (kind 1), including the folded constants
  *     mu/(4 pi) or 1/(4 pi eps) and 1/(2N)^3.
- *   aim_get_preconditioner: the right preconditioner M on the near-zone CSR pattern,
- *     val[e] = M[row, col[e]] ([nnz] aim_c128; for AIM_PRECOND_DIAG only the diagonal
- *     entries are non-zero).  AIM_ERR_ARG without a near zone.
+ *   aim_get_preconditioner: the right preconditioner M in CSR form: rowptr [ns+1],
+ *     col [precond_nnz], val [precond_nnz] aim_c128 with val[e] = M[row, col[e]]
+ *     (AIM_PRECOND_DIAG: one diagonal entry per row).
  */
 int aim_get_anterp(const aim_ctx* ctx, int32_t* anchor, double* lam);
 int aim_get_near(const aim_ctx* ctx, int32_t* rowptr, int32_t* col, aim_c128* val);
-int aim_get_preconditioner(const aim_ctx* ctx, aim_c128* val);
+int aim_get_preconditioner(const aim_ctx* ctx, int32_t* rowptr, int32_t* col, aim_c128* val);
 int aim_get_kernel_spectrum(const aim_ctx* ctx, int32_t delay_m, int32_t kind, aim_c128* out);
 
 #ifdef __cplusplus

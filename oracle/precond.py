@@ -7,13 +7,14 @@ library can instead use a right preconditioner M with the sparsity of the near z
 definition (a Frobenius-norm minimising approximate inverse on a fixed pattern),
 restated plainly:
 
-* S_k = the near set of RWG k (ascending indices; k is in it);
+* S_k = the pattern set of RWG k: the RWGs whose edge midpoints are within the pattern
+  radius of k's (by default the near radius; ascending indices; k is in it);
 * Zn[i, j] = Z_0[i, j] (the Galerkin entry of the immediate matrix, Eq. 4 with m = 0)
-  when (i, j) is a near pair, 0 otherwise;
+  when (i, j) is a pattern pair, 0 otherwise;
 * column k of M is supported on S_k and minimises || Zn[:, S_k] m_k - e_k ||_2 over all
   rows (only the rows R_k that meet a near set of S_k are non-zero);
-* M[s, k] = m_k[s]; the near pattern is symmetric, so M lives on the near CSR pattern
-  (row s, column k).
+* M[s, k] = m_k[s]; the pattern is symmetric, so M lives on its CSR form (row s,
+  column k).
 
 Special cases that pin it: a near zone of self pairs only gives M = diag(1 / Z_0[k, k])
 (the paper's diagonal preconditioner); a near zone covering every pair gives M = Z_0^{-1};

@@ -45,7 +45,7 @@ class aim_tbasis(ct.Structure):
 class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
-                ("preconditioner", ct.c_int32)]
+                ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double)]
 
 
 class aim_excitation(ct.Structure):
@@ -62,7 +62,7 @@ class aim_stats(ct.Structure):
 class aim_info(ct.Structure):
     _fields_ = [("ns", ct.c_int32), ("n_delays", ct.c_int32), ("n_active", ct.c_int32),
                 ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
-                ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32)]
+                ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
@@ -114,7 +114,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
         "aim_farfield_adjoint": (ct.c_int, [P, I32, P, P, P, I32, I32, I32, P, P]),
         "aim_get_anterp": (ct.c_int, [P, P, P]),
         "aim_get_near": (ct.c_int, [P, P, P, P]),
-        "aim_get_preconditioner": (ct.c_int, [P, P]),
+        "aim_get_preconditioner": (ct.c_int, [P, P, P, P]),
         "aim_get_kernel_spectrum": (ct.c_int, [P, I32, I32, P]),
     }
     for name, (res, args) in sig.items():
@@ -169,9 +169,10 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
-              restart=50, max_iter=500, stream=None, precond="diag"):
+              restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
-    diagonal preconditioner) or "sai" (near-zone sparse approximate inverse)."""
+    diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
+    precond_radius, default the near radius)."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -180,7 +181,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     tb = aim_tbasis(AIM_CPPIF, int(order))
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
-                    stream if stream is not None else _stream_handle(), PRECOND[precond])
+                    stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -381,12 +382,16 @@ def aim_get_near(ctx):
 
 
 def aim_get_preconditioner(ctx):
-    """The right preconditioner M on the near-zone CSR pattern: val[e] = M[row, col[e]]."""
+    """The right preconditioner M in CSR form (rowptr, col, val), val[e] = M[row, col[e]]."""
     lib = load()
-    nnz = aim_get_info(ctx)["near_nnz"]
+    info = aim_get_info(ctx)
+    ns, nnz = info["ns"], info["precond_nnz"]
+    rowptr = np.empty(ns + 1, dtype=np.int32)
+    col = np.empty(max(nnz, 1), dtype=np.int32)
     val = np.empty(max(nnz, 1), dtype=np.complex128)
-    _check(lib, ctx, lib.aim_get_preconditioner(ctx, val.ctypes.data), "aim_get_preconditioner")
-    return val[:nnz]
+    _check(lib, ctx, lib.aim_get_preconditioner(ctx, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data),
+           "aim_get_preconditioner")
+    return rowptr, col[:nnz], val[:nnz]
 
 
 def aim_get_kernel_spectrum(ctx, m, kind):
@@ -410,7 +415,8 @@ class AimContext:
     def from_workload(cls, w, **over):
         V, F = w.mesh
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
-                  f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond)
+                  f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
+                  precond_radius=w.precond_radius)
         kw.update(over)
         return cls(**kw)
 

@@ -1,5 +1,6 @@
 // Internal state of an ET-AIM context and the helpers shared by the translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -62,7 +63,7 @@ struct GmresState {
   int* jc = nullptr;         // [B] columns in the current cycle
   int* its = nullptr;        // [B] iterations of this solve
   int* jdev = nullptr;       // current Arnoldi column (shared by the batch)
-  int* flag = nullptr;       // [2] any active at cycle start / after a step
+  int* flag = nullptr;       // [3] any active at cycle start / after a step / a stop without convergence
   int* cnt = nullptr;        // [2] cycles and Arnoldi steps executed (launch accounting)
   double2* pd = nullptr;     // multi-dot partials [B][64][S]
   double* pu = nullptr;      // |w|^2 partials [B][U]
@@ -148,7 +149,12 @@ struct aim_ctx {
   double2* d_near = nullptr;   // [(N_g+1)][nnz]
   double2* d_dinv = nullptr;   // [ns] 1 / Z_0[k,k]
   int precond = 0;             // AIM_PRECOND_*
-  double2* d_sai = nullptr;    // [nnz] near-zone SAI on the near CSR pattern (AIM_PRECOND_NEAR_SAI)
+  double precond_radius = 0;   // SAI pattern radius (m)
+  double2* d_sai = nullptr;    // [snnz] SAI values on its CSR pattern (AIM_PRECOND_NEAR_SAI)
+  int* d_srowptr = nullptr;    // SAI pattern (the near-zone CSR when the radii agree)
+  int* d_scol = nullptr;
+  long long snnz = 0;
+  std::vector<int> h_srowptr;
   double2* d_u = nullptr;      // [B][ns] Krylov combination before the preconditioner (SAI)
   double2* d_nearT = nullptr;  // [(N_g+1)][nnz] values of the transposed near matrices (lazy)
 
@@ -157,6 +163,9 @@ struct aim_ctx {
   void* d_Bf = nullptr;        // [B][4][N][L][L]   after the y pass (z<N slab)
   void* d_P = nullptr;         // [B][4][N][N][N]   potentials on the grid
   void* d_ring = nullptr;      // [N_g][B][4][N][L][L] spectral history slabs
+  CUtensorMap ring_map;        // TMA view of the ring [slot][B*4*N][L][L] (complex64, power-of-two L)
+  bool ring_tma = false;
+  int* d_err = nullptr;        // device error flag (a bounded wait gave up)
   void* d_xs = nullptr;        // [B][ns] prepared operator input, grid precision
   double2* d_xd = nullptr;     // [B][ns] prepared operator input, FP64 (near zone)
   double2* d_iring = nullptr;  // [N_g][B][ns] current history (RWG space)

@@ -9,6 +9,7 @@
 
 #include "aim_internal.h"
 #include "gmres.h"
+#include "tma.cuh"
 #include "operator.h"
 #include "setup_gpu.h"
 #include "setup_host.h"
@@ -80,9 +81,10 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->max_iter = opts->gmres_max_iter > 0 ? opts->gmres_max_iter : 500;
   if (opts->preconditioner != AIM_PRECOND_DIAG && opts->preconditioner != AIM_PRECOND_NEAR_SAI)
     throw AimError{AIM_ERR_ARG, "aim_setup: unknown preconditioner"};
-  if (opts->preconditioner == AIM_PRECOND_NEAR_SAI && near_radius < 0)
-    throw AimError{AIM_ERR_ARG, "aim_setup: the near-zone SAI preconditioner needs a near zone"};
   c->precond = opts->preconditioner;
+  c->precond_radius = opts->precond_radius > 0 ? opts->precond_radius : near_radius;
+  if (c->precond == AIM_PRECOND_NEAR_SAI && c->precond_radius < 0)
+    throw AimError{AIM_ERR_ARG, "aim_setup: the SAI preconditioner needs a pattern radius or a near zone"};
   {
     const char* e = std::getenv("AIM_GB300_GRAPHS");  // "0": drive the solver from the host
     c->use_graphs = !(e && e[0] == '0');
@@ -141,6 +143,8 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_b = (double2*)aim_alloc(c, vec);
   c->d_r = (double2*)aim_alloc(c, vec);
   c->d_w = (double2*)aim_alloc(c, vec);
+  c->d_err = (int*)aim_alloc(c, sizeof(int));
+  AIM_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   if (c->d_sai) c->d_u = (double2*)aim_alloc(c, vec);
   c->d_V = (double2*)aim_alloc(c, (size_t)(c->restart + 1) * vec);
   c->d_hist = (double2*)aim_alloc(c, (size_t)ng * vec);
@@ -166,7 +170,18 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
 // the spectral history ring (N_g forward slabs per right-hand side) is the largest
 // buffer; it is allocated on the first call that needs it
 void ensure_ring(aim_ctx* c) {
-  if (!c->d_ring) c->d_ring = aim_alloc(c, (size_t)c->n_delays * op_slab_bytes(c, c->batch_max));
+  if (c->d_ring) return;
+  const size_t slab = op_slab_bytes(c, c->batch_max);
+  c->d_ring = aim_alloc(c, (size_t)c->n_delays * slab);
+  // TMA view for the complex64 delayed sum: [slot][B*4*N][L][L], boxes of 16 x 1 x N x 1
+  const int L = c->L, N = c->N;
+  if (c->precision == AIM_C64 && (L & (L - 1)) == 0 && L <= 256) {
+    const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)c->batch_max * 4 * N,
+                                (cuuint64_t)c->n_delays};
+    const cuuint64_t strides[3] = {(cuuint64_t)L * 8, (cuuint64_t)L * L * 8, (cuuint64_t)slab};
+    const cuuint32_t box[4] = {(cuuint32_t)(L < 16 ? L : 16), 1, (cuuint32_t)N, 1};
+    c->ring_tma = encode_tiled_map(&c->ring_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c->d_ring, dims, strides, box);
+  }
 }
 
 // copy a caller array to device staging if it is a host pointer
@@ -304,6 +319,7 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   info->precision = c->precision;
   info->device_bytes = (int64_t)c->device_bytes;
   info->preconditioner = c->precond;
+  info->precond_nnz = c->d_sai ? c->snnz : c->ns;
   return AIM_OK;
 }
 
@@ -369,7 +385,13 @@ int aim_rhs(aim_ctx* c, int32_t l, int32_t nb, const aim_c128* hist, aim_c128* r
     double2* ys = ydev ? reinterpret_cast<double2*>(rhs) : c->d_y;
     op_apply_rhs(c, nb, sl, nl, nullptr, 1.0, ys);
     if (!ydev) AIM_CUDA(cudaMemcpyAsync(rhs, ys, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    int h_err = 0;
+    AIM_CUDA(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     AIM_CUDA(cudaStreamSynchronize(c->stream));
+    if (h_err) {
+      AIM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+      throw AimError{AIM_ERR_TIMEOUT, "aim_rhs: a bounded wait of the delayed-sum kernel gave up"};
+    }
     return AIM_OK;
   });
 }
@@ -591,21 +613,19 @@ int aim_get_near(const aim_ctx* c, int32_t* rowptr, int32_t* col, aim_c128* val)
   });
 }
 
-int aim_get_preconditioner(const aim_ctx* c, aim_c128* val) {
+int aim_get_preconditioner(const aim_ctx* c, int32_t* rowptr, int32_t* col, aim_c128* val) {
   if (!c) return AIM_ERR_ARG;
   return guard(const_cast<aim_ctx*>(c), [&] {
-    if (!val || c->nnz == 0) throw AimError{AIM_ERR_ARG, "aim_get_preconditioner: no near zone"};
     if (c->d_sai) {
-      AIM_CUDA(cudaMemcpy(val, c->d_sai, c->nnz * sizeof(double2), cudaMemcpyDeviceToHost));
+      if (rowptr) std::memcpy(rowptr, c->h_srowptr.data(), (c->ns + 1) * sizeof(int));
+      if (col) AIM_CUDA(cudaMemcpy(col, c->d_scol, c->snnz * sizeof(int), cudaMemcpyDeviceToHost));
+      if (val) AIM_CUDA(cudaMemcpy(val, c->d_sai, c->snnz * sizeof(double2), cudaMemcpyDeviceToHost));
     } else {
-      std::vector<double2> dinv(c->ns);
-      std::vector<int> col(c->nnz);
-      AIM_CUDA(cudaMemcpy(dinv.data(), c->d_dinv, c->ns * sizeof(double2), cudaMemcpyDeviceToHost));
-      AIM_CUDA(cudaMemcpy(col.data(), c->d_col, c->nnz * sizeof(int), cudaMemcpyDeviceToHost));
-      double2* out = reinterpret_cast<double2*>(val);
+      for (int k = 0; k <= c->ns; ++k)
+        if (rowptr) rowptr[k] = k;
       for (int k = 0; k < c->ns; ++k)
-        for (int e = c->h_rowptr[k]; e < c->h_rowptr[k + 1]; ++e)
-          out[e] = col[e] == k ? dinv[k] : make_double2(0, 0);
+        if (col) col[k] = k;
+      if (val) AIM_CUDA(cudaMemcpy(val, c->d_dinv, c->ns * sizeof(double2), cudaMemcpyDeviceToHost));
     }
     return AIM_OK;
   });
@@ -684,7 +704,13 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
                              dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     gmres_norms(c, nb, c->d_x, d_nrm);
     AIM_CUDA(cudaMemcpyAsync(h_nrm.data(), d_nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int h_err = 0;
+    AIM_CUDA(cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     AIM_CUDA(cudaStreamSynchronize(st));
+    if (h_err) {
+      AIM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+      throw AimError{AIM_ERR_TIMEOUT, "a bounded wait of the delayed-sum kernel gave up at step " + std::to_string(l)};
+    }
     double mx = 0;
     for (int b = 0; b < nb; ++b) mx = std::max(mx, h_nrm[b]);
     norms.push_back(mx);

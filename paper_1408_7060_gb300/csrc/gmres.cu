@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_cycle_start(CycleArgs a, GmresStat
     s.cnt[0] += 1;
     s.flag[0] = any;
     s.flag[1] = any;
+    s.flag[2] = 0;
     if (a.use_cond) {
       cudaGraphSetConditional(a.outer, any ? 1u : 0u);
       cudaGraphSetConditional(a.inner, any ? 1u : 0u);
@@ -233,7 +234,7 @@ struct FinishArgs {
   const double* pn;   // |w|^2 partials after the second update [nb][Pu]
   int Pu;
   int use_cond;
-  cudaGraphConditionalHandle inner;
+  cudaGraphConditionalHandle inner, outer;
 };
 
 // affine map x -> a x + b on complex numbers; compose(earlier, later) = later o earlier
@@ -353,7 +354,10 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s)
       s.jc[b] = j + 1;
       s.its[b] += 1;
       s.sig[b * 64 + j + 1] = hn > 0 ? 1.0 / hn : 0.0;
-      const bool stop = res <= a.tol * s.bn[b] || !(hn > 0) || s.its[b] >= a.max_iter || j + 1 >= a.restart;
+      const bool conv = res <= a.tol * s.bn[b] || !(hn > 0);
+      const bool stop = conv || s.its[b] >= a.max_iter || j + 1 >= a.restart;
+      if (conv) s.done[b] = 1;          // converged by the Arnoldi residual estimate
+      else if (stop) s.flag[2] = 1;     // stopped by the cap or the restart length
       if (stop)
         s.act[b] = 0;
       else
@@ -366,6 +370,9 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s)
     s.cnt[1] += 1;
     s.flag[1] = any;
     if (a.use_cond) cudaGraphSetConditional(a.inner, any ? 1u : 0u);
+    // every RHS of this cycle converged by its estimate: no explicit residual and no
+    // further cycle (the epilogue still applies the update)
+    if (!any && !s.flag[2] && a.use_cond) cudaGraphSetConditional(a.outer, 0u);
   }
 }
 
@@ -515,7 +522,8 @@ void arnoldi_operator(aim_ctx* c, int nb) {
 }
 
 // one Arnoldi step for every active RHS: operator into slot j+1, CGS2, column finish
-void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle inner) {
+void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle inner,
+                  cudaGraphConditionalHandle outer) {
   GmresState& s = c->gs;
   cudaStream_t st = c->stream;
   const int ns = c->ns;
@@ -529,7 +537,7 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
                 k_mupdate<<<dim3(U, nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, s.jdev, ns, S, s.act, s.sig,
                                                                    s.pd, pass == 0 ? s.h1 : s.h2, s.pu));
   }
-  FinishArgs f{nb, c->restart, c->max_iter, tol, s.pu, U, use_cond ? 1 : 0, inner};
+  FinishArgs f{nb, c->restart, c->max_iter, tol, s.pu, U, use_cond ? 1 : 0, inner, outer};
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_finish<<<1, kThreads, 0, st>>>(f, s));
 }
 
@@ -546,7 +554,7 @@ void cycle_epilogue(aim_ctx* c, int nb, double2* x) {
     const long long warps = (long long)nb * ns;
     AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
                 k_sai_xupdate<<<(int)((warps * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-                    c->d_sai, c->d_rowptr, c->d_col, c->d_u, ns, nb, s, x));
+                    c->d_sai, c->d_srowptr, c->d_scol, c->d_u, ns, nb, s, x));
   }
 }
 
@@ -615,7 +623,7 @@ void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double 
     cudaGraphNode_t pro = leaf_of(obody);
     cudaGraph_t ibody;
     cudaGraphNode_t wn = add_cond(obody, &pro, 1, inner, cudaGraphCondTypeWhile, &ibody);
-    capture_into(c, ibody, nullptr, 0, [&] { arnoldi_step(c, nb, tol, true, inner); });
+    capture_into(c, ibody, nullptr, 0, [&] { arnoldi_step(c, nb, tol, true, inner, outer); });
     capture_into(c, obody, &wn, 1, [&] { cycle_epilogue(c, nb, x); });
     cudaGraphExec_t ex;
     AIM_CUDA(cudaGraphInstantiate(&ex, g, 0));
@@ -656,7 +664,7 @@ void gmres_alloc(aim_ctx* c) {
   s.jc = (int*)aim_alloc(c, B * sizeof(int));
   s.its = (int*)aim_alloc(c, B * sizeof(int));
   s.jdev = (int*)aim_alloc(c, sizeof(int));
-  s.flag = (int*)aim_alloc(c, 2 * sizeof(int));
+  s.flag = (int*)aim_alloc(c, 3 * sizeof(int));
   s.pd = (double2*)aim_alloc(c, (size_t)B * 64 * n_dot_chunks(ns) * sizeof(double2));
   s.pu = (double*)aim_alloc(c, (size_t)B * n_upd_blocks(ns) * sizeof(double));
   s.pr = (double*)aim_alloc(c, (size_t)B * n_norm_blocks(ns) * sizeof(double));
@@ -666,7 +674,7 @@ void gmres_alloc(aim_ctx* c) {
   AIM_CUDA(cudaMallocHost(&s.h_cnt, 2 * sizeof(int)));
   AIM_CUDA(cudaFuncSetAttribute(k_cycle_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(64 * 64 * sizeof(double2))));
-  AIM_CUDA(cudaMallocHost(&s.h_flag, 2 * sizeof(int)));
+  AIM_CUDA(cudaMallocHost(&s.h_flag, 3 * sizeof(int)));
   AIM_CUDA(cudaMallocHost(&s.h_its, B * sizeof(int)));
   AIM_CUDA(cudaMallocHost(&s.h_res, B * sizeof(double)));
   AIM_CUDA(cudaMallocHost(&s.h_done, B * sizeof(int)));
@@ -718,16 +726,19 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
                 k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, st>>>(b, c->ns, s.pbn));
     for (int cycle = 0;; ++cycle) {
       cycle_prologue(c, nb, b, x, tol, false, 0, 0);
-      AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
       AIM_CUDA(cudaStreamSynchronize(st));
       if (!s.h_flag[0]) break;
       for (;;) {
-        arnoldi_step(c, nb, tol, false, 0);
-        AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        arnoldi_step(c, nb, tol, false, 0, 0);
+        AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
         AIM_CUDA(cudaStreamSynchronize(st));
         if (!s.h_flag[1]) break;
       }
       cycle_epilogue(c, nb, x);
+      AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      AIM_CUDA(cudaStreamSynchronize(st));
+      if (!s.h_flag[2]) break;  // every RHS converged by its estimate (as in the graph)
       if (cycle > 4 * (c->max_iter / std::max(1, c->restart) + 2)) break;
     }
   }

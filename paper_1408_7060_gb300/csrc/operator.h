@@ -21,6 +21,13 @@ struct NearList {
   int n;
 };
 
+// ring slots (of the contiguous history ring) and delays of the slabs, for the TMA path
+struct SlabRing {
+  int slot[aimc::kMaxDelays];
+  int m[aimc::kMaxDelays];
+  int n;
+};
+
 // history slabs (forward x/y-transformed grids) and the delay each one carries
 struct SlabList {
   const void* p[aimc::kMaxDelays];

@@ -11,10 +11,12 @@
 // non-zero inputs, inverse passes write only the N needed outputs.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "aim_internal.h"
 #include "fft_kernels.cuh"
 #include "operator.h"
+#include "tma.cuh"
 
 template <class C> struct Real;
 template <> struct Real<float2> { using T = float; using F4 = float4; };
@@ -111,19 +113,20 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
   if (xd) xd[idx] = x;
 }
 
-// The same with the near-zone SAI as the preconditioner: x_b[k] = scale_b(j) *
-// sum_e M[k, col_e] v_b[col_e] over CSR row k (one warp per row, lanes over the row,
-// fixed-order warp sum).
+// The same with the SAI as the preconditioner: x_b[k] = scale_b(j) *
+// sum_e M[k, col_e] v_b[col_e] over row k of its CSR pattern.  16 lanes per row (two rows
+// per warp), fixed-order butterfly sum over the 16 lanes: the FP64 reduction stays small
+// next to the products.
 template <class C>
 __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v, const double2* __restrict__ sai,
                                                   const int* __restrict__ rowptr, const int* __restrict__ col,
                                                   VecSel vs, const int* __restrict__ active, int ns, int nb,
                                                   C* __restrict__ xs, double2* __restrict__ xd) {
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= (long long)nb * ns) return;
-  const int b = (int)(w / ns), k = (int)(w % ns);
-  if (active && !active[b]) return;
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+  const int lane = threadIdx.x & 15;
+  const bool valid = w < (long long)nb * ns;  // both rows of a warp join the shuffles
+  const int b = valid ? (int)(w / ns) : 0, k = valid ? (int)(w % ns) : 0;
+  const bool on = valid && !(active && !active[b]);
   double sc = 1.0;
   if (vs.sel) {
     const int j = *vs.sel + vs.off;
@@ -132,16 +135,17 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
   }
   const double2* vb = v + (size_t)b * ns;
   double2 x = make_double2(0, 0);
-  for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 32) {
-    const double2 m = sai[e], u = vb[col[e]];
-    x.x += m.x * u.x - m.y * u.y;
-    x.y += m.x * u.y + m.y * u.x;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
+  if (on)
+    for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 16) {
+      const double2 m = sai[e], u = vb[col[e]];
+      x.x += m.x * u.x - m.y * u.y;
+      x.y += m.x * u.y + m.y * u.x;
+    }
+  for (int o = 8; o > 0; o >>= 1) {
     x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
     x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
   }
-  if (lane == 0) {
+  if (on && lane == 0) {
     x = make_double2(sc * x.x, sc * x.y);
     const size_t idx = (size_t)b * ns + k;
     xs[idx] = cvt<C>(x);
@@ -358,6 +362,85 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_p2(SlabList sl, const C* 
   zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
 }
 
+// The same delay sum with the history slabs streamed by TMA (complex64, power-of-two L):
+// the N x W input tile of each slab is a 4-D box of the ring tensor, loaded into one of
+// two 128-byte aligned shared buffers by cp.async.bulk.tensor and signalled on an
+// mbarrier, so slab s + 2 streams in while slab s + 1 is transformed.  Waits are
+// bounded; a wait that gives up sets *err (the host reports it) and the sum goes on.
+template <int L, int W>
+__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_tma(const __grid_constant__ CUtensorMap ring, SlabRing sr,
+                                                           const float2* __restrict__ kspec_all, int N,
+                                                           float2* __restrict__ Bf, const float2* __restrict__ twg,
+                                                           int* __restrict__ err) {
+  using C = float2;
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
+  __shared__ __align__(8) uint64_t bar[2];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(aim_smem) + 127) & ~static_cast<uintptr_t>(127));
+  C* in0 = reinterpret_cast<C*>(base);  // [2][N][W]
+  C* tw = in0 + 2 * (L / 2) * W;
+  C* t = tw + L;
+  const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
+  const unsigned bytes = (unsigned)(N * W * sizeof(C));
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  load_twiddles(tw, twg, L);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < 2 && s < sr.n; ++s) {
+      mbar_arrive_expect_tx(&bar[s], bytes);
+      tma_load_4d(in0 + s * N * W, &ring, &bar[s], x0, y, bc * N, sr.slot[s]);
+    }
+  const long long es = (long long)L * L;
+  const int n1 = N + 1;
+  const size_t oct = (size_t)n1 * n1 * n1;
+  const int kind = (bc & 3) == 3 ? 1 : 0;
+  const int fy = fold(y, N);
+  C acc[U][R2];
+#pragma unroll
+  for (int j = 0; j < U; ++j)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
+  for (int s = 0; s < sr.n; ++s) {
+    const int buf = s & 1;
+    if (!mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1))) atomicExch(err, 1);
+    const C* tile = in0 + buf * N * W;
+    const C* Gy = kspec_all + ((size_t)sr.m[s] * 2 + kind) * oct + (size_t)fy * n1;
+    zcol_step_a<L, W, C>(tile, W, t, tw);
+    __syncthreads();  // the tile is consumed: it may be refilled
+    if (threadIdx.x == 0 && s + 2 < sr.n) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[buf], bytes);
+      tma_load_4d(in0 + buf * N * W, &ring, &bar[buf], x0, y, bc * N, sr.slot[s + 2]);
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = threadIdx.x + j * kZThreads;
+      if (u < W * R1) {
+        const int l = u % W, k1 = u / W;
+        const C* G = Gy + fold(x0 + l, N);
+        C g[R2], v[R2];
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
+        zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * g[k2];
+      }
+    }
+    __syncthreads();  // every step-B read of t is done
+  }
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int u = threadIdx.x + j * kZThreads;
+    if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
+  }
+  __syncthreads();
+  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
+}
+
 // Lengths with a factor 3.
 template <int L, int W, class C>
 __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__ kspec_all, int N,
@@ -505,8 +588,8 @@ struct GridOps {
     const long long n = (long long)nb * c->ns;
     KScope ks(c, AIM_K_PREP);
     if (dinv && c->d_sai)
-      k_prep_sai<C><<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(
-          v, c->d_sai, c->d_rowptr, c->d_col, vs, active, c->ns, nb, reinterpret_cast<C*>(c->d_xs),
+      k_prep_sai<C><<<(int)((n * 16 + 255) / 256), 256, 0, c->stream>>>(
+          v, c->d_sai, c->d_srowptr, c->d_scol, vs, active, c->ns, nb, reinterpret_cast<C*>(c->d_xs),
           want_fp64 ? c->d_xd : nullptr);
     else
       k_prep<C><<<(int)((n + 255) / 256), 256, 0, c->stream>>>(v, dinv, vs, active, c->ns, nb,
@@ -625,6 +708,28 @@ struct GridOps {
     const int N = c->N;
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     KScope ks(c, AIM_K_ZRHS);
+    if constexpr (pow2_len(L) && L <= 256 && std::is_same<C, float2>::value) {
+      // the slabs' ring slots (the march and aim_rhs keep every slab in the ring)
+      const size_t slab = op_slab_bytes(c, c->batch_max);
+      SlabRing sr{};
+      sr.n = sl.n;
+      bool in_ring = c->ring_tma && sl.n > 0;
+      for (int i = 0; i < sl.n && in_ring; ++i) {
+        const long long off = (const char*)sl.p[i] - (const char*)c->d_ring;
+        in_ring = off >= 0 && off % (long long)slab == 0 && off / (long long)slab < c->n_delays;
+        sr.slot[i] = in_ring ? (int)(off / (long long)slab) : 0;
+        sr.m[i] = sl.m[i];
+      }
+      if (in_ring) {
+        constexpr int ZW = L < 16 ? L : 16;
+        const size_t sm = 128 + (2 * (L / 2) * ZW + L + L * ZW) * sizeof(C);
+        smem_opt_in(k_zrhs_tma<L, ZW>, sm);
+        k_zrhs_tma<L, ZW><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(c->ring_map, sr, kspec(c), N, Bf,
+                                                                                  twiddles(c), c->d_err);
+        AIM_CHECK_LAUNCH();
+        return;
+      }
+    }
     if constexpr (pow2_len(L)) {
       // 16 columns per tile: one step-B item per thread, so the delay sum held in
       // registers stays at one radix-R2 slice

@@ -393,15 +393,35 @@ __device__ __forceinline__ int csr_find(const int* __restrict__ col, int e0, int
 // M[S_i, k] (the entry of column k in CSR row S_i).  A zero pivot sets *status and
 // leaves the column zero.
 constexpr int kSaiThreads = 128;
+template <class T> struct SaiReal;
+template <> struct SaiReal<double2> { using R = double; };
+template <> struct SaiReal<float2> { using R = float; };
+
+// T: the complex type of the elimination (double2, or float2 for wide patterns: the
+// factorisation is O(n^3) and GB300's FP64 rate is low; G is still summed in FP64).
+// The local system is scaled by sigma = 1 / |Z_0[k, k]| (A' = sigma A, m = sigma m') so
+// that its entries are O(1): |Z_0|^2 of a time-differentiated EFIE exceeds FP32's range.
+template <class T>
 __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict__ rowptr, const int* __restrict__ col,
                                                           const double2* __restrict__ z0, double2* __restrict__ M,
                                                           int* __restrict__ status) {
-  extern __shared__ double2 a[];  // row i at a[i * (n + 1)], column n = right-hand side
+  using R = typename SaiReal<T>::R;
+  extern __shared__ __align__(16) unsigned char sai_smem[];
+  T* a = reinterpret_cast<T*>(sai_smem);  // row i at a[i * (n + 1)], column n = right-hand side
   __shared__ int piv;
-  __shared__ double pbest;
+  __shared__ R pbest;
+  __shared__ double sig;
   const int k = blockIdx.x, tid = threadIdx.x;
   const int e0 = rowptr[k], n = rowptr[k + 1] - e0, ld = n + 1;
   const int* S = col + e0;
+  if (tid == 0) {
+    const int ek = csr_find(col, e0, e0 + n, k);
+    const double2 d = ek >= 0 ? z0[ek] : make_double2(1, 0);
+    const double ad = sqrt(d.x * d.x + d.y * d.y);
+    sig = ad > 0 ? 1.0 / ad : 1.0;
+  }
+  __syncthreads();
+  const double s2 = sig * sig;
   for (int t = tid; t < n * n; t += kSaiThreads) {
     const int i = t / n, j = t % n;
     if (i > j) continue;
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
     int p = rowptr[si], q = rowptr[sj];
     const int pe = rowptr[si + 1], qe = rowptr[sj + 1];
     double gx = 0, gy = 0;
-    while (p < pe && q < qe) {  // r in near(S_i) and near(S_j), ascending
+    while (p < pe && q < qe) {  // r in the sets of S_i and S_j, ascending
       const int rp = col[p], rq = col[q];
       if (rp < rq) {
         ++p;
@@ -424,32 +444,32 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
         ++q;
       }
     }
-    a[i * ld + j] = make_double2(gx, gy);
+    a[i * ld + j] = T{(R)(s2 * gx), (R)(s2 * gy)};
   }
   for (int i = tid; i < n; i += kSaiThreads) {
-    const double2 z = z0[e0 + i];  // Zn[k, S_i]
-    a[i * ld + n] = make_double2(z.x, -z.y);
+    const double2 z = z0[e0 + i];  // Zp[k, S_i]
+    a[i * ld + n] = T{(R)(sig * z.x), (R)(-sig * z.y)};
   }
   __syncthreads();
   for (int t = tid; t < n * n; t += kSaiThreads) {
     const int i = t / n, j = t % n;
-    if (i > j) a[i * ld + j] = make_double2(a[j * ld + i].x, -a[j * ld + i].y);
+    if (i > j) a[i * ld + j] = T{a[j * ld + i].x, -a[j * ld + i].y};
   }
   __syncthreads();
   for (int c = 0; c < n; ++c) {
     if (tid < 32) {
-      double best = -1.0;
+      R best = -1;
       int bi = c;
       for (int r = c + tid; r < n; r += 32) {
-        const double2 v = a[r * ld + c];
-        const double m2 = v.x * v.x + v.y * v.y;
+        const T v = a[r * ld + c];
+        const R m2 = v.x * v.x + v.y * v.y;
         if (m2 > best) {
           best = m2;
           bi = r;
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const R ob = __shfl_down_sync(0xffffffffu, best, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -462,36 +482,36 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
       }
     }
     __syncthreads();
-    if (!(pbest > 0.0)) {
+    if (!(pbest > (R)0)) {
       if (tid == 0) atomicExch(status, 1);
-      for (int i = tid; i < n; i += kSaiThreads) a[i * ld + n] = make_double2(0, 0);
+      for (int i = tid; i < n; i += kSaiThreads) a[i * ld + n] = T{0, 0};
       __syncthreads();
       break;
     }
     if (piv != c)
       for (int j = c + tid; j <= n; j += kSaiThreads) {
-        const double2 t = a[c * ld + j];
+        const T t = a[c * ld + j];
         a[c * ld + j] = a[piv * ld + j];
         a[piv * ld + j] = t;
       }
     __syncthreads();
-    const double2 d = a[c * ld + c];
-    const double dn = d.x * d.x + d.y * d.y;
+    const T d = a[c * ld + c];
+    const R dn = d.x * d.x + d.y * d.y;
     const int w = n - c;  // columns c+1 .. n
     for (int t = tid; t < (n - c - 1) * w; t += kSaiThreads) {
       const int r = c + 1 + t / w, j = c + 1 + t % w;
-      const double2 q = a[r * ld + c];
-      const double2 f = make_double2((q.x * d.x + q.y * d.y) / dn, (q.y * d.x - q.x * d.y) / dn);  // q / d
-      const double2 u = a[c * ld + j];
-      a[r * ld + j] = make_double2(a[r * ld + j].x - (f.x * u.x - f.y * u.y), a[r * ld + j].y - (f.x * u.y + f.y * u.x));
+      const T q = a[r * ld + c];
+      const T f = T{(q.x * d.x + q.y * d.y) / dn, (q.y * d.x - q.x * d.y) / dn};  // q / d
+      const T u = a[c * ld + j];
+      a[r * ld + j] = T{a[r * ld + j].x - (f.x * u.x - f.y * u.y), a[r * ld + j].y - (f.x * u.y + f.y * u.x)};
     }
     __syncthreads();
   }
   if (tid < 32) {
     for (int r = n - 1; r >= 0; --r) {
-      double sx = 0, sy = 0;
+      R sx = 0, sy = 0;
       for (int j = r + 1 + tid; j < n; j += 32) {
-        const double2 u = a[r * ld + j], x = a[j * ld + n];
+        const T u = a[r * ld + j], x = a[j * ld + n];
         sx += u.x * x.x - u.y * x.y;
         sy += u.x * x.y + u.y * x.x;
       }
@@ -500,11 +520,10 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
       }
       if (tid == 0) {
-        const double2 d = a[r * ld + r], b = a[r * ld + n];
-        const double dn = d.x * d.x + d.y * d.y;
-        const double2 t = make_double2(b.x - sx, b.y - sy);
-        a[r * ld + n] = dn > 0 ? make_double2((t.x * d.x + t.y * d.y) / dn, (t.y * d.x - t.x * d.y) / dn)
-                               : make_double2(0, 0);
+        const T d = a[r * ld + r], b = a[r * ld + n];
+        const R dn = d.x * d.x + d.y * d.y;
+        const T t = T{b.x - sx, b.y - sy};
+        a[r * ld + n] = dn > (R)0 ? T{(t.x * d.x + t.y * d.y) / dn, (t.y * d.x - t.x * d.y) / dn} : T{0, 0};
       }
       __syncwarp();
     }
@@ -513,7 +532,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
   for (int i = tid; i < n; i += kSaiThreads) {
     const int r = S[i];
     const int e = csr_find(col, rowptr[r], rowptr[r + 1], k);
-    if (e >= 0) M[e] = a[i * ld + n];
+    if (e >= 0) M[e] = make_double2(sig * (double)a[i * ld + n].x, sig * (double)a[i * ld + n].y);
   }
 }
 
@@ -724,24 +743,52 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
                                                                    tab, D, c->d_near);
       AIM_CHECK_LAUNCH();
     }
-    // near-zone SAI from the direct immediate entries Z_0 on the near pairs
+    // SAI from the direct immediate entries Z_0 on its pattern: the near pairs, or the
+    // pairs within precond_radius (their Z_0 filled here)
     if (c->precond == AIM_PRECOND_NEAR_SAI) {
+      std::vector<int> srowptr = rowptr, scol = col;
+      const double2* sz = zdir;
+      c->d_srowptr = c->d_rowptr;
+      c->d_scol = c->d_col;
+      if (c->precond_radius != c->near_radius) {
+        host_near_pairs(hm, c->precond_radius, srowptr, scol);
+        const int sn = (int)scol.size();
+        std::vector<int> sprow(sn);
+        for (int k = 0; k < ns; ++k)
+          for (int e = srowptr[k]; e < srowptr[k + 1]; ++e) sprow[e] = k;
+        c->d_srowptr = (int*)aim_alloc(c, (ns + 1) * sizeof(int));
+        c->d_scol = (int*)aim_alloc(c, std::max(1, sn) * sizeof(int));
+        int* d_sprow = (int*)aim_alloc(c, std::max(1, sn) * sizeof(int));
+        double2* zs = (double2*)aim_alloc(c, std::max(1, sn) * sizeof(double2));
+        AIM_CUDA(cudaMemcpyAsync(c->d_srowptr, srowptr.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (sn) {
+          AIM_CUDA(cudaMemcpyAsync(c->d_scol, scol.data(), sn * sizeof(int), cudaMemcpyHostToDevice, st));
+          AIM_CUDA(cudaMemcpyAsync(d_sprow, sprow.data(), sn * sizeof(int), cudaMemcpyHostToDevice, st));
+          k_near_direct<<<(sn + 127) / 128, 128, 0, st>>>(g, tk, sn, 1, d_sprow, c->d_scol, zs);
+          AIM_CHECK_LAUNCH();
+        }
+        sz = zs;
+      }
+      c->snnz = (long long)scol.size();
+      c->h_srowptr = srowptr;
       int nmax = 0;
-      for (int k = 0; k < ns; ++k) nmax = std::max(nmax, rowptr[k + 1] - rowptr[k]);
-      if (nmax > 112) throw AimError{AIM_ERR_ARG, "near-zone SAI: a near set has more than 112 RWGs"};
-      const size_t sm = (size_t)nmax * (nmax + 1) * sizeof(double2);
-      if (sm > 48 * 1024)
-        AIM_CUDA(cudaFuncSetAttribute(k_near_sai, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      c->d_sai = (double2*)aim_alloc(c, (size_t)nnz * sizeof(double2));
+      for (int k = 0; k < ns; ++k) nmax = std::max(nmax, srowptr[k + 1] - srowptr[k]);
+      if (nmax > 112) throw AimError{AIM_ERR_ARG, "SAI preconditioner: a pattern set has more than 112 RWGs"};
+      if (nmax < 1) throw AimError{AIM_ERR_ARG, "SAI preconditioner: empty pattern"};
+      const bool fp64 = nmax <= 32;
+      const size_t sm = (size_t)nmax * (nmax + 1) * (fp64 ? sizeof(double2) : sizeof(float2));
+      auto kern = fp64 ? k_near_sai<double2> : k_near_sai<float2>;
+      if (sm > 48 * 1024) AIM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      c->d_sai = (double2*)aim_alloc(c, (size_t)std::max<long long>(1, c->snnz) * sizeof(double2));
       int* d_status = (int*)aim_alloc(c, sizeof(int));
-      AIM_CUDA(cudaMemsetAsync(c->d_sai, 0, (size_t)nnz * sizeof(double2), st));
+      AIM_CUDA(cudaMemsetAsync(c->d_sai, 0, (size_t)c->snnz * sizeof(double2), st));
       AIM_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
-      k_near_sai<<<ns, kSaiThreads, sm, st>>>(c->d_rowptr, c->d_col, zdir, c->d_sai, d_status);
+      kern<<<ns, kSaiThreads, sm, st>>>(c->d_srowptr, c->d_scol, sz, c->d_sai, d_status);
       AIM_CHECK_LAUNCH();
       int h_status = 0;
       AIM_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
       AIM_CUDA(cudaStreamSynchronize(st));
-      if (h_status) throw AimError{AIM_ERR_ARG, "near-zone SAI: a singular near block"};
+      if (h_status) throw AimError{AIM_ERR_ARG, "SAI preconditioner: a singular local system"};
     }
     AIM_CUDA(cudaStreamSynchronize(st));
     c->h_rowptr = rowptr;

@@ -232,7 +232,8 @@ class Workload:
     order: int = 2         # CPPIF order Q
     precision: str = "c64"  # "c128" plain path, "c64" grid path with FP64 outer solve
     beta: float = 0.25
-    precond: str = "diag"  # GMRES right preconditioner: "diag" (Sec. 5.1) or "sai" (near zone)
+    precond: str = "diag"  # GMRES right preconditioner: "diag" (Sec. 5.1) or "sai"
+    precond_radius: float = 0.0  # SAI pattern radius (m); 0: the near radius
 
     @property
     def f_bw(self) -> float:
