@@ -84,6 +84,8 @@ struct GmresState {
   const void* g_x = nullptr;
   const void* g_near = nullptr;
   bool graph_failed = false;
+  bool last_graphed = false;  // the last enqueued solve ran as a graph
+  int last_nb = 0;
 };
 
 // per-kernel event timing (aim_profile / aim_get_profile); ids match AIM_K_* in aim.h
@@ -151,6 +153,7 @@ struct aim_ctx {
   int precond = 0;             // AIM_PRECOND_*
   double precond_radius = 0;   // SAI pattern radius (m)
   double2* d_sai = nullptr;    // [snnz] SAI values on its CSR pattern (AIM_PRECOND_NEAR_SAI)
+  float2* d_saif = nullptr;    // the same rounded to complex64 (applied by the complex64 path)
   int* d_srowptr = nullptr;    // SAI pattern (the near-zone CSR when the radii agree)
   int* d_scol = nullptr;
   long long snnz = 0;

@@ -693,7 +693,7 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
     }
     op_apply_rhs(c, nb, sl, nl, c->d_b, -1.0, c->d_b);  // b = V_l - sum_m Z_m I_{l-m}
     AIM_CUDA(cudaEventRecord(ev[1], st));
-    int r = gmres_solve(c, nb, c->d_b, c->d_x, tol, its.data(), res.data());
+    gmres_solve_async(c, nb, c->d_b, c->d_x, tol);
     AIM_CUDA(cudaEventRecord(ev[2], st));
     // commit I_l: RWG-space history and its forward slab
     const int s = l % ng;
@@ -711,6 +711,7 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
       AIM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
       throw AimError{AIM_ERR_TIMEOUT, "a bounded wait of the delayed-sum kernel gave up at step " + std::to_string(l)};
     }
+    const int r = gmres_collect(c, its.data(), res.data());
     double mx = 0;
     for (int b = 0; b < nb; ++b) mx = std::max(mx, h_nrm[b]);
     norms.push_back(mx);

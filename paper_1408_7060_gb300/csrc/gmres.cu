@@ -701,7 +701,10 @@ void gmres_free_host(aim_ctx* c) {
 // Solve Z_0 x = b for nb right-hand sides; x holds the initial guess on entry.
 // Returns AIM_OK or AIM_ERR_NOCONV; per-RHS iteration counts and final relative
 // residuals land in iters / relres (host arrays, may be null).
-int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, int* iters, double* relres) {
+// Enqueue the solve and the copies of its statistics to pinned host memory; they are read
+// by gmres_collect once the caller has synchronised the stream (the host-driven mode
+// synchronises inside).
+void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double tol) {
   GmresState& s = c->gs;
   cudaStream_t st = c->stream;
   AIM_CUDA(cudaMemsetAsync(s.its, 0, nb * sizeof(int), st));
@@ -746,8 +749,14 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
   AIM_CUDA(cudaMemcpyAsync(s.h_res, s.relres, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaMemcpyAsync(s.h_done, s.done, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaMemcpyAsync(s.h_cnt, s.cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  AIM_CUDA(cudaStreamSynchronize(st));
-  if (graphed) {
+  s.last_graphed = graphed;
+  s.last_nb = nb;
+}
+
+int gmres_collect(aim_ctx* c, int* iters, double* relres) {
+  GmresState& s = c->gs;
+  const int nb = s.last_nb;
+  if (s.last_graphed) {
     // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2, + 1
     // with the SAI) + steps * (operator + 2 x (dot, update) + finish)
     const long long op = op_kernel_count(c);
@@ -760,6 +769,12 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
     if (s.h_done[i] != 1) rc = AIM_ERR_NOCONV;
   }
   return rc;
+}
+
+int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, int* iters, double* relres) {
+  gmres_solve_async(c, nb, b, x, tol);
+  AIM_CUDA(cudaStreamSynchronize(c->stream));
+  return gmres_collect(c, iters, relres);
 }
 
 int gmres_blocks(int ns) { return n_norm_blocks(ns); }

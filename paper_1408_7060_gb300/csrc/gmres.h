@@ -6,4 +6,8 @@ void gmres_alloc(aim_ctx* c);
 void gmres_free_host(aim_ctx* c);
 int gmres_blocks(int ns);
 int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, int* iters, double* relres);
+// the same split at the synchronisation: enqueue, then (after the stream is synchronised)
+// collect the iteration counts, residuals and status
+void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double tol);
+int gmres_collect(aim_ctx* c, int* iters, double* relres);
 void gmres_norms(aim_ctx* c, int nb, const double2* v, double* d_out);

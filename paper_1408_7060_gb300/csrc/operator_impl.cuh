@@ -114,14 +114,16 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
 }
 
 // The same with the SAI as the preconditioner: x_b[k] = scale_b(j) *
-// sum_e M[k, col_e] v_b[col_e] over row k of its CSR pattern.  16 lanes per row (two rows
-// per warp), fixed-order butterfly sum over the 16 lanes: the FP64 reduction stays small
-// next to the products.
+// sum_e M[k, col_e] v_b[col_e] over row k of its CSR pattern (at most 112 entries).  16
+// lanes per row (two rows per warp), fixed-order butterfly sum over the 16 lanes.  M is
+// applied in the grid precision: complex64 (M rounded to FP32, products and sums in FP32,
+// like the grid stages it feeds) or complex128 (FP64).
 template <class C>
-__global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v, const double2* __restrict__ sai,
+__global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v, const C* __restrict__ sai,
                                                   const int* __restrict__ rowptr, const int* __restrict__ col,
                                                   VecSel vs, const int* __restrict__ active, int ns, int nb,
                                                   C* __restrict__ xs, double2* __restrict__ xd) {
+  using R = typename Real<C>::T;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
   const int lane = threadIdx.x & 15;
   const bool valid = w < (long long)nb * ns;  // both rows of a warp join the shuffles
@@ -134,19 +136,36 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
     if (vs.scale) sc = vs.scale[b * 64 + j];
   }
   const double2* vb = v + (size_t)b * ns;
-  double2 x = make_double2(0, 0);
-  if (on)
-    for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 16) {
-      const double2 m = sai[e], u = vb[col[e]];
-      x.x += m.x * u.x - m.y * u.y;
-      x.y += m.x * u.y + m.y * u.x;
+  R xr = 0, xi = 0;
+  if (on) {
+    // up to 8 entries per lane: indices and values first, then the gathered vector
+    // entries, then the products in entry order
+    const int e0 = rowptr[k] + lane, e1 = rowptr[k + 1];
+    int j[8];
+    C m[8];
+    double2 u[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + 16 * q;
+      j[q] = e < e1 ? col[e] : -1;
+      m[q] = e < e1 ? sai[e] : C{};
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) u[q] = j[q] >= 0 ? vb[j[q]] : make_double2(0, 0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (j[q] >= 0) {
+        const R ur = (R)u[q].x, ui = (R)u[q].y;
+        xr += m[q].x * ur - m[q].y * ui;
+        xi += m[q].x * ui + m[q].y * ur;
+      }
+  }
   for (int o = 8; o > 0; o >>= 1) {
-    x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
-    x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+    xr += __shfl_xor_sync(0xffffffffu, xr, o);
+    xi += __shfl_xor_sync(0xffffffffu, xi, o);
   }
   if (on && lane == 0) {
-    x = make_double2(sc * x.x, sc * x.y);
+    const double2 x = make_double2(sc * (double)xr, sc * (double)xi);
     const size_t idx = (size_t)b * ns + k;
     xs[idx] = cvt<C>(x);
     if (xd) xd[idx] = x;
@@ -572,6 +591,8 @@ inline const double2* sel_kspec(aim_ctx* c, double2*) { return c->d_kspec; }
 inline const float4* sel_ncoef(aim_ctx* c, float2*) { return c->d_ncoeff; }
 inline const double4_32a* sel_ncoef(aim_ctx* c, double2*) { return c->d_ncoef; }
 inline const float* sel_lam(aim_ctx* c, float2*) { return c->d_lamf; }
+inline const float2* sel_sai(aim_ctx* c, float2*) { return c->d_saif; }
+inline const double2* sel_sai(aim_ctx* c, double2*) { return c->d_sai; }
 inline const double* sel_lam(aim_ctx* c, double2*) { return c->d_lam; }
 
 template <int L, class C>
@@ -589,7 +610,7 @@ struct GridOps {
     KScope ks(c, AIM_K_PREP);
     if (dinv && c->d_sai)
       k_prep_sai<C><<<(int)((n * 16 + 255) / 256), 256, 0, c->stream>>>(
-          v, c->d_sai, c->d_srowptr, c->d_scol, vs, active, c->ns, nb, reinterpret_cast<C*>(c->d_xs),
+          v, sel_sai(c, (C*)nullptr), c->d_srowptr, c->d_scol, vs, active, c->ns, nb, reinterpret_cast<C*>(c->d_xs),
           want_fp64 ? c->d_xd : nullptr);
     else
       k_prep<C><<<(int)((n + 255) / 256), 256, 0, c->stream>>>(v, dinv, vs, active, c->ns, nb,

@@ -536,6 +536,11 @@ __global__ void __launch_bounds__(kSaiThreads) k_near_sai(const int* __restrict_
   }
 }
 
+__global__ void k_round_c64(const double2* __restrict__ in, long long n, float2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
 // ------------------------------------------------------------------ host driver
 
 static int launch_blocks(long long work, int threads) {
@@ -789,6 +794,11 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
       AIM_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
       AIM_CUDA(cudaStreamSynchronize(st));
       if (h_status) throw AimError{AIM_ERR_ARG, "SAI preconditioner: a singular local system"};
+      if (c->precision == AIM_C64) {  // the complex64 path applies M in FP32
+        c->d_saif = (float2*)aim_alloc(c, (size_t)std::max<long long>(1, c->snnz) * sizeof(float2));
+        k_round_c64<<<launch_blocks(c->snnz, 256), 256, 0, st>>>(c->d_sai, c->snnz, c->d_saif);
+        AIM_CHECK_LAUNCH();
+      }
     }
     AIM_CUDA(cudaStreamSynchronize(st));
     c->h_rowptr = rowptr;
