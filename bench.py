@@ -184,6 +184,7 @@ def run_aim(args):
     torch.cuda.init()
     w = make_workload(args.workload, precond=args.precond)
     w.precond_radius = args.precond_scale * w.near_radius if w.precond == "sai" else 0.0
+    w.zero_start = args.zero_start
     if ws > 1:   # each rank marches its own plane wave (independent right-hand side)
         k, p = random_plane_waves(ws, 100)
         w.khat, w.phat = k[rank:rank + 1], p[rank:rank + 1]
@@ -269,6 +270,7 @@ def run_aim(args):
                    "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "rhs_per_gpu": nb,
                    "tol": w.tol, "chi": round(w.chi, 3), "precond": w.precond,
                    "precond_radius_m": round(w.precond_radius, 6), "precond_nnz": info["precond_nnz"],
+                   "gmres_start": "zero" if w.zero_start else "previous step",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "independent plane waves per GPU" if ws > 1 else "single GPU"},
         "gmres_iters_per_step": float(np.mean(iters)),
@@ -304,7 +306,8 @@ def run_aim(args):
 
 
 def diag_comparison(w, ctx, stream, args):
-    """The same march with the paper's diagonal preconditioner: its s/step and GMRES
+    """The same march the paper's way (diagonal preconditioner, GMRES started from the
+    previous step's currents): its s/step and GMRES
     iterations over the same steps, and the relative difference of the two marches
     (both from rest, both converged to the workload's tolerance)."""
     import torch
@@ -313,7 +316,7 @@ def diag_comparison(w, ctx, stream, args):
 
     n = args.warmup + args.steps
     with torch.cuda.stream(stream):
-        cd = AimContext.from_workload(w, precond="diag", stream=stream.cuda_stream)
+        cd = AimContext.from_workload(w, precond="diag", zero_start=False, stream=stream.cuda_stream)
     outd = torch.empty((n, w.nb, cd.ns), dtype=torch.complex128, device="cuda")
     outs = torch.empty_like(outd)
     cd.march(w.khat, w.phat, w.sigma, w.t_d, args.warmup, w.tol, out=outd[: args.warmup])
@@ -459,6 +462,8 @@ def main():
                     help="GMRES right preconditioner (sparse approximate inverse, or the paper's diagonal)")
     ap.add_argument("--precond-scale", type=float, default=2.0,
                     help="SAI pattern radius in units of the near-zone radius")
+    ap.add_argument("--zero-start", action="store_true",
+                    help="start GMRES from zero instead of the previous step's currents")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -96,6 +96,9 @@ typedef struct {
   void* cuda_stream;     /* cudaStream_t to run on, or NULL for a private stream    */
   int32_t preconditioner;/* AIM_PRECOND_DIAG (0, the paper's) or AIM_PRECOND_NEAR_SAI */
   double precond_radius; /* SAI pattern radius (m); <= 0: the near radius             */
+  int32_t zero_start;    /* 0: GMRES starts from the previous step's currents (Sec. 5.1);
+                            1: from zero, whose residual is b itself (no operator product
+                            before the first Arnoldi step)                             */
 } aim_opts;
 
 typedef struct {

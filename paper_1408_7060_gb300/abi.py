@@ -45,7 +45,7 @@ class aim_tbasis(ct.Structure):
 class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
-                ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double)]
+                ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32)]
 
 
 class aim_excitation(ct.Structure):
@@ -169,10 +169,11 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
-              restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0):
+              restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
-    precond_radius, default the near radius)."""
+    precond_radius, default the near radius).  zero_start: GMRES from zero instead of
+    the previous step's currents."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -181,7 +182,8 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     tb = aim_tbasis(AIM_CPPIF, int(order))
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
-                    stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius))
+                    stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
+                    int(bool(zero_start)))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -416,7 +418,7 @@ class AimContext:
         V, F = w.mesh
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
-                  precond_radius=w.precond_radius)
+                  precond_radius=w.precond_radius, zero_start=w.zero_start)
         kw.update(over)
         return cls(**kw)
 

@@ -152,6 +152,7 @@ struct aim_ctx {
   double2* d_dinv = nullptr;   // [ns] 1 / Z_0[k,k]
   int precond = 0;             // AIM_PRECOND_*
   double precond_radius = 0;   // SAI pattern radius (m)
+  bool zero_start = false;     // GMRES initial guess 0 instead of the previous currents
   double2* d_sai = nullptr;    // [snnz] SAI values on its CSR pattern (AIM_PRECOND_NEAR_SAI)
   float2* d_saif = nullptr;    // the same rounded to complex64 (applied by the complex64 path)
   int* d_srowptr = nullptr;    // SAI pattern (the near-zone CSR when the radii agree)

@@ -82,6 +82,7 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   if (opts->preconditioner != AIM_PRECOND_DIAG && opts->preconditioner != AIM_PRECOND_NEAR_SAI)
     throw AimError{AIM_ERR_ARG, "aim_setup: unknown preconditioner"};
   c->precond = opts->preconditioner;
+  c->zero_start = opts->zero_start != 0;
   c->precond_radius = opts->precond_radius > 0 ? opts->precond_radius : near_radius;
   if (c->precond == AIM_PRECOND_NEAR_SAI && c->precond_radius < 0)
     throw AimError{AIM_ERR_ARG, "aim_setup: the SAI preconditioner needs a pattern radius or a near zone"};
@@ -693,6 +694,7 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
     }
     op_apply_rhs(c, nb, sl, nl, c->d_b, -1.0, c->d_b);  // b = V_l - sum_m Z_m I_{l-m}
     AIM_CUDA(cudaEventRecord(ev[1], st));
+    if (c->zero_start) AIM_CUDA(cudaMemsetAsync(c->d_x, 0, n * sizeof(double2), st));
     gmres_solve_async(c, nb, c->d_b, c->d_x, tol);
     AIM_CUDA(cudaEventRecord(ev[2], st));
     // commit I_l: RWG-space history and its forward slab

@@ -189,6 +189,8 @@ struct CycleArgs {
   int Pn;
   int use_cond;
   cudaGraphConditionalHandle outer, inner;
+  int use_resid;                       // zero start: later cycles need the explicit residual
+  cudaGraphConditionalHandle resid;
 };
 
 // cycle start: beta = |r| (explicit residual in slot 0), sig_0 = 1/beta, g = (beta, 0..),
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_cycle_start(CycleArgs a, GmresStat
     if (a.use_cond) {
       cudaGraphSetConditional(a.outer, any ? 1u : 0u);
       cudaGraphSetConditional(a.inner, any ? 1u : 0u);
+      if (a.use_resid) cudaGraphSetConditional(a.resid, 1u);
     }
   }
 }
@@ -492,15 +495,26 @@ int n_norm_blocks(int ns) { return (ns + kNormChunk - 1) / kNormChunk; }
 // ---------------------------------------------------------------- launch sequences
 
 // explicit residual into slot 0 and the cycle start
-void cycle_prologue(aim_ctx* c, int nb, const double2* b, double2* x, double tol, bool use_cond,
-                    cudaGraphConditionalHandle outer, cudaGraphConditionalHandle inner) {
+// explicit residual into slot 0 (slot 0 = b - Z_0 x); with a zero start, the first
+// cycle's residual is b itself (the caller copies it and skips this)
+void cycle_residual(aim_ctx* c, int nb, const double2* b, double2* x) {
+  op_apply(c, 0, nb, x, nullptr, b, -1.0, nullptr, c->d_V);
+}
+
+void copy_b_to_slot0(aim_ctx* c, int nb, const double2* b) {
+  AIM_CUDA(cudaMemcpyAsync(c->d_V, b, (size_t)nb * c->ns * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+}
+
+// |r|^2 of slot 0 and the cycle start
+void cycle_start(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle outer,
+                 cudaGraphConditionalHandle inner, cudaGraphConditionalHandle resid) {
   GmresState& s = c->gs;
   cudaStream_t st = c->stream;
   const int ns = c->ns;
-  op_apply(c, 0, nb, x, nullptr, b, -1.0, nullptr, c->d_V);  // slot 0 = b - Z_0 x
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
               k_normpart<<<dim3(n_norm_blocks(ns), nb), kThreads, 0, st>>>(c->d_V, ns, s.pr));
-  CycleArgs a{nb, c->restart, c->max_iter, tol, s.pbn, s.pr, n_norm_blocks(ns), use_cond ? 1 : 0, outer, inner};
+  CycleArgs a{nb, c->restart, c->max_iter, tol, s.pbn, s.pr, n_norm_blocks(ns), use_cond ? 1 : 0, outer, inner,
+              (use_cond && c->zero_start) ? 1 : 0, resid};
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_start<<<1, kThreads, 0, st>>>(a, s));
 }
 
@@ -614,12 +628,27 @@ void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double 
                   k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, c->stream>>>(b, c->ns, s.pbn));
     });
     cudaGraphNode_t pre = leaf_of(g);
-    cudaGraphConditionalHandle outer, inner;
+    cudaGraphConditionalHandle outer, inner, resid = 0;
     AIM_CUDA(cudaGraphConditionalHandleCreate(&outer, g, 1, cudaGraphCondAssignDefault));
+    if (c->zero_start)  // 0 for the first cycle of every launch; the cycle start sets it to 1
+      AIM_CUDA(cudaGraphConditionalHandleCreate(&resid, g, 0, cudaGraphCondAssignDefault));
     cudaGraph_t obody;
     add_cond(g, &pre, 1, outer, cudaGraphCondTypeWhile, &obody);
     AIM_CUDA(cudaGraphConditionalHandleCreate(&inner, obody, 0, cudaGraphCondAssignDefault));
-    capture_into(c, obody, nullptr, 0, [&] { cycle_prologue(c, nb, b, x, tol, true, outer, inner); });
+    if (c->zero_start) {
+      // slot 0 = b; IF(resid) { slot 0 = b - Z_0 x }; |r|^2 and the cycle start
+      capture_into(c, obody, nullptr, 0, [&] { copy_b_to_slot0(c, nb, b); });
+      cudaGraphNode_t cp = leaf_of(obody);
+      cudaGraph_t rbody;
+      cudaGraphNode_t rn = add_cond(obody, &cp, 1, resid, cudaGraphCondTypeIf, &rbody);
+      capture_into(c, rbody, nullptr, 0, [&] { cycle_residual(c, nb, b, x); });
+      capture_into(c, obody, &rn, 1, [&] { cycle_start(c, nb, tol, true, outer, inner, resid); });
+    } else {
+      capture_into(c, obody, nullptr, 0, [&] {
+        cycle_residual(c, nb, b, x);
+        cycle_start(c, nb, tol, true, outer, inner, resid);
+      });
+    }
     cudaGraphNode_t pro = leaf_of(obody);
     cudaGraph_t ibody;
     cudaGraphNode_t wn = add_cond(obody, &pro, 1, inner, cudaGraphCondTypeWhile, &ibody);
@@ -728,7 +757,9 @@ void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double 
     AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
                 k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, st>>>(b, c->ns, s.pbn));
     for (int cycle = 0;; ++cycle) {
-      cycle_prologue(c, nb, b, x, tol, false, 0, 0);
+      if (c->zero_start && cycle == 0) copy_b_to_slot0(c, nb, b);
+      else cycle_residual(c, nb, b, x);
+      cycle_start(c, nb, tol, false, 0, 0, 0);
       AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
       AIM_CUDA(cudaStreamSynchronize(st));
       if (!s.h_flag[0]) break;
@@ -758,9 +789,11 @@ int gmres_collect(aim_ctx* c, int* iters, double* relres) {
   const int nb = s.last_nb;
   if (s.last_graphed) {
     // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2, + 1
-    // with the SAI) + steps * (operator + 2 x (dot, update) + finish)
+    // with the SAI) + steps * (operator + 2 x (dot, update) + finish); a zero start skips
+    // the operator of the first cycle
     const long long op = op_kernel_count(c);
-    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 5) * s.h_cnt[1];
+    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 5) * s.h_cnt[1] -
+                        (c->zero_start && s.h_cnt[0] > 0 ? op : 0);
   }
   int rc = AIM_OK;
   for (int i = 0; i < nb; ++i) {

@@ -234,6 +234,7 @@ class Workload:
     beta: float = 0.25
     precond: str = "diag"  # GMRES right preconditioner: "diag" (Sec. 5.1) or "sai"
     precond_radius: float = 0.0  # SAI pattern radius (m); 0: the near radius
+    zero_start: bool = False  # GMRES from zero instead of the previous step's currents
 
     @property
     def f_bw(self) -> float:

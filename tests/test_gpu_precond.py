@@ -137,3 +137,35 @@ def test_sai_full_size_iterations():
     assert out["sai2"][1] < out["sai"][1] < out["diag"][1], {k: v[1] for k, v in out.items()}
     print(f"\nsphere7680, 30 steps: GMRES iterations diag {out['diag'][1]}, near SAI {out['sai'][1]}, "
           f"SAI on 2 x the near radius {out['sai2'][1]}")
+
+
+def test_zero_start_march_vs_oracle(s480):
+    """GMRES started from zero (the first residual is b, no operator product) reaches the
+    oracle's LU march like the warm start does, with either preconditioner."""
+    w, rwg, p, A, z0 = s480
+    nt = 60
+    ZA = np.stack([A.dense(m) for m in range(A.n_delays + 1)])
+    V = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, np.arange(1, nt + 1))
+    ref = march.march_dense(ZA, V)
+    for kw in ({}, {"precond": "sai"}):
+        with ctx(w, precision="c128", zero_start=True, **kw) as c:
+            cur, stats, rc = c.march(w.khat, w.phat, w.sigma, w.t_d, nt, 1e-10)
+        assert stats["last_step"] == nt
+        err = np.linalg.norm(cur - ref, axis=2) / np.linalg.norm(ref, axis=2).max(axis=0, keepdims=True)
+        assert err.max() < 1e-6, (kw, err.max())
+
+
+def test_zero_start_graph_matches_host_loop(s480):
+    import os
+
+    w = s480[0]
+    os.environ["AIM_GB300_GRAPHS"] = "0"
+    try:
+        with ctx(w, precision="c64", precond="sai", zero_start=True) as c0:
+            a, sa, _ = c0.march(w.khat, w.phat, w.sigma, w.t_d, 25, 1e-6)
+    finally:
+        del os.environ["AIM_GB300_GRAPHS"]
+    with ctx(w, precision="c64", precond="sai", zero_start=True) as c1:
+        b, sb, _ = c1.march(w.khat, w.phat, w.sigma, w.t_d, 25, 1e-6)
+    assert sa["total_iters"] == sb["total_iters"]
+    assert np.array_equal(a, b)
