@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/aim.h"
@@ -31,6 +32,29 @@ struct AimError {
   } while (0)
 
 #define AIM_CHECK_LAUNCH() AIM_CUDA(cudaGetLastError())
+
+// programmatic dependent launch: wait for the previous kernel's results (a no-op when the
+// kernel was launched without the attribute) / let the next kernel start launching
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with programmatic dependent launch allowed: the kernel may be scheduled while
+// the previous kernel in the stream finishes; it must execute pdl_wait() before touching
+// that kernel's results (every kernel launched this way does so first).
+template <typename... P, typename... A>
+inline void launch_pdl(cudaStream_t st, dim3 grid, dim3 block, size_t smem, void (*kern)(P...), A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  AIM_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...));
+}
 
 // one profiled kernel launch: AIM_KLAUNCH(ctx, AIM_K_..., kernel<<<...>>>(...))
 #define AIM_KLAUNCH(ctx, kid, ...)   \

@@ -76,6 +76,7 @@ template <int L, bool INV, class C>
 __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __restrict__ out, int nrows,
                                                  int n_in, int n_out, long long rs_in, long long rs_out,
                                                  const C* __restrict__ twg, int rpb) {
+  pdl_wait();
   constexpr int R1 = split_r1(L), R2 = L / R1, P = row_tmp_pitch<L>();
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __
       if (k < n_out) dst[k] = v[k2];
     }
   }
+  pdl_trigger();
 }
 
 // HALF: the input is the first L/2 samples (pruned zero padding, n_in = L/2), read
@@ -166,6 +168,7 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
                                                  int n_out, long long es_in, long long es_out, int nx,
                                                  long long ps1_in, long long ps1_out, long long ps2_in,
                                                  long long ps2_out, const C* __restrict__ twg) {
+  pdl_wait();
   constexpr int R1 = split_r1(L), R2 = L / R1;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
       if (k < n_out && l < nw) dst[(long long)k * es_out + l] = v[k2];
     }
   }
+  pdl_trigger();
 }
 
 // tile width of the direct power-of-two column passes (one L x W tile)

@@ -45,6 +45,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 __global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V, long long vstride,
                                                    const int* __restrict__ jdev, int ns,
                                                    const int* __restrict__ act, double2* __restrict__ pd) {
+  pdl_wait();
   const int i = blockIdx.x, s = blockIdx.y, b = blockIdx.z;
   const int j = *jdev;
   if (i > j || !act[b]) return;
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V
     }
     pd[((size_t)b * 64 + i) * gridDim.y + s] = make_double2(a, c);
   }
+  pdl_trigger();
 }
 
 // Gram-Schmidt update of slot j+1: h_i = sig_i sum_s pd[b][i][s] (coefficients in the
@@ -94,6 +96,7 @@ __global__ void __launch_bounds__(kThreads) k_mupdate(double2* __restrict__ V, l
                                                       const int* __restrict__ act, const double* __restrict__ sig,
                                                       const double2* __restrict__ pd, double2* __restrict__ h,
                                                       double* __restrict__ pn) {
+  pdl_wait();
   const int b = blockIdx.y;
   if (!act[b]) return;
   const int j = *jdev, J = j + 1;
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_mupdate(double2* __restrict__ V, l
     nrm = warp_sum(nrm);
     if (threadIdx.x == 0) pn[(size_t)b * gridDim.x + blockIdx.x] = nrm;
   }
+  pdl_trigger();
 }
 
 // partial sums of |v_b|^2 over chunks of kNormChunk: grid (P, nb)
@@ -264,6 +268,7 @@ __device__ __forceinline__ Aff shfl_up_aff(Aff v, int d) {
 // a composition of affine maps, evaluated by a warp-wide inclusive scan (2 entries
 // per lane) instead of a j-long dependent chain of FP64 operations.
 __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s) {
+  pdl_wait();
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int j = *s.jdev;
@@ -377,6 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s)
     // further cycle (the epilogue still applies the update)
     if (!any && !s.flag[2] && a.use_cond) cudaGraphSetConditional(a.outer, 0u);
   }
+  pdl_trigger();
 }
 
 
@@ -546,13 +552,15 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
   const int S = n_dot_chunks(ns), U = n_upd_blocks(ns);
   for (int pass = 0; pass < 2; ++pass) {
     AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
-                k_mdot<<<dim3(64, S, nb), kThreads, 0, st>>>(c->d_V, vstride, s.jdev, ns, s.act, s.pd));
+                launch_pdl(st, dim3(64, S, nb), dim3(kThreads), 0, k_mdot, (const double2*)c->d_V, vstride,
+                           (const int*)s.jdev, ns, (const int*)s.act, s.pd));
     AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-                k_mupdate<<<dim3(U, nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, s.jdev, ns, S, s.act, s.sig,
-                                                                   s.pd, pass == 0 ? s.h1 : s.h2, s.pu));
+                launch_pdl(st, dim3(U, nb), dim3(kUpdN, 8), 0, k_mupdate, c->d_V, vstride, (const int*)s.jdev, ns, S,
+                           (const int*)s.act, (const double*)s.sig, (const double2*)s.pd, pass == 0 ? s.h1 : s.h2,
+                           s.pu));
   }
   FinishArgs f{nb, c->restart, c->max_iter, tol, s.pu, U, use_cond ? 1 : 0, inner, outer};
-  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_finish<<<1, kThreads, 0, st>>>(f, s));
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, launch_pdl(st, dim3(1), dim3(kThreads), 0, k_finish, f, s));
 }
 
 void cycle_epilogue(aim_ctx* c, int nb, double2* x) {

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
                                                      const C* __restrict__ xs, const int* __restrict__ active,
                                                      int ns, int N, int ypb, C* __restrict__ A,
                                                      const C* __restrict__ twg) {
+  pdl_wait();
   using R = typename Real<C>::T;
   const int b = blockIdx.z;
   if (active && !active[b]) return;
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
     const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
     if (y < N) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
   }
+  pdl_trigger();
 }
 
 // Operator input: x_b = scale_b(j) * dinv .* v_b (selection, Krylov scale and
@@ -93,6 +95,7 @@ template <class C>
 __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, const double2* __restrict__ dinv,
                                               VecSel vs, const int* __restrict__ active, int ns, int nb,
                                               C* __restrict__ xs, double2* __restrict__ xd) {
+  pdl_wait();
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)nb * ns) return;
   const int b = (int)(idx / ns), k = (int)(idx % ns);
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
   }
   xs[idx] = cvt<C>(x);
   if (xd) xd[idx] = x;
+  pdl_trigger();
 }
 
 // The same with the SAI as the preconditioner: x_b[k] = scale_b(j) *
@@ -123,6 +127,7 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
                                                   const int* __restrict__ rowptr, const int* __restrict__ col,
                                                   VecSel vs, const int* __restrict__ active, int ns, int nb,
                                                   C* __restrict__ xs, double2* __restrict__ xd) {
+  pdl_wait();
   using R = typename Real<C>::T;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
   const int lane = threadIdx.x & 15;
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
     xs[idx] = cvt<C>(x);
     if (xd) xd[idx] = x;
   }
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------- z pass with the kernel
@@ -262,6 +268,7 @@ template <int L, int W, class C>
 __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
                                                         const int* __restrict__ active,
                                                         const C* __restrict__ twg) {
+  pdl_wait();
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
   const int bc = blockIdx.z;
   if (active && !active[bc >> 2]) return;
@@ -289,6 +296,7 @@ __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, cons
   }
   __syncthreads();
   zcol_step_c<L, W, C>(t, tw, col, es);
+  pdl_trigger();
 }
 
 // Lengths with a factor 3: staged tile, Stockham passes, separate product loop.
@@ -512,6 +520,7 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
                                                      const double2* __restrict__ base, double sign,
                                                      const int* __restrict__ active, double2* __restrict__ y,
                                                      VecSel ys) {
+  pdl_wait();
   using R = typename Real<C>::T;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -575,6 +584,7 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
     }
     y[(size_t)b * ns + k] = r;
   }
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------- launch helpers
@@ -609,14 +619,12 @@ struct GridOps {
     const long long n = (long long)nb * c->ns;
     KScope ks(c, AIM_K_PREP);
     if (dinv && c->d_sai)
-      k_prep_sai<C><<<(int)((n * 16 + 255) / 256), 256, 0, c->stream>>>(
-          v, sel_sai(c, (C*)nullptr), c->d_srowptr, c->d_scol, vs, active, c->ns, nb, reinterpret_cast<C*>(c->d_xs),
-          want_fp64 ? c->d_xd : nullptr);
+      launch_pdl(c->stream, dim3((unsigned)((n * 16 + 255) / 256)), dim3(256), 0, k_prep_sai<C>, v,
+                 sel_sai(c, (C*)nullptr), (const int*)c->d_srowptr, (const int*)c->d_scol, vs, active, c->ns, nb,
+                 reinterpret_cast<C*>(c->d_xs), want_fp64 ? c->d_xd : (double2*)nullptr);
     else
-      k_prep<C><<<(int)((n + 255) / 256), 256, 0, c->stream>>>(v, dinv, vs, active, c->ns, nb,
-                                                              reinterpret_cast<C*>(c->d_xs),
-                                                              want_fp64 ? c->d_xd : nullptr);
-    AIM_CHECK_LAUNCH();
+      launch_pdl(c->stream, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, k_prep<C>, v, dinv, vs, active, c->ns,
+                 nb, reinterpret_cast<C*>(c->d_xs), want_fp64 ? c->d_xd : (double2*)nullptr);
   }
 
   static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab,
@@ -631,10 +639,8 @@ struct GridOps {
       smem_opt_in(k_anterp_rows<L, C>, sm);
       dim3 grid((N + yp - 1) / yp, N, nb);
       KScope ks(c, AIM_K_ANTERP_XFFT);
-      k_anterp_rows<L, C><<<grid, 256, sm, c->stream>>>(c->d_nptr, c->d_nidx, ncoef(c),
-                                                        reinterpret_cast<const C*>(c->d_xs), active, c->ns, N, yp,
-                                                        A, tw);
-      AIM_CHECK_LAUNCH();
+      launch_pdl(c->stream, grid, dim3(256), sm, k_anterp_rows<L, C>, (const int*)c->d_nptr, (const int*)c->d_nidx,
+                 ncoef(c), reinterpret_cast<const C*>(c->d_xs), active, c->ns, N, yp, A, tw);
     }
     {
       KScope ks(c, AIM_K_YFFT_FWD);
@@ -642,8 +648,9 @@ struct GridOps {
         constexpr int CW = col_width_p2<L, C>();
         const size_t sm = (L + L * CW) * sizeof(C);
         smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
-        k_cols_p2<L, CW, false, C, true><<<dim3(L / CW, N, nb * 4), 256, sm, c->stream>>>(
-            A, slab, N, L, L, L, L, (long long)N * L, (long long)L * L, (long long)N * N * L, (long long)N * L * L, tw);
+        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>,
+                   (const C*)A, slab, N, L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L,
+                   (long long)N * N * L, (long long)N * L * L, tw);
       } else {
         const size_t sm = (L + 2 * L * W) * sizeof(C);
         smem_opt_in(k_cols<L, W, false, C, true>, sm);
@@ -668,8 +675,9 @@ struct GridOps {
         constexpr int CW = col_width_p2<L, C>();
         const size_t sm = (L + L * CW) * sizeof(C);
         smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
-        k_cols_p2<L, CW, true, C><<<dim3(L / CW, N, nb * 4), 256, sm, c->stream>>>(
-            Bf, A, L, N, L, L, L, (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, tw);
+        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>, (const C*)Bf, A, L,
+                   N, (long long)L, (long long)L, L, (long long)L * L, (long long)N * L, (long long)N * L * L,
+                   (long long)N * N * L, tw);
       } else {
         const size_t sm = (L + 2 * L * W) * sizeof(C);
         smem_opt_in(k_cols<L, W, true, C>, sm);
@@ -685,7 +693,8 @@ struct GridOps {
         const int rp = std::max(1, 4096 / L);
         const size_t sm = (L + rp * row_tmp_pitch<L>()) * sizeof(C);
         smem_opt_in(k_rows_p2<L, true, C>, sm);
-        k_rows_p2<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
+        launch_pdl(c->stream, dim3((nrows + rp - 1) / rp), dim3(256), sm, k_rows_p2<L, true, C>, (const C*)A, P, nrows,
+                   L, N, (long long)L, (long long)N, tw, rp);
       } else {
         const int rp = rpb();
         const size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(C);
@@ -701,9 +710,9 @@ struct GridOps {
                      const int* active, double2* y, VecSel ys = VecSel()) {
     long long warps = (long long)nb * c->ns;
     KScope ks(c, AIM_K_INTERP_NEAR);
-    k_interp_near<C><<<(int)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(
-        P, c->d_anchor, lam(c), c->N, c->ns, nb, c->d_rowptr, c->d_col, nl, base, sign, active, y, ys);
-    AIM_CHECK_LAUNCH();
+    launch_pdl(c->stream, dim3((unsigned)((warps * 32 + 255) / 256)), dim3(256), 0, k_interp_near<C>, P,
+               (const int*)c->d_anchor, lam(c), c->N, c->ns, nb, (const int*)c->d_rowptr, (const int*)c->d_col, nl,
+               base, sign, active, y, ys);
   }
 
   static void zconv(aim_ctx* c, int nb, int m, const int* active) {
@@ -716,7 +725,8 @@ struct GridOps {
       constexpr int ZW = zcol_width<L, C>();
       const size_t sm = (L + L * ZW) * sizeof(C);
       smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
-      k_zconv_p2<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(Bf, G, N, active, twiddles(c));
+      launch_pdl(c->stream, dim3(L / ZW, L, nb * 4), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
+                 twiddles(c));
     } else {
       const size_t sm = (L + 2 * L * W) * sizeof(C);
       smem_opt_in(k_zconv<L, W, C>, sm);
