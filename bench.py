@@ -72,7 +72,7 @@ def kernel_digest(kind):
 
 # DRAM bytes (read + write) of one launch from an ncu --set full capture (cold caches),
 # keyed by (kernel, workload, kernel_digest): profiles/zconv_sphere7680_ncu.md.
-TRAFFIC = {("zconv", "sphere7680", "d536617904978c8d"): 37967616 + 1280}
+TRAFFIC = {("zconv", "sphere7680", "a435e10b1cbf6410"): 37968128 + 2816}
 
 
 def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
@@ -460,7 +460,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--precond", default="sai", choices=["sai", "diag"],
                     help="GMRES right preconditioner (sparse approximate inverse, or the paper's diagonal)")
-    ap.add_argument("--precond-scale", type=float, default=2.0,
+    ap.add_argument("--precond-scale", type=float, default=2.5,
                     help="SAI pattern radius in units of the near-zone radius")
     ap.add_argument("--zero-start", action="store_true",
                     help="start GMRES from zero instead of the previous step's currents")

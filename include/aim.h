@@ -64,7 +64,7 @@ enum { AIM_PRECOND_DIAG = 0,      /* M = diag(1 / Z_0[k,k]) (Sec. 5.1)          
                                      the RWG pairs within precond_radius (edge
                                      midpoints), column k minimising ||Zp[:, S_k] m - e_k||
                                      (S_k the pattern set of RWG k, Zp = Z_0 kept on the
-                                     pattern).  A set wider than 112 RWGs is rejected.   */
+                                     pattern).  A set wider than 144 RWGs is rejected.   */
 
 typedef struct aim_ctx aim_ctx;                 /* opaque */
 typedef struct { double re, im; } aim_c128;

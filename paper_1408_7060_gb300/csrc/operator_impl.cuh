@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
 }
 
 // The same with the SAI as the preconditioner: x_b[k] = scale_b(j) *
-// sum_e M[k, col_e] v_b[col_e] over row k of its CSR pattern (at most 112 entries).  16
+// sum_e M[k, col_e] v_b[col_e] over row k of its CSR pattern (at most 144 entries).  16
 // lanes per row (two rows per warp), fixed-order butterfly sum over the 16 lanes.  M is
 // applied in the grid precision: complex64 (M rounded to FP32, products and sums in FP32,
 // like the grid stages it feeds) or complex128 (FP64).
@@ -143,22 +143,22 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
   const double2* vb = v + (size_t)b * ns;
   R xr = 0, xi = 0;
   if (on) {
-    // up to 8 entries per lane: indices and values first, then the gathered vector
+    // up to 9 entries per lane: indices and values first, then the gathered vector
     // entries, then the products in entry order
     const int e0 = rowptr[k] + lane, e1 = rowptr[k + 1];
-    int j[8];
-    C m[8];
-    double2 u[8];
+    int j[9];
+    C m[9];
+    double2 u[9];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 9; ++q) {
       const int e = e0 + 16 * q;
       j[q] = e < e1 ? col[e] : -1;
       m[q] = e < e1 ? sai[e] : C{};
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) u[q] = j[q] >= 0 ? vb[j[q]] : make_double2(0, 0);
+    for (int q = 0; q < 9; ++q) u[q] = j[q] >= 0 ? vb[j[q]] : make_double2(0, 0);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < 9; ++q)
       if (j[q] >= 0) {
         const R ur = (R)u[q].x, ui = (R)u[q].y;
         xr += m[q].x * ur - m[q].y * ui;

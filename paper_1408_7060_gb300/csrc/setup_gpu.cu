@@ -778,7 +778,7 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
       c->h_srowptr = srowptr;
       int nmax = 0;
       for (int k = 0; k < ns; ++k) nmax = std::max(nmax, srowptr[k + 1] - srowptr[k]);
-      if (nmax > 112) throw AimError{AIM_ERR_ARG, "SAI preconditioner: a pattern set has more than 112 RWGs"};
+      if (nmax > 144) throw AimError{AIM_ERR_ARG, "SAI preconditioner: a pattern set has more than 144 RWGs"};
       if (nmax < 1) throw AimError{AIM_ERR_ARG, "SAI preconditioner: empty pattern"};
       const bool fp64 = nmax <= 32;
       const size_t sm = (size_t)nmax * (nmax + 1) * (fp64 ? sizeof(double2) : sizeof(float2));
