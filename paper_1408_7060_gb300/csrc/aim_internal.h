@@ -72,7 +72,10 @@ struct TBasis {
 
 // GMRES small state, one row of 64 per right-hand side (restart <= 63)
 struct GmresState {
-  double2* H = nullptr;      // [B][64][64] rotated Hessenberg (upper triangle)
+  double2* H = nullptr;      // [B][64][64] Hessenberg columns, unrotated (upper triangle)
+  double2* rd = nullptr;     // [B][64] diagonal of the rotated triangle R
+  double2* rho = nullptr;    // [B][64] row j of the accumulated Givens rotation
+  unsigned* fin = nullptr;   // [2] column-finish arrivals, any RHS still iterating
   double2* g = nullptr;      // [B][64]
   double2* sn = nullptr;     // [B][64]
   double* cs = nullptr;      // [B][64]

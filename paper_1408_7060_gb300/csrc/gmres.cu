@@ -40,6 +40,21 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Sum over the lanes of a warp of a complex value, in 5 FP64 additions instead of 10:
+// the first exchange pairs lane l with l ^ 16, the lower half keeping the real and the
+// upper half the imaginary part, then both halves reduce their part in 4 more steps.
+// (A double-precision instruction holds its sub-partition's FP64 pipe for the whole
+// warp whatever the number of active lanes, so the instruction count is the cost.)
+__device__ __forceinline__ double2 warp_sum_c(double2 v) {
+  const int lane = threadIdx.x & 31;
+  const bool hi = lane & 16;
+  double keep = hi ? v.y : v.x;
+  const double send = hi ? v.x : v.y;
+  keep += __shfl_xor_sync(0xffffffffu, send, 16);
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return make_double2(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
+}
+
 // raw partial dots pd[b][i][s] = sum_{n in chunk s} conj(vt_i[n]) w[n], w = slot j+1.
 // grid (64, S, nb); blocks with i > j return at once.
 __global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V, long long vstride,
@@ -69,8 +84,11 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V
     im += p.y;
   }
   __shared__ double red[2][kThreads / 32];
-  re = warp_sum(re);
-  im = warp_sum(im);
+  {
+    const double2 t = warp_sum_c(make_double2(re, im));
+    re = t.x;
+    im = t.y;
+  }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = re;
     red[1][threadIdx.x >> 5] = im;
@@ -217,12 +235,15 @@ __global__ void __launch_bounds__(kThreads) k_cycle_start(CycleArgs a, GmresStat
       s.jc[b] = 0;
       s.sig[b * 64] = beta > 0 ? 1.0 / beta : 0.0;
       s.g[b * 64] = make_double2(beta, 0.0);
+      s.rho[b * 64] = make_double2(1.0, 0.0);
       if (s.act[b]) atomicOr(&any, 1);
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     *s.jdev = 0;
+    s.fin[0] = 0u;
+    s.fin[1] = 0u;
     s.cnt[0] += 1;
     s.flag[0] = any;
     s.flag[1] = any;
@@ -244,153 +265,155 @@ struct FinishArgs {
   cudaGraphConditionalHandle inner, outer;
 };
 
-// affine map x -> a x + b on complex numbers; compose(earlier, later) = later o earlier
-struct Aff {
-  double2 a, b;
-};
-__device__ __forceinline__ Aff aff_then(Aff e, Aff l) {  // l o e
-  return Aff{cmul(l.a, e.a), make_double2(cmul(l.a, e.b).x + l.b.x, cmul(l.a, e.b).y + l.b.y)};
-}
-__device__ __forceinline__ Aff shfl_up_aff(Aff v, int d) {
-  Aff r;
-  r.a.x = __shfl_up_sync(0xffffffffu, v.a.x, d);
-  r.a.y = __shfl_up_sync(0xffffffffu, v.a.y, d);
-  r.b.x = __shfl_up_sync(0xffffffffu, v.b.x, d);
-  r.b.y = __shfl_up_sync(0xffffffffu, v.b.y, d);
-  return r;
-}
-
-// Arnoldi column j for every active RHS: H[0..j][j] = h1 + h2, H[j+1][j] = |w|, the
-// previous rotations, a new complex Givens rotation, |g_{j+1}|, convergence / cap,
-// sig_{j+1} = 1/|w|; then j += 1 and the inner loop condition.  One warp per RHS.
-// Applying G_0..G_{j-1} to the column is the recurrence p_0 = h_0,
-// p_{i+1} = -conj(s_i) p_i + c_i h_{i+1}, with rotated entries c_i p_i + s_i h_{i+1}:
-// a composition of affine maps, evaluated by a warp-wide inclusive scan (2 entries
-// per lane) instead of a j-long dependent chain of FP64 operations.
+// Arnoldi column j for every active RHS.  The column h = h1 + h2 (entries 0..j) is stored
+// unrotated in H[.][j]; the Givens rotations G_0..G_{j-1} reach it only through
+//   p_j = (G_{j-1} ... G_0 h)_j = rho_j . h,
+// where rho_j is row j of the accumulated rotation, kept from step to step by
+// rho_{j+1} = (-conj(s_j) rho_j, c_j), rho_0 = (1).  With |w|^2 (sum of the partials) the
+// new rotation is c_j = |p|/r, s_j = (p/|p|) |w|/r, r^2 = |p|^2 + |w|^2, and
+// R[j][j] = p r/|p|, g_{j+1} = -conj(s_j) g_j, g_j <- c_j g_j, and the residual estimate
+// |g_{j+1}|/|b| = relres_j |w|/r -- three reciprocal square roots and no division.  The
+// rotated entries above the diagonal are formed once per cycle, in k_cycle_solve.
+// Block k of the grid takes the RHS b = k, k + gridDim.x, ...: warp 0 sums |w|^2 while
+// warp 1 forms p_j; the last block to finish advances j and sets the loop conditions.
 __global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s) {
   pdl_wait();
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int blk = blockIdx.x, nblk = gridDim.x;
   const int j = *s.jdev;
+  __shared__ double sh_hn2, sh_rhn, sh_p2, sh_rp;
+  __shared__ double2 sh_p, sh_s;
+  __shared__ double sh_c;
   __shared__ int any;
   if (tid == 0) any = 0;
-  __syncthreads();
-  for (int b = warp; b < a.nb; b += nw) {
+  for (int b = blk; b < a.nb; b += nblk) {
+    __syncthreads();
     if (!s.act[b]) continue;
-    const double hn = sqrt(warp_row_sum(a.pn + (size_t)b * a.Pu, a.Pu));
-    // entries i = 2 lane, 2 lane + 1 of the column and the rotations that act on them
-    double2 h[2], sn[2];
-    double cs[2];
-    Aff m[2];
-    for (int t = 0; t < 2; ++t) {
-      const int i = 2 * lane + t;
-      h[t] = make_double2(0, 0);
-      if (i <= j) {
+    double2 gj = make_double2(0, 0);
+    double rel = 0;
+    int its = 0;
+    if (warp == 0) {
+      const double hn2 = warp_row_sum(a.pn + (size_t)b * a.Pu, a.Pu);
+      if (lane == 0) {
+        sh_hn2 = hn2;
+        sh_rhn = hn2 > 0 ? rsqrt(hn2) : 0.0;
+        gj = s.g[b * 64 + j];
+        rel = s.relres[b];
+        its = s.its[b];
+      }
+    } else if (warp == 1) {
+      double2* H = s.H + (size_t)b * 64 * 64;  // H[i][k] at i*64 + k
+      double2 acc = make_double2(0, 0);
+      for (int i = lane; i <= j; i += 32) {
         const double2 x = s.h1[b * 64 + i], y = s.h2[b * 64 + i];
-        h[t] = make_double2(x.x + y.x, x.y + y.y);
+        const double2 h = make_double2(x.x + y.x, x.y + y.y);
+        H[i * 64 + j] = h;
+        const double2 r = s.rho[b * 64 + i];
+        acc.x += r.x * h.x - r.y * h.y;
+        acc.y += r.x * h.y + r.y * h.x;
+      }
+      const double2 pj = warp_sum_c(acc);
+      if (lane == 0) {
+        const double p2 = pj.x * pj.x + pj.y * pj.y;
+        sh_p = pj;
+        sh_p2 = p2;
+        sh_rp = p2 > 0 ? rsqrt(p2) : 0.0;
       }
     }
-    // h_{i+1} for the rotation G_i held by this lane (i = 2 lane + t)
-    const double2 hn0 = h[1];
-    double2 hn1 = make_double2(__shfl_down_sync(0xffffffffu, h[0].x, 1), __shfl_down_sync(0xffffffffu, h[0].y, 1));
-    const double2 hnext[2] = {hn0, hn1};
-    for (int t = 0; t < 2; ++t) {
-      const int i = 2 * lane + t;
-      if (i < j) {
-        cs[t] = s.cs[b * 64 + i];
-        sn[t] = s.sn[b * 64 + i];
-        m[t] = Aff{make_double2(-sn[t].x, sn[t].y), make_double2(cs[t] * hnext[t].x, cs[t] * hnext[t].y)};
-      } else {
-        cs[t] = 1.0;
-        sn[t] = make_double2(0, 0);
-        m[t] = Aff{make_double2(1, 0), make_double2(0, 0)};  // identity
-      }
-    }
-    // inclusive scan over i of the compositions M_i o ... o M_0
-    Aff inc1 = aff_then(m[0], m[1]);  // lane aggregate (entry 2 lane + 1)
-    Aff agg = inc1;
-    for (int d = 1; d < 32; d <<= 1) {
-      Aff o = shfl_up_aff(agg, d);
-      if (lane >= d) agg = aff_then(o, agg);
-    }
-    Aff excl = shfl_up_aff(agg, 1);
-    if (lane == 0) excl = Aff{make_double2(1, 0), make_double2(0, 0)};
-    const double2 h0 = make_double2(__shfl_sync(0xffffffffu, h[0].x, 0), __shfl_sync(0xffffffffu, h[0].y, 0));
-    // p_i for i = 2 lane (= excl(h0)) and i = 2 lane + 1 (= (M_{2 lane} o excl)(h0))
-    const Aff c0 = excl, c1 = aff_then(excl, m[0]);
-    double2 p[2];
-    p[0] = make_double2(cmul(c0.a, h0).x + c0.b.x, cmul(c0.a, h0).y + c0.b.y);
-    p[1] = make_double2(cmul(c1.a, h0).x + c1.b.x, cmul(c1.a, h0).y + c1.b.y);
-    double2* H = s.H + (size_t)b * 64 * 64;  // H[i][j] at i*64 + j
-    double2 pj = make_double2(0, 0);
-    for (int t = 0; t < 2; ++t) {
-      const int i = 2 * lane + t;
-      if (i < j) {
-        const double2 sq = cmul(sn[t], hnext[t]);
-        H[i * 64 + j] = make_double2(cs[t] * p[t].x + sq.x, cs[t] * p[t].y + sq.y);
-      } else if (i == j) {
-        pj = p[t];
-      }
-    }
-    // the new rotation (lane holding entry j)
-    if (2 * lane == j || 2 * lane + 1 == j) {
-      const double2 pp = pj;
-      const double na = sqrt(pp.x * pp.x + pp.y * pp.y);
-      const double nd = hn;
-      const double r = sqrt(na * na + nd * nd);
+    __syncthreads();
+    if (tid == 0) {
+      const double hn2 = sh_hn2, p2 = sh_p2, r2 = hn2 + p2, rhn = sh_rhn;
+      const double hn = hn2 * rhn;  // |w| (0 when |w| = 0)
+      const double rr = r2 > 0 ? rsqrt(r2) : 0.0;
+      const double2 pj = sh_p;
       double c;
-      double2 snew;
-      if (r == 0.0) {
+      double2 sv, rjj;
+      if (!(r2 > 0)) {
         c = 1.0;
-        snew = make_double2(0, 0);
-      } else if (na == 0.0) {
+        sv = make_double2(0, 0);
+        rjj = make_double2(0, 0);
+      } else if (!(p2 > 0)) {
         c = 0.0;
-        snew = make_double2(1.0, 0.0);
+        sv = make_double2(1.0, 0.0);
+        rjj = make_double2(hn, 0.0);
       } else {
-        c = na / r;
-        snew = make_double2(pp.x / na * (nd / r), pp.y / na * (nd / r));  // (p/|p|) hn/r, hn real
+        const double inv = rr * sh_rp;  // 1 / (|p| r)
+        c = p2 * inv;
+        const double q = hn * inv, t = r2 * inv;
+        sv = make_double2(pj.x * q, pj.y * q);
+        rjj = make_double2(pj.x * t, pj.y * t);
       }
+      sh_s = sv;
+      sh_c = c;
       s.cs[b * 64 + j] = c;
-      s.sn[b * 64 + j] = snew;
-      H[j * 64 + j] = make_double2(c * pp.x + snew.x * nd, c * pp.y + snew.y * nd);
-      const double2 gj = s.g[b * 64 + j];
+      s.sn[b * 64 + j] = sv;
+      s.rd[b * 64 + j] = rjj;
       s.g[b * 64 + j] = make_double2(c * gj.x, c * gj.y);
-      const double2 gn = make_double2(-(snew.x * gj.x + snew.y * gj.y), -(snew.x * gj.y - snew.y * gj.x));
-      s.g[b * 64 + j + 1] = gn;
-      const double res = sqrt(gn.x * gn.x + gn.y * gn.y);
-      s.relres[b] = res / s.bn[b];
+      s.g[b * 64 + j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
+      rel *= hn * rr;  // |s_j| = |w| / r
+      s.relres[b] = rel;
       s.jc[b] = j + 1;
-      s.its[b] += 1;
-      s.sig[b * 64 + j + 1] = hn > 0 ? 1.0 / hn : 0.0;
-      const bool conv = res <= a.tol * s.bn[b] || !(hn > 0);
-      const bool stop = conv || s.its[b] >= a.max_iter || j + 1 >= a.restart;
-      if (conv) s.done[b] = 1;          // converged by the Arnoldi residual estimate
-      else if (stop) s.flag[2] = 1;     // stopped by the cap or the restart length
+      s.its[b] = its + 1;
+      s.sig[b * 64 + j + 1] = rhn;
+      const bool conv = rel <= a.tol || !(hn > 0);
+      const bool stop = conv || its + 1 >= a.max_iter || j + 1 >= a.restart;
+      if (conv) s.done[b] = 1;       // converged by the Arnoldi residual estimate
+      else if (stop) s.flag[2] = 1;  // stopped by the cap or the restart length
       if (stop)
         s.act[b] = 0;
       else
-        atomicOr(&any, 1);
+        any = 1;
+    }
+    __syncthreads();
+    if (warp == 1) {  // rho_{j+1}
+      const double2 sv = sh_s;
+      for (int i = lane; i <= j + 1 && i < 64; i += 32) {
+        double2 r;
+        if (i <= j) {
+          const double2 o = s.rho[b * 64 + i];
+          r = make_double2(-(sv.x * o.x + sv.y * o.y), -(sv.x * o.y - sv.y * o.x));
+        } else {
+          r = make_double2(sh_c, 0.0);
+        }
+        s.rho[b * 64 + i] = r;
+      }
     }
   }
   __syncthreads();
   if (tid == 0) {
-    *s.jdev = j + 1;
-    s.cnt[1] += 1;
-    s.flag[1] = any;
-    if (a.use_cond) cudaGraphSetConditional(a.inner, any ? 1u : 0u);
-    // every RHS of this cycle converged by its estimate: no explicit residual and no
-    // further cycle (the epilogue still applies the update)
-    if (!any && !s.flag[2] && a.use_cond) cudaGraphSetConditional(a.outer, 0u);
+    bool last = true, anyall = any != 0;
+    if (nblk > 1) {  // the last block to arrive sees every block's result
+      if (any) atomicOr(s.fin + 1, 1u);
+      __threadfence();
+      last = atomicAdd(s.fin, 1u) == (unsigned)nblk - 1;
+      if (last) {
+        __threadfence();
+        anyall = atomicExch(s.fin + 1, 0u) != 0;
+        atomicExch(s.fin, 0u);
+      }
+    }
+    if (last) {
+      *s.jdev = j + 1;
+      s.cnt[1] += 1;
+      s.flag[1] = anyall;
+      if (a.use_cond) cudaGraphSetConditional(a.inner, anyall ? 1u : 0u);
+      // every RHS of this cycle converged by its estimate: no explicit residual and no
+      // further cycle (the epilogue still applies the update)
+      if (!anyall && !*(volatile int*)(s.flag + 2) && a.use_cond) cudaGraphSetConditional(a.outer, 0u);
+    }
   }
   pdl_trigger();
 }
 
+constexpr int kFinishBlocks = 64;  // k_finish grid: one block per RHS up to this many
 
-// y = H^{-1} g on the jc x jc triangle (one block per b; H staged in shared memory,
-// back-substitution by one warp); the scales sig_i are folded into y.
+// End of a cycle, one block per RHS: the rotated triangle R from the unrotated columns
+// (G_0, G_1, ... applied in turn to every later column at once, one column per lane,
+// with R[k][k] from the step that made the rotation), then R y = g by back substitution
+// with the reciprocals of the diagonal taken up front; y is stored as sig_i y_i.
 __global__ void __launch_bounds__(kThreads) k_cycle_solve(int nb, GmresState s) {
   extern __shared__ double2 hs[];  // [64][64]
-  __shared__ double2 ys[64];
+  __shared__ double2 ys[64], dinv[64];
   const int b = blockIdx.x;
   const int n = s.jc[b];
   if (n == 0) return;
@@ -399,22 +422,38 @@ __global__ void __launch_bounds__(kThreads) k_cycle_solve(int nb, GmresState s) 
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
+    for (int i = 0; i < n; ++i) {
+      const double c = s.cs[b * 64 + i];
+      const double2 sn = s.sn[b * 64 + i];
+      for (int k = lane; k < n; k += 32) {
+        if (k > i) {
+          const double2 u = hs[i * 64 + k], v = hs[(i + 1) * 64 + k];
+          hs[i * 64 + k] = make_double2(c * u.x + sn.x * v.x - sn.y * v.y, c * u.y + sn.x * v.y + sn.y * v.x);
+          hs[(i + 1) * 64 + k] = make_double2(c * v.x - sn.x * u.x - sn.y * u.y, c * v.y - sn.x * u.y + sn.y * u.x);
+        } else if (k == i) {
+          hs[i * 64 + i] = s.rd[b * 64 + i];
+        }
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) {
+      const double2 d = hs[i * 64 + i];
+      const double dd = d.x * d.x + d.y * d.y;
+      const double r = dd > 0 ? 1.0 / dd : 0.0;
+      dinv[i] = make_double2(d.x * r, -d.y * r);
+    }
+    __syncwarp();
     for (int i = n - 1; i >= 0; --i) {
-      double re = 0, im = 0;
+      double2 acc = make_double2(0, 0);
       for (int k = i + 1 + lane; k < n; k += 32) {
         const double2 p = cmul(hs[i * 64 + k], ys[k]);
-        re += p.x;
-        im += p.y;
+        acc.x += p.x;
+        acc.y += p.y;
       }
-      re = warp_sum(re);
-      im = warp_sum(im);
+      acc = warp_sum_c(acc);
       if (lane == 0) {
         const double2 g = s.g[b * 64 + i];
-        const double2 t = make_double2(g.x - re, g.y - im);
-        const double2 d = hs[i * 64 + i];
-        const double dd = d.x * d.x + d.y * d.y;
-        ys[i] = dd > 0 ? make_double2((t.x * d.x + t.y * d.y) / dd, (t.y * d.x - t.x * d.y) / dd)
-                       : make_double2(0, 0);
+        ys[i] = cmul(make_double2(g.x - acc.x, g.y - acc.y), dinv[i]);
       }
       __syncwarp();
     }
@@ -560,7 +599,8 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
                            s.pu));
   }
   FinishArgs f{nb, c->restart, c->max_iter, tol, s.pu, U, use_cond ? 1 : 0, inner, outer};
-  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, launch_pdl(st, dim3(1), dim3(kThreads), 0, k_finish, f, s));
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
+              launch_pdl(st, dim3(std::min(nb, kFinishBlocks)), dim3(kThreads), 0, k_finish, f, s));
 }
 
 void cycle_epilogue(aim_ctx* c, int nb, double2* x) {
@@ -687,6 +727,10 @@ void gmres_alloc(aim_ctx* c) {
   const int B = c->batch_max, ns = c->ns;
   GmresState& s = c->gs;
   s.H = (double2*)aim_alloc(c, (size_t)B * 64 * 64 * sizeof(double2));
+  s.rd = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
+  s.rho = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
+  s.fin = (unsigned*)aim_alloc(c, 2 * sizeof(unsigned));
+  AIM_CUDA(cudaMemset(s.fin, 0, 2 * sizeof(unsigned)));
   s.g = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.sn = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.cs = (double*)aim_alloc(c, (size_t)B * 64 * sizeof(double));
