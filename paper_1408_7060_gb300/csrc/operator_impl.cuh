@@ -511,7 +511,12 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
 
 // ---------------------------------------------------------------- stage iii + iv
 // y_k = sign * ( sum_c sum_{n in stencil(k)} L_c[n,k] P_c[n]  +  sum_terms Z~near_m x_m ) + base_k
-// One warp per (b, k).  Grid part accumulated in the grid precision, near part in FP64.
+// One warp per kInterpRows consecutive (b, k) rows.  Grid part: the whole warp per row,
+// accumulated in the grid precision.  Near part: 8 lanes per row, all rows at once, in
+// FP64 -- the warp's FP64 instructions (each holds the sub-partition's FP64 pipe for the
+// whole warp) serve kInterpRows rows instead of one.
+constexpr int kInterpRows = 4;
+
 template <class C>
 __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, const int* __restrict__ anchor,
                                                      const typename Real<C>::T* __restrict__ lam, int N, int ns,
@@ -522,34 +527,48 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
                                                      VecSel ys) {
   pdl_wait();
   using R = typename Real<C>::T;
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long w0 = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * kInterpRows;
   const int lane = threadIdx.x & 31;
-  if (w >= (long long)nb * ns) return;
-  const int b = (int)(w / ns), k = (int)(w % ns);
-  if (active && !active[b]) return;
-  double2 tot = make_double2(0, 0);
+  const long long total = (long long)nb * ns;
+  if (w0 >= total) return;
+  // grid part, row by row; lane group r (lanes 8r .. 8r+7) keeps row r's sum
+  C mine{};
   if (P) {
-    // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node) terms
-    // of an RWG take 8 warp loads of 8 rows x 32 B each, coefficients contiguous
-    const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
     const size_t N3 = (size_t)N * N * N;
-    const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
-    const R* lk = lam + (size_t)k * 256 + lane;
-    C g{};
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      const int q = it * 8 + (lane >> 2);  // (component, row) pair, 0..63
-      const int c = q >> 4, row = q & 15;
-      const int dz = row >> 2, dy = row & 3;
-      g += lk[it * 32] * Pb[c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N];
+    for (int r = 0; r < kInterpRows; ++r) {
+      const long long w = w0 + r;
+      C g{};
+      if (w < total) {
+        const int b = (int)(w / ns), k = (int)(w % ns);
+        if (!(active && !active[b])) {
+          // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node)
+          // terms of an RWG take 8 warp loads of 8 rows x 32 B each
+          const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
+          const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
+          const R* lk = lam + (size_t)k * 256 + lane;
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int q = it * 8 + (lane >> 2);  // (component, row) pair, 0..63
+            const int c = q >> 4, row = q & 15;
+            const int dz = row >> 2, dy = row & 3;
+            g += lk[it * 32] * Pb[c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N];
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
+        g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
+      }
+      if ((lane >> 3) == r) mine = g;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
-      g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
-    }
-    tot = make_double2((double)g.x, (double)g.y);
   }
-  double2 nr = make_double2(0, 0);
+  // near part: lane group r, sub-lane sl
+  const int r = lane >> 3, sl = lane & 7;
+  const long long w = w0 + r;
+  const bool valid = w < total;
+  const int b = valid ? (int)(w / ns) : 0, k = valid ? (int)(w % ns) : 0;
+  const bool on = valid && !(active && !active[b]);
   long long xoff = 0;
   double xscale = 1.0;
   if (nl.xsel.sel) {
@@ -557,32 +576,39 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
     xoff = jj * nl.xsel.stride;
     if (nl.xsel.scale) xscale = nl.xsel.scale[b * 64 + jj];
   }
-  for (int e = rowptr[k] + lane; e < rowptr[k + 1]; e += 32) {
-    const int j = col[e];
-    for (int t = 0; t < nl.n; ++t) {
-      const double2 z = nl.val[t][e];
-      double2 xv = nl.x[t][xoff + (size_t)b * ns + j];
-      xv = make_double2(xscale * xv.x, xscale * xv.y);
-      if (nl.dinv) {
-        const double2 d = nl.dinv[j];
-        xv = make_double2(xv.x * d.x - xv.y * d.y, xv.x * d.y + xv.y * d.x);
+  double2 nr = make_double2(0, 0);
+  if (on) {
+    for (int e = rowptr[k] + sl; e < rowptr[k + 1]; e += 8) {
+      const int j = col[e];
+      for (int t = 0; t < nl.n; ++t) {
+        const double2 z = nl.val[t][e];
+        double2 xv = nl.x[t][xoff + (size_t)b * ns + j];
+        if (nl.dinv) {
+          const double2 d = nl.dinv[j];
+          xv = make_double2(xv.x * d.x - xv.y * d.y, xv.x * d.y + xv.y * d.x);
+        }
+        nr.x += z.x * xv.x - z.y * xv.y;
+        nr.y += z.x * xv.y + z.y * xv.x;
       }
-      nr.x += z.x * xv.x - z.y * xv.y;
-      nr.y += z.x * xv.y + z.y * xv.x;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    nr.x += __shfl_xor_sync(0xffffffffu, nr.x, o);
-    nr.y += __shfl_xor_sync(0xffffffffu, nr.y, o);
-  }
-  if (lane == 0) {
+  // sum over the 8 lanes of a group: the first exchange splits real (sl < 4) and
+  // imaginary (sl >= 4) parts, so 3 FP64 additions cover both
+  const bool hi = sl & 4;
+  double keep = hi ? nr.y : nr.x;
+  keep += __shfl_xor_sync(0xffffffffu, hi ? nr.x : nr.y, 4);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+  keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+  const double nim = __shfl_down_sync(0xffffffffu, keep, 4);
+  if (on && sl == 0) {
     if (ys.sel) y += (*ys.sel + ys.off) * ys.stride;
-    double2 r = make_double2(sign * (tot.x + nr.x), sign * (tot.y + nr.y));
+    const double re = (double)mine.x + xscale * keep, im = (double)mine.y + xscale * nim;
+    double2 out = make_double2(sign * re, sign * im);
     if (base) {
       const double2 bb = base[(size_t)b * ns + k];
-      r = make_double2(bb.x + r.x, bb.y + r.y);
+      out = make_double2(bb.x + out.x, bb.y + out.y);
     }
-    y[(size_t)b * ns + k] = r;
+    y[(size_t)b * ns + k] = out;
   }
   pdl_trigger();
 }
@@ -708,7 +734,7 @@ struct GridOps {
 
   static void interp(aim_ctx* c, int nb, const C* P, const NearList& nl, const double2* base, double sign,
                      const int* active, double2* y, VecSel ys = VecSel()) {
-    long long warps = (long long)nb * c->ns;
+    long long warps = ((long long)nb * c->ns + kInterpRows - 1) / kInterpRows;
     KScope ks(c, AIM_K_INTERP_NEAR);
     launch_pdl(c->stream, dim3((unsigned)((warps * 32 + 255) / 256)), dim3(256), 0, k_interp_near<C>, P,
                (const int*)c->d_anchor, lam(c), c->N, c->ns, nb, (const int*)c->d_rowptr, (const int*)c->d_col, nl,
