@@ -93,7 +93,11 @@ struct GmresState {
   int* flag = nullptr;       // [3] any active at cycle start / after a step / a stop without convergence
   int* cnt = nullptr;        // [2] cycles and Arnoldi steps executed (launch accounting)
   double2* pd = nullptr;     // multi-dot partials [B][64][S]
-  double* pu = nullptr;      // |w|^2 partials [B][U]
+  double* pu = nullptr;      // |w|^2 partials [B][cgs_P]
+  double2* pd2 = nullptr;    // raw dot partials of the first CGS update [B][64][cgs_P]
+  double2* d2 = nullptr;     // their sums: the second pass's dots [B][64]
+  unsigned* ucnt = nullptr;  // [B] CGS update blocks arrived per RHS
+  int cgs_E = 0, cgs_P = 0;  // elements per CGS update block, blocks per RHS
   double* pr = nullptr;      // |r|^2 partials [B][P]
   double* pbn = nullptr;     // |b|^2 partials [B][P]
   double* nrm = nullptr;     // [B] norms for the march's growth check
@@ -199,6 +203,8 @@ struct aim_ctx {
   int* d_err = nullptr;        // device error flag (a bounded wait gave up)
   void* d_xs = nullptr;        // [B][ns] prepared operator input, grid precision
   double2* d_xd = nullptr;     // [B][ns] prepared operator input, FP64 (near zone)
+  float2* d_vf = nullptr;      // [B][ns] complex64 copy of the Krylov vector the next SAI application
+                               // reads (complex64 path; written by the kernel that finishes it)
   double2* d_iring = nullptr;  // [N_g][B][ns] current history (RWG space)
   double2* d_x = nullptr;      // [B][ns] staging / solution
   double2* d_y = nullptr;      // [B][ns]

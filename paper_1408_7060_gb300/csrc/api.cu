@@ -137,6 +137,7 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_P = aim_alloc(c, (size_t)B * 4 * N * N * N * es);
   c->d_xs = aim_alloc(c, (size_t)B * ns * es);
   c->d_xd = (double2*)aim_alloc(c, (size_t)B * ns * sizeof(double2));
+  c->d_vf = (float2*)aim_alloc(c, (size_t)B * ns * sizeof(float2));
   const size_t vec = (size_t)B * ns * sizeof(double2);
   c->d_iring = (double2*)aim_alloc(c, (size_t)ng * vec);
   c->d_x = (double2*)aim_alloc(c, vec);

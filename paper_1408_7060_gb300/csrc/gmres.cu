@@ -105,75 +105,17 @@ __global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V
   pdl_trigger();
 }
 
-// Gram-Schmidt update of slot j+1: h_i = sig_i sum_s pd[b][i][s] (coefficients in the
-// normalised basis, written by block 0 to h), w -= sum_i vt_i (sig_i h_i); the block
-// also writes the partial sum of |w|^2 of its 32 elements to pn[b][blk].
-// grid (ceil(ns/32), nb), block (32, 8).
-__global__ void __launch_bounds__(kThreads) k_mupdate(double2* __restrict__ V, long long vstride,
-                                                      const int* __restrict__ jdev, int ns, int S,
-                                                      const int* __restrict__ act, const double* __restrict__ sig,
-                                                      const double2* __restrict__ pd, double2* __restrict__ h,
-                                                      double* __restrict__ pn) {
-  pdl_wait();
-  const int b = blockIdx.y;
-  if (!act[b]) return;
-  const int j = *jdev, J = j + 1;
-  __shared__ double2 coef[64];
-  __shared__ double2 red[8][kUpdN];
-  const int tid = threadIdx.y * kUpdN + threadIdx.x;
-  if (tid < J) {
-    double2 t = make_double2(0, 0);
-    for (int q = 0; q < S; ++q) {
-      double2 v = pd[((size_t)b * 64 + tid) * S + q];
-      t.x += v.x;
-      t.y += v.y;
-    }
-    const double sg = sig[b * 64 + tid];
-    t = make_double2(sg * t.x, sg * t.y);  // h_i
-    if (blockIdx.x == 0) h[b * 64 + tid] = t;
-    coef[tid] = make_double2(sg * t.x, sg * t.y);  // sig_i h_i multiplies vt_i
-  }
-  __syncthreads();
-  const int n = blockIdx.x * kUpdN + threadIdx.x;
-  double2 acc = make_double2(0, 0);
-  if (n < ns) {
-    for (int i = threadIdx.y; i < J; i += 8) {
-      double2 p = cmul(V[i * vstride + (size_t)b * ns + n], coef[i]);
-      acc.x += p.x;
-      acc.y += p.y;
-    }
-  }
-  red[threadIdx.y][threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.y == 0) {
-    double nrm = 0;
-    if (n < ns) {
-      double2 t = make_double2(0, 0);
-      for (int q = 0; q < 8; ++q) {
-        t.x += red[q][threadIdx.x].x;
-        t.y += red[q][threadIdx.x].y;
-      }
-      double2* w = V + (J)*vstride + (size_t)b * ns + n;
-      double2 wv = *w;
-      wv = make_double2(wv.x - t.x, wv.y - t.y);
-      *w = wv;
-      nrm = wv.x * wv.x + wv.y * wv.y;
-    }
-    nrm = warp_sum(nrm);
-    if (threadIdx.x == 0) pn[(size_t)b * gridDim.x + blockIdx.x] = nrm;
-  }
-  pdl_trigger();
-}
-
-// partial sums of |v_b|^2 over chunks of kNormChunk: grid (P, nb)
+// partial sums of |v_b|^2 over chunks of kNormChunk: grid (P, nb); with vf non-null
+// also the complex64 copy of v
 __global__ void __launch_bounds__(kThreads) k_normpart(const double2* __restrict__ v, int ns,
-                                                       double* __restrict__ pn) {
+                                                       double* __restrict__ pn, float2* __restrict__ vf) {
   const int b = blockIdx.y;
   const int n = blockIdx.x * kNormChunk + threadIdx.x;
   double a = 0;
   if (n < ns) {
     double2 x = v[(size_t)b * ns + n];
     a = x.x * x.x + x.y * x.y;
+    if (vf) vf[(size_t)b * ns + n] = make_float2((float)x.x, (float)x.y);
   }
   __shared__ double red[kThreads / 32];
   a = warp_sum(a);
@@ -259,153 +201,289 @@ __global__ void __launch_bounds__(kThreads) k_cycle_start(CycleArgs a, GmresStat
 struct FinishArgs {
   int nb, restart, max_iter;
   double tol;
-  const double* pn;   // |w|^2 partials after the second update [nb][Pu]
-  int Pu;
   int use_cond;
   cudaGraphConditionalHandle inner, outer;
 };
 
-// Arnoldi column j for every active RHS.  The column h = h1 + h2 (entries 0..j) is stored
-// unrotated in H[.][j]; the Givens rotations G_0..G_{j-1} reach it only through
+// ---------------------------------------------------------------- CGS2 updates and column finish
+
+// the same as warp_row_sum over partials that other blocks of the running kernel wrote
+// (read through L2)
+__device__ __forceinline__ double warp_row_sum_cg(const double* p, int P) {
+  const int lane = threadIdx.x & 31;
+  double s = 0;
+  for (int q0 = 0; q0 < P; q0 += 256) {
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int q = q0 + 32 * t + lane;
+      v[t] = q < P ? __ldcg(p + q) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s += v[t];
+  }
+  return warp_sum(s);
+}
+
+// complex partials p[0 .. P) summed by one warp in a fixed order (ld.cg when cg)
+template <bool CG>
+__device__ __forceinline__ double2 warp_row_sum_c(const double2* p, int P) {
+  const int lane = threadIdx.x & 31;
+  double2 t = make_double2(0, 0);
+  for (int q = lane; q < P; q += 32) {
+    const double2 v = CG ? __ldcg(p + q) : p[q];
+    t.x += v.x;
+    t.y += v.y;
+  }
+  return warp_sum_c(t);
+}
+
+// Column j of one RHS, by the warps 0 and 1 of the calling block (every thread calls it;
+// hn2 = |w|^2 on thread 0).  The column h = h1 + h2 (entries 0..j) is stored unrotated in
+// H[.][j]; the Givens rotations G_0..G_{j-1} reach it only through
 //   p_j = (G_{j-1} ... G_0 h)_j = rho_j . h,
 // where rho_j is row j of the accumulated rotation, kept from step to step by
-// rho_{j+1} = (-conj(s_j) rho_j, c_j), rho_0 = (1).  With |w|^2 (sum of the partials) the
-// new rotation is c_j = |p|/r, s_j = (p/|p|) |w|/r, r^2 = |p|^2 + |w|^2, and
-// R[j][j] = p r/|p|, g_{j+1} = -conj(s_j) g_j, g_j <- c_j g_j, and the residual estimate
-// |g_{j+1}|/|b| = relres_j |w|/r -- three reciprocal square roots and no division.  The
-// rotated entries above the diagonal are formed once per cycle, in k_cycle_solve.
-// Block k of the grid takes the RHS b = k, k + gridDim.x, ...: warp 0 sums |w|^2 while
-// warp 1 forms p_j; the last block to finish advances j and sets the loop conditions.
-__global__ void __launch_bounds__(kThreads) k_finish(FinishArgs a, GmresState s) {
-  pdl_wait();
+// rho_{j+1} = (-conj(s_j) rho_j, c_j), rho_0 = (1).  With |w| the new rotation is
+// c_j = |p|/r, s_j = (p/|p|) |w|/r, r^2 = |p|^2 + |w|^2, and R[j][j] = p r/|p|,
+// g_{j+1} = -conj(s_j) g_j, g_j <- c_j g_j, the residual estimate
+// |g_{j+1}|/|b| = relres_j |w|/r and sig_{j+1} = 1/|w| -- three reciprocal square roots
+// and no division.  The rotated entries above the diagonal are formed once per cycle, in
+// k_cycle_solve.  Returns (on every thread) whether the RHS takes another step.
+__device__ bool finish_rhs(const FinishArgs& a, GmresState& s, int b, int j, double hn2) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int blk = blockIdx.x, nblk = gridDim.x;
-  const int j = *s.jdev;
-  __shared__ double sh_hn2, sh_rhn, sh_p2, sh_rp;
+  __shared__ double sh_p2, sh_rp, sh_c;
   __shared__ double2 sh_p, sh_s;
-  __shared__ double sh_c;
-  __shared__ int any;
-  if (tid == 0) any = 0;
-  for (int b = blk; b < a.nb; b += nblk) {
-    __syncthreads();
-    if (!s.act[b]) continue;
-    double2 gj = make_double2(0, 0);
-    double rel = 0;
-    int its = 0;
-    if (warp == 0) {
-      const double hn2 = warp_row_sum(a.pn + (size_t)b * a.Pu, a.Pu);
-      if (lane == 0) {
-        sh_hn2 = hn2;
-        sh_rhn = hn2 > 0 ? rsqrt(hn2) : 0.0;
-        gj = s.g[b * 64 + j];
-        rel = s.relres[b];
-        its = s.its[b];
-      }
-    } else if (warp == 1) {
-      double2* H = s.H + (size_t)b * 64 * 64;  // H[i][k] at i*64 + k
-      double2 acc = make_double2(0, 0);
-      for (int i = lane; i <= j; i += 32) {
-        const double2 x = s.h1[b * 64 + i], y = s.h2[b * 64 + i];
-        const double2 h = make_double2(x.x + y.x, x.y + y.y);
-        H[i * 64 + j] = h;
-        const double2 r = s.rho[b * 64 + i];
-        acc.x += r.x * h.x - r.y * h.y;
-        acc.y += r.x * h.y + r.y * h.x;
-      }
-      const double2 pj = warp_sum_c(acc);
-      if (lane == 0) {
-        const double p2 = pj.x * pj.x + pj.y * pj.y;
-        sh_p = pj;
-        sh_p2 = p2;
-        sh_rp = p2 > 0 ? rsqrt(p2) : 0.0;
-      }
+  __shared__ int cont;
+  double2 gj = make_double2(0, 0);
+  double rel = 0, rhn = 0;
+  int its = 0;
+  if (tid == 0) {
+    rhn = hn2 > 0 ? rsqrt(hn2) : 0.0;
+    gj = s.g[b * 64 + j];
+    rel = s.relres[b];
+    its = s.its[b];
+  } else if (warp == 1) {
+    double2* H = s.H + (size_t)b * 64 * 64;  // H[i][k] at i*64 + k
+    double2 acc = make_double2(0, 0);
+    for (int i = lane; i <= j; i += 32) {
+      const double2 x = __ldcg(s.h1 + b * 64 + i), y = __ldcg(s.h2 + b * 64 + i);
+      const double2 h = make_double2(x.x + y.x, x.y + y.y);
+      H[i * 64 + j] = h;
+      const double2 r = s.rho[b * 64 + i];
+      acc.x += r.x * h.x - r.y * h.y;
+      acc.y += r.x * h.y + r.y * h.x;
     }
-    __syncthreads();
-    if (tid == 0) {
-      const double hn2 = sh_hn2, p2 = sh_p2, r2 = hn2 + p2, rhn = sh_rhn;
-      const double hn = hn2 * rhn;  // |w| (0 when |w| = 0)
-      const double rr = r2 > 0 ? rsqrt(r2) : 0.0;
-      const double2 pj = sh_p;
-      double c;
-      double2 sv, rjj;
-      if (!(r2 > 0)) {
-        c = 1.0;
-        sv = make_double2(0, 0);
-        rjj = make_double2(0, 0);
-      } else if (!(p2 > 0)) {
-        c = 0.0;
-        sv = make_double2(1.0, 0.0);
-        rjj = make_double2(hn, 0.0);
-      } else {
-        const double inv = rr * sh_rp;  // 1 / (|p| r)
-        c = p2 * inv;
-        const double q = hn * inv, t = r2 * inv;
-        sv = make_double2(pj.x * q, pj.y * q);
-        rjj = make_double2(pj.x * t, pj.y * t);
-      }
-      sh_s = sv;
-      sh_c = c;
-      s.cs[b * 64 + j] = c;
-      s.sn[b * 64 + j] = sv;
-      s.rd[b * 64 + j] = rjj;
-      s.g[b * 64 + j] = make_double2(c * gj.x, c * gj.y);
-      s.g[b * 64 + j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
-      rel *= hn * rr;  // |s_j| = |w| / r
-      s.relres[b] = rel;
-      s.jc[b] = j + 1;
-      s.its[b] = its + 1;
-      s.sig[b * 64 + j + 1] = rhn;
-      const bool conv = rel <= a.tol || !(hn > 0);
-      const bool stop = conv || its + 1 >= a.max_iter || j + 1 >= a.restart;
-      if (conv) s.done[b] = 1;       // converged by the Arnoldi residual estimate
-      else if (stop) s.flag[2] = 1;  // stopped by the cap or the restart length
-      if (stop)
-        s.act[b] = 0;
-      else
-        any = 1;
-    }
-    __syncthreads();
-    if (warp == 1) {  // rho_{j+1}
-      const double2 sv = sh_s;
-      for (int i = lane; i <= j + 1 && i < 64; i += 32) {
-        double2 r;
-        if (i <= j) {
-          const double2 o = s.rho[b * 64 + i];
-          r = make_double2(-(sv.x * o.x + sv.y * o.y), -(sv.x * o.y - sv.y * o.x));
-        } else {
-          r = make_double2(sh_c, 0.0);
-        }
-        s.rho[b * 64 + i] = r;
-      }
+    const double2 pj = warp_sum_c(acc);
+    if (lane == 0) {
+      const double p2 = pj.x * pj.x + pj.y * pj.y;
+      sh_p = pj;
+      sh_p2 = p2;
+      sh_rp = p2 > 0 ? rsqrt(p2) : 0.0;
     }
   }
   __syncthreads();
   if (tid == 0) {
-    bool last = true, anyall = any != 0;
-    if (nblk > 1) {  // the last block to arrive sees every block's result
-      if (any) atomicOr(s.fin + 1, 1u);
-      __threadfence();
-      last = atomicAdd(s.fin, 1u) == (unsigned)nblk - 1;
-      if (last) {
-        __threadfence();
-        anyall = atomicExch(s.fin + 1, 0u) != 0;
-        atomicExch(s.fin, 0u);
+    const double p2 = sh_p2, r2 = hn2 + p2;
+    const double hn = hn2 * rhn;  // |w| (0 when |w| = 0)
+    const double rr = r2 > 0 ? rsqrt(r2) : 0.0;
+    const double2 pj = sh_p;
+    double c;
+    double2 sv, rjj;
+    if (!(r2 > 0)) {
+      c = 1.0;
+      sv = make_double2(0, 0);
+      rjj = make_double2(0, 0);
+    } else if (!(p2 > 0)) {
+      c = 0.0;
+      sv = make_double2(1.0, 0.0);
+      rjj = make_double2(hn, 0.0);
+    } else {
+      const double inv = rr * sh_rp;  // 1 / (|p| r)
+      c = p2 * inv;
+      const double q = hn * inv, t = r2 * inv;
+      sv = make_double2(pj.x * q, pj.y * q);
+      rjj = make_double2(pj.x * t, pj.y * t);
+    }
+    sh_s = sv;
+    sh_c = c;
+    s.cs[b * 64 + j] = c;
+    s.sn[b * 64 + j] = sv;
+    s.rd[b * 64 + j] = rjj;
+    s.g[b * 64 + j] = make_double2(c * gj.x, c * gj.y);
+    s.g[b * 64 + j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
+    rel *= hn * rr;  // |s_j| = |w| / r
+    s.relres[b] = rel;
+    s.jc[b] = j + 1;
+    s.its[b] = its + 1;
+    s.sig[b * 64 + j + 1] = rhn;
+    const bool conv = rel <= a.tol || !(hn > 0);
+    const bool stop = conv || its + 1 >= a.max_iter || j + 1 >= a.restart;
+    if (conv) s.done[b] = 1;       // converged by the Arnoldi residual estimate
+    else if (stop) s.flag[2] = 1;  // stopped by the cap or the restart length
+    if (stop) s.act[b] = 0;
+    cont = !stop;
+  }
+  __syncthreads();
+  if (warp == 1) {  // rho_{j+1}
+    const double2 sv = sh_s;
+    for (int i = lane; i <= j + 1 && i < 64; i += 32) {
+      double2 r;
+      if (i <= j) {
+        const double2 o = s.rho[b * 64 + i];
+        r = make_double2(-(sv.x * o.x + sv.y * o.y), -(sv.x * o.y - sv.y * o.x));
+      } else {
+        r = make_double2(sh_c, 0.0);
       }
+      s.rho[b * 64 + i] = r;
     }
-    if (last) {
-      *s.jdev = j + 1;
-      s.cnt[1] += 1;
-      s.flag[1] = anyall;
-      if (a.use_cond) cudaGraphSetConditional(a.inner, anyall ? 1u : 0u);
-      // every RHS of this cycle converged by its estimate: no explicit residual and no
-      // further cycle (the epilogue still applies the update)
-      if (!anyall && !*(volatile int*)(s.flag + 2) && a.use_cond) cudaGraphSetConditional(a.outer, 0u);
+  }
+  return cont != 0;
+}
+
+// Thread 0 of the block that finished one RHS (or of block 0 of an inactive one): the
+// last of the nb arrivals advances j and sets the loop conditions.
+__device__ void finish_arrive(const FinishArgs& a, GmresState& s, int j, bool cont) {
+  if (cont) atomicOr(s.fin + 1, 1u);
+  __threadfence();
+  if (atomicAdd(s.fin, 1u) != (unsigned)a.nb - 1) return;
+  __threadfence();
+  const bool any = atomicExch(s.fin + 1, 0u) != 0;
+  atomicExch(s.fin, 0u);
+  *s.jdev = j + 1;
+  s.cnt[1] += 1;
+  s.flag[1] = any;
+  if (a.use_cond) cudaGraphSetConditional(a.inner, any ? 1u : 0u);
+  // every RHS of this cycle converged by its estimate: no explicit residual and no
+  // further cycle (the epilogue still applies the update)
+  if (!any && !*(volatile int*)(s.flag + 2) && a.use_cond) cudaGraphSetConditional(a.outer, 0u);
+}
+
+constexpr int kCgsSub = 64;       // elements per sub-chunk: 64 lanes x 4 groups of basis vectors
+constexpr int kCgsMaxE = 2048;    // elements per block at most
+constexpr int kCgsTargetP = 256;  // blocks per RHS aimed at (the chunk grows beyond)
+
+struct CgsArgs {
+  double2* V;
+  long long vstride;
+  int ns, E, P;          // RHS length, elements per block (multiple of kCgsSub), blocks per RHS
+  const double2* pd1;    // first pass: raw dot partials of k_mdot [B][64][S]
+  int S;
+  double2* pd2;          // first pass: raw dot partials of the updated w [B][64][P]
+  double2* d2;           // their sums, by the last block of each RHS [B][64]
+  double* pn;            // second pass: |w|^2 partials [B][P]
+  unsigned* ucnt;        // [B] block arrivals per RHS
+  float2* wf;            // second pass: complex64 copy of w (or null)
+};
+
+// One classical Gram-Schmidt pass on slot j+1 of every active RHS, grid (P, nb):
+//   h_i = sig_i d_i (d_i = sum of the raw dots conj(vt_i) . w, block 0 stores h),
+//   w -= sum_i vt_i (sig_i h_i) on the block's E elements (64 at a time: 4 groups of
+//   threads take every 4th basis vector, group 0 sums and writes),
+// then for the first pass the raw dots of the updated w over the block's elements (warp y
+// takes i = y, y + 8, ...), summed over the P blocks by the last block of the RHS into
+// d2 -- the second pass's d; for the second pass |w|^2 over the block, summed by the last
+// block, which then finishes column j (finish_rhs) and arrives at the step's counter.
+template <int PASS>
+__global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a, FinishArgs f, GmresState s) {
+  pdl_wait();
+  const int b = blockIdx.y, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int j = *s.jdev, J = j + 1;
+  if (!s.act[b]) {
+    if (PASS == 1 && blk == 0 && tid == 0) finish_arrive(f, s, j, false);
+    return;
+  }
+  __shared__ double2 coef[64];
+  __shared__ double2 red[4][kCgsSub];
+  __shared__ double2 wsm[kCgsMaxE];
+  __shared__ double nrd[kThreads / 32];
+  __shared__ int last;
+  // coefficients: warp y sums the raw dots of i = y, y + 8, ...
+  for (int i = warp; i < J; i += kThreads / 32) {
+    const double2 d = PASS == 0 ? warp_row_sum_c<false>(a.pd1 + ((size_t)b * 64 + i) * a.S, a.S) : a.d2[b * 64 + i];
+    if (lane == 0) {
+      const double sg = s.sig[b * 64 + i];
+      const double2 h = make_double2(sg * d.x, sg * d.y);
+      if (blk == 0) (PASS == 0 ? s.h1 : s.h2)[b * 64 + i] = h;
+      coef[i] = make_double2(sg * h.x, sg * h.y);  // sig_i h_i multiplies vt_i
     }
+  }
+  __syncthreads();
+  const double2* Vb = a.V + (size_t)b * a.ns;
+  double2* w = a.V + (size_t)J * a.vstride + (size_t)b * a.ns;
+  const int n0 = blk * a.E, cnt = min(a.ns, n0 + a.E) - n0;
+  const int e = tid & (kCgsSub - 1), grp = tid / kCgsSub;
+  for (int s0 = 0; s0 < cnt; s0 += kCgsSub) {
+    const int n = n0 + s0 + e;
+    const bool in = s0 + e < cnt;
+    double2 pv = make_double2(0, 0);
+    if (in)
+      for (int i = grp; i < J; i += 4) {
+        const double2 v = cmul(Vb[i * a.vstride + n], coef[i]);
+        pv.x += v.x;
+        pv.y += v.y;
+      }
+    red[grp][e] = pv;
+    __syncthreads();
+    if (grp == 0 && in) {
+      double2 wv = w[n];
+      wv.x -= (red[0][e].x + red[1][e].x) + (red[2][e].x + red[3][e].x);
+      wv.y -= (red[0][e].y + red[1][e].y) + (red[2][e].y + red[3][e].y);
+      w[n] = wv;
+      if (PASS == 1 && a.wf) a.wf[(size_t)b * a.ns + n] = make_float2((float)wv.x, (float)wv.y);
+      wsm[s0 + e] = wv;
+    }
+    __syncthreads();
+  }
+  if (PASS == 0) {
+    for (int i = warp; i < J; i += kThreads / 32) {
+      const double2* vi = Vb + i * a.vstride + n0;
+      double2 t = make_double2(0, 0);
+      for (int q = lane; q < cnt; q += 32) {
+        const double2 p = cmulc(vi[q], wsm[q]);
+        t.x += p.x;
+        t.y += p.y;
+      }
+      t = warp_sum_c(t);
+      if (lane == 0) a.pd2[((size_t)b * 64 + i) * a.P + blk] = t;
+    }
+  } else {
+    double t = 0;
+    for (int q = tid; q < cnt; q += kThreads) t += wsm[q].x * wsm[q].x + wsm[q].y * wsm[q].y;
+    t = warp_sum(t);
+    if (lane == 0) nrd[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double u = 0;
+      for (int q = 0; q < kThreads / 32; ++q) u += nrd[q];
+      a.pn[(size_t)b * a.P + blk] = u;
+    }
+  }
+  // the last block of this RHS to arrive sums the P partials
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(a.ucnt + b, 1u) == (unsigned)a.P - 1;
+  }
+  __syncthreads();
+  if (!last) {
+    pdl_trigger();
+    return;
+  }
+  __threadfence();
+  if (tid == 0) a.ucnt[b] = 0u;
+  if (PASS == 0) {
+    for (int i = warp; i < J; i += kThreads / 32) {
+      const double2 d = warp_row_sum_c<true>(a.pd2 + ((size_t)b * 64 + i) * a.P, a.P);
+      if (lane == 0) a.d2[b * 64 + i] = d;
+    }
+  } else {
+    double hn2 = 0;
+    if (warp == 0) hn2 = warp_row_sum_cg(a.pn + (size_t)b * a.P, a.P);
+    const bool cont = finish_rhs(f, s, b, j, hn2);
+    if (tid == 0) finish_arrive(f, s, j, cont);
   }
   pdl_trigger();
 }
-
-constexpr int kFinishBlocks = 64;  // k_finish grid: one block per RHS up to this many
 
 // End of a cycle, one block per RHS: the rotated triangle R from the unrotated columns
 // (G_0, G_1, ... applied in turn to every later column at once, one column per lane,
@@ -465,10 +543,12 @@ __global__ void __launch_bounds__(kThreads) k_cycle_solve(int nb, GmresState s) 
 }
 
 // x += dinv .* sum_i vt_i (sig_i y_i);  grid (ceil(ns/32), nb), block (32, 8)
-// (with u non-null: u = sum_i vt_i (sig_i y_i) is stored instead, for the SAI below)
+// (with u non-null: u = sum_i vt_i (sig_i y_i) is stored instead, for the SAI below,
+// and with uf non-null its complex64 copy as well)
 __global__ void __launch_bounds__(kThreads) k_xupdate(const double2* __restrict__ V, long long vstride, int ns,
                                                       const double2* __restrict__ dinv, GmresState s,
-                                                      double2* __restrict__ x, double2* __restrict__ u_out) {
+                                                      double2* __restrict__ x, double2* __restrict__ u_out,
+                                                      float2* __restrict__ uf) {
   const int b = blockIdx.y;
   const int J = s.jc[b];
   if (J == 0) return;
@@ -491,6 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_xupdate(const double2* __restrict_
     }
     if (u_out) {
       u_out[(size_t)b * ns + n] = t;
+      if (uf) uf[(size_t)b * ns + n] = make_float2((float)t.x, (float)t.y);
       return;
     }
     const double2 du = cmul(dinv[n], t);
@@ -524,6 +605,49 @@ __global__ void __launch_bounds__(kThreads) k_sai_xupdate(const double2* __restr
   }
 }
 
+// The same on the complex64 path with the complex64 SAI (the M the Arnoldi process
+// applied): 16 lanes per row, up to 9 entries per lane, FP32 products and butterfly sum,
+// the sum added to x in FP64.
+__global__ void __launch_bounds__(kThreads) k_sai_xupdate_c64(const float2* __restrict__ sai,
+                                                              const int* __restrict__ rowptr,
+                                                              const int* __restrict__ col,
+                                                              const float2* __restrict__ uf, int ns, int nb,
+                                                              GmresState s, double2* __restrict__ x) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 4;
+  const int lane = threadIdx.x & 15;
+  const bool valid = w < (long long)nb * ns;  // both rows of a warp join the shuffles
+  const int b = valid ? (int)(w / ns) : 0, k = valid ? (int)(w % ns) : 0;
+  const bool on = valid && s.jc[b] != 0;
+  float tr = 0, ti = 0;
+  if (on) {
+    const float2* ub = uf + (size_t)b * ns;
+    const int e0 = rowptr[k] + lane, e1 = rowptr[k + 1];
+    int j[9];
+    float2 m[9], u[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const int e = e0 + 16 * q;
+      j[q] = e < e1 ? col[e] : -1;
+      m[q] = e < e1 ? sai[e] : make_float2(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) u[q] = j[q] >= 0 ? ub[j[q]] : make_float2(0, 0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      tr += m[q].x * u[q].x - m[q].y * u[q].y;
+      ti += m[q].x * u[q].y + m[q].y * u[q].x;
+    }
+  }
+  for (int o = 8; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    ti += __shfl_xor_sync(0xffffffffu, ti, o);
+  }
+  if (on && lane == 0) {
+    double2 xv = x[(size_t)b * ns + k];
+    x[(size_t)b * ns + k] = make_double2(xv.x + (double)tr, xv.y + (double)ti);
+  }
+}
+
 // |v_b| for every b into out[b]
 __global__ void __launch_bounds__(kThreads) k_norm_finish(int nb, const double* __restrict__ pn, int P, double* __restrict__ out) {
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -550,6 +674,10 @@ void copy_b_to_slot0(aim_ctx* c, int nb, const double2* b) {
   AIM_CUDA(cudaMemcpyAsync(c->d_V, b, (size_t)nb * c->ns * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
 }
 
+// the complex64 copy of the Krylov vector that the SAI application of the complex64 path
+// gathers from (null when that path is not in use)
+float2* krylov_c64(aim_ctx* c) { return c->d_sai && c->precision == AIM_C64 ? c->d_vf : nullptr; }
+
 // |r|^2 of slot 0 and the cycle start
 void cycle_start(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle outer,
                  cudaGraphConditionalHandle inner, cudaGraphConditionalHandle resid) {
@@ -557,7 +685,7 @@ void cycle_start(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditi
   cudaStream_t st = c->stream;
   const int ns = c->ns;
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-              k_normpart<<<dim3(n_norm_blocks(ns), nb), kThreads, 0, st>>>(c->d_V, ns, s.pr));
+              k_normpart<<<dim3(n_norm_blocks(ns), nb), kThreads, 0, st>>>(c->d_V, ns, s.pr, krylov_c64(c)));
   CycleArgs a{nb, c->restart, c->max_iter, tol, s.pbn, s.pr, n_norm_blocks(ns), use_cond ? 1 : 0, outer, inner,
               (use_cond && c->zero_start) ? 1 : 0, resid};
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_start<<<1, kThreads, 0, st>>>(a, s));
@@ -588,19 +716,16 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
   const int ns = c->ns;
   const long long vstride = (long long)c->batch_max * ns;
   arnoldi_operator(c, nb);
-  const int S = n_dot_chunks(ns), U = n_upd_blocks(ns);
-  for (int pass = 0; pass < 2; ++pass) {
-    AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
-                launch_pdl(st, dim3(64, S, nb), dim3(kThreads), 0, k_mdot, (const double2*)c->d_V, vstride,
-                           (const int*)s.jdev, ns, (const int*)s.act, s.pd));
-    AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-                launch_pdl(st, dim3(U, nb), dim3(kUpdN, 8), 0, k_mupdate, c->d_V, vstride, (const int*)s.jdev, ns, S,
-                           (const int*)s.act, (const double*)s.sig, (const double2*)s.pd, pass == 0 ? s.h1 : s.h2,
-                           s.pu));
-  }
-  FinishArgs f{nb, c->restart, c->max_iter, tol, s.pu, U, use_cond ? 1 : 0, inner, outer};
-  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
-              launch_pdl(st, dim3(std::min(nb, kFinishBlocks)), dim3(kThreads), 0, k_finish, f, s));
+  const int S = n_dot_chunks(ns);
+  AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
+              launch_pdl(st, dim3(64, S, nb), dim3(kThreads), 0, k_mdot, (const double2*)c->d_V, vstride,
+                         (const int*)s.jdev, ns, (const int*)s.act, s.pd));
+  FinishArgs f{nb, c->restart, c->max_iter, tol, use_cond ? 1 : 0, inner, outer};
+  CgsArgs a{c->d_V, vstride, ns, s.cgs_E, s.cgs_P, s.pd, S, s.pd2, s.d2, s.pu, s.ucnt, krylov_c64(c)};
+  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
+              launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs<0>, a, f, s));
+  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
+              launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs<1>, a, f, s));
 }
 
 void cycle_epilogue(aim_ctx* c, int nb, double2* x) {
@@ -611,8 +736,14 @@ void cycle_epilogue(aim_ctx* c, int nb, double2* x) {
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_solve<<<nb, kThreads, 64 * 64 * sizeof(double2), st>>>(nb, s));
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
               k_xupdate<<<dim3(n_upd_blocks(ns), nb), dim3(kUpdN, 8), 0, st>>>(c->d_V, vstride, ns, c->d_dinv, s, x,
-                                                                                c->d_sai ? c->d_u : nullptr));
-  if (c->d_sai) {
+                                                                                c->d_sai ? c->d_u : nullptr,
+                                                                                krylov_c64(c)));
+  if (krylov_c64(c)) {
+    const long long rows = (long long)nb * ns;
+    AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
+                k_sai_xupdate_c64<<<(int)((rows * 16 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+                    c->d_saif, c->d_srowptr, c->d_scol, krylov_c64(c), ns, nb, s, x));
+  } else if (c->d_sai) {
     const long long warps = (long long)nb * ns;
     AIM_KLAUNCH(c, AIM_K_GMRES_SMALL,
                 k_sai_xupdate<<<(int)((warps * 32 + kThreads - 1) / kThreads), kThreads, 0, st>>>(
@@ -673,7 +804,7 @@ void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double 
     // |b|^2 partials, then WHILE(cycles) { prologue; WHILE(arnoldi) { step }; epilogue }
     capture_into(c, g, nullptr, 0, [&] {
       AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-                  k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, c->stream>>>(b, c->ns, s.pbn));
+                  k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, c->stream>>>(b, c->ns, s.pbn, nullptr));
     });
     cudaGraphNode_t pre = leaf_of(g);
     cudaGraphConditionalHandle outer, inner, resid = 0;
@@ -747,7 +878,14 @@ void gmres_alloc(aim_ctx* c) {
   s.jdev = (int*)aim_alloc(c, sizeof(int));
   s.flag = (int*)aim_alloc(c, 3 * sizeof(int));
   s.pd = (double2*)aim_alloc(c, (size_t)B * 64 * n_dot_chunks(ns) * sizeof(double2));
-  s.pu = (double*)aim_alloc(c, (size_t)B * n_upd_blocks(ns) * sizeof(double));
+  // CGS update blocks: E elements each (a multiple of 64), about kCgsTargetP per RHS
+  s.cgs_E = std::min(kCgsMaxE, std::max(kCgsSub, ((ns + kCgsTargetP - 1) / kCgsTargetP + kCgsSub - 1) / kCgsSub * kCgsSub));
+  s.cgs_P = (ns + s.cgs_E - 1) / s.cgs_E;
+  s.pu = (double*)aim_alloc(c, (size_t)B * s.cgs_P * sizeof(double));
+  s.pd2 = (double2*)aim_alloc(c, (size_t)B * 64 * s.cgs_P * sizeof(double2));
+  s.d2 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
+  s.ucnt = (unsigned*)aim_alloc(c, (size_t)B * sizeof(unsigned));
+  AIM_CUDA(cudaMemset(s.ucnt, 0, (size_t)B * sizeof(unsigned)));
   s.pr = (double*)aim_alloc(c, (size_t)B * n_norm_blocks(ns) * sizeof(double));
   s.pbn = (double*)aim_alloc(c, (size_t)B * n_norm_blocks(ns) * sizeof(double));
   s.nrm = (double*)aim_alloc(c, B * sizeof(double));
@@ -807,7 +945,7 @@ void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double 
   if (!graphed) {
     // the same kernels driven from the host (one synchronisation per Arnoldi step)
     AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
-                k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, st>>>(b, c->ns, s.pbn));
+                k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, st>>>(b, c->ns, s.pbn, nullptr));
     for (int cycle = 0;; ++cycle) {
       if (c->zero_start && cycle == 0) copy_b_to_slot0(c, nb, b);
       else cycle_residual(c, nb, b, x);
@@ -841,10 +979,10 @@ int gmres_collect(aim_ctx* c, int* iters, double* relres) {
   const int nb = s.last_nb;
   if (s.last_graphed) {
     // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2, + 1
-    // with the SAI) + steps * (operator + 2 x (dot, update) + finish); a zero start skips
+    // with the SAI) + steps * (operator + dot + 2 updates); a zero start skips
     // the operator of the first cycle
     const long long op = op_kernel_count(c);
-    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 5) * s.h_cnt[1] -
+    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 3) * s.h_cnt[1] -
                         (c->zero_start && s.h_cnt[0] > 0 ? op : 0);
   }
   int rc = AIM_OK;
@@ -866,6 +1004,6 @@ int gmres_blocks(int ns) { return n_norm_blocks(ns); }
 
 void gmres_norms(aim_ctx* c, int nb, const double2* v, double* d_out) {
   const int P = n_norm_blocks(c->ns);
-  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE, k_normpart<<<dim3(P, nb), kThreads, 0, c->stream>>>(v, c->ns, c->gs.pr));
+  AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE, k_normpart<<<dim3(P, nb), kThreads, 0, c->stream>>>(v, c->ns, c->gs.pr, nullptr));
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_norm_finish<<<1, kThreads, 0, c->stream>>>(nb, c->gs.pr, P, d_out));
 }

@@ -123,9 +123,10 @@ __global__ void __launch_bounds__(256) k_prep(const double2* __restrict__ v, con
 // applied in the grid precision: complex64 (M rounded to FP32, products and sums in FP32,
 // like the grid stages it feeds) or complex128 (FP64).
 template <class C>
-__global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v, const C* __restrict__ sai,
-                                                  const int* __restrict__ rowptr, const int* __restrict__ col,
-                                                  VecSel vs, const int* __restrict__ active, int ns, int nb,
+__global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v, const float2* __restrict__ vf,
+                                                  const C* __restrict__ sai, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ col, VecSel vs,
+                                                  const int* __restrict__ active, int ns, int nb,
                                                   C* __restrict__ xs, double2* __restrict__ xd) {
   pdl_wait();
   using R = typename Real<C>::T;
@@ -155,15 +156,29 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
       j[q] = e < e1 ? col[e] : -1;
       m[q] = e < e1 ? sai[e] : C{};
     }
+    if (vf) {  // complex64 copy of v_j: no FP64 -> FP32 conversion per gathered entry
+      const float2* vfb = vf + (size_t)b * ns;
+      float2 uf[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) u[q] = j[q] >= 0 ? vb[j[q]] : make_double2(0, 0);
+      for (int q = 0; q < 9; ++q) uf[q] = j[q] >= 0 ? vfb[j[q]] : make_float2(0, 0);
 #pragma unroll
-    for (int q = 0; q < 9; ++q)
-      if (j[q] >= 0) {
-        const R ur = (R)u[q].x, ui = (R)u[q].y;
-        xr += m[q].x * ur - m[q].y * ui;
-        xi += m[q].x * ui + m[q].y * ur;
-      }
+      for (int q = 0; q < 9; ++q)
+        if (j[q] >= 0) {
+          const R ur = (R)uf[q].x, ui = (R)uf[q].y;
+          xr += m[q].x * ur - m[q].y * ui;
+          xi += m[q].x * ui + m[q].y * ur;
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) u[q] = j[q] >= 0 ? vb[j[q]] : make_double2(0, 0);
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        if (j[q] >= 0) {
+          const R ur = (R)u[q].x, ui = (R)u[q].y;
+          xr += m[q].x * ur - m[q].y * ui;
+          xi += m[q].x * ui + m[q].y * ur;
+        }
+    }
   }
   for (int o = 8; o > 0; o >>= 1) {
     xr += __shfl_xor_sync(0xffffffffu, xr, o);
@@ -646,6 +661,7 @@ struct GridOps {
     KScope ks(c, AIM_K_PREP);
     if (dinv && c->d_sai)
       launch_pdl(c->stream, dim3((unsigned)((n * 16 + 255) / 256)), dim3(256), 0, k_prep_sai<C>, v,
+                 std::is_same<C, float2>::value ? (const float2*)c->d_vf : (const float2*)nullptr,
                  sel_sai(c, (C*)nullptr), (const int*)c->d_srowptr, (const int*)c->d_scol, vs, active, c->ns, nb,
                  reinterpret_cast<C*>(c->d_xs), want_fp64 ? c->d_xd : (double2*)nullptr);
     else
