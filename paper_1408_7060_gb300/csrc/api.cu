@@ -16,6 +16,8 @@
 
 namespace {
 
+void ensure_ring(aim_ctx* c);
+
 thread_local std::string g_last_setup_error;
 
 bool is_device_ptr(const void* p) {
@@ -156,10 +158,11 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   // attributes of each instantiation and surfaces launch errors at setup
   AIM_CUDA(cudaMemsetAsync(c->d_x, 0, vec, c->stream));
   op_apply(c, 0, 1, c->d_x, nullptr, nullptr, 1.0, nullptr, c->d_y);
-  op_forward_slab(c, 1, c->d_x, c->d_Bf);
+  ensure_ring(c);
+  op_forward_slab(c, 1, c->d_x, c->d_ring);
   {
     SlabList sl{};
-    sl.p[0] = c->d_Bf;
+    sl.p[0] = c->d_ring;
     sl.m[0] = 1;
     sl.n = 1;
     NearList nl{};
@@ -175,13 +178,14 @@ void ensure_ring(aim_ctx* c) {
   if (c->d_ring) return;
   const size_t slab = op_slab_bytes(c, c->batch_max);
   c->d_ring = aim_alloc(c, (size_t)c->n_delays * slab);
-  // TMA view for the complex64 delayed sum: [slot][B*4*N][L][L], boxes of 16 x 1 x N x 1
-  const int L = c->L, N = c->N;
+  // TMA view for the complex64 delayed sum over the z-spectra: [slot][B*4*L][L][L],
+  // boxes of 16 x 1 x L x 1
+  const int L = c->L;
   if (c->precision == AIM_C64 && (L & (L - 1)) == 0 && L <= 256) {
-    const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)c->batch_max * 4 * N,
+    const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)c->batch_max * 4 * L,
                                 (cuuint64_t)c->n_delays};
     const cuuint64_t strides[3] = {(cuuint64_t)L * 8, (cuuint64_t)L * L * 8, (cuuint64_t)slab};
-    const cuuint32_t box[4] = {(cuuint32_t)(L < 16 ? L : 16), 1, (cuuint32_t)N, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)(L < 16 ? L : 16), 1, (cuuint32_t)L, 1};
     c->ring_tma = encode_tiled_map(&c->ring_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c->d_ring, dims, strides, box);
   }
 }

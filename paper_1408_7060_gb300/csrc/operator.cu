@@ -36,8 +36,11 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
 // kernels one operator application launches: prep, anterp + x, y, z, y^-1, x^-1, interp
 int op_kernel_count(const aim_ctx*) { return 7; }
 
+// bytes of one history slab: [nb][4][Z][L][L] with Z = L (z-transformed, power-of-two L)
+// or N (x/y-transformed only)
 size_t op_slab_bytes(const aim_ctx* c, int nb) {
-  return (size_t)nb * 4 * c->N * (size_t)c->L * c->L * (c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2));
+  const int L = c->L, Z = (L & (L - 1)) == 0 ? L : c->N;
+  return (size_t)nb * 4 * Z * (size_t)L * L * (c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2));
 }
 
 // V_l[k] = <S_k, p (g'(tau) + j w g(tau)) e^{-j w (r.k/c + t_d)}>,  tau = l dt - r.k/c - t_d,

@@ -351,17 +351,48 @@ __global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __re
   }
 }
 
-// Delay sum of the right-hand side in the spectral domain:
-//   P^_col = sum_i G^_{m_i} . FFT_z(slab_i column), then one inverse z-FFT.
-// Power-of-two L: steps A and B per slab, the sum kept in registers of the step-B
-// threads, then one inverse (B, C).
+// History slabs of power-of-two length are kept z-transformed: S[bc][kz][y][x], all L
+// frequencies kz of every (x, y) line (twice the bytes of the x/y-transformed slab, whose
+// z holds only the N nonzero samples).  The delay sum of the right-hand side is then a
+// multiply-accumulate streamed over the N_g spectra and one inverse z-FFT, instead of N_g
+// forward z-FFTs recomputed at every step.
+//
+// k_zfwd_spec: the forward z-FFT (steps A and B of the z pass) of the slab in Bf into the
+// spectral layout; thread (l, k1) of step B stores X[k1 + R1 k2] for all k2.
 template <int L, int W, class C>
-__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_p2(SlabList sl, const C* __restrict__ kspec_all, int N,
-                                                       C* __restrict__ Bf, const C* __restrict__ twg) {
+__global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ Bf, C* __restrict__ S, int N,
+                                                         const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* t = tw + L;
+  load_twiddles(tw, twg, L);
+  __syncthreads();
+  const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
+  const long long es = (long long)L * L;
+  zcol_step_a<L, W, C>(Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, t, tw);
+  __syncthreads();
+  C* out = S + (size_t)bc * L * L * L + (size_t)y * L + x0;
+  for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
+    const int l = u % W, k1 = u / W;
+    C v[R2];
+    zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) out[(long long)(k1 + R1 * k2) * es + l] = v[k2];
+  }
+}
+
+// Delay sum of the right-hand side in the spectral domain:
+//   P^_col = sum_i G^_{m_i} . S_i(col), then one inverse z-FFT (steps B inverse and C),
+// the sum kept in the registers of the step-B threads (thread (l, k1) owns the
+// frequencies k1 + R1 k2).
+template <int L, int W, class C>
+__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec(SlabList sl, const C* __restrict__ kspec_all, int N,
+                                                         C* __restrict__ Bf, const C* __restrict__ twg) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
   load_twiddles(tw, twg, L);
+  __syncthreads();
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
   const long long es = (long long)L * L;
   const int n1 = N + 1;
@@ -374,11 +405,8 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_p2(SlabList sl, const C* 
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
   for (int s = 0; s < sl.n; ++s) {
-    const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
+    const C* Sc = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * L * L * L + (size_t)y * L + x0;
     const C* Gy = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct + (size_t)fy * n1;
-    __syncthreads();  // twiddles published; the previous slab's step B is done with t
-    zcol_step_a<L, W, C>(col, es, t, tw);
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kZThreads;
@@ -387,14 +415,16 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_p2(SlabList sl, const C* 
         const C* G = Gy + fold(x0 + l, N);
         C g[R2], v[R2];
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
-        zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const int kz = k1 + R1 * k2;
+          v[k2] = Sc[(long long)kz * es + l];
+          g[k2] = __ldg(G + (size_t)fold(kz, N) * n1 * n1);
+        }
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * g[k2];
       }
     }
   }
-  __syncthreads();  // every step-B read of t is done (also orders the sl.n == 0 case)
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const int u = threadIdx.x + j * kZThreads;
@@ -404,26 +434,26 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_p2(SlabList sl, const C* 
   zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
 }
 
-// The same delay sum with the history slabs streamed by TMA (complex64, power-of-two L):
-// the N x W input tile of each slab is a 4-D box of the ring tensor, loaded into one of
-// two 128-byte aligned shared buffers by cp.async.bulk.tensor and signalled on an
-// mbarrier, so slab s + 2 streams in while slab s + 1 is transformed.  Waits are
-// bounded; a wait that gives up sets *err (the host reports it) and the sum goes on.
+// The same with the spectra streamed by TMA (complex64): the L x W tile of each spectrum
+// is a 4-D box of the ring tensor [slot][B*4*L][L][L], loaded into one of two 128-byte
+// aligned shared buffers by cp.async.bulk.tensor and signalled on an mbarrier, so
+// spectrum s + 2 streams in while spectrum s + 1 is accumulated.  Waits are bounded; a
+// wait that gives up sets *err (the host reports it) and the sum goes on.
 template <int L, int W>
-__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_tma(const __grid_constant__ CUtensorMap ring, SlabRing sr,
-                                                           const float2* __restrict__ kspec_all, int N,
-                                                           float2* __restrict__ Bf, const float2* __restrict__ twg,
-                                                           int* __restrict__ err) {
+__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_constant__ CUtensorMap ring,
+                                                                SlabRing sr, const float2* __restrict__ kspec_all,
+                                                                int N, float2* __restrict__ Bf,
+                                                                const float2* __restrict__ twg, int* __restrict__ err) {
   using C = float2;
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   __shared__ __align__(8) uint64_t bar[2];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(aim_smem) + 127) & ~static_cast<uintptr_t>(127));
-  C* in0 = reinterpret_cast<C*>(base);  // [2][N][W]
-  C* tw = in0 + 2 * (L / 2) * W;
+  C* in0 = reinterpret_cast<C*>(base);  // [2][L][W]
+  C* tw = in0 + 2 * L * W;
   C* t = tw + L;
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
-  const unsigned bytes = (unsigned)(N * W * sizeof(C));
+  const unsigned bytes = (unsigned)(L * W * sizeof(C));
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -434,7 +464,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_tma(const __grid_constant
   if (threadIdx.x == 0)
     for (int s = 0; s < 2 && s < sr.n; ++s) {
       mbar_arrive_expect_tx(&bar[s], bytes);
-      tma_load_4d(in0 + s * N * W, &ring, &bar[s], x0, y, bc * N, sr.slot[s]);
+      tma_load_4d(in0 + s * L * W, &ring, &bar[s], x0, y, bc * L, sr.slot[s]);
     }
   const long long es = (long long)L * L;
   const int n1 = N + 1;
@@ -448,31 +478,34 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_tma(const __grid_constant
     for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
   for (int s = 0; s < sr.n; ++s) {
     const int buf = s & 1;
-    if (!mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1))) atomicExch(err, 1);
-    const C* tile = in0 + buf * N * W;
     const C* Gy = kspec_all + ((size_t)sr.m[s] * 2 + kind) * oct + (size_t)fy * n1;
-    zcol_step_a<L, W, C>(tile, W, t, tw);
-    __syncthreads();  // the tile is consumed: it may be refilled
-    if (threadIdx.x == 0 && s + 2 < sr.n) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bar[buf], bytes);
-      tma_load_4d(in0 + buf * N * W, &ring, &bar[buf], x0, y, bc * N, sr.slot[s + 2]);
+    C g[U][R2];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {  // the kernel spectrum while the tile streams in
+      const int u = threadIdx.x + j * kZThreads;
+      if (u < W * R1) {
+        const C* G = Gy + fold(x0 + u % W, N);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) g[j][k2] = __ldg(G + (size_t)fold(u / W + R1 * k2, N) * n1 * n1);
+      }
     }
+    if (!mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1))) atomicExch(err, 1);
+    const C* tile = in0 + buf * L * W;  // [kz][l]
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kZThreads;
       if (u < W * R1) {
         const int l = u % W, k1 = u / W;
-        const C* G = Gy + fold(x0 + l, N);
-        C g[R2], v[R2];
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
-        zcol_step_b_fwd<L, W, C>(t, k1, l, v);
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * g[k2];
+        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += tile[(k1 + R1 * k2) * W + l] * g[j][k2];
       }
     }
-    __syncthreads();  // every step-B read of t is done
+    __syncthreads();  // the tile is consumed: it may be refilled
+    if (threadIdx.x == 0 && s + 2 < sr.n) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[buf], bytes);
+      tma_load_4d(in0 + buf * L * W, &ring, &bar[buf], x0, y, bc * L, sr.slot[s + 2]);
+    }
   }
 #pragma unroll
   for (int j = 0; j < U; ++j) {
@@ -777,12 +810,25 @@ struct GridOps {
     AIM_CHECK_LAUNCH();
   }
 
+  // forward z-FFT of the slab in Bf into the z-spectral history layout at dst
+  // (power-of-two lengths only)
+  static void zfwd(aim_ctx* c, int nb, C* dst) {
+    if constexpr (pow2_len(L)) {
+      constexpr int ZW = zcol_width<L, C>();
+      const size_t sm = (L + L * ZW) * sizeof(C);
+      smem_opt_in(k_zfwd_spec<L, ZW, C>, sm);
+      k_zfwd_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
+          reinterpret_cast<const C*>(c->d_Bf), dst, c->N, twiddles(c));
+      AIM_CHECK_LAUNCH();
+    }
+  }
+
   static void zrhs(aim_ctx* c, int nb, const SlabList& sl) {
     const int N = c->N;
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     KScope ks(c, AIM_K_ZRHS);
     if constexpr (pow2_len(L) && L <= 256 && std::is_same<C, float2>::value) {
-      // the slabs' ring slots (the march and aim_rhs keep every slab in the ring)
+      // the spectra's ring slots (the march and aim_rhs keep every history slab in the ring)
       const size_t slab = op_slab_bytes(c, c->batch_max);
       SlabRing sr{};
       sr.n = sl.n;
@@ -795,10 +841,10 @@ struct GridOps {
       }
       if (in_ring) {
         constexpr int ZW = L < 16 ? L : 16;
-        const size_t sm = 128 + (2 * (L / 2) * ZW + L + L * ZW) * sizeof(C);
-        smem_opt_in(k_zrhs_tma<L, ZW>, sm);
-        k_zrhs_tma<L, ZW><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(c->ring_map, sr, kspec(c), N, Bf,
-                                                                                  twiddles(c), c->d_err);
+        const size_t sm = 128 + (2 * L * ZW + L + L * ZW) * sizeof(C);
+        smem_opt_in(k_zrhs_spec_tma<L, ZW>, sm);
+        k_zrhs_spec_tma<L, ZW><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
+            c->ring_map, sr, kspec(c), N, Bf, twiddles(c), c->d_err);
         AIM_CHECK_LAUNCH();
         return;
       }
@@ -808,8 +854,8 @@ struct GridOps {
       // registers stays at one radix-R2 slice
       constexpr int ZW = L < 16 ? L : 16;
       const size_t sm = (L + L * ZW) * sizeof(C);
-      smem_opt_in(k_zrhs_p2<L, ZW, C>, sm);
-      k_zrhs_p2<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+      smem_opt_in(k_zrhs_spec<L, ZW, C>, sm);
+      k_zrhs_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
     } else {
       const size_t sm = (L + 3 * L * W) * sizeof(C);
       smem_opt_in(k_zrhs<L, W, C>, sm);
