@@ -92,7 +92,8 @@ struct GmresState {
   int* jdev = nullptr;       // current Arnoldi column (shared by the batch)
   int* flag = nullptr;       // [3] any active at cycle start / after a step / a stop without convergence
   int* cnt = nullptr;        // [2] cycles and Arnoldi steps executed (launch accounting)
-  double2* pd = nullptr;     // multi-dot partials [B][64][S]
+  double2* pd = nullptr;     // raw dot partials of the new Krylov vector [B][64][cgs_P]
+  double2* d1 = nullptr;     // their sums: the first CGS pass's dots [B][64]
   double* pu = nullptr;      // |w|^2 partials [B][cgs_P]
   double2* pd2 = nullptr;    // raw dot partials of the first CGS update [B][64][cgs_P]
   double2* d2 = nullptr;     // their sums: the second pass's dots [B][64]

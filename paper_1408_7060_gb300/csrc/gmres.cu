@@ -23,7 +23,6 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kDotChunk = 2048;  // elements per multi-dot block
 constexpr int kUpdN = 32;        // elements per update block (x 8 column groups)
 constexpr int kNormChunk = 256;  // elements per norm-partial block
 
@@ -53,56 +52,6 @@ __device__ __forceinline__ double2 warp_sum_c(double2 v) {
   keep += __shfl_xor_sync(0xffffffffu, send, 16);
   for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
   return make_double2(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
-}
-
-// raw partial dots pd[b][i][s] = sum_{n in chunk s} conj(vt_i[n]) w[n], w = slot j+1.
-// grid (64, S, nb); blocks with i > j return at once.
-__global__ void __launch_bounds__(kThreads) k_mdot(const double2* __restrict__ V, long long vstride,
-                                                   const int* __restrict__ jdev, int ns,
-                                                   const int* __restrict__ act, double2* __restrict__ pd) {
-  pdl_wait();
-  const int i = blockIdx.x, s = blockIdx.y, b = blockIdx.z;
-  const int j = *jdev;
-  if (i > j || !act[b]) return;
-  const double2* vi = V + i * vstride + (size_t)b * ns;
-  const double2* w = V + (j + 1) * vstride + (size_t)b * ns;
-  // all loads of the chunk in flight before the (ordered) sum
-  constexpr int T = kDotChunk / kThreads;
-  const int base = s * kDotChunk + threadIdx.x;
-  double2 av[T], wv[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int n = base + t * kThreads;
-    av[t] = n < ns ? vi[n] : make_double2(0, 0);
-    wv[t] = n < ns ? w[n] : make_double2(0, 0);
-  }
-  double re = 0, im = 0;
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const double2 p = cmulc(av[t], wv[t]);
-    re += p.x;
-    im += p.y;
-  }
-  __shared__ double red[2][kThreads / 32];
-  {
-    const double2 t = warp_sum_c(make_double2(re, im));
-    re = t.x;
-    im = t.y;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = re;
-    red[1][threadIdx.x >> 5] = im;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, c = 0;
-    for (int q = 0; q < kThreads / 32; ++q) {
-      a += red[0][q];
-      c += red[1][q];
-    }
-    pd[((size_t)b * 64 + i) * gridDim.y + s] = make_double2(a, c);
-  }
-  pdl_trigger();
 }
 
 // partial sums of |v_b|^2 over chunks of kNormChunk: grid (P, nb); with vf non-null
@@ -366,14 +315,55 @@ struct CgsArgs {
   double2* V;
   long long vstride;
   int ns, E, P;          // RHS length, elements per block (multiple of kCgsSub), blocks per RHS
-  const double2* pd1;    // first pass: raw dot partials of k_mdot [B][64][S]
-  int S;
+  double2* pd1;          // raw dot partials of w (k_cgs_dots) [B][64][P]
+  double2* d1;           // their sums: the first pass's dots [B][64]
   double2* pd2;          // first pass: raw dot partials of the updated w [B][64][P]
   double2* d2;           // their sums, by the last block of each RHS [B][64]
   double* pn;            // second pass: |w|^2 partials [B][P]
   unsigned* ucnt;        // [B] block arrivals per RHS
   float2* wf;            // second pass: complex64 copy of w (or null)
 };
+
+// Raw dots d_i = conj(vt_i) . w of the new vector w = slot j+1 with vt_0..vt_j, the
+// first CGS pass's d, grid (P, nb) over the same element blocks as k_cgs: warp y takes
+// i = y, y + 8, ... over the block's elements; the last block of each RHS sums the P
+// partials in a fixed order into d1.
+__global__ void __launch_bounds__(kThreads) k_cgs_dots(CgsArgs a, GmresState s) {
+  pdl_wait();
+  const int b = blockIdx.y, blk = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!s.act[b]) return;
+  const int j = *s.jdev, J = j + 1;
+  __shared__ int last;
+  const double2* Vb = a.V + (size_t)b * a.ns;
+  const double2* w = a.V + (size_t)J * a.vstride + (size_t)b * a.ns;
+  const int n0 = blk * a.E, cnt = min(a.ns, n0 + a.E) - n0;
+  for (int i = warp; i < J; i += kThreads / 32) {
+    const double2* vi = Vb + i * a.vstride + n0;
+    double2 t = make_double2(0, 0);
+    for (int q = lane; q < cnt; q += 32) {
+      const double2 p = cmulc(vi[q], w[n0 + q]);
+      t.x += p.x;
+      t.y += p.y;
+    }
+    t = warp_sum_c(t);
+    if (lane == 0) a.pd1[((size_t)b * 64 + i) * a.P + blk] = t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(a.ucnt + b, 1u) == (unsigned)a.P - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    if (tid == 0) a.ucnt[b] = 0u;
+    for (int i = warp; i < J; i += kThreads / 32) {
+      const double2 d = warp_row_sum_c<true>(a.pd1 + ((size_t)b * 64 + i) * a.P, a.P);
+      if (lane == 0) a.d1[b * 64 + i] = d;
+    }
+  }
+  pdl_trigger();
+}
 
 // One classical Gram-Schmidt pass on slot j+1 of every active RHS, grid (P, nb):
 //   h_i = sig_i d_i (d_i = sum of the raw dots conj(vt_i) . w, block 0 stores h),
@@ -399,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a, FinishArgs f, Gmres
   __shared__ int last;
   // coefficients: warp y sums the raw dots of i = y, y + 8, ...
   for (int i = warp; i < J; i += kThreads / 32) {
-    const double2 d = PASS == 0 ? warp_row_sum_c<false>(a.pd1 + ((size_t)b * 64 + i) * a.S, a.S) : a.d2[b * 64 + i];
+    const double2 d = PASS == 0 ? a.d1[b * 64 + i] : a.d2[b * 64 + i];
     if (lane == 0) {
       const double sg = s.sig[b * 64 + i];
       const double2 h = make_double2(sg * d.x, sg * d.y);
@@ -657,7 +647,6 @@ __global__ void __launch_bounds__(kThreads) k_norm_finish(int nb, const double* 
   }
 }
 
-int n_dot_chunks(int ns) { return (ns + kDotChunk - 1) / kDotChunk; }
 int n_upd_blocks(int ns) { return (ns + kUpdN - 1) / kUpdN; }
 int n_norm_blocks(int ns) { return (ns + kNormChunk - 1) / kNormChunk; }
 
@@ -716,12 +705,9 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
   const int ns = c->ns;
   const long long vstride = (long long)c->batch_max * ns;
   arnoldi_operator(c, nb);
-  const int S = n_dot_chunks(ns);
-  AIM_KLAUNCH(c, AIM_K_GMRES_DOT,
-              launch_pdl(st, dim3(64, S, nb), dim3(kThreads), 0, k_mdot, (const double2*)c->d_V, vstride,
-                         (const int*)s.jdev, ns, (const int*)s.act, s.pd));
   FinishArgs f{nb, c->restart, c->max_iter, tol, use_cond ? 1 : 0, inner, outer};
-  CgsArgs a{c->d_V, vstride, ns, s.cgs_E, s.cgs_P, s.pd, S, s.pd2, s.d2, s.pu, s.ucnt, krylov_c64(c)};
+  CgsArgs a{c->d_V, vstride, ns, s.cgs_E, s.cgs_P, s.pd, s.d1, s.pd2, s.d2, s.pu, s.ucnt, krylov_c64(c)};
+  AIM_KLAUNCH(c, AIM_K_GMRES_DOT, launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs_dots, a, s));
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
               launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs<0>, a, f, s));
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
@@ -877,11 +863,12 @@ void gmres_alloc(aim_ctx* c) {
   s.its = (int*)aim_alloc(c, B * sizeof(int));
   s.jdev = (int*)aim_alloc(c, sizeof(int));
   s.flag = (int*)aim_alloc(c, 3 * sizeof(int));
-  s.pd = (double2*)aim_alloc(c, (size_t)B * 64 * n_dot_chunks(ns) * sizeof(double2));
   // CGS update blocks: E elements each (a multiple of 64), about kCgsTargetP per RHS
   s.cgs_E = std::min(kCgsMaxE, std::max(kCgsSub, ((ns + kCgsTargetP - 1) / kCgsTargetP + kCgsSub - 1) / kCgsSub * kCgsSub));
   s.cgs_P = (ns + s.cgs_E - 1) / s.cgs_E;
   s.pu = (double*)aim_alloc(c, (size_t)B * s.cgs_P * sizeof(double));
+  s.pd = (double2*)aim_alloc(c, (size_t)B * 64 * s.cgs_P * sizeof(double2));
+  s.d1 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.pd2 = (double2*)aim_alloc(c, (size_t)B * 64 * s.cgs_P * sizeof(double2));
   s.d2 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.ucnt = (unsigned*)aim_alloc(c, (size_t)B * sizeof(unsigned));
@@ -979,7 +966,7 @@ int gmres_collect(aim_ctx* c, int* iters, double* relres) {
   const int nb = s.last_nb;
   if (s.last_graphed) {
     // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2, + 1
-    // with the SAI) + steps * (operator + dot + 2 updates); a zero start skips
+    // with the SAI) + steps * (operator + dots + 2 updates); a zero start skips
     // the operator of the first cycle
     const long long op = op_kernel_count(c);
     c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 3) * s.h_cnt[1] -
