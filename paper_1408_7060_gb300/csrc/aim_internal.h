@@ -70,6 +70,34 @@ struct TBasis {
   double coef[aimc::kMaxOrder + 1][aimc::kMaxOrder + 1];
 };
 
+// Sum over the lanes of a warp of a complex value, in 5 FP64 additions instead of 10:
+// the first exchange pairs lane l with l ^ 16, the lower half keeping the real and the
+// upper half the imaginary part, then both halves reduce their part in 4 more steps.
+// (A double-precision instruction holds its sub-partition's FP64 pipe for the whole
+// warp whatever the number of active lanes, so the instruction count is the cost.)
+__device__ __forceinline__ double2 warp_sum_c(double2 v) {
+  const int lane = threadIdx.x & 31;
+  const bool hi = lane & 16;
+  double keep = hi ? v.y : v.x;
+  const double send = hi ? v.x : v.y;
+  keep += __shfl_xor_sync(0xffffffffu, send, 16);
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return make_double2(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
+}
+
+// Raw Krylov dots formed by the interpolation kernel of an Arnoldi step's operator:
+// d[b][i] = conj(vt_i) . y_b for i <= *jdev, y the kernel's output (Krylov slot j+1);
+// partials per block of 32 rows, summed by the last block of each RHS.
+struct DotFuse {
+  const double2* V = nullptr;  // Krylov basis; null: no dots
+  long long vstride = 0;
+  const int* jdev = nullptr;
+  double2* pd = nullptr;       // partials [B][64][P]
+  double2* d = nullptr;        // sums [B][64]
+  unsigned* ucnt = nullptr;    // [B] block arrivals per RHS
+  int P = 0;                   // interpolation blocks per RHS
+};
+
 // GMRES small state, one row of 64 per right-hand side (restart <= 63)
 struct GmresState {
   double2* H = nullptr;      // [B][64][64] Hessenberg columns, unrotated (upper triangle)
@@ -94,6 +122,8 @@ struct GmresState {
   int* cnt = nullptr;        // [2] cycles and Arnoldi steps executed (launch accounting)
   double2* pd = nullptr;     // raw dot partials of the new Krylov vector [B][64][cgs_P]
   double2* d1 = nullptr;     // their sums: the first CGS pass's dots [B][64]
+  double2* pdi = nullptr;    // the same partials formed by the interpolation kernel [B][64][P_i]
+  int interp_P = 0;          // interpolation blocks per RHS when it forms the dots (0: it does not)
   double* pu = nullptr;      // |w|^2 partials [B][cgs_P]
   double2* pd2 = nullptr;    // raw dot partials of the first CGS update [B][64][cgs_P]
   double2* d2 = nullptr;     // their sums: the second pass's dots [B][64]
@@ -204,6 +234,7 @@ struct aim_ctx {
   int* d_err = nullptr;        // device error flag (a bounded wait gave up)
   void* d_xs = nullptr;        // [B][ns] prepared operator input, grid precision
   double2* d_xd = nullptr;     // [B][ns] prepared operator input, FP64 (near zone)
+  DotFuse dotfuse;             // set by the Arnoldi step around its operator application
   float2* d_vf = nullptr;      // [B][ns] complex64 copy of the Krylov vector the next SAI application
                                // reads (complex64 path; written by the kernel that finishes it)
   double2* d_iring = nullptr;  // [N_g][B][ns] current history (RWG space)

@@ -39,21 +39,6 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Sum over the lanes of a warp of a complex value, in 5 FP64 additions instead of 10:
-// the first exchange pairs lane l with l ^ 16, the lower half keeping the real and the
-// upper half the imaginary part, then both halves reduce their part in 4 more steps.
-// (A double-precision instruction holds its sub-partition's FP64 pipe for the whole
-// warp whatever the number of active lanes, so the instruction count is the cost.)
-__device__ __forceinline__ double2 warp_sum_c(double2 v) {
-  const int lane = threadIdx.x & 31;
-  const bool hi = lane & 16;
-  double keep = hi ? v.y : v.x;
-  const double send = hi ? v.x : v.y;
-  keep += __shfl_xor_sync(0xffffffffu, send, 16);
-  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
-  return make_double2(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
-}
-
 // partial sums of |v_b|^2 over chunks of kNormChunk: grid (P, nb); with vf non-null
 // also the complex64 copy of v
 __global__ void __launch_bounds__(kThreads) k_normpart(const double2* __restrict__ v, int ns,
@@ -694,7 +679,22 @@ void arnoldi_operator(aim_ctx* c, int nb) {
   vout.sel = s.jdev;
   vout.stride = vstride;
   vout.off = 1;
-  op_apply(c, 0, nb, c->d_V, c->d_dinv, nullptr, 1.0, s.act, c->d_V, vin, vout);
+  if (s.interp_P > 0) {  // the interpolation kernel also forms the first pass's dots
+    c->dotfuse.V = c->d_V;
+    c->dotfuse.vstride = vstride;
+    c->dotfuse.jdev = s.jdev;
+    c->dotfuse.pd = s.pdi;
+    c->dotfuse.d = s.d1;
+    c->dotfuse.ucnt = s.ucnt;
+    c->dotfuse.P = s.interp_P;
+  }
+  try {
+    op_apply(c, 0, nb, c->d_V, c->d_dinv, nullptr, 1.0, s.act, c->d_V, vin, vout);
+  } catch (...) {
+    c->dotfuse = DotFuse();
+    throw;
+  }
+  c->dotfuse = DotFuse();
 }
 
 // one Arnoldi step for every active RHS: operator into slot j+1, CGS2, column finish
@@ -707,7 +707,8 @@ void arnoldi_step(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphCondit
   arnoldi_operator(c, nb);
   FinishArgs f{nb, c->restart, c->max_iter, tol, use_cond ? 1 : 0, inner, outer};
   CgsArgs a{c->d_V, vstride, ns, s.cgs_E, s.cgs_P, s.pd, s.d1, s.pd2, s.d2, s.pu, s.ucnt, krylov_c64(c)};
-  AIM_KLAUNCH(c, AIM_K_GMRES_DOT, launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs_dots, a, s));
+  if (s.interp_P == 0)
+    AIM_KLAUNCH(c, AIM_K_GMRES_DOT, launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs_dots, a, s));
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
               launch_pdl(st, dim3(s.cgs_P, nb), dim3(kThreads), 0, k_cgs<0>, a, f, s));
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
@@ -869,6 +870,11 @@ void gmres_alloc(aim_ctx* c) {
   s.pu = (double*)aim_alloc(c, (size_t)B * s.cgs_P * sizeof(double));
   s.pd = (double2*)aim_alloc(c, (size_t)B * 64 * s.cgs_P * sizeof(double2));
   s.d1 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
+  // the interpolation kernel forms the first pass's dots when its blocks of 32 rows are
+  // few enough for one block to sum their partials
+  const int pi = (ns + 31) / 32;
+  s.interp_P = pi <= 1024 ? pi : 0;
+  if (s.interp_P) s.pdi = (double2*)aim_alloc(c, (size_t)B * 64 * s.interp_P * sizeof(double2));
   s.pd2 = (double2*)aim_alloc(c, (size_t)B * 64 * s.cgs_P * sizeof(double2));
   s.d2 = (double2*)aim_alloc(c, (size_t)B * 64 * sizeof(double2));
   s.ucnt = (unsigned*)aim_alloc(c, (size_t)B * sizeof(unsigned));
@@ -966,10 +972,12 @@ int gmres_collect(aim_ctx* c, int* iters, double* relres) {
   const int nb = s.last_nb;
   if (s.last_graphed) {
     // kernels the graph executed: 1 + cycles * (prologue: operator + 2, epilogue 2, + 1
-    // with the SAI) + steps * (operator + dots + 2 updates); a zero start skips
+    // with the SAI) + steps * (operator + dots + 2 updates, the dots inside the operator's
+    // interpolation kernel when it forms them); a zero start skips
     // the operator of the first cycle
     const long long op = op_kernel_count(c);
-    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + 3) * s.h_cnt[1] -
+    const long long krylov = s.interp_P > 0 ? 2 : 3;
+    c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + krylov) * s.h_cnt[1] -
                         (c->zero_start && s.h_cnt[0] > 0 ? op : 0);
   }
   int rc = AIM_OK;

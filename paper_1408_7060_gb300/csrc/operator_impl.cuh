@@ -559,49 +559,49 @@ __global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__
 
 // ---------------------------------------------------------------- stage iii + iv
 // y_k = sign * ( sum_c sum_{n in stencil(k)} L_c[n,k] P_c[n]  +  sum_terms Z~near_m x_m ) + base_k
-// One warp per kInterpRows consecutive (b, k) rows.  Grid part: the whole warp per row,
-// accumulated in the grid precision.  Near part: 8 lanes per row, all rows at once, in
-// FP64 -- the warp's FP64 instructions (each holds the sub-partition's FP64 pipe for the
-// whole warp) serve kInterpRows rows instead of one.
+// Grid (ceil(ns / 32), nb): a block takes 32 rows of one RHS, one warp per kInterpRows
+// consecutive rows.  Grid part: the whole warp per row, accumulated in the grid precision.
+// Near part: 8 lanes per row, all rows at once, in FP64 -- the warp's FP64 instructions
+// (each holds the sub-partition's FP64 pipe for the whole warp) serve kInterpRows rows
+// instead of one.  With df.V set (the operator of an Arnoldi step, y = Krylov slot j+1)
+// the block also forms the raw dots conj(vt_i) . y over its 32 rows for i <= j, and the
+// last block of the RHS sums them into df.d.
 constexpr int kInterpRows = 4;
+constexpr int kInterpBlockRows = 8 * kInterpRows;  // 256 threads
 
 template <class C>
-__global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, const int* __restrict__ anchor,
+__global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P, const int* __restrict__ anchor,
                                                      const typename Real<C>::T* __restrict__ lam, int N, int ns,
                                                      int nb, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col, NearList nl,
                                                      const double2* __restrict__ base, double sign,
                                                      const int* __restrict__ active, double2* __restrict__ y,
-                                                     VecSel ys) {
+                                                     VecSel ys, DotFuse df) {
   pdl_wait();
   using R = typename Real<C>::T;
-  const long long w0 = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * kInterpRows;
-  const int lane = threadIdx.x & 31;
-  const long long total = (long long)nb * ns;
-  if (w0 >= total) return;
+  const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (active && !active[b]) return;
+  const int k0 = blockIdx.x * kInterpBlockRows + warp * kInterpRows;  // the warp's first row
   // grid part, row by row; lane group r (lanes 8r .. 8r+7) keeps row r's sum
   C mine{};
   if (P) {
     const size_t N3 = (size_t)N * N * N;
 #pragma unroll
     for (int r = 0; r < kInterpRows; ++r) {
-      const long long w = w0 + r;
+      const int k = k0 + r;
       C g{};
-      if (w < total) {
-        const int b = (int)(w / ns), k = (int)(w % ns);
-        if (!(active && !active[b])) {
-          // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node)
-          // terms of an RWG take 8 warp loads of 8 rows x 32 B each
-          const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
-          const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
-          const R* lk = lam + (size_t)k * 256 + lane;
+      if (k < ns) {
+        // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node)
+        // terms of an RWG take 8 warp loads of 8 rows x 32 B each
+        const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
+        const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
+        const R* lk = lam + (size_t)k * 256 + lane;
 #pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            const int q = it * 8 + (lane >> 2);  // (component, row) pair, 0..63
-            const int c = q >> 4, row = q & 15;
-            const int dz = row >> 2, dy = row & 3;
-            g += lk[it * 32] * Pb[c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N];
-          }
+        for (int it = 0; it < 8; ++it) {
+          const int q = it * 8 + (lane >> 2);  // (component, row) pair, 0..63
+          const int c = q >> 4, row = q & 15;
+          const int dz = row >> 2, dy = row & 3;
+          g += lk[it * 32] * Pb[c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N];
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -613,10 +613,8 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
   }
   // near part: lane group r, sub-lane sl
   const int r = lane >> 3, sl = lane & 7;
-  const long long w = w0 + r;
-  const bool valid = w < total;
-  const int b = valid ? (int)(w / ns) : 0, k = valid ? (int)(w % ns) : 0;
-  const bool on = valid && !(active && !active[b]);
+  const int k = k0 + r;
+  const bool on = k < ns;
   long long xoff = 0;
   double xscale = 1.0;
   if (nl.xsel.sel) {
@@ -648,15 +646,55 @@ __global__ void __launch_bounds__(256) k_interp_near(const C* __restrict__ P, co
   keep += __shfl_xor_sync(0xffffffffu, keep, 2);
   keep += __shfl_xor_sync(0xffffffffu, keep, 1);
   const double nim = __shfl_down_sync(0xffffffffu, keep, 4);
+  double2 out = make_double2(0, 0);
   if (on && sl == 0) {
     if (ys.sel) y += (*ys.sel + ys.off) * ys.stride;
     const double re = (double)mine.x + xscale * keep, im = (double)mine.y + xscale * nim;
-    double2 out = make_double2(sign * re, sign * im);
+    out = make_double2(sign * re, sign * im);
     if (base) {
       const double2 bb = base[(size_t)b * ns + k];
       out = make_double2(bb.x + out.x, bb.y + out.y);
     }
     y[(size_t)b * ns + k] = out;
+  }
+  if (df.V) {
+    __shared__ double2 wsm[kInterpBlockRows];
+    __shared__ int last;
+    if (sl == 0) wsm[warp * kInterpRows + r] = out;  // zero for rows past ns
+    __syncthreads();
+    const int J = *df.jdev + 1;
+    const int kb = blockIdx.x * kInterpBlockRows + lane;
+    const double2* Vb = df.V + (size_t)b * ns;
+    for (int i = warp; i < J; i += 8) {
+      double2 t = make_double2(0, 0);
+      if (kb < ns) {
+        const double2 v = Vb[i * df.vstride + kb], w = wsm[lane];
+        t = make_double2(v.x * w.x + v.y * w.y, v.x * w.y - v.y * w.x);  // conj(v) w
+      }
+      t = warp_sum_c(t);
+      if (lane == 0) df.pd[((size_t)b * 64 + i) * df.P + blockIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(df.ucnt + b, 1u) == (unsigned)df.P - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      if (threadIdx.x == 0) df.ucnt[b] = 0u;
+      for (int i = warp; i < J; i += 8) {
+        const double2* p = df.pd + ((size_t)b * 64 + i) * df.P;
+        double2 t = make_double2(0, 0);
+        for (int q = lane; q < df.P; q += 32) {
+          const double2 v = __ldcg(p + q);
+          t.x += v.x;
+          t.y += v.y;
+        }
+        t = warp_sum_c(t);
+        if (lane == 0) df.d[b * 64 + i] = t;
+      }
+    }
   }
   pdl_trigger();
 }
@@ -783,11 +821,10 @@ struct GridOps {
 
   static void interp(aim_ctx* c, int nb, const C* P, const NearList& nl, const double2* base, double sign,
                      const int* active, double2* y, VecSel ys = VecSel()) {
-    long long warps = ((long long)nb * c->ns + kInterpRows - 1) / kInterpRows;
     KScope ks(c, AIM_K_INTERP_NEAR);
-    launch_pdl(c->stream, dim3((unsigned)((warps * 32 + 255) / 256)), dim3(256), 0, k_interp_near<C>, P,
-               (const int*)c->d_anchor, lam(c), c->N, c->ns, nb, (const int*)c->d_rowptr, (const int*)c->d_col, nl,
-               base, sign, active, y, ys);
+    launch_pdl(c->stream, dim3((unsigned)((c->ns + kInterpBlockRows - 1) / kInterpBlockRows), (unsigned)nb), dim3(256),
+               0, k_interp_near<C>, P, (const int*)c->d_anchor, lam(c), c->N, c->ns, nb, (const int*)c->d_rowptr,
+               (const int*)c->d_col, nl, base, sign, active, y, ys, c->dotfuse);
   }
 
   static void zconv(aim_ctx* c, int nb, int m, const int* active) {
