@@ -79,6 +79,8 @@ def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
     """Algorithmic HBM bytes of one launch of each kernel (each byte counted once)."""
     L = 2 * N
     slab = 4 * N * L * L * esz * nb           # [nb][4][N][L][L]
+    spec = 4 * L * L * L * esz * nb           # [nb][4][L][L][L]: z-spectrum of a slab (power-of-two L)
+    pow2 = (L & (L - 1)) == 0
     A = 4 * N * N * L * esz * nb              # [nb][4][N][N][L]
     P = 4 * N * N * N * esz * nb              # [nb][4][N][N][N]
     oct_ = (N + 1) ** 3 * esz                 # one kernel spectrum octant
@@ -91,7 +93,8 @@ def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
         "anterp_xfft": csrT + ns * esz * nb + A,
         "yfft_fwd": A + slab,
         "zconv": 2 * slab + 2 * oct_,
-        "zrhs": ng * slab + slab + 2 * ng * oct_,
+        "zrhs": ng * (spec if pow2 else slab) + slab + 2 * ng * oct_,
+        "zfwd": slab + spec if pow2 else None,
         "yfft_inv": slab + A,
         "xfft_inv": A + P,
         "interp_near": P + lam + ns * 12 + near + 2 * vec,

@@ -157,15 +157,19 @@ enum {
   AIM_K_ANTERP_XFFT = 0, /* anterpolation gather + forward x-FFT                          */
   AIM_K_YFFT_FWD,        /* forward y-FFT (pruned input)                                   */
   AIM_K_ZCONV,           /* forward z-FFT, kernel product, inverse z-FFT (immediate term)  */
-  AIM_K_ZRHS,            /* forward z-FFTs, delay sum over N_g spectra, inverse z-FFT      */
+  AIM_K_ZRHS,            /* delay sum over the N_g z-spectra of the history, inverse z-FFT */
+                         /* (forward z-FFTs per delay for lengths with a factor 3)        */
   AIM_K_YFFT_INV,        /* inverse y-FFT (pruned output)                                  */
   AIM_K_XFFT_INV,        /* inverse x-FFT (pruned output)                                  */
   AIM_K_INTERP_NEAR,     /* interpolation gather + near-zone CSR product                   */
   AIM_K_EXCITATION,      /* excitation vector V_l                                          */
-  AIM_K_GMRES_DOT,       /* Krylov multi-dot products (two-stage reduction)                */
-  AIM_K_GMRES_UPDATE,    /* Gram-Schmidt update and norms                                  */
-  AIM_K_GMRES_SMALL,     /* Givens rotations, scaling, cycle bookkeeping                   */
+  AIM_K_GMRES_DOT,       /* separate Krylov dot kernel (systems beyond 32 768 unknowns;    */
+                         /* smaller ones form the dots in the interpolation kernel)       */
+  AIM_K_GMRES_UPDATE,    /* Gram-Schmidt updates with their reductions and column finish,  */
+                         /* residual norms                                                 */
+  AIM_K_GMRES_SMALL,     /* cycle start, rotations + back substitution, solution update    */
   AIM_K_PREP,            /* operator input: selection, Krylov scale, preconditioner, cast  */
+  AIM_K_ZFWD,            /* z-spectrum of a committed history slab (power-of-two lengths)  */
   AIM_K_COUNT
 };
 

@@ -70,7 +70,7 @@ EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_nu
            "aim_get_near", "aim_get_preconditioner", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
            "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
            "aim_farfield", "aim_farfield_adjoint"]
-AIM_K_COUNT = 12
+AIM_K_COUNT = 13
 
 _LIB = None
 

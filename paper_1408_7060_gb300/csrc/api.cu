@@ -473,7 +473,8 @@ int aim_get_profile(aim_ctx* c, int64_t* launches, double* ms, int64_t* total) {
 
 const char* aim_kernel_name(int32_t id) {
   static const char* names[AIM_K_COUNT] = {"anterp_xfft", "yfft_fwd", "zconv", "zrhs", "yfft_inv", "xfft_inv",
-                                          "interp_near", "excitation", "gmres_dot", "gmres_update", "gmres_small", "prep"};
+                                          "interp_near", "excitation", "gmres_dot", "gmres_update", "gmres_small", "prep",
+                                          "zfwd"};
   return id >= 0 && id < AIM_K_COUNT ? names[id] : "?";
 }
 

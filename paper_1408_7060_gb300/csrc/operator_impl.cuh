@@ -853,6 +853,7 @@ struct GridOps {
     if constexpr (pow2_len(L)) {
       constexpr int ZW = zcol_width<L, C>();
       const size_t sm = (L + L * ZW) * sizeof(C);
+      KScope ks(c, AIM_K_ZFWD);
       smem_opt_in(k_zfwd_spec<L, ZW, C>, sm);
       k_zfwd_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
           reinterpret_cast<const C*>(c->d_Bf), dst, c->N, twiddles(c));
