@@ -1,16 +1,19 @@
-// Batched, restarted GMRES with right diagonal preconditioning for the immediate
-// system of Eq. 5 (Sec. 5.1: diagonally preconditioned GMRES, warm start from the
-// previous step).  Krylov basis, Hessenberg matrix, Givens rotations and residuals
-// are FP64; the operator is the ET-AIM matvec in the context's precision.
+// Batched, restarted GMRES with a right preconditioner (the diagonal of Sec. 5.1, or the
+// near-zone SAI) for the immediate system of Eq. 5 (Sec. 5.1: preconditioned GMRES, warm
+// start from the previous step).  Krylov basis, Hessenberg matrix, Givens rotations and
+// residuals are FP64; the operator is the ET-AIM matvec in the context's precision.
 //
 // Layout: the Krylov vectors are stored unnormalised, v_i = sig_i * vt_i, with the
 // scales sig [B][64] kept beside the Hessenberg matrix.  The operator reads vt_j
 // (times sig_j and the preconditioner) and writes A v_j straight into slot j+1, which
 // classical Gram-Schmidt applied twice (CGS2) then orthogonalises in place -- no
 // copies, no normalisation pass.  Reductions are two-stage with a fixed summation
-// order (bitwise reproducible).  The column index j lives in device memory, so a
-// whole solve is one CUDA graph: an outer conditional WHILE over restart cycles and
-// an inner one over Arnoldi steps; kernels set the loop conditions.
+// order (bitwise reproducible): partials per block, summed by the last block of each
+// right-hand side to arrive (a fenced atomic counter, no waiting).  An Arnoldi step is
+// the operator (whose interpolation kernel also forms the first pass's dots) and two
+// update kernels (the second also finishes the column).  The column index j lives in
+// device memory, so a whole solve is one CUDA graph: an outer conditional WHILE over
+// restart cycles and an inner one over Arnoldi steps; kernels set the loop conditions.
 #include <algorithm>
 #include <cmath>
 #include <functional>
