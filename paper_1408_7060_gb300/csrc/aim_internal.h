@@ -228,7 +228,8 @@ struct aim_ctx {
   void* d_A = nullptr;         // [B][4][N][N][L]   after the x pass
   void* d_Bf = nullptr;        // [B][4][N][L][L]   after the y pass (z<N slab)
   void* d_P = nullptr;         // [B][4][N][N][N]   potentials on the grid
-  void* d_ring = nullptr;      // [N_g][B][4][N][L][L] spectral history slabs
+  void* d_ring = nullptr;      // [N_g][B][4][Z][L][L] history slabs: z-spectra (Z = L, power-of-two L)
+                               // or x/y-transformed grids (Z = N)
   CUtensorMap ring_map;        // TMA view of the ring [slot][B*4*N][L][L] (complex64, power-of-two L)
   bool ring_tma = false;
   int* d_err = nullptr;        // device error flag (a bounded wait gave up)

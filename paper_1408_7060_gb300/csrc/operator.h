@@ -28,7 +28,8 @@ struct SlabRing {
   int n;
 };
 
-// history slabs (forward x/y-transformed grids) and the delay each one carries
+// history slabs (z-spectra of the forward x/y-transformed grids for power-of-two lengths,
+// the x/y-transformed grids otherwise) and the delay each one carries
 struct SlabList {
   const void* p[aimc::kMaxDelays];
   int m[aimc::kMaxDelays];
