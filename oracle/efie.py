@@ -111,11 +111,7 @@ class Geometry:
         self.coef = self.s * ell / (2.0 * rwg.area[:, None])         # S = coef (r - vfree)
         self.div = self.s * ell / rwg.area[:, None]                  # div S
         self.cent = rwg.V[rwg.F].mean(axis=1)
-        # plain left-to-right sum: the singular-pair test compares against 2x this value
-        tot = 0.0
-        for v in rwg.length.tolist():
-            tot += v
-        self.mean_edge = tot / rwg.ns
+        self.mean_edge = float(np.mean(rwg.length))
 
     def singular_mask(self, t: np.ndarray, tp: np.ndarray) -> np.ndarray:
         F = self.rwg.F

@@ -406,3 +406,27 @@ def test_setup_shortcuts_match_plain(s480_aim):
     A = s480_aim
     assert A._n_delays_grid(hull_above=0) == A._n_delays_grid(hull_above=10 ** 9)
     assert np.array_equal(A._near_pairs(tree_above=0), A._near_pairs(tree_above=10 ** 9))
+
+
+def test_singular_threshold_has_margin_on_test_meshes():
+    """Singular pairs are those sharing a vertex or with centroids closer than twice the
+    mean edge length (R15).  On every mesh the parity tests use, no centroid distance lies
+    within 1e-9 (relative) of that threshold, so the decision cannot depend on the order
+    in which either side sums the edge lengths (a difference of ~1e-16 relative)."""
+    from scipy.spatial import cKDTree
+
+    from paper_1408_7060_gb300.inputs import ellipsoid_mesh, sphere_array
+
+    meshes = [icosphere(s, 1.0) for s in range(1, 6)] + [sphere_array(s, 0.5, 1.5) for s in (2, 3, 5)]
+    meshes.append(ellipsoid_mesh())
+    for V, F in meshes:
+        rwg = build_rwg(V, F) if len(F) < 30000 else None
+        if rwg is not None:
+            me = efie.Geometry(rwg).mean_edge
+        else:  # the same mean over the unique edges, without the RWG table
+            e = np.unique(np.sort(np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]]), 1), axis=0)
+            me = float(np.mean(np.linalg.norm(V[e[:, 1]] - V[e[:, 0]], axis=1)))
+        c = V[F].mean(axis=1)
+        pr = cKDTree(c).query_pairs(2 * me * (1 + 1e-6), output_type="ndarray")
+        d = np.linalg.norm(c[pr[:, 0]] - c[pr[:, 1]], axis=1)
+        assert np.abs(d - 2 * me).min() > 1e-9 * 2 * me, len(F)
