@@ -99,6 +99,13 @@ typedef struct {
   int32_t zero_start;    /* 0: GMRES starts from the previous step's currents (Sec. 5.1);
                             1: from zero, whose residual is b itself (no operator product
                             before the first Arnoldi step)                             */
+  int32_t refine;        /* AIM_C64 only: FP64 refinement of every immediate solve.  0: off.
+                            k > 0: after the complex64-operator GMRES, the residual
+                            b - Z_0 x is formed with every grid stage in FP64; while its
+                            relative norm exceeds tol, up to k correction solves
+                            Z_0 d = r (complex64 operator, from zero, to 1e-2) update
+                            x += d.  The march's tolerance then holds for the FP64
+                            operator (AIM_ERR_NOCONV if k corrections do not reach it).  */
 } aim_opts;
 
 typedef struct {
@@ -114,8 +121,10 @@ typedef struct {
   int32_t max_iters;     /* largest per-step iteration count                        */
   double max_rel_res;    /* largest final relative residual over steps and RHS      */
   double rhs_ms;         /* device time in right-hand-side work (all steps)         */
-  double solve_ms;       /* device time in the iterative solves (all steps)         */
+  double solve_ms;       /* device time in the iterative solves (all steps, with the
+                            FP64 refinement)                                          */
   int32_t* iters;        /* optional caller array [n_steps][nb] of iteration counts */
+  int32_t refine_corrections; /* correction solves of the FP64 refinement (all steps)  */
 } aim_stats;
 
 typedef struct {
@@ -128,6 +137,7 @@ typedef struct {
   int64_t device_bytes;  /* device memory held by the context                       */
   int32_t preconditioner;/* AIM_PRECOND_*                                           */
   int64_t precond_nnz;   /* entries of the preconditioner's sparsity pattern          */
+  int32_t refine;        /* aim_opts.refine as set up (0 on the complex128 path)       */
 } aim_info;
 
 /*
@@ -205,20 +215,23 @@ int aim_matvec(aim_ctx* ctx, int32_t delay_m, int32_t nb, const aim_c128* x, aim
 
 /*
  * aim_matvec_noalloc -- the same product as aim_matvec, for callers that must not
- * allocate device memory while they run (a solver being captured into a CUDA graph,
- * a real-time or certified path whose memory is fixed at start-up, an application
- * whose device memory belongs to another allocator).  The paper has no counterpart:
- * this is a library convenience.
+ * allocate device memory while they run: a real-time or certified path whose memory is
+ * fixed at start-up, an application whose device memory belongs to another allocator
+ * (a framework's caching pool it must not bypass), a process under a hard device-memory
+ * quota.  The paper has no counterpart: this is a library convenience.
  *   Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).  The
  *   grid work space comes from one fixed 16 MiB device array in the library, held by
  *   every GPU that loads it until process exit; the context's other tables are used
  *   as set up by aim_setup.  nb * 4 * (N*N*2N + N*2N*2N + N^3) elements (complex64 or
  *   complex128 by precision) must fit in 16 MiB, else AIM_ERR_ARG (e.g. N <= 32 in
  *   complex64 for one right-hand side).  The first call on a device looks up the
- *   array's device address (cudaGetSymbolAddress) with that device current; make that
- *   first call before any stream capture.  All calls share the array, so calls whose
- *   work overlaps on the GPU (two streams, two contexts) race; nothing in it needs to
- *   start at zero.  x, y: [nb][ns] aim_c128, host or device, not overlapping.
+ *   array's device address (cudaGetSymbolAddress) with that device current and keeps
+ *   it for the process; the kept address does not survive cudaDeviceReset, so do not
+ *   call this entry point on a device after resetting it.  All calls share the array,
+ *   so calls whose work overlaps on the GPU (two streams, two contexts) race; nothing in
+ *   it needs to start at zero, and it keeps the last call's contents.
+ *   x, y: [nb][ns] aim_c128, host or device, not overlapping.  The call returns after
+ *   synchronising the context's stream.
  */
 int aim_matvec_noalloc(aim_ctx* ctx, int32_t delay_m, int32_t nb, const aim_c128* x, aim_c128* y);
 
@@ -243,9 +256,9 @@ int aim_excitation_vector(aim_ctx* ctx, const aim_excitation* exc, int32_t step_
  * Each step: excitation, delayed sum (spectral history ring), then GMRES on the
  * immediate system to relative residual tol, warm-started from I_{l-1}.
  *   currents: [n_steps][nb][ns] aim_c128, host or device (written step by step).
- *   stats: optional.  Returns AIM_ERR_NOCONV if a solve hits gmres_max_iter (steps
- *   up to stats->last_step are valid), AIM_WARN_UNSTABLE if the march completed
- *   with late-time growth.
+ *   stats: optional.  Returns AIM_ERR_NOCONV if a solve hits gmres_max_iter, or the
+ *   FP64 refinement (aim_opts.refine) does not reach tol (steps up to stats->last_step
+ *   are valid), AIM_WARN_UNSTABLE if the march completed with late-time growth.
  */
 int aim_march(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double tol,
               aim_c128* currents, aim_stats* stats);
@@ -291,6 +304,42 @@ int aim_march_continue(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps,
  */
 int aim_march_source(aim_ctx* ctx, int32_t transpose, int32_t nb, int32_t n_steps, const aim_c128* src,
                      double tol, aim_c128* currents, aim_stats* stats);
+
+/*
+ * aim_march_adjoint -- the adjoint march M^H lam = G of the march of Eq. 5 (M block
+ * lower-triangular Toeplitz in Z_0..Z_{N_g}): lam_l solves
+ *   Z_0^H lam_l = G_l - sum_{m=1..N_g, l+m <= n_steps} Z_m^H lam_{l+m},  l = n_steps..1,
+ * run as the transposed march of conj(G) in reversed time, conjugated (Z_m^H =
+ * conj(Z_m^T); the grid part is symmetric, the near-zone values are transposed).  Only
+ * the N_g most recent adjoint states are held.
+ *   G, lam: [n_steps][nb][ns], host or device.  stats and errors as aim_march.
+ */
+int aim_march_adjoint(aim_ctx* ctx, int32_t nb, int32_t n_steps, const aim_c128* G, double tol, aim_c128* lam,
+                      aim_stats* stats);
+
+/*
+ * aim_march_farfield -- forward pass of the far-field objective without a current
+ * history: march Eq. 5 from rest for the sampled-envelope excitation of one plane wave
+ * (as aim_excitation_samples: samples a [n_samp], i = i0..) and add each committed I_l's
+ * contribution to the far-field envelope F (as aim_farfield: nd directions, n = n0..
+ * n0+n_out-1) as soon as it is committed.  Only the march's N_g-step history exists.
+ *   F: [n_out][nd][2], host or device (overwritten).  stats and errors as aim_march.
+ *
+ * aim_march_adjoint_farfield -- its adjoint: grad = B^H M^{-H} A^H F, i.e. the
+ * derivative dJ/d conj(a) of J = sum |F|^2 (B: samples -> excitation, A: currents -> far
+ * field).  The adjoint march runs in reversed time; at each of its steps the source
+ * G_l = A^H F is formed for that l only and lam_l is added into grad at once, so neither
+ * G nor lam is ever stored for all steps.  F: [n_out][nd][2], grad: [n_samp]; host or
+ * device.
+ */
+int aim_march_farfield(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                       const aim_c128* a, int32_t n_steps, double tol, int32_t nd, const double* rhat,
+                       const double* e1, const double* e2, int32_t n0, int32_t n_out, aim_c128* F,
+                       aim_stats* stats);
+int aim_march_adjoint_farfield(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                               int32_t n_steps, double tol, int32_t nd, const double* rhat, const double* e1,
+                               const double* e2, int32_t n0, int32_t n_out, const aim_c128* F, aim_c128* grad,
+                               aim_stats* stats);
 int aim_excitation_samples(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
                            const aim_c128* a, int32_t n_steps, aim_c128* V);
 int aim_excitation_samples_adjoint(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0,

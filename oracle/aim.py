@@ -190,12 +190,20 @@ class AimOracle:
         G[:, :, self.n] = 0
         return G
 
+    def kernel_fft(self, m: int, kind: int) -> np.ndarray:
+        """numpy FFT of ``kernel_grid(m, kind)``, kept after the first request."""
+        if not hasattr(self, "_kfft"):
+            self._kfft = {}
+        if (m, kind) not in self._kfft:
+            self._kfft[(m, kind)] = np.fft.fftn(self.kernel_grid(m, kind))
+        return self._kfft[(m, kind)]
+
     def conv_fft(self, m: int, src: np.ndarray, kind: int) -> np.ndarray:
         """The same linear convolution through a zero-padded FFT of size (2N)^3."""
         n, n2 = self.n, 2 * self.n
         a = np.zeros((n2, n2, n2), dtype=complex)
         a[:n, :n, :n] = src.reshape(n, n, n)
-        out = np.fft.ifftn(np.fft.fftn(a) * np.fft.fftn(self.kernel_grid(m, kind)))
+        out = np.fft.ifftn(np.fft.fftn(a) * self.kernel_fft(m, kind))
         return out[:n, :n, :n].ravel()
 
     # ------------------------------------------------------------------ operators

@@ -34,8 +34,12 @@ def rhs_operator(matvec, ng: int, hist: np.ndarray, l: int) -> np.ndarray:
     return out
 
 
-def march_operator(matvec, ng: int, V: np.ndarray, tol: float = 1e-10, maxiter: int = 2000):
-    """The same march with Z_m given as ``matvec(m, x)`` and GMRES for Z_0.
+def march_operator(matvec, ng: int, V: np.ndarray, tol: float = 1e-10, maxiter: int = 2000, precond=None):
+    """The same march with Z_m given as ``matvec(m, x)`` and GMRES for Z_0 (warm start:
+    the previous step's currents).  ``precond`` (optional) is a linear operator
+    approximating Z_0^{-1}, passed to scipy's GMRES; whatever it is, each step repeats
+    GMRES from its last iterate until the true relative residual ||b - Z_0 x|| / ||b||
+    is at most ``tol``.
 
     Returns ``(I, iterations[N_t, nb])``."""
     nt, nb, ns = V.shape
@@ -49,9 +53,12 @@ def march_operator(matvec, ng: int, V: np.ndarray, tol: float = 1e-10, maxiter: 
 
             def cb(_):
                 cnt[0] += 1
-            x, info = spla.gmres(A, rhs, x0=I[l - 2, b] if l > 1 else None, rtol=tol,
-                                 atol=0.0, restart=50, maxiter=maxiter, callback=cb,
-                                 callback_type="pr_norm")
+            x = I[l - 2, b].copy() if l > 1 else np.zeros(ns, dtype=complex)
+            for _ in range(20):
+                x, info = spla.gmres(A, rhs, x0=x, rtol=tol, atol=0.0, restart=50, maxiter=maxiter,
+                                     callback=cb, callback_type="pr_norm", M=precond)
+                if np.linalg.norm(rhs - A.matvec(x)) <= tol * np.linalg.norm(rhs):
+                    break
             I[l - 1, b] = x
             its[l - 1, b] = cnt[0]
     return I, its

@@ -45,7 +45,8 @@ class aim_tbasis(ct.Structure):
 class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
-                ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32)]
+                ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32),
+                ("refine", ct.c_int32)]
 
 
 class aim_excitation(ct.Structure):
@@ -56,20 +57,22 @@ class aim_excitation(ct.Structure):
 class aim_stats(ct.Structure):
     _fields_ = [("last_step", ct.c_int32), ("total_iters", ct.c_int32), ("max_iters", ct.c_int32),
                 ("max_rel_res", ct.c_double), ("rhs_ms", ct.c_double), ("solve_ms", ct.c_double),
-                ("iters", ct.c_void_p)]
+                ("iters", ct.c_void_p), ("refine_corrections", ct.c_int32)]
 
 
 class aim_info(ct.Structure):
     _fields_ = [("ns", ct.c_int32), ("n_delays", ct.c_int32), ("n_active", ct.c_int32),
                 ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
-                ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64)]
+                ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64),
+                ("refine", ct.c_int32)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
            "aim_matvec", "aim_rhs", "aim_excitation_vector", "aim_march", "aim_march_continue", "aim_get_anterp",
            "aim_get_near", "aim_get_preconditioner", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
            "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
-           "aim_farfield", "aim_farfield_adjoint"]
+           "aim_farfield", "aim_farfield_adjoint", "aim_march_adjoint", "aim_march_farfield",
+           "aim_march_adjoint_farfield"]
 AIM_K_COUNT = 13
 
 _LIB = None
@@ -112,6 +115,11 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
         "aim_excitation_samples_adjoint": (ct.c_int, [P, P, P, I32, I32, I32, P, P]),
         "aim_farfield": (ct.c_int, [P, I32, P, P, P, I32, P, I32, I32, P]),
         "aim_farfield_adjoint": (ct.c_int, [P, I32, P, P, P, I32, I32, I32, P, P]),
+        "aim_march_adjoint": (ct.c_int, [P, I32, I32, P, D, P, ct.POINTER(aim_stats)]),
+        "aim_march_farfield": (ct.c_int, [P, P, P, I32, I32, P, I32, D, I32, P, P, P, I32, I32, P,
+                                          ct.POINTER(aim_stats)]),
+        "aim_march_adjoint_farfield": (ct.c_int, [P, P, P, I32, I32, I32, D, I32, P, P, P, I32, I32, P, P,
+                                                  ct.POINTER(aim_stats)]),
         "aim_get_anterp": (ct.c_int, [P, P, P]),
         "aim_get_near": (ct.c_int, [P, P, P, P]),
         "aim_get_preconditioner": (ct.c_int, [P, P, P, P]),
@@ -147,11 +155,19 @@ def _like(x, shape):
     return torch.empty(shape, dtype=torch.complex128, device=x.device)
 
 
-def _check(lib, ctx, rc, what):
+def _check(lib, ctx, rc, what, stats=None):
     if rc < 0:
         msg = lib.aim_last_error(ctx)
-        raise AimError(rc, f"{what}: {msg.decode() if msg else ''}")
+        err = AimError(rc, f"{what}: {msg.decode() if msg else ''}")
+        err.stats = stats   # march statistics (AIM_ERR_NOCONV: steps up to last_step are valid)
+        raise err
     return rc
+
+
+def _stats(st, iters):
+    out = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
+    out["iters"] = iters
+    return out
 
 
 def _stream_handle():
@@ -169,11 +185,13 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
-              restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False):
+              restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False,
+              refine=0):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
     precond_radius, default the near radius).  zero_start: GMRES from zero instead of
-    the previous step's currents."""
+    the previous step's currents.  refine (complex64 only): up to this many FP64
+    refinement corrections per step (0: off)."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -183,7 +201,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
                     stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
-                    int(bool(zero_start)))
+                    int(bool(zero_start)), int(refine))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -264,11 +282,10 @@ def aim_march(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
     e, keep = _exc(khat, phat, sigma, t_d)
     cur = np.empty((n_steps, e.nb, ns), dtype=np.complex128) if out is None else out
     iters = np.zeros((n_steps, e.nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
     rc = lib.aim_march(ctx, ct.byref(e), int(n_steps), float(tol), _ptr(cur), ct.byref(st))
-    _check(lib, ctx, rc, "aim_march")
-    stats = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
-    stats["iters"] = iters
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march", stats)
     return cur, stats, rc
 
 
@@ -279,11 +296,10 @@ def aim_march_continue(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
     e, keep = _exc(khat, phat, sigma, t_d)
     cur = np.empty((n_steps, e.nb, ns), dtype=np.complex128) if out is None else out
     iters = np.zeros((n_steps, e.nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
     rc = lib.aim_march_continue(ctx, ct.byref(e), int(n_steps), float(tol), _ptr(cur), ct.byref(st))
-    _check(lib, ctx, rc, "aim_march_continue")
-    stats = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
-    stats["iters"] = iters
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march_continue", stats)
     return cur, stats, rc
 
 
@@ -314,13 +330,58 @@ def aim_march_source(ctx, src, tol, transpose=False, out=None):
     n_steps, nb, ns = src.shape
     cur = _like(src, tuple(src.shape)) if out is None else out
     iters = np.zeros((n_steps, nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
     rc = lib.aim_march_source(ctx, int(bool(transpose)), int(nb), int(n_steps), _ptr(src), float(tol), _ptr(cur),
                               ct.byref(st))
-    _check(lib, ctx, rc, "aim_march_source")
-    stats = {f: getattr(st, f) for f, _ in aim_stats._fields_ if f != "iters"}
-    stats["iters"] = iters
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march_source", stats)
     return cur, stats, rc
+
+
+def aim_march_adjoint(ctx, G, tol, out=None):
+    """The adjoint march M^H lam = G for G[n_steps, nb, ns]; returns (lam, stats, status)."""
+    lib = load()
+    n_steps, nb, ns = G.shape
+    lam = _like(G, tuple(G.shape)) if out is None else out
+    iters = np.zeros((n_steps, nb), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    rc = lib.aim_march_adjoint(ctx, int(nb), int(n_steps), _ptr(G), float(tol), _ptr(lam), ct.byref(st))
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march_adjoint", stats)
+    return lam, stats, rc
+
+
+def aim_march_farfield(ctx, khat, phat, i0, a, n_steps, tol, rhat, e1, e2, n0, n_out, out=None):
+    """Far-field envelope F[n_out, nd, 2] of the march driven by envelope samples a (no
+    current history is kept); returns (F, stats, status)."""
+    lib = load()
+    k, p = _vec3(khat), _vec3(phat)
+    r, u, v = _vec3(rhat), _vec3(e1), _vec3(e2)
+    F = _like(a, (int(n_out), len(r), 2)) if out is None else out
+    iters = np.zeros((int(n_steps), 1), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    rc = lib.aim_march_farfield(ctx, k.ctypes.data, p.ctypes.data, int(i0), int(a.shape[0]), _ptr(a), int(n_steps),
+                                float(tol), len(r), r.ctypes.data, u.ctypes.data, v.ctypes.data, int(n0),
+                                int(n_out), _ptr(F), ct.byref(st))
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march_farfield", stats)
+    return F, stats, rc
+
+
+def aim_march_adjoint_farfield(ctx, khat, phat, i0, n_samp, n_steps, tol, rhat, e1, e2, n0, F, out=None):
+    """grad[n_samp] = B^H M^{-H} A^H F (dJ/d conj(a) of J = sum |F|^2); returns (grad, stats, status)."""
+    lib = load()
+    k, p = _vec3(khat), _vec3(phat)
+    r, u, v = _vec3(rhat), _vec3(e1), _vec3(e2)
+    g = _like(F, (int(n_samp),)) if out is None else out
+    iters = np.zeros((int(n_steps), 1), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    rc = lib.aim_march_adjoint_farfield(ctx, k.ctypes.data, p.ctypes.data, int(i0), int(n_samp), int(n_steps),
+                                        float(tol), len(r), r.ctypes.data, u.ctypes.data, v.ctypes.data, int(n0),
+                                        int(F.shape[0]), _ptr(F), _ptr(g), ct.byref(st))
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march_adjoint_farfield", stats)
+    return g, stats, rc
 
 
 def aim_excitation_samples(ctx, khat, phat, i0, a, n_steps, out=None):
@@ -418,7 +479,7 @@ class AimContext:
         V, F = w.mesh
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
-                  precond_radius=w.precond_radius, zero_start=w.zero_start)
+                  precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine)
         kw.update(over)
         return cls(**kw)
 

@@ -2,14 +2,17 @@
 
 J(a) = sum_n sum_d sum_q |F_q(n; r_d)|^2, where the march of Eq. 5 is driven by the
 incident envelope samples a (complex128 [n_samp]) and F is the far-field envelope of
-the marched currents.  The forward pass runs the march on the device and keeps only
-F (the march itself holds just its N_g-step history); the backward pass runs the
-adjoint march M^H lam = dJ/d conj(I) -- the transposed march of the conjugated
-source in reversed time -- and maps lam back to the samples.  All steps run in the
-CUDA library; this module only orders the calls.
+the marched currents.  Both passes are single library calls and neither stores a
+history of N_t steps:
 
-PyTorch's convention for a real loss of complex inputs: a.grad = 2 dJ/d conj(a)
-(so that dJ = Re(sum conj(a.grad) da)).
+* forward, aim_march_farfield: the march adds each committed step's contribution to F
+  at once, so only F and the march's own N_g-step history exist;
+* backward, aim_march_adjoint_farfield: the adjoint march M^H lam = A^H F runs in
+  reversed time (the transposed march of the conjugated source, conjugated), forming
+  each step's source from F and adding each lam_l into the gradient B^H lam at once.
+
+This module only orders the calls.  PyTorch's convention for a real loss of complex
+inputs: a.grad = 2 dJ/d conj(a) (so that dJ = Re(sum conj(a.grad) da)).
 """
 from __future__ import annotations
 
@@ -23,10 +26,8 @@ class FarFieldObjective(torch.autograd.Function):
     def forward(fctx, a, handle, wave, dirs, n_steps, tol, i0, n0, n_out):
         khat, phat = wave
         rhat, e1, e2 = dirs
-        a_ = a.detach().contiguous()
-        V = abi.aim_excitation_samples(handle, khat, phat, i0, a_, n_steps)
-        I, _, _ = abi.aim_march_source(handle, V.reshape(n_steps, 1, -1), tol)
-        F = abi.aim_farfield(handle, rhat, e1, e2, I.reshape(n_steps, -1), n0, n_out)
+        F, _, _ = abi.aim_march_farfield(handle, khat, phat, i0, a.detach().contiguous(), n_steps, tol,
+                                         rhat, e1, e2, n0, n_out)
         fctx.save_for_backward(F)
         fctx.meta = (handle, wave, dirs, n_steps, tol, i0, n0, a.shape[0])
         return (F.abs() ** 2).sum()
@@ -35,11 +36,8 @@ class FarFieldObjective(torch.autograd.Function):
     def backward(fctx, gJ):
         (F,) = fctx.saved_tensors
         handle, (khat, phat), (rhat, e1, e2), n_steps, tol, i0, n0, n_samp = fctx.meta
-        G = abi.aim_farfield_adjoint(handle, rhat, e1, e2, n_steps, n0, F)          # dJ/d conj(I)
-        src = torch.flip(G, dims=[0]).conj().resolve_conj().contiguous().reshape(n_steps, 1, -1)
-        u, _, _ = abi.aim_march_source(handle, src, tol, transpose=True)
-        lam = torch.flip(u, dims=[0]).conj().resolve_conj().contiguous().reshape(n_steps, -1)  # M^H lam = G
-        g = abi.aim_excitation_samples_adjoint(handle, khat, phat, i0, n_samp, lam)
+        g, _, _ = abi.aim_march_adjoint_farfield(handle, khat, phat, i0, n_samp, n_steps, tol, rhat, e1, e2, n0,
+                                                 F.contiguous())
         return 2.0 * gJ * g, None, None, None, None, None, None, None, None
 
 

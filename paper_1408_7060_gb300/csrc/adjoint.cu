@@ -61,13 +61,13 @@ __device__ __forceinline__ double2 cmc(double2 a, double2 b) {  // conj(a) b
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
-// V_l[k], l = 1..n_steps (thread per (l, k))
+// V_l[k], l = l0..l0+n_steps-1 into out[l - l0] (thread per (l, k))
 __global__ void __launch_bounds__(kT) k_exc_samples(MeshArgs m, WaveArgs w, int i0, int n_samp,
-                                                    const double2* __restrict__ a, int n_steps,
+                                                    const double2* __restrict__ a, int l0, int n_steps,
                                                     double2* __restrict__ out) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)n_steps * m.ns) return;
-  const int l = (int)(idx / m.ns) + 1, k = (int)(idx % m.ns);
+  const int l = (int)(idx / m.ns) + l0, k = (int)(idx % m.ns);
   double2 acc = make_double2(0, 0);
   for (int side = 0; side < 2; ++side) {
     const int t = m.rtri[2 * k + side];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kT) k_exc_samples(MeshArgs m, WaveArgs w, int 
       acc.y += wt * e.y;
     }
   }
-  out[(size_t)(l - 1) * m.ns + k] = acc;
+  out[(size_t)(l - l0) * m.ns + k] = acc;
 }
 
 template <class T>
@@ -122,9 +122,11 @@ __device__ __forceinline__ double2 block_sum(double2 v) {
   return s;
 }
 
-// grad_i = sum_l sum_k conj(B_{l-i}[k]) lam_l[k]  (block per sample i)
-__global__ void __launch_bounds__(kT) k_exc_samples_adj(MeshArgs m, WaveArgs w, int i0, int n_steps,
-                                                        const double2* __restrict__ lam, double2* __restrict__ grad) {
+// grad_i (+)= sum_l sum_k conj(B_{l-i}[k]) lam_l[k] over l = l0..l0+n_steps-1, lam_l =
+// lam[l - l0] (or its conjugate with conj_lam); block per sample i = i0 + blockIdx.x
+__global__ void __launch_bounds__(kT) k_exc_samples_adj(MeshArgs m, WaveArgs w, int i0, int l0, int n_steps,
+                                                        const double2* __restrict__ lam, int conj_lam, int accumulate,
+                                                        double2* __restrict__ grad) {
   const int i = i0 + blockIdx.x;
   double2 acc = make_double2(0, 0);
   for (int k = threadIdx.x; k < m.ns; k += blockDim.x) {
@@ -140,10 +142,12 @@ __global__ void __launch_bounds__(kT) k_exc_samples_adj(MeshArgs m, WaveArgs w, 
         sincos(-m.kc * rk, &s, &c);
         const double sp = cS * ((r[0] - vf[0]) * w.px + (r[1] - vf[1]) * w.py + (r[2] - vf[2]) * w.pz);
         const double wt = m.qw[7 * t + q] * sp;
-        const int llo = max(1, (int)floor(i + u - 1)), lhi = min(n_steps, (int)ceil(i + u + m.tb.Q));
+        const int llo = max(l0, (int)floor(i + u - 1)), lhi = min(l0 + n_steps - 1, (int)ceil(i + u + m.tb.Q));
         for (int l = llo; l <= lhi; ++l) {
           const double2 f = cm(dt_basis(m, l - i - u), make_double2(c, s));
-          const double2 p = cmc(f, lam[(size_t)(l - 1) * m.ns + k]);
+          double2 lv = lam[(size_t)(l - l0) * m.ns + k];
+          if (conj_lam) lv.y = -lv.y;
+          const double2 p = cmc(f, lv);
           acc.x += wt * p.x;
           acc.y += wt * p.y;
         }
@@ -151,13 +155,22 @@ __global__ void __launch_bounds__(kT) k_exc_samples_adj(MeshArgs m, WaveArgs w, 
     }
   }
   const double2 sum = block_sum(acc);
-  if (threadIdx.x == 0) grad[blockIdx.x] = sum;
+  if (threadIdx.x == 0) {
+    if (accumulate) {
+      grad[blockIdx.x].x += sum.x;
+      grad[blockIdx.x].y += sum.y;
+    } else {
+      grad[blockIdx.x] = sum;
+    }
+  }
 }
 
-// F[n][d][q], n = n0..n0+n_out-1 (block per (n, d))
-__global__ void __launch_bounds__(kT) k_farfield(MeshArgs m, DirArgs d, int n_steps, const double2* __restrict__ I,
-                                                 int n0, double2* __restrict__ F) {
-  const int n = n0 + blockIdx.x / d.nd, di = blockIdx.x % d.nd;
+// F[n - n0][d][q] (+)= the contribution of I_l, l = l0..l0+n_steps-1 (I_l = I[l - l0]), for
+// n = n1..n1+gridDim.x/nd-1 (block per (n, d))
+__global__ void __launch_bounds__(kT) k_farfield(MeshArgs m, DirArgs d, int l0, int n_steps,
+                                                 const double2* __restrict__ I, int n0, int n1, int accumulate,
+                                                 double2* __restrict__ F) {
+  const int n = n1 + blockIdx.x / d.nd, di = blockIdx.x % d.nd;
   const double* rh = d.r + 3 * di;
   const double* e1 = d.e1 + 3 * di;
   const double* e2 = d.e2 + 3 * di;
@@ -176,10 +189,10 @@ __global__ void __launch_bounds__(kT) k_farfield(MeshArgs m, DirArgs d, int n_st
         const double sx = cS * (r[0] - vf[0]), sy = cS * (r[1] - vf[1]), sz = cS * (r[2] - vf[2]);
         const double p1 = m.qw[7 * t + q] * (sx * e1[0] + sy * e1[1] + sz * e1[2]);
         const double p2 = m.qw[7 * t + q] * (sx * e2[0] + sy * e2[1] + sz * e2[2]);
-        const int llo = max(1, (int)floor(n + wv - m.tb.Q)), lhi = min(n_steps, (int)ceil(n + wv + 1));
+        const int llo = max(l0, (int)floor(n + wv - m.tb.Q)), lhi = min(l0 + n_steps - 1, (int)ceil(n + wv + 1));
         double2 sum = make_double2(0, 0);
         for (int l = llo; l <= lhi; ++l) {
-          const double2 p = cm(dt_basis(m, n - l + wv), I[(size_t)(l - 1) * m.ns + k]);
+          const double2 p = cm(dt_basis(m, n - l + wv), I[(size_t)(l - l0) * m.ns + k]);
           sum.x += p.x;
           sum.y += p.y;
         }
@@ -195,17 +208,27 @@ __global__ void __launch_bounds__(kT) k_farfield(MeshArgs m, DirArgs d, int n_st
   const double2 s1 = block_sum(a1);
   const double2 s2 = block_sum(a2);
   if (threadIdx.x == 0) {
-    F[((size_t)blockIdx.x) * 2] = make_double2(cf * s1.x, cf * s1.y);
-    F[((size_t)blockIdx.x) * 2 + 1] = make_double2(cf * s2.x, cf * s2.y);
+    double2* f = F + ((size_t)(n - n0) * d.nd + di) * 2;
+    if (accumulate) {
+      f[0].x += cf * s1.x;
+      f[0].y += cf * s1.y;
+      f[1].x += cf * s2.x;
+      f[1].y += cf * s2.y;
+    } else {
+      f[0] = make_double2(cf * s1.x, cf * s1.y);
+      f[1] = make_double2(cf * s2.x, cf * s2.y);
+    }
   }
 }
 
-// G_l[k] = conj(-mu/4pi) sum_n sum_{d,q} conj(A_{n-l}[d][q][k]) F[n][d][q]  (thread per (l, k))
-__global__ void __launch_bounds__(kT) k_farfield_adj(MeshArgs m, DirArgs d, int n_steps, int n0, int n_out,
-                                                     const double2* __restrict__ F, double2* __restrict__ G) {
+// G_l[k] = conj(-mu/4pi) sum_n sum_{d,q} conj(A_{n-l}[d][q][k]) F[n][d][q] for l = l0..l0+n_steps-1
+// into G[l - l0] (conjugated with conj_out); thread per (l, k)
+__global__ void __launch_bounds__(kT) k_farfield_adj(MeshArgs m, DirArgs d, int l0, int n_steps, int n0, int n_out,
+                                                     const double2* __restrict__ F, int conj_out,
+                                                     double2* __restrict__ G) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)n_steps * m.ns) return;
-  const int l = (int)(idx / m.ns) + 1, k = (int)(idx % m.ns);
+  const int l = (int)(idx / m.ns) + l0, k = (int)(idx % m.ns);
   double2 acc = make_double2(0, 0);
   for (int di = 0; di < d.nd; ++di) {
     const double* rh = d.r + 3 * di;
@@ -236,7 +259,7 @@ __global__ void __launch_bounds__(kT) k_farfield_adj(MeshArgs m, DirArgs d, int 
     }
   }
   const double cf = -aimc::kMu0 / (4.0 * aimc::kPi);  // real: conj(cf) = cf
-  G[(size_t)(l - 1) * m.ns + k] = make_double2(cf * acc.x, cf * acc.y);
+  G[(size_t)(l - l0) * m.ns + k] = make_double2(cf * acc.x, conj_out ? -cf * acc.y : cf * acc.y);
 }
 
 // valT[m][e] = val[m][perm[e]]: the near-zone values of the transposed matrices
@@ -268,33 +291,58 @@ MeshArgs mesh_args(aim_ctx* c) {
 
 }  // namespace
 
+// time reach of the cubature points in units of dt: every point r has |r.u| / (c dt) <= this
+// for any unit u (the largest vertex distance from the origin bounds the points)
+static double reach(aim_ctx* c) { return c->rmax / (aimc::kC0 * c->dt); }
+
 void adj_excitation_samples(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
-                            const double2* a, int n_steps, double2* V) {
+                            const double2* a, int l0, int n_steps, double2* V) {
   WaveArgs w{khat[0], khat[1], khat[2], phat[0], phat[1], phat[2]};
   const long long n = (long long)n_steps * c->ns;
-  k_exc_samples<<<(int)((n + kT - 1) / kT), kT, 0, c->stream>>>(mesh_args(c), w, i0, n_samp, a, n_steps, V);
+  k_exc_samples<<<(int)((n + kT - 1) / kT), kT, 0, c->stream>>>(mesh_args(c), w, i0, n_samp, a, l0, n_steps, V);
   AIM_CHECK_LAUNCH();
 }
 
+// grad over the samples i0..i0+n_samp-1; with accumulate only the samples whose taps reach
+// steps l0..l0+n_steps-1 are visited (the others receive nothing)
 void adj_excitation_samples_adjoint(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
-                                    int n_steps, const double2* lam, double2* grad) {
+                                    int l0, int n_steps, const double2* lam, bool conj_lam, bool accumulate,
+                                    double2* grad) {
   WaveArgs w{khat[0], khat[1], khat[2], phat[0], phat[1], phat[2]};
-  k_exc_samples_adj<<<n_samp, kT, 0, c->stream>>>(mesh_args(c), w, i0, n_steps, lam, grad);
+  int ia = i0, ib = i0 + n_samp - 1;
+  if (accumulate) {  // B_{l-i} is non-zero only for l - i - u in (-1, Q], |u| <= reach
+    const double u = reach(c);
+    ia = std::max(ia, (int)std::floor(l0 - u - c->tb.Q) - 1);
+    ib = std::min(ib, (int)std::ceil(l0 + n_steps - 1 + u + 1) + 1);
+    if (ib < ia) return;
+  }
+  k_exc_samples_adj<<<ib - ia + 1, kT, 0, c->stream>>>(mesh_args(c), w, ia, l0, n_steps, lam, conj_lam ? 1 : 0,
+                                                     accumulate ? 1 : 0, grad + (ia - i0));
   AIM_CHECK_LAUNCH();
 }
 
-void adj_farfield(aim_ctx* c, int nd, const double* d_dirs, int n_steps, const double2* I, int n0, int n_out,
-                  double2* F) {
+// F over n = n0..n0+n_out-1; with accumulate only the n the steps l0..l0+n_steps-1 reach
+void adj_farfield(aim_ctx* c, int nd, const double* d_dirs, int l0, int n_steps, const double2* I, int n0, int n_out,
+                  bool accumulate, double2* F) {
   DirArgs d{nd, d_dirs, d_dirs + 3 * nd, d_dirs + 6 * nd};
-  k_farfield<<<n_out * nd, kT, 0, c->stream>>>(mesh_args(c), d, n_steps, I, n0, F);
+  int na = n0, nb_ = n0 + n_out - 1;
+  if (accumulate) {  // A_{n-l} is non-zero only for n - l + w in (-1, Q], |w| <= reach
+    const double u = reach(c);
+    na = std::max(na, (int)std::floor(l0 - u - 1) - 1);
+    nb_ = std::min(nb_, (int)std::ceil(l0 + n_steps - 1 + u + c->tb.Q) + 1);
+    if (nb_ < na) return;
+  }
+  k_farfield<<<(nb_ - na + 1) * nd, kT, 0, c->stream>>>(mesh_args(c), d, l0, n_steps, I, n0, na, accumulate ? 1 : 0,
+                                                        F);
   AIM_CHECK_LAUNCH();
 }
 
-void adj_farfield_adjoint(aim_ctx* c, int nd, const double* d_dirs, int n_steps, int n0, int n_out,
-                          const double2* F, double2* G) {
+void adj_farfield_adjoint(aim_ctx* c, int nd, const double* d_dirs, int l0, int n_steps, int n0, int n_out,
+                          const double2* F, bool conj_out, double2* G) {
   DirArgs d{nd, d_dirs, d_dirs + 3 * nd, d_dirs + 6 * nd};
   const long long n = (long long)n_steps * c->ns;
-  k_farfield_adj<<<(int)((n + kT - 1) / kT), kT, 0, c->stream>>>(mesh_args(c), d, n_steps, n0, n_out, F, G);
+  k_farfield_adj<<<(int)((n + kT - 1) / kT), kT, 0, c->stream>>>(mesh_args(c), d, l0, n_steps, n0, n_out, F,
+                                                                conj_out ? 1 : 0, G);
   AIM_CHECK_LAUNCH();
 }
 

@@ -137,16 +137,21 @@ struct GmresState {
   double* h_res = nullptr;
   int* h_done = nullptr;
   int* h_cnt = nullptr;
-  // captured solve (one graph with conditional loops), rebuilt when its inputs change
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  int g_nb = 0;
-  double g_tol = 0;
-  const void* g_b = nullptr;
-  const void* g_x = nullptr;
-  const void* g_near = nullptr;
+  // captured solves (one graph with conditional loops each), rebuilt when their inputs
+  // change: slot 0 for solves warm-started from x, slot 1 for solves from zero (the
+  // correction solves of the FP64 refinement, or every solve with zero_start)
+  struct SolveGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nb = 0;
+    double tol = 0;
+    const void* b = nullptr;
+    const void* x = nullptr;
+    const void* near = nullptr;
+  } graphs[2];
   bool graph_failed = false;
   bool last_graphed = false;  // the last enqueued solve ran as a graph
+  bool last_zs = false;       // ... and started from zero
   int last_nb = 0;
 };
 
@@ -194,6 +199,8 @@ struct aim_ctx {
   double* d_qw = nullptr;      // [nt][7] weights * area
   double* d_cent = nullptr;    // [nt][3]
   double mean_edge = 0;
+  double rmax = 0;             // largest vertex distance from the origin (bounds the time reach
+                               // r.u / (c dt) of every cubature point)
 
   int* d_anchor = nullptr;     // [ns][3]
   double* d_lam = nullptr;     // [ns][4][64]  FP64 anterpolation rows
@@ -215,6 +222,14 @@ struct aim_ctx {
   int precond = 0;             // AIM_PRECOND_*
   double precond_radius = 0;   // SAI pattern radius (m)
   bool zero_start = false;     // GMRES initial guess 0 instead of the previous currents
+  int refine = 0;              // complex64 path: FP64-operator refinement sweeps per step (0: off)
+  int ref_nb = 0;              // right-hand sides per FP64 residual product (its buffers' batch)
+  void* d_A64 = nullptr;       // FP64 grid work buffers of the refinement residual ([ref_nb] x the
+  void* d_Bf64 = nullptr;      // layouts of d_A, d_Bf, d_P), and its FP64 operator input
+  void* d_P64 = nullptr;
+  void* d_xs64 = nullptr;
+  double* d_rn = nullptr;      // [2][B] |r| and |b| of the refinement check
+  double* h_rn = nullptr;      // pinned host copy
   double2* d_sai = nullptr;    // [snnz] SAI values on its CSR pattern (AIM_PRECOND_NEAR_SAI)
   float2* d_saif = nullptr;    // the same rounded to complex64 (applied by the complex64 path)
   int* d_srowptr = nullptr;    // SAI pattern (the near-zone CSR when the radii agree)

@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -85,6 +87,8 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
     throw AimError{AIM_ERR_ARG, "aim_setup: unknown preconditioner"};
   c->precond = opts->preconditioner;
   c->zero_start = opts->zero_start != 0;
+  if (opts->refine < 0 || opts->refine > 64) throw AimError{AIM_ERR_ARG, "aim_setup: refine out of range"};
+  c->refine = opts->precision == AIM_C64 ? opts->refine : 0;
   c->precond_radius = opts->precond_radius > 0 ? opts->precond_radius : near_radius;
   if (c->precond == AIM_PRECOND_NEAR_SAI && c->precond_radius < 0)
     throw AimError{AIM_ERR_ARG, "aim_setup: the SAI preconditioner needs a pattern radius or a near zone"};
@@ -106,6 +110,9 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->nt = hm.nt;
   c->ns = hm.ns;
   c->mean_edge = hm.mean_edge;
+  for (int i = 0; i < hm.nv; ++i)
+    c->rmax = std::max(c->rmax, std::sqrt(hm.V[3 * i] * hm.V[3 * i] + hm.V[3 * i + 1] * hm.V[3 * i + 1] +
+                                          hm.V[3 * i + 2] * hm.V[3 * i + 2]));
   c->h_edge = hm.edge;
   c->h_tri = hm.rtri;
   c->h_free = hm.rfree;
@@ -153,11 +160,25 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_V = (double2*)aim_alloc(c, (size_t)(c->restart + 1) * vec);
   c->d_hist = (double2*)aim_alloc(c, (size_t)ng * vec);
   c->d_exc = (double*)aim_alloc(c, (size_t)B * 6 * sizeof(double));
+  if (c->refine > 0) {
+    // FP64 grid buffers for the refinement residual, for as many right-hand sides at a
+    // time as fit in 8 GiB (at least one)
+    const size_t per = (size_t)4 * ((size_t)N * N * L + (size_t)N * L * L + (size_t)N * N * N) * sizeof(double2);
+    c->ref_nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (size_t(8) << 30) / per));
+    const size_t rb = (size_t)c->ref_nb;
+    c->d_A64 = aim_alloc(c, rb * 4 * N * N * L * sizeof(double2));
+    c->d_Bf64 = aim_alloc(c, rb * 4 * N * L * L * sizeof(double2));
+    c->d_P64 = aim_alloc(c, rb * 4 * N * N * N * sizeof(double2));
+    c->d_xs64 = aim_alloc(c, rb * ns * sizeof(double2));
+    c->d_rn = (double*)aim_alloc(c, 2 * (size_t)B * sizeof(double));
+    AIM_CUDA(cudaMallocHost(&c->h_rn, 2 * (size_t)B * sizeof(double)));
+  }
   gmres_alloc(c);
   // run every operator kernel once outside any stream capture: sets the shared-memory
   // attributes of each instantiation and surfaces launch errors at setup
   AIM_CUDA(cudaMemsetAsync(c->d_x, 0, vec, c->stream));
   op_apply(c, 0, 1, c->d_x, nullptr, nullptr, 1.0, nullptr, c->d_y);
+  if (c->refine > 0) op_apply_f64(c, 0, 1, c->d_x, nullptr, 1.0, c->d_y);
   ensure_ring(c);
   op_forward_slab(c, 1, c->d_x, c->d_ring);
   {
@@ -265,18 +286,58 @@ void prof_flush(aim_ctx* c) {
   cudaGetLastError();
 }
 
-static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, double tol, aim_c128* currents,
-                       aim_stats* stats, int nb_src = 0, const aim_c128* src = nullptr);
+// Where the right-hand side b of each step of a march comes from and where its currents
+// go.  Steps are counted j = 1..n_steps within one call.  With rev, the explicit sources
+// are read and the currents stored in reversed order (j <-> n_steps + 1 - j) and
+// conjugated: the adjoint march M^H lam = G is the transposed march of conj(G) in
+// reversed time, conjugated.
+struct StepIO {
+  const aim_excitation* exc = nullptr;                  // plane waves (Eq. 1)
+  int nb = 0;
+  const aim_c128* src = nullptr;                        // explicit sources [n_steps][nb][ns]
+  aim_c128* out = nullptr;                              // currents [n_steps][nb][ns] (may be null)
+  bool rev = false;
+  std::function<void(int j, double2* b)> make_src;      // custom source written to b (device)
+  std::function<void(int j, const double2* x)> commit;  // after I_j is committed (device)
+};
+
+static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, aim_stats* stats);
 
 void adj_excitation_samples(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
-                            const double2* a, int n_steps, double2* V);
+                            const double2* a, int l0, int n_steps, double2* V);
 void adj_excitation_samples_adjoint(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
-                                    int n_steps, const double2* lam, double2* grad);
-void adj_farfield(aim_ctx* c, int nd, const double* d_dirs, int n_steps, const double2* I, int n0, int n_out,
-                  double2* F);
-void adj_farfield_adjoint(aim_ctx* c, int nd, const double* d_dirs, int n_steps, int n0, int n_out,
-                          const double2* F, double2* G);
+                                    int l0, int n_steps, const double2* lam, bool conj_lam, bool accumulate,
+                                    double2* grad);
+void adj_farfield(aim_ctx* c, int nd, const double* d_dirs, int l0, int n_steps, const double2* I, int n0, int n_out,
+                  bool accumulate, double2* F);
+void adj_farfield_adjoint(aim_ctx* c, int nd, const double* d_dirs, int l0, int n_steps, int n0, int n_out,
+                          const double2* F, bool conj_out, double2* G);
 void adj_ensure_near_transpose(aim_ctx* c);
+
+namespace {
+__global__ void __launch_bounds__(256) k_conj(long long n, const double2* __restrict__ a, double2* __restrict__ b) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = a[i];
+    b[i] = make_double2(v.x, -v.y);
+  }
+}
+void conj_copy(aim_ctx* c, size_t n, const double2* a, double2* b) {
+  k_conj<<<(int)((n + 255) / 256), 256, 0, c->stream>>>((long long)n, a, b);
+  AIM_CHECK_LAUNCH();
+}
+
+// the near-zone values of the transposed matrices Z_m^T for the life of one call
+struct TransposeNear {
+  aim_ctx* c;
+  double2* fwd;
+  explicit TransposeNear(aim_ctx* c_) : c(c_), fwd(c_->d_near) {
+    adj_ensure_near_transpose(c);
+    if (c->nnz) c->d_near = c->d_nearT;
+  }
+  ~TransposeNear() { c->d_near = fwd; }
+};
+}  // namespace
 
 extern "C" {
 
@@ -309,6 +370,7 @@ void aim_destroy(aim_ctx* c) {
   }
   for (auto e : c->prof.pool) cudaEventDestroy(e);
   gmres_free_host(c);
+  if (c->h_rn) cudaFreeHost(c->h_rn);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -326,6 +388,7 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   info->device_bytes = (int64_t)c->device_bytes;
   info->preconditioner = c->precond;
   info->precond_nnz = c->d_sai ? c->snnz : c->ns;
+  info->refine = c->refine;
   return AIM_OK;
 }
 
@@ -426,7 +489,11 @@ int aim_march(aim_ctx* c, const aim_excitation* exc, int32_t n_steps, double tol
     AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)exc->nb * c->ns * sizeof(double2), c->stream));
     c->l_done = 0;
     c->march_nb = exc->nb;
-    return march_steps(c, exc, n_steps, tol, currents, stats);
+    StepIO io;
+    io.exc = exc;
+    io.nb = exc->nb;
+    io.out = currents;
+    return march_steps(c, io, n_steps, tol, stats);
   });
 }
 
@@ -438,7 +505,11 @@ int aim_march_continue(aim_ctx* c, const aim_excitation* exc, int32_t n_steps, d
     if (c->march_nb < 1 || !exc || exc->nb != c->march_nb)
       throw AimError{AIM_ERR_ARG, "aim_march_continue: no march with this batch was started on the context"};
     upload_waves(c, exc);
-    return march_steps(c, exc, n_steps, tol, currents, stats);
+    StepIO io;
+    io.exc = exc;
+    io.nb = exc->nb;
+    io.out = currents;
+    return march_steps(c, io, n_steps, tol, stats);
   });
 }
 
@@ -484,20 +555,15 @@ int aim_march_source(aim_ctx* c, int32_t transpose, int32_t nb, int32_t n_steps,
   return guard(c, [&] {
     if (!src || !currents || n_steps < 1 || nb < 1 || nb > c->batch_max || !(tol > 0))
       throw AimError{AIM_ERR_ARG, "aim_march_source: bad arguments"};
-    double2* fwd = c->d_near;
-    if (transpose) {
-      adj_ensure_near_transpose(c);
-      if (c->nnz) c->d_near = c->d_nearT;
-    }
-    struct Restore {
-      aim_ctx* c;
-      double2* p;
-      ~Restore() { c->d_near = p; }
-    } restore{c, fwd};
+    std::unique_ptr<TransposeNear> tn(transpose ? new TransposeNear(c) : nullptr);
     AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)nb * c->ns * sizeof(double2), c->stream));
     c->l_done = 0;
     c->march_nb = 0;  // a source march cannot be continued with aim_march_continue
-    return march_steps(c, nullptr, n_steps, tol, currents, stats, nb, src);
+    StepIO io;
+    io.nb = nb;
+    io.src = src;
+    io.out = currents;
+    return march_steps(c, io, n_steps, tol, stats);
   });
 }
 
@@ -542,7 +608,7 @@ int aim_excitation_samples(aim_ctx* c, const double* khat, const double* phat, i
     const double2* da = dev_in(c, a, n_samp, scratch(c, n_samp, 0));
     const bool dev = is_device_ptr(V);
     double2* out = dev ? reinterpret_cast<double2*>(V) : scratch(c, n, 1);
-    adj_excitation_samples(c, khat, phat, i0, n_samp, da, n_steps, out);
+    adj_excitation_samples(c, khat, phat, i0, n_samp, da, 1, n_steps, out);
     finish_out(c, V, out, n, dev);
     return AIM_OK;
   });
@@ -558,7 +624,7 @@ int aim_excitation_samples_adjoint(aim_ctx* c, const double* khat, const double*
     const double2* dl = dev_in(c, lam, n, scratch(c, n, 1));
     const bool dev = is_device_ptr(grad);
     double2* out = dev ? reinterpret_cast<double2*>(grad) : scratch(c, n_samp, 0);
-    adj_excitation_samples_adjoint(c, khat, phat, i0, n_samp, n_steps, dl, out);
+    adj_excitation_samples_adjoint(c, khat, phat, i0, n_samp, 1, n_steps, dl, false, false, out);
     finish_out(c, grad, out, n_samp, dev);
     return AIM_OK;
   });
@@ -575,7 +641,7 @@ int aim_farfield(aim_ctx* c, int32_t nd, const double* rhat, const double* e1, c
     const double2* dI = dev_in(c, I, n, scratch(c, n, 1));
     const bool dev = is_device_ptr(F);
     double2* out = dev ? reinterpret_cast<double2*>(F) : scratch(c, nf, 2);
-    adj_farfield(c, nd, dd, n_steps, dI, n0, n_out, out);
+    adj_farfield(c, nd, dd, 1, n_steps, dI, n0, n_out, false, out);
     finish_out(c, F, out, nf, dev);
     return AIM_OK;
   });
@@ -592,9 +658,91 @@ int aim_farfield_adjoint(aim_ctx* c, int32_t nd, const double* rhat, const doubl
     const double2* dF = dev_in(c, F, nf, scratch(c, nf, 2));
     const bool dev = is_device_ptr(G);
     double2* out = dev ? reinterpret_cast<double2*>(G) : scratch(c, n, 3);
-    adj_farfield_adjoint(c, nd, dd, n_steps, n0, n_out, dF, out);
+    adj_farfield_adjoint(c, nd, dd, 1, n_steps, n0, n_out, dF, false, out);
     finish_out(c, G, out, n, dev);
     return AIM_OK;
+  });
+}
+
+int aim_march_adjoint(aim_ctx* c, int32_t nb, int32_t n_steps, const aim_c128* G, double tol, aim_c128* lam,
+                      aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!G || !lam || n_steps < 1 || nb < 1 || nb > c->batch_max || !(tol > 0))
+      throw AimError{AIM_ERR_ARG, "aim_march_adjoint: bad arguments"};
+    TransposeNear tn(c);
+    AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)nb * c->ns * sizeof(double2), c->stream));
+    c->l_done = 0;
+    c->march_nb = 0;
+    StepIO io;
+    io.nb = nb;
+    io.src = G;
+    io.out = lam;
+    io.rev = true;
+    return march_steps(c, io, n_steps, tol, stats);
+  });
+}
+
+int aim_march_farfield(aim_ctx* c, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                       const aim_c128* a, int32_t n_steps, double tol, int32_t nd, const double* rhat,
+                       const double* e1, const double* e2, int32_t n0, int32_t n_out, aim_c128* F,
+                       aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!khat || !phat || !a || n_samp < 1 || n_steps < 1 || !(tol > 0) || nd < 1 || !rhat || !e1 || !e2 ||
+        n_out < 1 || !F)
+      throw AimError{AIM_ERR_ARG, "aim_march_farfield: bad arguments"};
+    const size_t nf = (size_t)n_out * nd * 2;
+    const double* dd = upload_dirs(c, nd, rhat, e1, e2);
+    const double2* da = dev_in(c, a, n_samp, scratch(c, n_samp, 0));
+    const bool dev = is_device_ptr(F);
+    double2* Fd = dev ? reinterpret_cast<double2*>(F) : scratch(c, nf, 2);
+    AIM_CUDA(cudaMemsetAsync(Fd, 0, nf * sizeof(double2), c->stream));
+    AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)c->ns * sizeof(double2), c->stream));
+    c->l_done = 0;
+    c->march_nb = 0;
+    StepIO io;
+    io.nb = 1;
+    io.make_src = [&](int j, double2* b) { adj_excitation_samples(c, khat, phat, i0, n_samp, da, j, 1, b); };
+    io.commit = [&](int j, const double2* x) { adj_farfield(c, nd, dd, j, 1, x, n0, n_out, true, Fd); };
+    const int rc = march_steps(c, io, n_steps, tol, stats);
+    finish_out(c, F, Fd, nf, dev);
+    return rc;
+  });
+}
+
+int aim_march_adjoint_farfield(aim_ctx* c, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
+                               int32_t n_steps, double tol, int32_t nd, const double* rhat, const double* e1,
+                               const double* e2, int32_t n0, int32_t n_out, const aim_c128* F, aim_c128* grad,
+                               aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!khat || !phat || !grad || n_samp < 1 || n_steps < 1 || !(tol > 0) || nd < 1 || !rhat || !e1 || !e2 ||
+        n_out < 1 || !F)
+      throw AimError{AIM_ERR_ARG, "aim_march_adjoint_farfield: bad arguments"};
+    const size_t nf = (size_t)n_out * nd * 2;
+    const double* dd = upload_dirs(c, nd, rhat, e1, e2);
+    const double2* dF = dev_in(c, F, nf, scratch(c, nf, 2));
+    const bool dev = is_device_ptr(grad);
+    double2* gd = dev ? reinterpret_cast<double2*>(grad) : scratch(c, n_samp, 0);
+    AIM_CUDA(cudaMemsetAsync(gd, 0, (size_t)n_samp * sizeof(double2), c->stream));
+    TransposeNear tn(c);
+    AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)c->ns * sizeof(double2), c->stream));
+    c->l_done = 0;
+    c->march_nb = 0;
+    StepIO io;
+    io.nb = 1;
+    // step j of the transposed march is time step l = n_steps + 1 - j: source conj(G_l),
+    // and its solution u gives lam_l = conj(u)
+    io.make_src = [&](int j, double2* b) {
+      adj_farfield_adjoint(c, nd, dd, n_steps + 1 - j, 1, n0, n_out, dF, true, b);
+    };
+    io.commit = [&](int j, const double2* u) {
+      adj_excitation_samples_adjoint(c, khat, phat, i0, n_samp, n_steps + 1 - j, 1, u, true, true, gd);
+    };
+    const int rc = march_steps(c, io, n_steps, tol, stats);
+    finish_out(c, grad, gd, n_samp, dev);
+    return rc;
   });
 }
 
@@ -652,14 +800,58 @@ int aim_get_kernel_spectrum(const aim_ctx* c, int32_t m, int32_t kind, aim_c128*
 
 }  // extern "C"
 
-static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, double tol, aim_c128* currents,
-                       aim_stats* stats, int nb_src, const aim_c128* src) {
+// FP64 refinement of the immediate solve just enqueued (complex64 path): the GMRES with
+// the complex64 operator has run to tol on the stream (synchronised by the caller).
+// Then, with every grid stage of the residual in FP64,
+//   r = b - Z_0 x;  while |r| > tol |b| (any RHS) and corrections remain:
+//     solve Z_0 d = r with the complex64 operator from zero to kCorrTol;  x += d;  r = b - Z_0 x.
+// The complex64 operator's error (relative ~1e-7) limits each correction, not the
+// result: the error of the corrected x is that of the FP64 operator plus tol.
+// Returns AIM_OK or AIM_ERR_NOCONV; its = GMRES iterations of all solves of the step,
+// res = final FP64 relative residuals, n_corr = correction solves.
+static int refine_solution(aim_ctx* c, int nb, double tol, std::vector<int>& its, std::vector<double>& res,
+                           int& n_corr) {
+  constexpr double kCorrTol = 1e-2;
   cudaStream_t st = c->stream;
-  const int nb = src ? nb_src : exc->nb, ns = c->ns, ng = c->n_delays, B = c->batch_max;
+  const size_t n = (size_t)nb * c->ns;
+  std::vector<int> it(nb);
+  std::vector<double> rr(nb);
+  int rc = gmres_collect(c, it.data(), rr.data());
+  for (int b = 0; b < nb; ++b) its[b] += it[b];
+  res.assign(nb, 0.0);
+  n_corr = 0;
+  for (int k = 0;; ++k) {
+    op_apply_f64(c, 0, nb, c->d_x, c->d_b, -1.0, c->d_r);  // r = b - Z_0 x, FP64 grid stages
+    gmres_norms(c, nb, c->d_r, c->d_rn);
+    gmres_norms(c, nb, c->d_b, c->d_rn + nb);
+    AIM_CUDA(cudaMemcpyAsync(c->h_rn, c->d_rn, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AIM_CUDA(cudaStreamSynchronize(st));
+    bool ok = true;
+    for (int b = 0; b < nb; ++b) {
+      res[b] = c->h_rn[nb + b] > 0 ? c->h_rn[b] / c->h_rn[nb + b] : 0.0;
+      ok = ok && res[b] <= tol;
+    }
+    if (ok) return AIM_OK;
+    if (rc != AIM_OK || k == c->refine) return AIM_ERR_NOCONV;
+    AIM_CUDA(cudaMemsetAsync(c->d_w, 0, n * sizeof(double2), st));
+    gmres_solve_async(c, nb, c->d_r, c->d_w, kCorrTol, true);
+    gmres_axpy(c, nb, c->d_w, c->d_x);
+    AIM_CUDA(cudaStreamSynchronize(st));
+    rc = gmres_collect(c, it.data(), rr.data());
+    for (int b = 0; b < nb; ++b) its[b] += it[b];
+    ++n_corr;
+  }
+}
+
+static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, aim_stats* stats) {
+  cudaStream_t st = c->stream;
+  const int nb = io.nb, ns = c->ns, ng = c->n_delays, B = c->batch_max;
+  const aim_c128* src = io.src;
+  aim_c128* currents = io.out;
   const bool src_dev = src && is_device_ptr(src);
   const size_t n = (size_t)nb * ns;
   const size_t slab = op_slab_bytes(c, B);
-  const bool dev_out = is_device_ptr(currents);
+  const bool dev_out = currents && is_device_ptr(currents);
   ensure_ring(c);
   cudaEvent_t ev[3];
   for (auto& e : ev) AIM_CUDA(cudaEventCreate(&e));
@@ -674,16 +866,23 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
     stats->max_rel_res = 0;
     stats->rhs_ms = 0;
     stats->solve_ms = 0;
+    stats->refine_corrections = 0;
   }
   int rc = AIM_OK;
   const int l0 = c->l_done;
   for (int l = l0 + 1; l <= l0 + n_steps; ++l) {
     AIM_CUDA(cudaEventRecord(ev[0], st));
-    if (src)  // explicit right-hand side samples S_l
-      AIM_CUDA(cudaMemcpyAsync(c->d_b, src + (size_t)(l - l0 - 1) * n, n * sizeof(double2),
+    const int j = l - l0;                                       // step within this call
+    const size_t jo = (size_t)(io.rev ? n_steps - j : j - 1);  // its slot in src / currents
+    if (io.make_src) {
+      io.make_src(j, c->d_b);
+    } else if (src) {  // explicit right-hand side samples S_l
+      AIM_CUDA(cudaMemcpyAsync(c->d_b, src + jo * n, n * sizeof(double2),
                                src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    else
-      op_excitation(c, nb, c->d_exc, exc->sigma, exc->t_d, l, c->d_b);
+      if (io.rev) conj_copy(c, n, c->d_b, c->d_b);
+    } else {
+      op_excitation(c, nb, c->d_exc, io.exc->sigma, io.exc->t_d, l, c->d_b);
+    }
     SlabList sl{};
     NearList nl{};
     for (int m = 1; m <= ng; ++m) {
@@ -702,14 +901,29 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
     AIM_CUDA(cudaEventRecord(ev[1], st));
     if (c->zero_start) AIM_CUDA(cudaMemsetAsync(c->d_x, 0, n * sizeof(double2), st));
     gmres_solve_async(c, nb, c->d_b, c->d_x, tol);
+    int r_ref = AIM_OK, n_corr = 0;
+    std::vector<int> its_ref(nb, 0);
+    std::vector<double> res_ref;
+    if (c->refine > 0) {
+      AIM_CUDA(cudaStreamSynchronize(st));
+      r_ref = refine_solution(c, nb, tol, its_ref, res_ref, n_corr);
+    }
     AIM_CUDA(cudaEventRecord(ev[2], st));
     // commit I_l: RWG-space history and its forward slab
     const int s = l % ng;
     AIM_CUDA(cudaMemcpyAsync(c->d_iring + (size_t)s * B * ns, c->d_x, n * sizeof(double2),
                              cudaMemcpyDeviceToDevice, st));
     op_forward_slab(c, nb, c->d_x, (char*)c->d_ring + (size_t)s * slab);
-    AIM_CUDA(cudaMemcpyAsync(currents + (size_t)(l - l0 - 1) * n, c->d_x, n * sizeof(double2),
-                             dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (currents) {
+      const double2* xo = c->d_x;
+      if (io.rev) {
+        conj_copy(c, n, c->d_x, c->d_y);
+        xo = c->d_y;
+      }
+      AIM_CUDA(cudaMemcpyAsync(currents + jo * n, xo, n * sizeof(double2),
+                               dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    if (io.commit) io.commit(j, c->d_x);
     gmres_norms(c, nb, c->d_x, d_nrm);
     AIM_CUDA(cudaMemcpyAsync(h_nrm.data(), d_nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     int h_err = 0;
@@ -719,7 +933,14 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
       AIM_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
       throw AimError{AIM_ERR_TIMEOUT, "a bounded wait of the delayed-sum kernel gave up at step " + std::to_string(l)};
     }
-    const int r = gmres_collect(c, its.data(), res.data());
+    int r;
+    if (c->refine > 0) {  // statistics gathered by the refinement (solves and FP64 residuals)
+      r = r_ref;
+      its = its_ref;
+      res = res_ref;
+    } else {
+      r = gmres_collect(c, its.data(), res.data());
+    }
     double mx = 0;
     for (int b = 0; b < nb; ++b) mx = std::max(mx, h_nrm[b]);
     norms.push_back(mx);
@@ -736,12 +957,15 @@ static int march_steps(aim_ctx* c, const aim_excitation* exc, int n_steps, doubl
         if (stats->iters) stats->iters[(size_t)(l - l0 - 1) * nb + b] = its[b];
       }
       stats->last_step = l;
+      stats->refine_corrections += n_corr;
     }
     c->l_done = l;
     prof_flush(c);
     if (r != AIM_OK) {
       if (stats) stats->last_step = l - 1;
-      c->err = "GMRES reached its iteration cap at step " + std::to_string(l);
+      c->err = (c->refine > 0 ? "GMRES reached its iteration cap or the FP64 refinement did not reach tol at step "
+                               : "GMRES reached its iteration cap at step ") +
+               std::to_string(l);
       rc = r;
       break;
     }

@@ -657,14 +657,14 @@ float2* krylov_c64(aim_ctx* c) { return c->d_sai && c->precision == AIM_C64 ? c-
 
 // |r|^2 of slot 0 and the cycle start
 void cycle_start(aim_ctx* c, int nb, double tol, bool use_cond, cudaGraphConditionalHandle outer,
-                 cudaGraphConditionalHandle inner, cudaGraphConditionalHandle resid) {
+                 cudaGraphConditionalHandle inner, cudaGraphConditionalHandle resid, bool zs) {
   GmresState& s = c->gs;
   cudaStream_t st = c->stream;
   const int ns = c->ns;
   AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
               k_normpart<<<dim3(n_norm_blocks(ns), nb), kThreads, 0, st>>>(c->d_V, ns, s.pr, krylov_c64(c)));
   CycleArgs a{nb, c->restart, c->max_iter, tol, s.pbn, s.pr, n_norm_blocks(ns), use_cond ? 1 : 0, outer, inner,
-              (use_cond && c->zero_start) ? 1 : 0, resid};
+              (use_cond && zs) ? 1 : 0, resid};
   AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_cycle_start<<<1, kThreads, 0, st>>>(a, s));
 }
 
@@ -784,8 +784,9 @@ cudaGraphNode_t add_cond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndep
   return node;
 }
 
-void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double tol) {
+void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double tol, bool zs) {
   GmresState& s = c->gs;
+  GmresState::SolveGraph& sg = s.graphs[zs ? 1 : 0];
   cudaGraph_t g;
   AIM_CUDA(cudaGraphCreate(&g, 0));
   const ProfState saved = c->prof;  // capture-time launches are not executions
@@ -799,23 +800,23 @@ void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double 
     cudaGraphNode_t pre = leaf_of(g);
     cudaGraphConditionalHandle outer, inner, resid = 0;
     AIM_CUDA(cudaGraphConditionalHandleCreate(&outer, g, 1, cudaGraphCondAssignDefault));
-    if (c->zero_start)  // 0 for the first cycle of every launch; the cycle start sets it to 1
+    if (zs)  // 0 for the first cycle of every launch; the cycle start sets it to 1
       AIM_CUDA(cudaGraphConditionalHandleCreate(&resid, g, 0, cudaGraphCondAssignDefault));
     cudaGraph_t obody;
     add_cond(g, &pre, 1, outer, cudaGraphCondTypeWhile, &obody);
     AIM_CUDA(cudaGraphConditionalHandleCreate(&inner, obody, 0, cudaGraphCondAssignDefault));
-    if (c->zero_start) {
+    if (zs) {
       // slot 0 = b; IF(resid) { slot 0 = b - Z_0 x }; |r|^2 and the cycle start
       capture_into(c, obody, nullptr, 0, [&] { copy_b_to_slot0(c, nb, b); });
       cudaGraphNode_t cp = leaf_of(obody);
       cudaGraph_t rbody;
       cudaGraphNode_t rn = add_cond(obody, &cp, 1, resid, cudaGraphCondTypeIf, &rbody);
       capture_into(c, rbody, nullptr, 0, [&] { cycle_residual(c, nb, b, x); });
-      capture_into(c, obody, &rn, 1, [&] { cycle_start(c, nb, tol, true, outer, inner, resid); });
+      capture_into(c, obody, &rn, 1, [&] { cycle_start(c, nb, tol, true, outer, inner, resid, zs); });
     } else {
       capture_into(c, obody, nullptr, 0, [&] {
         cycle_residual(c, nb, b, x);
-        cycle_start(c, nb, tol, true, outer, inner, resid);
+        cycle_start(c, nb, tol, true, outer, inner, resid, zs);
       });
     }
     cudaGraphNode_t pro = leaf_of(obody);
@@ -825,15 +826,15 @@ void build_solve_graph(aim_ctx* c, int nb, const double2* b, double2* x, double 
     capture_into(c, obody, &wn, 1, [&] { cycle_epilogue(c, nb, x); });
     cudaGraphExec_t ex;
     AIM_CUDA(cudaGraphInstantiate(&ex, g, 0));
-    if (s.graph_exec) cudaGraphExecDestroy(s.graph_exec);
-    if (s.graph) cudaGraphDestroy(s.graph);
-    s.graph = g;
-    s.graph_exec = ex;
-    s.g_nb = nb;
-    s.g_tol = tol;
-    s.g_b = b;
-    s.g_x = x;
-    s.g_near = c->d_near;
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (sg.graph) cudaGraphDestroy(sg.graph);
+    sg.graph = g;
+    sg.exec = ex;
+    sg.nb = nb;
+    sg.tol = tol;
+    sg.b = b;
+    sg.x = x;
+    sg.near = c->d_near;
   } catch (...) {
     c->prof = saved;
     cudaGraphDestroy(g);
@@ -897,10 +898,12 @@ void gmres_alloc(aim_ctx* c) {
 
 void gmres_free_host(aim_ctx* c) {
   GmresState& s = c->gs;
-  if (s.graph_exec) cudaGraphExecDestroy(s.graph_exec);
-  if (s.graph) cudaGraphDestroy(s.graph);
-  s.graph_exec = nullptr;
-  s.graph = nullptr;
+  for (auto& sg : s.graphs) {
+    if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (sg.graph) cudaGraphDestroy(sg.graph);
+    sg.exec = nullptr;
+    sg.graph = nullptr;
+  }
   if (s.h_flag) cudaFreeHost(s.h_flag);
   if (s.h_its) cudaFreeHost(s.h_its);
   if (s.h_res) cudaFreeHost(s.h_res);
@@ -920,6 +923,12 @@ void gmres_free_host(aim_ctx* c) {
 // by gmres_collect once the caller has synchronised the stream (the host-driven mode
 // synchronises inside).
 void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double tol) {
+  gmres_solve_async(c, nb, b, x, tol, c->zero_start);
+}
+
+// zs: start from zero (x must hold zeros; the first residual is b itself, no operator
+// product) instead of the guess in x
+void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double tol, bool zs) {
   GmresState& s = c->gs;
   cudaStream_t st = c->stream;
   AIM_CUDA(cudaMemsetAsync(s.its, 0, nb * sizeof(int), st));
@@ -928,9 +937,10 @@ void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double 
   // per-kernel event timing needs host-side launches: profiling runs the host-driven loop
   if (c->use_graphs && !s.graph_failed && !c->prof.on) {
     try {
-      if (!s.graph_exec || s.g_nb != nb || s.g_tol != tol || s.g_b != b || s.g_x != x || s.g_near != c->d_near)
-        build_solve_graph(c, nb, b, x, tol);
-      AIM_CUDA(cudaGraphLaunch(s.graph_exec, st));
+      const GmresState::SolveGraph& sg = s.graphs[zs ? 1 : 0];
+      if (!sg.exec || sg.nb != nb || sg.tol != tol || sg.b != b || sg.x != x || sg.near != c->d_near)
+        build_solve_graph(c, nb, b, x, tol, zs);
+      AIM_CUDA(cudaGraphLaunch(sg.exec, st));
       graphed = true;
     } catch (const AimError& e) {
       s.graph_failed = true;
@@ -943,9 +953,9 @@ void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double 
     AIM_KLAUNCH(c, AIM_K_GMRES_UPDATE,
                 k_normpart<<<dim3(n_norm_blocks(c->ns), nb), kThreads, 0, st>>>(b, c->ns, s.pbn, nullptr));
     for (int cycle = 0;; ++cycle) {
-      if (c->zero_start && cycle == 0) copy_b_to_slot0(c, nb, b);
+      if (zs && cycle == 0) copy_b_to_slot0(c, nb, b);
       else cycle_residual(c, nb, b, x);
-      cycle_start(c, nb, tol, false, 0, 0, 0);
+      cycle_start(c, nb, tol, false, 0, 0, 0, zs);
       AIM_CUDA(cudaMemcpyAsync(s.h_flag, s.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
       AIM_CUDA(cudaStreamSynchronize(st));
       if (!s.h_flag[0]) break;
@@ -967,6 +977,7 @@ void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double 
   AIM_CUDA(cudaMemcpyAsync(s.h_done, s.done, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
   AIM_CUDA(cudaMemcpyAsync(s.h_cnt, s.cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   s.last_graphed = graphed;
+  s.last_zs = zs;
   s.last_nb = nb;
 }
 
@@ -981,7 +992,7 @@ int gmres_collect(aim_ctx* c, int* iters, double* relres) {
     const long long op = op_kernel_count(c);
     const long long krylov = s.interp_P > 0 ? 2 : 3;
     c->prof.launches += 1 + (op + 4 + (c->d_sai ? 1 : 0)) * s.h_cnt[0] + (op + krylov) * s.h_cnt[1] -
-                        (c->zero_start && s.h_cnt[0] > 0 ? op : 0);
+                        (s.last_zs && s.h_cnt[0] > 0 ? op : 0);
   }
   int rc = AIM_OK;
   for (int i = 0; i < nb; ++i) {
@@ -999,6 +1010,21 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
 }
 
 int gmres_blocks(int ns) { return n_norm_blocks(ns); }
+
+namespace {
+__global__ void __launch_bounds__(kThreads) k_axpy(long long n, const double2* __restrict__ a, double2* __restrict__ x) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 u = a[i], v = x[i];
+    x[i] = make_double2(v.x + u.x, v.y + u.y);
+  }
+}
+}  // namespace
+
+void gmres_axpy(aim_ctx* c, int nb, const double2* a, double2* x) {
+  const long long n = (long long)nb * c->ns;
+  AIM_KLAUNCH(c, AIM_K_GMRES_SMALL, k_axpy<<<(int)((n + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(n, a, x));
+}
 
 void gmres_norms(aim_ctx* c, int nb, const double2* v, double* d_out) {
   const int P = n_norm_blocks(c->ns);

@@ -9,5 +9,9 @@ int gmres_solve(aim_ctx* c, int nb, const double2* b, double2* x, double tol, in
 // the same split at the synchronisation: enqueue, then (after the stream is synchronised)
 // collect the iteration counts, residuals and status
 void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double tol);
+// the same with the start chosen per solve: zs = start from zero (x holds zeros)
+void gmres_solve_async(aim_ctx* c, int nb, const double2* b, double2* x, double tol, bool zs);
+// y = x + a (elementwise, nb right-hand sides)
+void gmres_axpy(aim_ctx* c, int nb, const double2* a, double2* x);
 int gmres_collect(aim_ctx* c, int* iters, double* relres);
 void gmres_norms(aim_ctx* c, int nb, const double2* v, double* d_out);

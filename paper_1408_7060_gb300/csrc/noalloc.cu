@@ -2,18 +2,22 @@
 // from a fixed device array instead of the context's allocations.
 //
 // Who needs it: callers that may not allocate device memory once they are running --
-// for example a solver that is itself being captured into a CUDA graph, a real-time or
-// certified code path that fixes its memory budget at start-up, or a host application
-// whose device memory belongs to another allocator.  The entry point allocates nothing:
-// no cudaMalloc, no cudaFree, no allocating library call.
+// a real-time or certified code path that fixes its memory budget at start-up, a host
+// application whose device memory belongs to another allocator (a framework's caching
+// pool that must not be bypassed), or a process running under a hard device-memory
+// quota.  The entry point allocates nothing: no cudaMalloc, no cudaFree, no allocating
+// library call.
 //
 // The work space is one file-scope __device__ array of kNoAllocScratchBytes (16 MiB),
 // which every GPU that loads this library holds until the process exits.  Host code
-// cannot pass the array's name to a kernel (it is a host-side stand-in, not a device
-// address), so the device address is looked up with cudaGetSymbolAddress, once per
-// device, by the first call made on that device with the device current; that first
-// call should therefore come before any stream capture.
+// cannot pass the array's name to a kernel (in host code it is a host-side stand-in, not
+// a device address), so the device address is looked up with cudaGetSymbolAddress once
+// per device, by the first call made on that device, with the device current (guarded by
+// a per-device once-flag, so concurrent first calls from several host threads are safe).
+// The cached address does not survive cudaDeviceReset: a process that resets a device
+// must not call this entry point on that device afterwards.
 #include <cstring>
+#include <mutex>
 
 #include "aim_internal.h"
 #include "operator.h"
@@ -26,6 +30,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::once_flag g_scratch_once[kMaxDevices];
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -76,11 +81,15 @@ extern "C" int aim_matvec_noalloc(aim_ctx* c, int32_t m, int32_t nb, const aim_c
     int dev = 0;
     AIM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) throw AimError{AIM_ERR_ARG, "aim_matvec_noalloc: device index"};
-    if (!g_scratch_addr[dev]) {
+    // set-up, once per device with that device current (a failure leaves the flag unset,
+    // so a later call retries)
+    std::call_once(g_scratch_once[dev], [] {
       void* ptr = nullptr;
       AIM_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-      g_scratch_addr[dev] = ptr;
-    }
+      int d = 0;
+      AIM_CUDA(cudaGetDevice(&d));
+      g_scratch_addr[d] = ptr;
+    });
     const size_t n = (size_t)nb * c->ns;
     const double2* xs = reinterpret_cast<const double2*>(x);
     if (!is_device_ptr(x)) {

@@ -1,4 +1,6 @@
 // Precision dispatch of the operator and the excitation kernel (Eq. 1).
+#include <algorithm>
+
 #include "aim_internal.h"
 #include "operator.h"
 
@@ -16,6 +18,37 @@ void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, 
     body_apply<float2>(c, m, nb, v, dinv, base, sign, active, y, vin, yout);
   else
     body_apply<double2>(c, m, nb, v, dinv, base, sign, active, y, vin, yout);
+}
+
+void op_apply_f64(aim_ctx* c, int m, int nb, const double2* v, const double2* base, double sign, double2* y) {
+  if (c->precision == AIM_C128) {
+    op_apply(c, m, nb, v, nullptr, base, sign, nullptr, y);
+    return;
+  }
+  if (!c->d_A64 || c->ref_nb < 1) throw AimError{AIM_ERR_ARG, "FP64 operator: refinement buffers not set up"};
+  // the FP64 grid buffers stand in for the context's complex64 ones for the duration
+  struct Swap {
+    aim_ctx* c;
+    void *A, *Bf, *P, *xs;
+    explicit Swap(aim_ctx* c_) : c(c_), A(c_->d_A), Bf(c_->d_Bf), P(c_->d_P), xs(c_->d_xs) {
+      c->d_A = c->d_A64;
+      c->d_Bf = c->d_Bf64;
+      c->d_P = c->d_P64;
+      c->d_xs = c->d_xs64;
+    }
+    ~Swap() {
+      c->d_A = A;
+      c->d_Bf = Bf;
+      c->d_P = P;
+      c->d_xs = xs;
+    }
+  } sw(c);
+  const size_t ns = c->ns;
+  for (int b0 = 0; b0 < nb; b0 += c->ref_nb) {
+    const int n = std::min(c->ref_nb, nb - b0);
+    body_apply<double2>(c, m, n, v + b0 * ns, nullptr, base ? base + b0 * ns : nullptr, sign, nullptr, y + b0 * ns,
+                        VecSel(), VecSel());
+  }
 }
 
 void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst) {

@@ -39,6 +39,10 @@ struct SlabList {
 // y = base + sign * Z~AIM_m (dinv .* v)     (dinv, base optional; m = delay)
 void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
               const int* active, double2* y, VecSel vin = VecSel(), VecSel yout = VecSel());
+// y = base + sign * Z~AIM_m v with every grid stage in FP64, whatever the context's
+// precision (the residual of the FP64 refinement on the complex64 path); needs the
+// refinement buffers of a complex64 context
+void op_apply_f64(aim_ctx* c, int m, int nb, const double2* v, const double2* base, double sign, double2* y);
 // slab of one current vector (anterpolation + forward x and y passes) written to dst
 void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst);
 // y = base + sign * [ sum_s Z~FFT_{m_s} (slab_s) + near terms ]

@@ -437,8 +437,11 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec(SlabList sl, const C
 // The same with the spectra streamed by TMA (complex64): the L x W tile of each spectrum
 // is a 4-D box of the ring tensor [slot][B*4*L][L][L], loaded into one of two 128-byte
 // aligned shared buffers by cp.async.bulk.tensor and signalled on an mbarrier, so
-// spectrum s + 2 streams in while spectrum s + 1 is accumulated.  Waits are bounded; a
-// wait that gives up sets *err (the host reports it) and the sum goes on.
+// spectrum s + 2 streams in while spectrum s + 1 is accumulated.  Waits are bounded.  A
+// wait that gives up sets *err (the host reports AIM_ERR_TIMEOUT) and a block-wide flag;
+// the block then issues no further load, drains the loads it has in flight with one more
+// bounded wait each and returns without writing its output (which is undefined whenever
+// *err is set).
 template <int L, int W>
 __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_constant__ CUtensorMap ring,
                                                                 SlabRing sr, const float2* __restrict__ kspec_all,
@@ -447,6 +450,8 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
   using C = float2;
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int gave_up[2];  // by iteration parity: a write in iteration s + 1 cannot reach a
+                              // thread still reading the flag of iteration s
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(aim_smem) + 127) & ~static_cast<uintptr_t>(127));
   C* in0 = reinterpret_cast<C*>(base);  // [2][L][W]
@@ -455,6 +460,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
   const unsigned bytes = (unsigned)(L * W * sizeof(C));
   if (threadIdx.x == 0) {
+    gave_up[0] = gave_up[1] = 0;
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
@@ -489,18 +495,33 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
         for (int k2 = 0; k2 < R2; ++k2) g[j][k2] = __ldg(G + (size_t)fold(u / W + R1 * k2, N) * n1 * n1);
       }
     }
-    if (!mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1))) atomicExch(err, 1);
+    const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1));
+    if (!ok) {
+      atomicExch(err, 1);
+      gave_up[s & 1] = 1;
+    }
     const C* tile = in0 + buf * L * W;  // [kz][l]
+    if (ok) {
 #pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const int u = threadIdx.x + j * kZThreads;
-      if (u < W * R1) {
-        const int l = u % W, k1 = u / W;
+      for (int j = 0; j < U; ++j) {
+        const int u = threadIdx.x + j * kZThreads;
+        if (u < W * R1) {
+          const int l = u % W, k1 = u / W;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += tile[(k1 + R1 * k2) * W + l] * g[j][k2];
+          for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += tile[(k1 + R1 * k2) * W + l] * g[j][k2];
+        }
       }
     }
-    __syncthreads();  // the tile is consumed: it may be refilled
+    __syncthreads();  // the tile is consumed: it may be refilled (gave_up[s & 1] is block-uniform)
+    if (gave_up[s & 1]) {
+      // loads in flight: spectrum s (the wait that gave up, for some thread) and s + 1
+      if (threadIdx.x == 0) {
+        mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1));
+        if (s + 1 < sr.n) mbar_wait_bounded(&bar[buf ^ 1], (unsigned)(((s + 1) >> 1) & 1));
+      }
+      __syncthreads();
+      return;
+    }
     if (threadIdx.x == 0 && s + 2 < sr.n) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bar[buf], bytes);

@@ -235,6 +235,7 @@ class Workload:
     precond: str = "diag"  # GMRES right preconditioner: "diag" (Sec. 5.1) or "sai"
     precond_radius: float = 0.0  # SAI pattern radius (m); 0: the near radius
     zero_start: bool = False  # GMRES from zero instead of the previous step's currents
+    refine: int = 0        # complex64 path: FP64 refinement corrections per step (0: off)
 
     @property
     def f_bw(self) -> float:

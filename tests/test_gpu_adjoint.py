@@ -132,3 +132,52 @@ def test_gradient_vs_oracle_and_fd(case, ctx):
             fd = (jp - jm) / (2 * eps)
             an = float(np.real(np.vdot(g, d.cpu().numpy())))
             assert abs(fd - an) <= 1e-4 * abs(an) + 1e-9 * J.item(), (fd, an)
+
+
+def test_march_adjoint_vs_dense(case, ctx):
+    """aim_march_adjoint solves M^H lam = G: backward substitution with Z_m^H."""
+    w, rwg, p, A, ZA = case
+    from paper_1408_7060_gb300 import abi
+
+    rng = np.random.default_rng(5)
+    nt = 20
+    G = crandn(rng, nt, 1, rwg.ns)
+    ZH = np.conj(np.transpose(ZA, (0, 2, 1)))
+    ref = np.zeros_like(G)
+    for l in range(nt, 0, -1):
+        r = G[l - 1, 0].copy()
+        for m in range(1, len(ZA)):
+            if l + m <= nt:
+                r -= ZH[m] @ ref[l + m - 1, 0]
+        ref[l - 1, 0] = np.linalg.solve(ZH[0], r)
+    lam, st, rc = abi.aim_march_adjoint(ctx.handle, G, 1e-12)
+    assert st["last_step"] == nt
+    assert rel(lam, ref) < 1e-9
+
+
+def test_fused_farfield_passes_match_composed_calls(case, ctx):
+    """aim_march_farfield (far field added step by step, no current history) equals the
+    far field of the stored march; aim_march_adjoint_farfield (sources and gradient formed
+    step by step in reversed time) equals B^H of the adjoint march of A^H F."""
+    import torch
+
+    w, rwg, p, A, ZA = case
+    from paper_1408_7060_gb300 import abi
+
+    r, e1, e2 = dirs()
+    rng = np.random.default_rng(6)
+    a = torch.tensor(crandn(rng, NSAMP), device="cuda")
+    F, st, _ = abi.aim_march_farfield(ctx.handle, *WAVE, I0, a, NT, 1e-12, r, e1, e2, N0, NOUT)
+    V = abi.aim_excitation_samples(ctx.handle, *WAVE, I0, a, NT)
+    I, _, _ = abi.aim_march_source(ctx.handle, V.reshape(NT, 1, -1), 1e-12)
+    F2 = abi.aim_farfield(ctx.handle, r, e1, e2, I.reshape(NT, -1), N0, NOUT)
+    assert rel(F.cpu().numpy(), F2.cpu().numpy()) < 1e-12
+    Fy = torch.tensor(crandn(rng, NOUT, len(r), 2), device="cuda")
+    g, _, _ = abi.aim_march_adjoint_farfield(ctx.handle, *WAVE, I0, NSAMP, NT, 1e-12, r, e1, e2, N0, Fy)
+    G = abi.aim_farfield_adjoint(ctx.handle, r, e1, e2, NT, N0, Fy)
+    lam, _, _ = abi.aim_march_adjoint(ctx.handle, G.reshape(NT, 1, -1), 1e-12)
+    g2 = abi.aim_excitation_samples_adjoint(ctx.handle, *WAVE, I0, NSAMP, lam.reshape(NT, -1))
+    assert rel(g.cpu().numpy(), g2.cpu().numpy()) < 1e-10
+    # the adjoint identity of the whole map a -> F
+    lhs = np.vdot(Fy.cpu().numpy(), F.cpu().numpy())
+    assert abs(lhs - np.vdot(g.cpu().numpy(), a.cpu().numpy())) < 1e-9 * abs(lhs)

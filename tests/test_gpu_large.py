@@ -62,6 +62,45 @@ def test_array_384_sampled_rows():
     assert e64 < 1e-5 * max(1.0, ratio)
 
 
+def test_array_384_rhs_sampled_rows():
+    """The delayed sum of Eq. 5 on the 384^3 grid (padded length 768 = 256 x 3) with
+    delays 1, N_g/2 and N_g active: sampled rows against the oracle's direct grid sums
+    and near-zone entries (complex128 1e-10; complex64 within 1e-5 times the rows'
+    cancellation ratio, as for the product above)."""
+    import torch
+
+    from paper_1408_7060_gb300 import AimContext
+
+    w = make_workload("array_sub3_n384")
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    ng = A.n_delays
+    used = sorted({1, max(1, ng // 2), ng})
+    rng = np.random.default_rng(14)
+    hist = np.zeros((ng, 1, rwg.ns), dtype=complex)
+    for m in used:
+        hist[m - 1, 0] = rng.standard_normal(rwg.ns) + 1j * rng.standard_normal(rwg.ns)
+    rows = np.sort(rng.choice(rwg.ns, 2, replace=False))
+    grid = sum(A.fft_part_rows(m, hist[m - 1, 0], rows) for m in used)
+    ref = grid.copy()
+    pr = A.pairs[np.isin(A.pairs[:, 0], rows)]
+    Zn = efie.fill_pairs(rwg, p, pr, ng)
+    for m in used:
+        Zm = Zn[m] - A.fft_pairs(m, pr)
+        for (k, kp), z in zip(pr, Zm):
+            ref[np.searchsorted(rows, k)] += z * hist[m - 1, 0, kp]
+    hd = torch.tensor(hist, device="cuda")
+    with AimContext.from_workload(w, precision="c128") as c:
+        assert c.n_delays == ng
+        r128 = c.rhs(ng + 1, hd).cpu().numpy()[0]
+    with AimContext.from_workload(w, precision="c64") as c:
+        r64 = c.rhs(ng + 1, hd).cpu().numpy()[0]
+    assert rel(r128[rows], ref) < 1e-10
+    ratio = np.linalg.norm(grid) / np.linalg.norm(ref)
+    assert rel(r64[rows], ref) < 1e-5 * max(1.0, ratio), (rel(r64[rows], ref), ratio)
+
+
 def test_array491k_full_size():
     import torch
 
@@ -84,17 +123,19 @@ def test_array491k_full_size():
 
 
 def test_ellipsoid_adjoint_at_scale():
-    """Ellipsoid (19 998 RWG, 96^3 grid, complex64 grid path, near-zone SAI
-    preconditioner with near sets of up to 83 RWGs), 40-step march.
+    """Ellipsoid (19 998 RWG, 96^3 grid), 40-step march on the complex64 grid path with
+    FP64 refinement to a relative residual of 1e-10 (near-zone SAI preconditioner).
 
-    The march solves each step only to the GMRES tolerance, so the map from incident
-    samples a to far field F(a) is linear only up to solver error, and the adjoint
-    consistency <y, F d> = <F^H y, d> holds to an error that shrinks with the
-    tolerance.  Checked: that error at tol 1e-6 is below 2e-3 and at least 3x smaller
-    than at 1e-5; and the autograd gradient of J = sum |F|^2 agrees with central
-    differences along band-limited directions to 3 % at tol 1e-6 (a wrong factor 2 or
-    a missing conjugation would be off by 50 % or more).  The exact algebra of the
-    adjoint is pinned against the oracle in complex128 on the 480-RWG sphere."""
+    Both passes run without an N_t-long history (aim_march_farfield adds each step's far
+    field at once; aim_march_adjoint_farfield forms each step's adjoint source and
+    gradient term at once).  The refined solves make the map from incident samples a to
+    the far field F linear to ~tol, so:
+    * adjoint consistency <y, F d> = <F^H y, d> holds to 1e-6 on two band-limited d;
+    * the autograd gradient of J = sum |F|^2 agrees with central differences (exact for
+      a quadratic J up to solver error) to 1e-4 on 32 band-limited directions (PCG64
+      seed 1).
+    The exact algebra of the adjoint is pinned against the oracle in complex128 on the
+    480-RWG sphere."""
     import torch
 
     from paper_1408_7060_gb300 import AimContext, abi
@@ -103,6 +144,7 @@ def test_ellipsoid_adjoint_at_scale():
 
     w = make_workload("ellipsoid20k")
     nt, i0, n_samp, n0, n_out = 40, -3, 46, -6, 54
+    tol = 1e-10
     r, _ = random_plane_waves(8, 2)
     e1 = np.cross(r, np.where(np.abs(r[:, 2:3]) < 0.9, [[0, 0, 1.0]], [[1.0, 0, 0]]))
     e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
@@ -119,46 +161,34 @@ def test_ellipsoid_adjoint_at_scale():
         d = np.fft.ifft(np.fft.fft(z) * np.exp(-0.5 * (2 * np.pi * f * w.sigma) ** 2))
         return d / np.linalg.norm(d)
 
-    with AimContext.from_workload(w, precision="c64", max_iter=2000, restart=63, precond="sai") as c:
+    with AimContext.from_workload(w, precision="c64", max_iter=4000, restart=63, precond="sai", refine=8) as c:
         h = c.handle
-
-        def F(a, tol):
-            V = abi.aim_excitation_samples(h, k, p, i0, torch.tensor(a, device="cuda"), nt)
-            I, _, rc = abi.aim_march_source(h, V.reshape(nt, 1, -1), tol)
+        dirs = (r, e1, e2)
+        for _ in range(2):
+            d = torch.tensor(band(), device="cuda")
+            Fd, st, rc = abi.aim_march_farfield(h, k, p, i0, d, nt, tol, r, e1, e2, n0, n_out)
+            assert rc == 0 and st["max_rel_res"] <= tol
+            y = torch.tensor(rng.standard_normal(tuple(Fd.shape)) + 1j * rng.standard_normal(tuple(Fd.shape)),
+                             device="cuda")
+            g, st, rc = abi.aim_march_adjoint_farfield(h, k, p, i0, n_samp, nt, tol, r, e1, e2, n0, y)
             assert rc == 0
-            return abi.aim_farfield(h, r, e1, e2, I.reshape(nt, -1), n0, n_out).cpu().numpy()
+            lhs = torch.vdot(y.flatten(), Fd.flatten()).item()
+            rhs = torch.vdot(g, d).item()
+            assert abs(lhs - rhs) <= 1e-6 * abs(lhs), (lhs, rhs)
 
-        def FH(y, tol):
-            G = abi.aim_farfield_adjoint(h, r, e1, e2, nt, n0, torch.tensor(y, device="cuda"))
-            src = torch.flip(G, dims=[0]).conj().resolve_conj().contiguous().reshape(nt, 1, -1)
-            u, _, rc = abi.aim_march_source(h, src, tol, transpose=True)
-            assert rc == 0
-            lam = torch.flip(u, dims=[0]).conj().resolve_conj().contiguous().reshape(nt, -1)
-            return abi.aim_excitation_samples_adjoint(h, k, p, i0, n_samp, lam).cpu().numpy()
-
-        dirs = [band() for _ in range(2)]
-        err = {}
-        for tol in (1e-5, 1e-6):
-            e = []
-            for d in dirs:
-                Fd = F(d, tol)
-                y = rng.standard_normal(Fd.shape) + 1j * rng.standard_normal(Fd.shape)
-                e.append(abs(np.vdot(y, Fd) - np.vdot(FH(y, tol), d)) / abs(np.vdot(y, Fd)))
-            err[tol] = max(e)
-        assert err[1e-6] < 2e-3, err
-        assert err[1e-6] < err[1e-5] / 3, err
-
-        tol = 1e-6
         a = torch.tensor(a0, device="cuda", requires_grad=True)
-        J = far_field_objective(a, c, (k, p), (r, e1, e2), nt, tol, i0, n0, n_out)
+        J = far_field_objective(a, c, (k, p), dirs, nt, tol, i0, n0, n_out)
         J.backward()
         g = a.grad.detach().cpu().numpy()
         eps = 0.5 * np.linalg.norm(a0)
+        worst = 0.0
         with torch.no_grad():
-            for _ in range(2):
+            for _ in range(32):
                 dd = torch.tensor(band(), device="cuda")
-                jp = far_field_objective(a + eps * dd, c, (k, p), (r, e1, e2), nt, tol, i0, n0, n_out).item()
-                jm = far_field_objective(a - eps * dd, c, (k, p), (r, e1, e2), nt, tol, i0, n0, n_out).item()
+                jp = far_field_objective(a + eps * dd, c, (k, p), dirs, nt, tol, i0, n0, n_out).item()
+                jm = far_field_objective(a - eps * dd, c, (k, p), dirs, nt, tol, i0, n0, n_out).item()
                 fd = (jp - jm) / (2 * eps)
                 an = float(np.real(np.vdot(g, dd.cpu().numpy())))
-                assert abs(fd - an) <= 3e-2 * abs(an), (fd, an)
+                worst = max(worst, abs(fd - an) / abs(an))
+        print(f"ellipsoid adjoint: worst relative FD error over 32 directions {worst:.2e}")
+        assert worst <= 1e-4, worst

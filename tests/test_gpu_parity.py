@@ -348,3 +348,24 @@ def test_pow2_lengths_matvec_and_rhs(name):
             for m in (0, 1):
                 assert rel(c.matvec(m, x[None])[0][rows], ref_mv[m]) < tol, (m, prec)
             assert rel(c.rhs(ng + 2, hist)[0][rows], ref_rhs) < tol, prec
+
+
+def test_rhs_factor3_sampled():
+    """The delayed sum of Eq. 5 on the 96^3 grid (padded length 192 = 64 x 3: the staged
+    radix-3 delay-sum kernel, which recomputes each history slab's z-transform), every
+    delay m = 1..N_g active, both precisions, sampled rows against the oracle's direct
+    grid sums and near-zone entries."""
+    w = make_workload("sphere_sub3_n96")
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
+    ng = A.n_delays
+    rng = np.random.default_rng(31)
+    hist = rng.standard_normal((ng, 1, rwg.ns)) + 1j * rng.standard_normal((ng, 1, rwg.ns))
+    rows = np.sort(rng.choice(rwg.ns, 6, replace=False))
+    ref = sum(_oracle_rows(A, rwg, p, m, hist[m - 1, 0], rows) for m in range(1, ng + 1))
+    for prec, tol in (("c128", 1e-10), ("c64", 1e-5)):
+        with ctx_for(w, precision=prec) as c:
+            assert c.n_delays == ng
+            got = c.rhs(ng + 1, hist)[0]
+            assert rel(got[rows], ref) < tol, prec
