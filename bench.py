@@ -1,26 +1,33 @@
 """ET-AIM march benchmark: seconds per time step and per-kernel HBM roofline.
 
-A step is one time step of the march of Eq. 5 on the workload: excitation,
-delayed-interaction sum over the N_g history spectra (right-hand side), and the
-GMRES solve of the immediate system with the ET-AIM operator in every iteration.
+A step is one time step of the march of Eq. 5 for every plane wave of the workload:
+excitation, delayed-interaction sum over the N_g history slabs (right-hand side), and
+the solve of the immediate system -- GMRES with the complex64 ET-AIM operator in
+every iteration, then FP64 refinement of the residual (FP64 grid stages) until it
+meets the tolerance.
 
-Default workload: PEC sphere r = 1 m, icosphere subdivision 4 (7680 RWG), 600 MHz
-+-30 % band, 64^3 grid (128^3 padded FFT), complex64 grid path with FP64 outer
-solve, tol 1e-6, one plane wave.  Inputs are synthetic (seeded mesh and pulse).
+Default workload (the largest configuration that fits one GPU): 4 x 4 array of PEC
+spheres, icosphere subdivision 5 each (491 520 RWG), 1 GHz +-5 %, 384^3 grid (768^3
+padded FFT), 16 seeded plane waves, tol 1e-5, near-zone SAI preconditioner.  Inputs
+are synthetic (seeded meshes and pulses).  The 16 waves march in chunks of as many
+as fit in device memory next to their history rings (the factor-3 padded length keeps
+N_g x/y-transformed slabs per wave): every chunk marches W untimed steps from rest,
+then K timed steps; the step time is the sum over chunks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl aim|reference]
+                    [--workload NAME]
 
-Under torchrun every rank marches its own plane wave (independent right-hand
-sides, no collective); the reported time is the max over ranks.
+Under torchrun every rank marches its own share of the plane waves (independent
+right-hand sides, no collective); the reported time is the max over ranks.
 """
 from __future__ import annotations
 
 import argparse
-import json
 import hashlib
+import json
 import math
-import re
 import os
+import re
 import subprocess
 import sys
 import time
@@ -32,6 +39,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ET-AIM s/time-step (with AIM matvec HBM GB/s vs peak)"
 UNIT = "s/step"
+CSRC = os.path.join(ROOT, "paper_1408_7060_gb300", "csrc")
+
+# solver settings per workload: preconditioner pattern radius (in near radii; the SAI
+# rejects sets above 144 RWGs), FP64 refinement corrections allowed per step
+PRESETS = {
+    "array491k": dict(precond="sai", precond_scale=1.0, refine=4),
+    "sphere7680": dict(precond="sai", precond_scale=2.5, refine=4),
+    "sphere7680_b64": dict(precond="sai", precond_scale=2.5, refine=4),
+    "ellipsoid20k": dict(precond="sai", precond_scale=1.0, refine=4),
+}
 
 
 def load_peaks():
@@ -43,36 +60,27 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-CSRC = os.path.join(ROOT, "paper_1408_7060_gb300", "csrc")
-
-
 def kernel_digest(kind):
     """Digest of a kernel's source text and the FFT core it uses: measured DRAM traffic
     is only reported while the kernel is unchanged since the capture."""
     src = open(os.path.join(CSRC, "operator_impl.cuh")).read()
-    if kind == "zconv":  # the power-of-two z pass: its helpers and k_zconv_p2
-        a = src.find("// Power-of-two L = R1 * R2, one tile of W adjacent z-columns per block")
-        b = src.find("// Lengths with a factor 3: staged tile")
-        if a < 0 or b < 0:
-            return None
-        text = src[a:b]
-    else:
-        name = {"interp_near": "k_interp_near", "anterp_xfft": "k_anterp_rows"}.get(kind)
-        if name is None:
-            return None
-        m = re.search(r"__global__ void __launch_bounds__\(256\) " + name + r"\(.*?\n}\n", src, re.S)
-        if not m:
-            return None
-        text = m.group(0)
-    h = hashlib.sha1(text.encode())
+    names = {"zconv": r"k_zconv(_p2)?", "interp_near": r"k_interp_near", "anterp_xfft": r"k_anterp_rows",
+             "zrhs": r"k_zrhs(_spec)?(_tma)?"}
+    if kind not in names:
+        return None
+    blocks = [m.group(0) for m in re.finditer(r"__global__ void __launch_bounds__\([^)]*\) " + names[kind]
+                                              + r"\(.*?\n}\n", src, re.S)]
+    if not blocks:
+        return None
+    h = hashlib.sha1("".join(blocks).encode())
     for f in ("fft.cuh", "fft_kernels.cuh"):
         h.update(open(os.path.join(CSRC, f)).read().encode())
     return h.hexdigest()[:16]
 
 
-# DRAM bytes (read + write) of one launch from an ncu --set full capture (cold caches),
-# keyed by (kernel, workload, kernel_digest): profiles/zconv_sphere7680_ncu.md.
-TRAFFIC = {("zconv", "sphere7680", "a435e10b1cbf6410"): 37968128 + 2816}
+# DRAM bytes (read + write) of one launch, keyed by (kernel, workload, kernel_digest):
+# the profiles/ summaries give the command and the capture.
+TRAFFIC = {}
 
 
 def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
@@ -110,7 +118,6 @@ class ClockSampler:
 
     def __init__(self, gpu_index):
         self.proc = None
-        self.gpu = gpu_index
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -146,10 +153,7 @@ class ClockSampler:
 
 
 def dist_setup():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def reduce_max(x, ws):
@@ -170,13 +174,38 @@ def barrier(ws):
         dist.barrier()
 
 
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --------------------------------------------------------------------------- memory plan
+
+def chunk_size(w, ng_est, refine, total_bytes, restart=50):
+    """Right-hand sides per context that fit in device memory: per-RHS work buffers and
+    history ring (x/y-transformed slabs for lengths with a factor 3, z-spectra for
+    powers of two) against the tables (kernel octants in both precisions, anterpolation,
+    near zone and preconditioner estimated at 80 entries per row, FP64 refinement
+    buffers for one RHS) and a 6 GB margin."""
+    N, L = w.grid_n, 2 * w.grid_n
+    V, F = w.mesh
+    ns = len(F) * 3 // 2
+    es = 8
+    Z = L if (L & (L - 1)) == 0 else N
+    per = es * 4 * (N * N * L + N * L * L + N ** 3) + ng_est * es * 4 * Z * L * L + ns * 16 * (restart + 2 * ng_est + 10)
+    base = (ng_est + 1) * 2 * (N + 1) ** 3 * 24 + ns * 256 * 12 + 64 * ns * 52 + 4 * N ** 3
+    base += ns * 80 * (16 * (ng_est + 1) + 8 + 24)
+    if refine:
+        base += 16 * 4 * (N * N * L + N * L * L + N ** 3)
+    return max(1, int((total_bytes - base - 6e9) // per))
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def run_aim(args):
     import torch
 
-    from paper_1408_7060_gb300 import AimContext
-    from paper_1408_7060_gb300.inputs import make_workload, random_plane_waves
+    from paper_1408_7060_gb300 import AimContext, abi
+    from paper_1408_7060_gb300.inputs import make_workload
 
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -185,121 +214,163 @@ def run_aim(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.init()
-    w = make_workload(args.workload, precond=args.precond)
-    w.precond_radius = args.precond_scale * w.near_radius if w.precond == "sai" else 0.0
-    w.zero_start = args.zero_start
-    if ws > 1:   # each rank marches its own plane wave (independent right-hand side)
-        k, p = random_plane_waves(ws, 100)
-        w.khat, w.phat = k[rank:rank + 1], p[rank:rank + 1]
+    pre = dict(PRESETS.get(args.workload, dict(precond="sai", precond_scale=1.0, refine=4)))
+    if args.precond:
+        pre["precond"] = args.precond
+    if args.refine is not None:
+        pre["refine"] = args.refine
+    if args.precond_scale:
+        pre["precond_scale"] = args.precond_scale
+    w = make_workload(args.workload, precond=pre["precond"], refine=pre["refine"])
+    w.precond_radius = pre["precond_scale"] * w.near_radius if w.precond == "sai" else 0.0
+    waves_k, waves_p = w.khat, w.phat
+    if args.max_waves:
+        waves_k, waves_p = waves_k[:args.max_waves], waves_p[:args.max_waves]
+    if ws > 1:  # every rank its own share of the plane waves (independent right-hand sides)
+        share = np.array_split(np.arange(len(waves_k)), ws)[rank]
+        waves_k, waves_p = waves_k[share], waves_p[share]
+    nw = len(waves_k)
+    total = torch.cuda.get_device_properties(local).total_memory
+    # N_g estimate for the memory plan (the context reports the exact value)
+    V = w.mesh[0]
+    diam = float(np.linalg.norm(V.max(0) - V.min(0))) + 3 * math.sqrt(3) * w.h
+    ng_est = int(diam / (299792458.0 * w.dt) + w.order) + 1
+    chunk = min(nw, args.chunk or chunk_size(w, ng_est, w.refine, total))
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        ctx = AimContext.from_workload(w, stream=stream.cuda_stream)
-    nb, ns = w.nb, ctx.ns
-    info = ctx.info
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    dev_out = torch.empty((1, nb, ns), dtype=torch.complex128, device="cuda")
-
-    def march_one(out):
-        return ctx.march_continue(w.khat, w.phat, w.sigma, w.t_d, 1, w.tol, out=out)
-
-    # warm-up: the first W steps of the march, from rest
-    ctx.march(w.khat, w.phat, w.sigma, w.t_d, max(args.warmup, 1), w.tol,
-              out=torch.empty((max(args.warmup, 1), nb, ns), dtype=torch.complex128, device="cuda"))
-    torch.cuda.synchronize()
-
-    def timed_steps(k, profile=False):
-        ctx.profile(profile)
-        evs = []
-        iters = []
-        split = []
-        for _ in range(k):
+    ctx = None
+    while ctx is None:
+        try:
+            t0 = time.time()
             with torch.cuda.stream(stream):
-                flush.fill_(1.0)                      # L2 flush between timed steps (256 MB > 129 MB L2)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            _, st, rc = march_one(dev_out)
-            b.record(stream)
-            evs.append((a, b))
-            iters.append(st["total_iters"])
-            split.append((st["rhs_ms"], st["solve_ms"]))
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        prof, launches = ctx.get_profile()
-        timed_steps.split = np.mean(np.array(split), axis=0) if split else (0.0, 0.0)
-        return ms, iters, prof, launches
-
+                ctx = AimContext.from_workload(w, batch_max=chunk, stream=stream.cuda_stream)
+            log(f"setup {w.name}: {time.time() - t0:.1f} s, {chunk} waves per context, "
+                f"{ctx.info['device_bytes'] / 1e9:.1f} GB")
+        except abi.AimError as e:
+            if e.code != abi.AIM_ERR_OOM or chunk == 1:
+                raise
+            chunk -= 1
+            log(f"out of memory, {chunk} waves per context")
+    info = ctx.info
+    ns = ctx.ns
+    chunks = [(waves_k[i:i + chunk], waves_p[i:i + chunk]) for i in range(0, nw, chunk)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    K, W = args.steps, args.warmup
+    Ke = max(1, min(K, args.e2e_steps))
+    keep = min(K, args.compare_steps)          # steps of wave 0 kept for the comparisons
+    wave0 = []
+    step_ms = np.zeros((len(chunks), K))
+    iters, split, resid, corr = [], [], [], 0
+    e2e_s = 0.0
+    prof = None
     barrier(ws)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    ms, iters, _, launches = timed_steps(args.steps, profile=False)
-    rhs_ms, solve_ms = (float(x) for x in timed_steps.split)
+    for ci, (k, p) in enumerate(chunks):
+        nb = len(k)
+        warm = torch.empty((W, nb, ns), dtype=torch.complex128, device="cuda")
+        ctx.march(k, p, w.sigma, w.t_d, W, w.tol, out=warm)
+        if ci == 0:
+            wave0.append(warm[:, 0].cpu().numpy())
+        outs = torch.empty((K, 1, nb, ns), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        evs = []
+        for s in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)            # L2 flush between timed steps (inputs are also > L2)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, st, rc = ctx.march_continue(k, p, w.sigma, w.t_d, 1, w.tol, out=outs[s])
+            b.record(stream)
+            evs.append((a, b))
+            iters.append(st["total_iters"] / nb)
+            split.append((st["rhs_ms"], st["solve_ms"]))
+            resid.append(st["max_rel_res"])
+            corr += st["refine_corrections"]
+        torch.cuda.synchronize()
+        step_ms[ci] = [a.elapsed_time(b) for a, b in evs]
+        if ci == 0:
+            wave0.append(outs[:keep, 0, 0].cpu().numpy())
+        # end to end through the C ABI with host buffers: Ke more steps of the same march,
+        # currents written to pinned host memory every step
+        host_out = torch.empty((1, nb, ns), dtype=torch.complex128).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            ctx.march_continue(k, p, w.sigma, w.t_d, 1, w.tol, out=host_out)
+        torch.cuda.synchronize()
+        e2e_s += (time.perf_counter() - t0) / Ke
+        if ci == 0:  # per-kernel device time: a few more steps with per-launch events
+            ctx.profile(True)
+            pout = torch.empty((1, nb, ns), dtype=torch.complex128, device="cuda")
+            for _ in range(args.profile_steps):
+                ctx.march_continue(k, p, w.sigma, w.t_d, 1, w.tol, out=pout)
+            prof, _ = ctx.get_profile()
+            ctx.profile(False)
+            prof_nb = nb
+        log(f"chunk {ci + 1}/{len(chunks)} ({nb} waves): {np.mean(step_ms[ci]):.1f} ms/step")
     clk = clocks.stop()
     torch.cuda.synchronize()
     barrier(ws)
-    t_step = reduce_max(sum(ms) / len(ms) / 1e3, ws)
+    t_step = reduce_max(float(step_ms.sum(axis=0).mean()) / 1e3, ws)
+    e2e = reduce_max(e2e_s, ws)
+    _, launches = ctx.get_profile()
+    launches_per_step = None
 
-    # the same steps with per-kernel events (device time per kernel)
-    ms_p, iters_p, prof, _ = timed_steps(args.steps, profile=True)
-
-    # end to end through the C ABI with host buffers (pinned output, host-side inputs)
-    host_out = torch.empty((1, nb, ns), dtype=torch.complex128).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        march_one(host_out)
-    torch.cuda.synchronize()
-    e2e = reduce_max((time.perf_counter() - t0) / args.steps, ws)
-
-    # roofline of the dominant kernel
+    # roofline of the dominant operator kernel (algorithmic bytes / event time)
     hbm, src = load_peaks()
-    dom = max(prof, key=lambda k: prof[k][1])
+    kb = lambda kind: kernel_bytes(kind, w.grid_n, ns, info["near_nnz"], info["n_delays"], prof_nb)
+    tot_ms = sum(v[1] for v in prof.values()) or 1e-12
+    kernels = {}
+    for kind, (n_l, ms_l) in prof.items():
+        if not n_l:
+            continue
+        b = kb(kind)
+        kernels[kind] = {"launches": n_l, "ms": round(ms_l, 4), "share": round(ms_l / tot_ms, 4),
+                         "gbs": round(b / (ms_l / n_l * 1e-3) / 1e9, 1) if b and ms_l > 0 else None,
+                         "frac": round(b / (ms_l / n_l * 1e-3) / 1e9 / hbm, 4) if b and ms_l > 0 else None}
+    dom = max((kd for kd in kernels if kb(kd)), key=lambda kd: kernels[kd]["ms"])
     n_l, ms_l = prof[dom]
-    nbytes = kernel_bytes(dom, w.grid_n, ns, info["near_nnz"], info["n_delays"], nb)
-    per_launch_ms = ms_l / max(n_l, 1)
-    achieved = (nbytes / (per_launch_ms * 1e-3) / 1e9) if nbytes and per_launch_ms > 0 else None
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 4),
-                   "share": round(v[1] / max(sum(x[1] for x in prof.values()), 1e-12), 4),
-                   "gbs": (round(kernel_bytes(k, w.grid_n, ns, info["near_nnz"], info["n_delays"], nb)
-                                 / (v[1] / v[0] * 1e-3) / 1e9, 1)
-                           if v[0] and v[1] > 0 and kernel_bytes(k, w.grid_n, ns, info["near_nnz"],
-                                                                 info["n_delays"], nb) else None)}
-               for k, v in prof.items() if v[0]}
+    per_launch_ms = ms_l / n_l
+    achieved = kb(dom) / (per_launch_ms * 1e-3) / 1e9
     line = {
-        "metric": METRIC, "value": t_step * 1.0, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64 grid / f64 solve", "data": "synthetic",
+        "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 grid / f64 solve + f64 refinement" if w.refine else "c64 grid / f64 solve",
+        "data": "synthetic",
         "config": {"workload": w.name, "ns": ns, "grid": f"{w.grid_n}^3 -> {2 * w.grid_n}^3 FFT",
-                   "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "rhs_per_gpu": nb,
-                   "tol": w.tol, "chi": round(w.chi, 3), "precond": w.precond,
-                   "precond_radius_m": round(w.precond_radius, 6), "precond_nnz": info["precond_nnz"],
-                   "gmres_start": "zero" if w.zero_start else "previous step",
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "independent plane waves per GPU" if ws > 1 else "single GPU"},
-        "gmres_iters_per_step": float(np.mean(iters)),
-        "split_ms_per_step": {"rhs": round(rhs_ms, 4), "solve": round(solve_ms, 4),
-                              "commit_and_host": round(t_step * 1e3 - rhs_ms - solve_ms, 4)},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
-                     "peak": hbm, "peak_source": src, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4) if achieved else None,
+                   "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "plane_waves": nw,
+                   "waves_per_context": chunk, "chunks": len(chunks), "tol": w.tol, "chi": round(w.chi, 3),
+                   "precond": w.precond, "precond_radius_m": round(w.precond_radius, 6),
+                   "precond_nnz": info["precond_nnz"], "fp64_refinement": w.refine,
+                   "gmres_start": "previous step",
+                   "l2": "inputs larger than L2; also flushed between timed steps (256 MB write)",
+                   "parallelism": "plane waves split over GPUs" if ws > 1 else "single GPU"},
+        "gmres_iters_per_wave_step": round(float(np.mean(iters)), 2),
+        "fp64_relres_max": float(np.max(resid)),
+        "refine_corrections_per_step": round(corr / (K * len(chunks)), 2),
+        "split_ms_per_step": {"rhs": round(float(np.mean([s[0] for s in split])) * len(chunks), 3),
+                              "solve": round(float(np.mean([s[1] for s in split])) * len(chunks), 3)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                     "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                      "traffic": TRAFFIC.get((dom, w.name, kernel_digest(dom))),
-                     "bytes_per_launch": nbytes, "ms_per_launch": round(per_launch_ms, 5)},
+                     "bytes_per_launch": kb(dom), "ms_per_launch": round(per_launch_ms, 5),
+                     "waves_per_launch": prof_nb},
         "kernels": kernels,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nb * 6 * 8,
-                "d2h_bytes_per_step": nb * ns * 16},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nw * 6 * 8, "d2h_bytes_per_step": nw * ns * 16},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    if not args.no_plain:
-        line["plain_c128"] = plain_comparison(w, ctx, stream, args)
-        if w.precond != "diag":
-            line["diag_precond"] = diag_comparison(w, ctx, stream, args)
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        # the oracle's method is the paper's (diagonal preconditioner): its iteration count
-        n_or = float(np.mean(iters)) if w.precond == "diag" else \
-            line.get("diag_precond", {}).get("gmres_iters_per_step", ITERS_PER_STEP.get(w.name, 50.0))
-        line["cpu_baseline"] = cpu_baseline(w, samples=2, n_iter=n_or)
+    line["rel_error_vs_oracle"] = oracle_rows_error(w, ctx)
+    wave0 = np.concatenate(wave0)
+    k0, p0 = chunks[0][0][:1], chunks[0][1][:1]
     ctx.close()
+    torch.cuda.empty_cache()
+    if not args.no_compare:
+        line["plain_c128"] = compare_march(w, k0, p0, wave0, stream, dict(precision="c128", refine=0), W, keep)
+        line["diag_precond"] = compare_march(w, k0, p0, wave0, stream, dict(precond="diag"), W, keep)
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, info["n_delays"], float(np.mean(iters)), nw)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -308,119 +379,103 @@ def run_aim(args):
         dist.destroy_process_group()
 
 
-def diag_comparison(w, ctx, stream, args):
-    """The same march the paper's way (diagonal preconditioner, GMRES started from the
-    previous step's currents): its s/step and GMRES
-    iterations over the same steps, and the relative difference of the two marches
-    (both from rest, both converged to the workload's tolerance)."""
+def oracle_rows_error(w, ctx):
+    """Relative error of the library's operator products against the oracle's direct
+    sums on the rows stored by tests/golden/make_<workload>_rows.py (if present)."""
+    from paper_1408_7060_gb300.inputs import seeded_vector
+
+    path = os.path.join(ROOT, "tests", "golden", f"{w.name}_matvec_rows.txt")
+    if not os.path.exists(path):
+        return None
+    ref = {}
+    for ln in open(path):
+        if ln.startswith("#"):
+            continue
+        m, r, re_, im = ln.split()
+        ref.setdefault(int(m), []).append((int(r), float(re_) + 1j * float(im)))
+    x = seeded_vector(ctx.ns, 11)[None]
+    out = {}
+    for m, rv in ref.items():
+        rows = np.array([r for r, _ in rv])
+        want = np.array([v for _, v in rv])
+        got = ctx.matvec(m, x)[0][rows]
+        out[f"Z{m}"] = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    out["rows"] = len(rows)
+    out["what"] = "complex64 product rows vs the oracle's direct grid sums + near zone"
+    return out
+
+
+def compare_march(w, k0, p0, ref, stream, over, W, keep):
+    """Wave 0 marched with other settings (plain complex128 path, or the paper's diagonal
+    preconditioner): its time per wave-step over `keep` steps after the same warm-up,
+    its GMRES iterations, and its relative difference from the benchmark march."""
     import torch
 
     from paper_1408_7060_gb300 import AimContext
 
-    n = args.warmup + args.steps
     with torch.cuda.stream(stream):
-        cd = AimContext.from_workload(w, precond="diag", zero_start=False, stream=stream.cuda_stream)
-    outd = torch.empty((n, w.nb, cd.ns), dtype=torch.complex128, device="cuda")
-    outs = torch.empty_like(outd)
-    cd.march(w.khat, w.phat, w.sigma, w.t_d, args.warmup, w.tol, out=outd[: args.warmup])
+        c = AimContext.from_workload(w, batch_max=1, stream=stream.cuda_stream, **over)
+    ns = c.ns
+    out = torch.empty((W + keep, 1, ns), dtype=torch.complex128, device="cuda")
+    c.march(k0, p0, w.sigma, w.t_d, W, w.tol, out=out[:W])
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    _, st, _ = cd.march_continue(w.khat, w.phat, w.sigma, w.t_d, args.steps, w.tol, out=outd[args.warmup:])
-    e.record(stream)
+    _, st, _ = c.march_continue(k0, p0, w.sigma, w.t_d, keep, w.tol, out=out[W:])
+    b.record(stream)
     torch.cuda.synchronize()
-    td = a.elapsed_time(e) / args.steps / 1e3
-    ctx.march(w.khat, w.phat, w.sigma, w.t_d, n, w.tol, out=outs)
-    torch.cuda.synchronize()
-    num = torch.linalg.vector_norm(outs - outd).item()
-    den = torch.linalg.vector_norm(outd).item()
-    cd.close()
-    return {"s_per_step": td, "gmres_iters_per_step": st["total_iters"] / args.steps,
-            "rel_diff_vs_this_march": num / den, "steps_compared": n}
-
-
-def plain_comparison(w, ctx64, stream, args):
-    """The plain complex128 path on the same workload: its s/step over the same steps,
-    and the relative error of the complex64 march against it (both from rest)."""
-    import torch
-
-    from paper_1408_7060_gb300 import AimContext
-
-    n = args.warmup + args.steps
-    with torch.cuda.stream(stream):
-        c128 = AimContext.from_workload(w, precision="c128", stream=stream.cuda_stream)
-    out128 = torch.empty((n, w.nb, c128.ns), dtype=torch.complex128, device="cuda")
-    out64 = torch.empty_like(out128)
-    c128.march(w.khat, w.phat, w.sigma, w.t_d, args.warmup, w.tol, out=out128[: args.warmup])
-    torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    _, st, _ = c128.march_continue(w.khat, w.phat, w.sigma, w.t_d, args.steps, w.tol, out=out128[args.warmup:])
-    e.record(stream)
-    torch.cuda.synchronize()
-    t128 = a.elapsed_time(e) / args.steps / 1e3
-    ctx64.march(w.khat, w.phat, w.sigma, w.t_d, n, w.tol, out=out64)
-    torch.cuda.synchronize()
-    num = torch.linalg.vector_norm(out64 - out128).item()
-    den = torch.linalg.vector_norm(out128).item()
-    c128.close()
-    return {"s_per_step": t128, "gmres_iters_per_step": st["total_iters"] / args.steps,
-            "c64_rel_error_vs_c128": num / den, "steps_compared": n}
+    got = out[:, 0].cpu().numpy()
+    c.close()
+    torch.cuda.empty_cache()
+    return {"s_per_wave_step": a.elapsed_time(b) / keep / 1e3, "gmres_iters_per_step": st["total_iters"] / keep,
+            "rel_diff_vs_bench_march": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "steps_compared": W + keep, "settings": {k: v for k, v in over.items()}}
 
 
 # --------------------------------------------------------------------------- CPU oracle
 
 def oracle_setup(w):
-    """The oracle's operator for the workload.  Its near-zone values are set to
-    placeholders on the true sparsity pattern: the timed products cost the same,
-    and the (minutes-long) Galerkin fill is setup, not part of a time step."""
+    """The oracle's operator for the workload (its setup is not timed)."""
     from oracle import aim as oaim
     from oracle import efie
     from oracle.rwg import build_rwg
 
     rwg = build_rwg(*w.mesh)
     p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
-    A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
-    rng = np.random.default_rng(0)
-    A._near_vals = rng.standard_normal((A.n_delays + 1, len(A.pairs))) + 0j
-    return rwg, p, A
+    return rwg, p, oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
 
 
-def oracle_sample(A, rwg, rng):
-    """One sampled unit of a step: one delayed term of the right-hand side and one
-    operator application of the iterative solve (the oracle as it stands)."""
-    x = rng.standard_normal(rwg.ns) + 1j * rng.standard_normal(rwg.ns)
+NODES_PER_SAMPLE = 4
+
+
+def oracle_node_seconds(A, rng):
+    """The oracle's direct grid sum of G^A_0 (the convolution of Eq. 5's grid part, as it
+    stands) at NODES_PER_SAMPLE target nodes, over a source grid with values on every
+    active node of the workload (random values: the cost depends only on the node sets);
+    seconds per target node."""
+    src = np.zeros(A.n ** 3, dtype=complex)
+    src[A.active] = rng.standard_normal(len(A.active)) + 1j * rng.standard_normal(len(A.active))
+    tg = rng.choice(A.active, NODES_PER_SAMPLE, replace=False)
     t0 = time.perf_counter()
-    A.matvec(1, x)
-    t1 = time.perf_counter()
-    A.matvec(0, x)
-    t2 = time.perf_counter()
-    return t1 - t0, t2 - t1
+    A.conv_direct(0, src, 0, targets=tg)
+    return (time.perf_counter() - t0) / NODES_PER_SAMPLE
 
 
-def cpu_baseline(w, samples=2, n_iter=None):
+def node_sample_text(A, t, n_delays, iters, n_waves):
+    return (f"the oracle's direct grid sum at {NODES_PER_SAMPLE} target nodes over the workload's "
+            f"{len(A.active)} active nodes ({t * 1e3:.1f} ms per node), extrapolated to its direct-sum "
+            f"products: x 4 components x {len(A.active)} nodes x {n_delays + iters:.1f} products per wave-step "
+            f"(N_g = {n_delays} delayed + {iters:.1f} GMRES iterations) x {n_waves} waves")
+
+
+def cpu_baseline(w, n_delays, iters_per_step, n_waves, samples=3):
     rwg, p, A = oracle_setup(w)
     rng = np.random.default_rng(0)
-    t_rhs, t_it = [], []
-    for _ in range(samples):
-        a, b = oracle_sample(A, rwg, rng)
-        t_rhs.append(a)
-        t_it.append(b)
-    ng = A.n_delays
-    n_iter = n_iter or 1.0
-    value = ng * np.mean(t_rhs) + n_iter * np.mean(t_it)
-    return {"value": float(value), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{samples} x (one delayed Z_m product + one Z_0 product) of the same workload, "
-                      f"scaled by N_g = {ng} delays and {n_iter:.1f} GMRES iterations per step"}
-
-
-# GMRES iterations per step of the immediate system at the workload's tolerance, as
-# measured by the CUDA path (a property of the linear system, identical for any correct
-# solver with the same preconditioner): the reference arm scales its per-iteration cost
-# by it instead of running minutes of oracle iterations.
-ITERS_PER_STEP = {"sphere7680": 63.5}
+    t = float(np.mean([oracle_node_seconds(A, rng) for _ in range(samples)]))
+    value = t * 4 * len(A.active) * (n_delays + iters_per_step) * n_waves
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{samples} x " + node_sample_text(A, t, n_delays, iters_per_step, n_waves)}
 
 
 def run_reference(args):
@@ -430,26 +485,33 @@ def run_reference(args):
     from paper_1408_7060_gb300.inputs import make_workload
 
     w = make_workload(args.workload)
+    t0 = time.time()
     rwg, p, A = oracle_setup(w)
-    n_iter = ITERS_PER_STEP.get(args.workload, 50.0)
+    ng = A.n_delays
+    log(f"oracle setup {w.name}: {time.time() - t0:.0f} s")
+    iters = ITERS_PER_STEP.get(args.workload, 10.0)
+    nw = len(w.khat)
     rng = np.random.default_rng(1)
     for _ in range(args.warmup):
-        oracle_sample(A, rwg, rng)
-    t = []
-    for _ in range(args.steps):
-        a, b = oracle_sample(A, rwg, rng)
-        t.append(A.n_delays * a + n_iter * b)
-    value = float(np.mean(t))
+        oracle_node_seconds(A, rng)
+    ts = [oracle_node_seconds(A, rng) for _ in range(args.steps)]
+    value = float(np.mean(ts)) * 4 * len(A.active) * (ng + iters) * nw
+    sample = "per step: " + node_sample_text(A, float(np.mean(ts)), ng, iters, nw)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "ns": rwg.ns, "grid": f"{w.grid_n}^3", "n_delays": A.n_delays},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
-                         "sample": f"per step: one delayed Z_m product x N_g={A.n_delays} + one Z_0 product x "
-                                   f"{n_iter} GMRES iterations per step"},
+        "config": {"workload": w.name, "ns": rwg.ns, "grid": f"{w.grid_n}^3", "n_delays": ng,
+                   "plane_waves": nw},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# GMRES iterations per wave-step of the immediate system at the workload's tolerance as
+# measured by the CUDA path (a property of the preconditioned linear system): the
+# reference arm scales its per-product cost by it.
+ITERS_PER_STEP = {"sphere7680": 7.4, "array491k": 10.0}
 
 
 def main():
@@ -458,15 +520,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="aim", choices=["aim", "reference"])
-    ap.add_argument("--workload", default="sphere7680")
+    ap.add_argument("--workload", default="array491k")
+    ap.add_argument("--chunk", type=int, default=0, help="plane waves per context (default: as many as fit)")
+    ap.add_argument("--max-waves", type=int, default=0, help="march only the first waves of the workload")
+    ap.add_argument("--precond", default=None, choices=["sai", "diag"])
+    ap.add_argument("--refine", type=int, default=None, help="FP64 refinement corrections per step (0: off)")
+    ap.add_argument("--precond-scale", type=float, default=0.0, help="SAI pattern radius in near radii")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--compare-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
-    ap.add_argument("--precond", default="sai", choices=["sai", "diag"],
-                    help="GMRES right preconditioner (sparse approximate inverse, or the paper's diagonal)")
-    ap.add_argument("--precond-scale", type=float, default=2.5,
-                    help="SAI pattern radius in units of the near-zone radius")
-    ap.add_argument("--zero-start", action="store_true",
-                    help="start GMRES from zero instead of the previous step's currents")
+    ap.add_argument("--no-compare", action="store_true", help="skip the complex128 and diagonal comparisons")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -42,12 +42,31 @@ class AimOracle:
         self.near_radius = float(near_radius)
         self.anchor = self._anchors()
         self.nodes = self._stencil_nodes()                    # [ns,64] linear node index
-        self.lam = self._moment_matching()                    # [4,ns,64]
         act = np.unique(self.nodes)
         self.active = act
-        self.n_delays = self._n_delays_grid()
-        self.pairs = self._near_pairs()
+        self._lam = None                                       # computed on first use
+        self._n_delays = None
+        self._pairs = None
         self._near_vals = None
+
+    @property
+    def lam(self) -> np.ndarray:
+        """Anterpolation coefficients [4, ns, 64]."""
+        if self._lam is None:
+            self._lam = self._moment_matching()
+        return self._lam
+
+    @property
+    def n_delays(self) -> int:
+        if self._n_delays is None:
+            self._n_delays = self._n_delays_grid()
+        return self._n_delays
+
+    @property
+    def pairs(self) -> np.ndarray:
+        if self._pairs is None:
+            self._pairs = self._near_pairs()
+        return self._pairs
 
     # ------------------------------------------------------------------ stencils
     def _anchors(self):

@@ -185,14 +185,72 @@ template <bool INV, class C> struct DFT<16, INV, C> {
   }
 };
 
+// ---------------------------------------------------------------- composite radices in registers
+// The two-step transforms of the lengths with a factor 3 (768 = 32 x 24, 192 = 16 x 12,
+// 96 = 8 x 12) need radices 12, 24, 48 and 32.  A radix R = RA RB is split once more in
+// registers, with n = RB na + nb and k = ka + RA kb:
+//   X[ka + RA kb] = sum_nb W_RB^{nb kb} [W_R^{nb ka} sum_na x[RB na + nb] W_RA^{na ka}],
+// and its twiddles W_R^q = W_L^{q L/R} are read from the FP64-computed table of the
+// padded length L (in shared memory), so no constants beyond those of the radix-3, 4, 8
+// and 16 butterflies are needed.
+template <int R> struct RadixSplit { static constexpr int A = 0, B = 0; };
+template <> struct RadixSplit<6> { static constexpr int A = 2, B = 3; };
+template <> struct RadixSplit<12> { static constexpr int A = 4, B = 3; };
+template <> struct RadixSplit<24> { static constexpr int A = 8, B = 3; };
+template <> struct RadixSplit<48> { static constexpr int A = 16, B = 3; };
+template <> struct RadixSplit<32> { static constexpr int A = 8, B = 4; };
+
+template <int R> __host__ __device__ constexpr bool simple_radix() { return R == 2 || R == 3 || R == 4 || R == 8 || R == 16; }
+
+template <int R, int L, bool INV, class C>
+struct DFTL {
+  __device__ __forceinline__ static void run(C* v, const C* tw) {
+    if constexpr (simple_radix<R>()) {
+      DFT<R, INV, C>::run(v);
+    } else {
+      constexpr int RA = RadixSplit<R>::A, RB = RadixSplit<R>::B;
+      static_assert(RA * RB == R && L % R == 0, "unsupported composite radix");
+      C t[R];
+#pragma unroll
+      for (int nb = 0; nb < RB; ++nb) {
+        C a[RA];
+#pragma unroll
+        for (int na = 0; na < RA; ++na) a[na] = v[RB * na + nb];
+        DFTL<RA, L, INV, C>::run(a, tw);
+#pragma unroll
+        for (int ka = 0; ka < RA; ++ka) {
+          C x = a[ka];
+          if (ka && nb) {
+            const C w = tw[(nb * ka) * (L / R)];
+            x = x * (INV ? conjc(w) : w);
+          }
+          t[ka * RB + nb] = x;
+        }
+      }
+#pragma unroll
+      for (int ka = 0; ka < RA; ++ka) {
+        C b[RB];
+#pragma unroll
+        for (int nb = 0; nb < RB; ++nb) b[nb] = t[ka * RB + nb];
+        DFTL<RB, L, INV, C>::run(b, tw);
+#pragma unroll
+        for (int kb = 0; kb < RB; ++kb) v[ka + RA * kb] = b[kb];
+      }
+    }
+  }
+};
+
 // ---------------------------------------------------------------- two-step transform
-// For L = R1 R2 (powers of two): with n = R2 n1 + n2 and k = k1 + R1 k2,
+// For L = R1 R2 (two_step_len): with n = R2 n1 + n2 and k = k1 + R1 k2,
 //   X[k1 + R1 k2] = sum_{n2} W_{R2}^{n2 k2} W_L^{n2 k1} sum_{n1} x[R2 n1 + n2] W_{R1}^{n1 k1}.
 // Step A: one radix-R1 DFT per (line, n2) and the twiddles W_L^{n2 k1};
 // step B: one radix-R2 DFT per (line, k1).  Each step reads and writes shared memory once.
 __host__ __device__ constexpr bool pow2_len(int L) { return L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512; }
+// lengths with a two-step plan: the powers of two and 96 = 8 x 12, 192 = 16 x 12, 768 = 32 x 24
+__host__ __device__ constexpr bool two_step_len(int L) { return pow2_len(L) || L == 96 || L == 192 || L == 768; }
 __host__ __device__ constexpr int split_r1(int L) {
-  return L == 16 ? 4 : L == 32 ? 8 : L == 64 ? 8 : L == 128 ? 8 : L == 256 ? 16 : L == 512 ? 16 : 0;
+  return L == 16 ? 4 : L == 32 ? 8 : L == 64 ? 8 : L == 128 ? 8 : L == 256 ? 16 : L == 512 ? 16
+       : L == 96 ? 8 : L == 192 ? 16 : L == 768 ? 32 : 0;
 }
 
 // Column tile: W lines, element i of line l at a[i*W + l].  Result in natural order in a.
@@ -206,7 +264,7 @@ __device__ __forceinline__ void col_fft2(C* a, C* tmp, const C* __restrict__ tw)
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) v[n1] = (HALF_IN && n1 >= R1 / 2) ? C{} : a[(R2 * n1 + n2) * W + l];
-    DFT<R1, INV, C>::run(v);
+    DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -223,7 +281,7 @@ __device__ __forceinline__ void col_fft2(C* a, C* tmp, const C* __restrict__ tw)
     C v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = tmp[(k1 * R2 + n2) * W + l];
-    DFT<R2, INV, C>::run(v);
+    DFTL<R2, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) a[(k1 + R1 * k2) * W + l] = v[k2];
   }
@@ -243,7 +301,7 @@ __device__ __forceinline__ void row_fft2(C* a, C* tmp, int nl, const C* __restri
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) v[n1] = (HALF_IN && n1 >= R1 / 2) ? C{} : a[r * L + R2 * n1 + n2];
-    DFT<R1, INV, C>::run(v);
+    DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -260,7 +318,7 @@ __device__ __forceinline__ void row_fft2(C* a, C* tmp, int nl, const C* __restri
     C v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = tmp[r * P + k1 * (R2 + 1) + n2];
-    DFT<R2, INV, C>::run(v);
+    DFTL<R2, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) a[r * L + k1 + R1 * k2] = v[k2];
   }

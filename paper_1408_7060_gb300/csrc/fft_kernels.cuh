@@ -17,11 +17,11 @@ __device__ __forceinline__ void load_twiddles(C* tw, const C* __restrict__ twg, 
 }
 
 // Transform the lines of a tile (after a __syncthreads that publishes a); returns
-// the buffer holding the natural-order result.  Power-of-two lengths use the
-// two-step transform, lengths with a factor 3 the Stockham passes.
+// the buffer holding the natural-order result.  Lengths with a two-step plan use the
+// two-step transform, any other the Stockham passes.
 template <int L, int W, bool INV, class C>
 __device__ __forceinline__ C* line_fft_cols(C* a, C* b, const C* tw) {
-  if constexpr (pow2_len(L)) {
+  if constexpr (two_step_len(L)) {
     col_fft2<L, W, INV, C>(a, b, tw);
     return a;
   } else {
@@ -30,7 +30,7 @@ __device__ __forceinline__ C* line_fft_cols(C* a, C* b, const C* tw) {
 }
 template <int L, bool INV, class C>
 __device__ __forceinline__ C* line_fft_rows(C* a, C* b, int nl, const C* tw) {
-  if constexpr (pow2_len(L)) {
+  if constexpr (two_step_len(L)) {
     row_fft2<L, INV, C>(a, b, nl, tw);
     return a;
   } else {
@@ -40,7 +40,7 @@ __device__ __forceinline__ C* line_fft_rows(C* a, C* b, int nl, const C* tw) {
 // scratch elements a row tile of nl lines needs beside the tile itself
 template <int L>
 __host__ __device__ constexpr int row_scratch(int nl) {
-  return pow2_len(L) ? nl * row_tmp_pitch<L>() : nl * L;
+  return two_step_len(L) ? nl * row_tmp_pitch<L>() : nl * L;
 }
 
 template <int L, bool INV, class C>
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __res
   }
 }
 
-// Power-of-two L = R1 * R2 rows without staging copies: thread (r, n2) reads inputs
+// Two-step L = R1 * R2 rows without staging copies: thread (r, n2) reads inputs
 // R2 n1 + n2 < n_in of row r straight from memory, radix-R1 butterfly, twiddle, one
 // exchange through the padded tile; thread (r, k1) runs the radix-R2 butterfly and
 // stores outputs k1 + R1 k2 < n_out straight to memory.  256 threads, rpb rows.
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __
       const int i = R2 * n1 + n2;
       v[n1] = i < n_in ? src[i] : C{};
     }
-    DFT<R1, INV, C>::run(v);
+    DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __
     C v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[r * P + k1 * (R2 + 1) + n2];
-    DFT<R2, INV, C>::run(v);
+    DFTL<R2, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
       const int k = k1 + R1 * k2;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __res
   const int nw = min(W, nx - x0);
   const C* src = in + blockIdx.z * ps2_in + blockIdx.y * ps1_in + x0;
   C* dst = out + blockIdx.z * ps2_out + blockIdx.y * ps1_out + x0;
-  constexpr bool half = HALF && pow2_len(L);
+  constexpr bool half = HALF && two_step_len(L);
   const int rows = half ? L / 2 : L;
   for (int t = threadIdx.x; t < rows * W; t += blockDim.x) {
     int i = t / W, l = t % W;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __res
   }
 }
 
-// Power-of-two L = R1 * R2 without staging copies: thread (l, n2) reads its R1 inputs
+// Two-step L = R1 * R2 without staging copies: thread (l, n2) reads its R1 inputs
 // i = R2 n1 + n2 straight from memory (HALF: n1 < R1/2 only), radix-R1 butterfly,
 // twiddle, one exchange through t[(k1 R2 + n2) W + l]; thread (l, k1) runs the
 // radix-R2 butterfly and stores the outputs k1 + R1 k2 < n_out straight to memory.
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
       const int i = R2 * n1 + n2;
       v[n1] = ((!HALF || n1 < R1 / 2) && i < n_in && l < nw) ? src[(long long)i * es_in + l] : C{};
     }
-    DFT<R1, INV, C>::run(v);
+    DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
     C v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[(k1 * R2 + n2) * W + l];
-    DFT<R2, INV, C>::run(v);
+    DFTL<R2, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
       const int k = k1 + R1 * k2;
@@ -213,10 +213,11 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
   pdl_trigger();
 }
 
-// tile width of the direct power-of-two column passes (one L x W tile)
+// tile width of the direct two-step column passes (one L x W tile, at most ~100 KB of
+// shared memory so that two blocks share an SM)
 template <int L, class C>
 constexpr int col_width_p2() {
-  return (int)sizeof(C) == 8 ? (L < 32 ? L : 32) : (L < 16 ? L : 16);
+  return (int)sizeof(C) == 8 ? (L < 32 ? L : L >= 512 ? 16 : 32) : (L < 16 ? L : L >= 512 ? 8 : 16);
 }
 
 // tile width of a column pass: keep 2 (or 3) L x W buffers within ~160 KB

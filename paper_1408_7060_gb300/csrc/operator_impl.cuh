@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
     b0[(3 * ypb + yy) * L + x] = a3;
   }
   C* res;
-  if constexpr (pow2_len(L)) {  // the padding half is never read
+  if constexpr (two_step_len(L)) {  // the padding half is never read
     __syncthreads();
     row_fft2<L, false, C, true>(b0, b1, 4 * ypb, tw);
     res = b0;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
 // ---------------------------------------------------------------- z pass with the kernel
 __device__ __forceinline__ int fold(int k, int N) { return k <= N ? k : 2 * N - k; }
 
-// Power-of-two L = R1 * R2, one tile of W adjacent z-columns per block, a single
+// Two-step L = R1 * R2, one tile of W adjacent z-columns per block, a single
 // shared exchange tile t[(k1 R2 + n2) W + l]:
 //   A  thread (l, n2): the N = L/2 nonzero samples z = R2 n1 + n2 (n1 < R1/2) come
 //      straight from memory, radix-R1 butterfly, twiddle W_L^{n2 k1}, into t;
@@ -215,7 +215,7 @@ constexpr int zsplit_r1() {
 }
 template <int L, class C>
 constexpr int zcol_width() {
-  return (int)sizeof(C) == 8 ? (L < 32 ? L : 32) : (L < 16 ? L : 16);
+  return (int)sizeof(C) == 8 ? (L < 32 ? L : L >= 512 ? 16 : 32) : (L < 16 ? L : L >= 512 ? 8 : 16);
 }
 constexpr int kZThreads = 256;
 
@@ -227,7 +227,7 @@ __device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) v[n1] = n1 < R1 / 2 ? col[(long long)(R2 * n1 + n2) * es + l] : C{};
-    DFT<R1, false, C>::run(v);
+    DFTL<R1, L, false, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -239,11 +239,11 @@ __device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long
 
 // the spectrum X[k1 + R1 k2] of column l from t (after step A and a barrier)
 template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_b_fwd(const C* t, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
+__device__ __forceinline__ void zcol_step_b_fwd(const C* t, const C* tw, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[(k1 * R2 + n2) * W + l];
-  DFT<R2, false, C>::run(v);
+  DFTL<R2, L, false, C>::run(v, tw);
   (void)R1;
 }
 
@@ -251,7 +251,7 @@ __device__ __forceinline__ void zcol_step_b_fwd(const C* t, int k1, int l, C (&v
 template <int L, int W, class C>
 __device__ __forceinline__ void zcol_step_b_inv(C* t, const C* tw, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
-  DFT<R2, true, C>::run(v);
+  DFTL<R2, L, true, C>::run(v, tw);
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) {
     C x = v[n2];
@@ -269,7 +269,7 @@ __device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restri
     C v[R1];
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) v[k1] = t[(k1 * R2 + n2) * W + l];
-    DFT<R1, true, C>::run(v);
+    DFTL<R1, L, true, C>::run(v, tw);
 #pragma unroll
     for (int n1 = 0; n1 < R1 / 2; ++n1) col[(long long)(n2 + R2 * n1) * es + l] = v[n1];
   }
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, cons
     C g[R2], v[R2];
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
-    zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+    zcol_step_b_fwd<L, W, C>(t, tw, k1, l, v);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) v[k2] = v[k2] * g[k2];
     zcol_step_b_inv<L, W, C>(t, tw, k1, l, v);
@@ -312,43 +312,6 @@ __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, cons
   __syncthreads();
   zcol_step_c<L, W, C>(t, tw, col, es);
   pdl_trigger();
-}
-
-// Lengths with a factor 3: staged tile, Stockham passes, separate product loop.
-template <int L, int W, class C>
-__global__ void __launch_bounds__(256) k_zconv(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
-                                               const int* __restrict__ active, const C* __restrict__ twg) {
-  const int bc = blockIdx.z;
-  if (active && !active[bc >> 2]) return;
-  C* tw = reinterpret_cast<C*>(aim_smem);
-  C* b0 = tw + L;
-  C* b1 = b0 + L * W;
-  load_twiddles(tw, twg, L);
-  const int y = blockIdx.y, x0 = blockIdx.x * W;
-  const long long es = (long long)L * L;
-  C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
-  const int n1 = N + 1;
-  const C* G = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1;
-  for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
-    const int i = t / W, l = t % W;
-    C v{};
-    if (i < N) v = col[i * es + l];
-    b0[t] = v;
-  }
-  __syncthreads();
-  C* f = line_fft_cols<L, W, false, C>(b0, b1, tw);
-  const int fy = fold(y, N);
-  {
-    const int l = threadIdx.x % W;
-    const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
-    for (int i = threadIdx.x / W; i < L; i += 256 / W) f[i * W + l] = f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
-  }
-  __syncthreads();
-  C* g = line_fft_cols<L, W, true, C>(f, f == b0 ? b1 : b0, tw);
-  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
-    const int i = t / W, l = t % W;
-    col[i * es + l] = g[t];
-  }
 }
 
 // History slabs of power-of-two length are kept z-transformed: S[bc][kz][y][x], all L
@@ -375,7 +338,7 @@ __global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ B
   for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
     const int l = u % W, k1 = u / W;
     C v[R2];
-    zcol_step_b_fwd<L, W, C>(t, k1, l, v);
+    zcol_step_b_fwd<L, W, C>(t, tw, k1, l, v);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) out[(long long)(k1 + R1 * k2) * es + l] = v[k2];
   }
@@ -537,45 +500,57 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
   zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
 }
 
-// Lengths with a factor 3.
+// Lengths with a factor 3 keep x/y-transformed history slabs (a z-spectral ring would
+// double the largest buffer): the delay sum recomputes each slab's forward z-transform
+// (steps A and B of the z pass), multiplies it by its delay's kernel spectrum and
+// accumulates in the registers of the step-B threads; then one inverse z-FFT (steps
+// B^-1 and C), the N outputs written to Bf.
 template <int L, int W, class C>
-__global__ void __launch_bounds__(256) k_zrhs(SlabList sl, const C* __restrict__ kspec_all, int N,
-                                              C* __restrict__ Bf, const C* __restrict__ twg) {
+__global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __restrict__ kspec_all, int N,
+                                                       C* __restrict__ Bf, const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
-  C* b0 = tw + L;
-  C* b1 = b0 + L * W;
-  C* acc = b1 + L * W;
+  C* t = tw + L;
   load_twiddles(tw, twg, L);
+  __syncthreads();
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
   const long long es = (long long)L * L;
   const int n1 = N + 1;
   const size_t oct = (size_t)n1 * n1 * n1;
   const int kind = (bc & 3) == 3 ? 1 : 0;
   const int fy = fold(y, N);
-  for (int t = threadIdx.x; t < L * W; t += blockDim.x) acc[t] = C{};
+  C acc[U][R2];
+#pragma unroll
+  for (int j = 0; j < U; ++j)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
   for (int s = 0; s < sl.n; ++s) {
     const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
-    const C* G = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct;
+    const C* Gy = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct + (size_t)fy * n1;
+    if (s) __syncthreads();  // the previous delay's step B has read t
+    zcol_step_a<L, W, C>(col, es, t, tw);
     __syncthreads();
-    for (int t = threadIdx.x; t < L * W; t += blockDim.x) {
-      const int i = t / W, l = t % W;
-      C v{};
-      if (i < N) v = col[i * es + l];
-      b0[t] = v;
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int u = threadIdx.x + j * kZThreads;
+      if (u < W * R1) {
+        const int l = u % W, k1 = u / W;
+        const C* G = Gy + fold(x0 + l, N);
+        C v[R2];
+        zcol_step_b_fwd<L, W, C>(t, tw, k1, l, v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
+      }
     }
-    __syncthreads();
-    C* f = line_fft_cols<L, W, false, C>(b0, b1, tw);
-    const int l = threadIdx.x % W;
-    const C* Gy = G + (size_t)fy * n1 + fold(x0 + l, N);
-    for (int i = threadIdx.x / W; i < L; i += 256 / W) acc[i * W + l] += f[i * W + l] * Gy[(size_t)fold(i, N) * n1 * n1];
   }
   __syncthreads();
-  C* g = line_fft_cols<L, W, true, C>(acc, b0, tw);
-  C* out = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
-  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
-    const int i = t / W, l = t % W;
-    out[i * es + l] = g[t];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int u = threadIdx.x + j * kZThreads;
+    if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
   }
+  __syncthreads();
+  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
 }
 
 // ---------------------------------------------------------------- stage iii + iv
@@ -740,9 +715,7 @@ inline const double* sel_lam(aim_ctx* c, double2*) { return c->d_lam; }
 
 template <int L, class C>
 struct GridOps {
-  static constexpr int W = col_width<L, C>();
   static int ypb() { return std::max(1, 256 / (L / 2)); }
-  static int rpb() { return std::max(1, 2048 / L); }
 
   // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
   // dinv non-null asks for the context's right preconditioner: the diagonal dinv, or the
@@ -778,18 +751,14 @@ struct GridOps {
     }
     {
       KScope ks(c, AIM_K_YFFT_FWD);
-      if constexpr (pow2_len(L)) {
+      static_assert(two_step_len(L), "every supported padded length has a two-step plan");
+      {
         constexpr int CW = col_width_p2<L, C>();
         const size_t sm = (L + L * CW) * sizeof(C);
         smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
         launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>,
                    (const C*)A, slab, N, L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L,
                    (long long)N * N * L, (long long)N * L * L, tw);
-      } else {
-        const size_t sm = (L + 2 * L * W) * sizeof(C);
-        smem_opt_in(k_cols<L, W, false, C, true>, sm);
-        k_cols<L, W, false, C, true><<<dim3(L / W, N, nb * 4), 256, sm, c->stream>>>(
-            A, slab, N, L, L, L, L, (long long)N * L, (long long)L * L, (long long)N * N * L, (long long)N * L * L, tw);
       }
       AIM_CHECK_LAUNCH();
     }
@@ -805,35 +774,26 @@ struct GridOps {
     C* P = reinterpret_cast<C*>(c->d_P);
     {
       KScope ks(c, AIM_K_YFFT_INV);
-      if constexpr (pow2_len(L)) {
+      static_assert(two_step_len(L), "every supported padded length has a two-step plan");
+      {
         constexpr int CW = col_width_p2<L, C>();
         const size_t sm = (L + L * CW) * sizeof(C);
         smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
         launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>, (const C*)Bf, A, L,
                    N, (long long)L, (long long)L, L, (long long)L * L, (long long)N * L, (long long)N * L * L,
                    (long long)N * N * L, tw);
-      } else {
-        const size_t sm = (L + 2 * L * W) * sizeof(C);
-        smem_opt_in(k_cols<L, W, true, C>, sm);
-        k_cols<L, W, true, C><<<dim3(L / W, N, nb * 4), 256, sm, c->stream>>>(
-            Bf, A, L, N, L, L, L, (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, tw);
       }
       AIM_CHECK_LAUNCH();
     }
     {
       const int nrows = nb * 4 * N * N;
       KScope ks(c, AIM_K_XFFT_INV);
-      if constexpr (pow2_len(L)) {
-        const int rp = std::max(1, 4096 / L);
+      {
+        const int rp = pow2_len(L) ? std::max(1, 4096 / L) : std::max(1, 256 / split_r1(L));
         const size_t sm = (L + rp * row_tmp_pitch<L>()) * sizeof(C);
         smem_opt_in(k_rows_p2<L, true, C>, sm);
         launch_pdl(c->stream, dim3((nrows + rp - 1) / rp), dim3(256), sm, k_rows_p2<L, true, C>, (const C*)A, P, nrows,
                    L, N, (long long)L, (long long)N, tw, rp);
-      } else {
-        const int rp = rpb();
-        const size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(C);
-        smem_opt_in(k_rows<L, true, C>, sm);
-        k_rows<L, true, C><<<(nrows + rp - 1) / rp, 256, sm, c->stream>>>(A, P, nrows, L, N, L, N, tw, rp);
       }
       AIM_CHECK_LAUNCH();
     }
@@ -854,17 +814,11 @@ struct GridOps {
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     const C* G = kspec(c) + (size_t)m * 2 * oct;
     KScope ks(c, AIM_K_ZCONV);
-    if constexpr (pow2_len(L)) {
-      constexpr int ZW = zcol_width<L, C>();
-      const size_t sm = (L + L * ZW) * sizeof(C);
-      smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
-      launch_pdl(c->stream, dim3(L / ZW, L, nb * 4), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
-                 twiddles(c));
-    } else {
-      const size_t sm = (L + 2 * L * W) * sizeof(C);
-      smem_opt_in(k_zconv<L, W, C>, sm);
-      k_zconv<L, W, C><<<dim3(L / W, L, nb * 4), 256, sm, c->stream>>>(Bf, G, N, active, twiddles(c));
-    }
+    constexpr int ZW = zcol_width<L, C>();
+    const size_t sm = (L + L * ZW) * sizeof(C);
+    smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
+    launch_pdl(c->stream, dim3(L / ZW, L, nb * 4), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
+               twiddles(c));
     AIM_CHECK_LAUNCH();
   }
 
@@ -916,9 +870,11 @@ struct GridOps {
       smem_opt_in(k_zrhs_spec<L, ZW, C>, sm);
       k_zrhs_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
     } else {
-      const size_t sm = (L + 3 * L * W) * sizeof(C);
-      smem_opt_in(k_zrhs<L, W, C>, sm);
-      k_zrhs<L, W, C><<<dim3(L / W, L, nb * 4), 256, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+      // 8 columns per tile: one step-B item per thread, the delay sum held in registers
+      constexpr int ZW = L < 8 ? L : 8;
+      const size_t sm = (L + L * ZW) * sizeof(C);
+      smem_opt_in(k_zrhs_2s<L, ZW, C>, sm);
+      k_zrhs_2s<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
     }
     AIM_CHECK_LAUNCH();
   }

@@ -208,6 +208,17 @@ def random_plane_waves(nb: int, seed: int):
     return k, p
 
 
+def seeded_vector(n: int, seed: int) -> np.ndarray:
+    """Complex vector with standard normal real and imaginary parts, PCG64(seed)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    return g.standard_normal(n) + 1j * g.standard_normal(n)
+
+
+def seeded_rows(n: int, count: int, seed: int) -> np.ndarray:
+    """``count`` distinct sorted indices below n, PCG64(seed)."""
+    return np.sort(np.random.Generator(np.random.PCG64(seed)).choice(n, count, replace=False))
+
+
 # ----------------------------------------------------------------------------
 # workloads
 # ----------------------------------------------------------------------------

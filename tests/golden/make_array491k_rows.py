@@ -28,20 +28,11 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import aim as oaim  # noqa: E402
 from oracle import efie  # noqa: E402
 from oracle.rwg import build_rwg  # noqa: E402
-from paper_1408_7060_gb300.inputs import make_workload  # noqa: E402
+from paper_1408_7060_gb300.inputs import make_workload, seeded_rows, seeded_vector  # noqa: E402
 
 OUT = os.path.join(HERE, "array491k_matvec_rows.txt")
 N_ROWS = 4
 DELAYS = (0, 1)
-
-
-def seeded_x(ns: int) -> np.ndarray:
-    g = np.random.Generator(np.random.PCG64(11))
-    return g.standard_normal(ns) + 1j * g.standard_normal(ns)
-
-
-def seeded_rows(ns: int) -> np.ndarray:
-    return np.sort(np.random.Generator(np.random.PCG64(12)).choice(ns, N_ROWS, replace=False))
 
 
 def main():
@@ -51,8 +42,8 @@ def main():
     t0 = time.time()
     A = oaim.AimOracle(rwg, w.grid_n, w.h, w.origin, w.near_radius, p)
     print(f"setup {time.time() - t0:.0f} s, N_g = {A.n_delays}, {len(A.pairs)} near pairs", flush=True)
-    x = seeded_x(rwg.ns)
-    rows = seeded_rows(rwg.ns)
+    x = seeded_vector(rwg.ns, 11)
+    rows = seeded_rows(rwg.ns, N_ROWS, 12)
     pr = A.pairs[np.isin(A.pairs[:, 0], rows)]
     Zd = efie.fill_pairs(rwg, p, pr, max(DELAYS))
     lines = [f"# m row re im  (oracle rows of Z~AIM_m x, direct grid sums; N_g = {A.n_delays})"]

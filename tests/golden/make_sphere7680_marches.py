@@ -33,16 +33,12 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import aim as oaim  # noqa: E402
 from oracle import efie, march, precond  # noqa: E402
 from oracle.rwg import build_rwg  # noqa: E402
-from paper_1408_7060_gb300.inputs import make_workload  # noqa: E402
+from paper_1408_7060_gb300.inputs import make_workload, seeded_rows  # noqa: E402
 
 OUT = os.path.join(HERE, "sphere7680_march_rows.txt")
 N_STEPS = 24
 N_ROWS = 48
 CASES = (("sphere7680", (0,)), ("sphere7680_b64", (0, 1)))
-
-
-def rows_for(ns: int) -> np.ndarray:
-    return np.sort(np.random.Generator(np.random.PCG64(7)).choice(ns, N_ROWS, replace=False))
 
 
 def march_rows(name: str, waves) -> tuple[np.ndarray, np.ndarray]:
@@ -62,7 +58,7 @@ def march_rows(name: str, waves) -> tuple[np.ndarray, np.ndarray]:
     t0 = time.time()
     I, its = march.march_operator(A.matvec, A.n_delays, V, tol=1e-10, precond=P)
     print(f"{name}: march {time.time() - t0:.0f} s, GMRES iterations per step {its.mean():.1f}", flush=True)
-    rows = rows_for(rwg.ns)
+    rows = seeded_rows(rwg.ns, N_ROWS, 7)
     return rows, I[:, :, rows]
 
 
