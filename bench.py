@@ -44,7 +44,7 @@ CSRC = os.path.join(ROOT, "paper_1408_7060_gb300", "csrc")
 # solver settings per workload: preconditioner pattern radius (in near radii; the SAI
 # rejects sets above 144 RWGs), FP64 refinement corrections allowed per step
 PRESETS = {
-    "array491k": dict(precond="sai", precond_scale=1.0, refine=4),
+    "array491k": dict(precond="sai", precond_scale=1.4, refine=4),
     "sphere7680": dict(precond="sai", precond_scale=2.5, refine=4),
     "sphere7680_b64": dict(precond="sai", precond_scale=2.5, refine=4),
     "ellipsoid20k": dict(precond="sai", precond_scale=1.0, refine=4),
@@ -221,7 +221,7 @@ def run_aim(args):
         pre["refine"] = args.refine
     if args.precond_scale:
         pre["precond_scale"] = args.precond_scale
-    w = make_workload(args.workload, precond=pre["precond"], refine=pre["refine"])
+    w = make_workload(args.workload, precond=pre["precond"], refine=pre["refine"], autotune=args.autotune)
     w.precond_radius = pre["precond_scale"] * w.near_radius if w.precond == "sai" else 0.0
     waves_k, waves_p = w.khat, w.phat
     if args.max_waves:
@@ -343,6 +343,8 @@ def run_aim(args):
                    "waves_per_context": chunk, "chunks": len(chunks), "tol": w.tol, "chi": round(w.chi, 3),
                    "precond": w.precond, "precond_radius_m": round(w.precond_radius, 6),
                    "precond_nnz": info["precond_nnz"], "fp64_refinement": w.refine,
+                   "launch_plan": {k: info["plan_" + k] for k in ("zw", "cw", "rp", "ypb")} |
+                   {"source": ["default", "measured", "cached"][info["plan_source"]]},
                    "gmres_start": "previous step",
                    "l2": "inputs larger than L2; also flushed between timed steps (256 MB write)",
                    "parallelism": "plane waves split over GPUs" if ws > 1 else "single GPU"},
@@ -526,6 +528,8 @@ def main():
     ap.add_argument("--precond", default=None, choices=["sai", "diag"])
     ap.add_argument("--refine", type=int, default=None, help="FP64 refinement corrections per step (0: off)")
     ap.add_argument("--precond-scale", type=float, default=0.0, help="SAI pattern radius in near radii")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1, 2],
+                    help="launch plan: 0 defaults, 1 tuned at setup (cached plan reused), 2 re-tuned")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--profile-steps", type=int, default=2)
     ap.add_argument("--compare-steps", type=int, default=3)

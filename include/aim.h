@@ -106,6 +106,14 @@ typedef struct {
                             Z_0 d = r (complex64 operator, from zero, to 1e-2) update
                             x += d.  The march's tolerance then holds for the FP64
                             operator (AIM_ERR_NOCONV if k corrections do not reach it).  */
+  int32_t autotune;      /* launch shapes of the grid passes (the tile widths of the z and y
+                            passes, rows per block of the x passes): 0 built-in defaults;
+                            1 time every candidate on this context's buffers at setup and
+                            keep the fastest, reusing a plan cached for the same GPU model,
+                            padded length, precision and batch; 2 time and refresh the cache.
+                            Cache: the file named by AIM_GB300_PLAN_CACHE, else
+                            $HOME/.cache/aim_gb300_plans.jsonl (one JSON object per line).
+                            The results do not depend on the plan (same arithmetic per line). */
 } aim_opts;
 
 typedef struct {
@@ -138,7 +146,11 @@ typedef struct {
   int32_t preconditioner;/* AIM_PRECOND_*                                           */
   int64_t precond_nnz;   /* entries of the preconditioner's sparsity pattern          */
   int32_t refine;        /* aim_opts.refine as set up (0 on the complex128 path)       */
+  int32_t plan_zw, plan_cw, plan_rp, plan_ypb; /* launch shapes in use (see aim_opts.autotune) */
+  int32_t plan_source;   /* AIM_PLAN_*                                                  */
 } aim_info;
+
+enum { AIM_PLAN_DEFAULT = 0, AIM_PLAN_MEASURED = 1, AIM_PLAN_CACHED = 2 };
 
 /*
  * aim_setup -- build every table of the method on the device (Sec. 4 and Eq. 5):

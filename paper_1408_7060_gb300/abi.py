@@ -19,6 +19,7 @@ AIM_OK, AIM_ERR_ARG, AIM_ERR_MESH, AIM_ERR_CUDA, AIM_ERR_OOM, AIM_ERR_NOCONV, AI
 AIM_WARN_UNSTABLE = 1
 AIM_C128, AIM_C64 = 0, 1
 AIM_CPPIF = 0
+AIM_PLAN_DEFAULT, AIM_PLAN_MEASURED, AIM_PLAN_CACHED = 0, 1, 2
 
 _NAMES = {0: "AIM_OK", -1: "AIM_ERR_ARG", -2: "AIM_ERR_MESH", -3: "AIM_ERR_CUDA", -4: "AIM_ERR_OOM",
           -5: "AIM_ERR_NOCONV", -6: "AIM_ERR_TIMEOUT", 1: "AIM_WARN_UNSTABLE"}
@@ -46,7 +47,7 @@ class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32),
-                ("refine", ct.c_int32)]
+                ("refine", ct.c_int32), ("autotune", ct.c_int32)]
 
 
 class aim_excitation(ct.Structure):
@@ -64,7 +65,8 @@ class aim_info(ct.Structure):
     _fields_ = [("ns", ct.c_int32), ("n_delays", ct.c_int32), ("n_active", ct.c_int32),
                 ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
                 ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64),
-                ("refine", ct.c_int32)]
+                ("refine", ct.c_int32), ("plan_zw", ct.c_int32), ("plan_cw", ct.c_int32), ("plan_rp", ct.c_int32),
+                ("plan_ypb", ct.c_int32), ("plan_source", ct.c_int32)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
@@ -186,12 +188,13 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
               restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False,
-              refine=0):
+              refine=0, autotune=0):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
     precond_radius, default the near radius).  zero_start: GMRES from zero instead of
     the previous step's currents.  refine (complex64 only): up to this many FP64
-    refinement corrections per step (0: off)."""
+    refinement corrections per step (0: off).  autotune: 0 default launch shapes, 1 tuned
+    at setup (cached plan reused), 2 tuned and cache refreshed."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -201,7 +204,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
                     stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
-                    int(bool(zero_start)), int(refine))
+                    int(bool(zero_start)), int(refine), int(autotune))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -479,7 +482,8 @@ class AimContext:
         V, F = w.mesh
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
-                  precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine)
+                  precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine,
+                  autotune=w.autotune)
         kw.update(over)
         return cls(**kw)
 

@@ -155,6 +155,17 @@ struct GmresState {
   int last_nb = 0;
 };
 
+// Launch shapes of the grid passes (tile widths and rows per block).  Zero fields take
+// the built-in defaults; aim_opts.autotune fills them by timing the candidates on the
+// context's own buffers at setup (or from the plan cache).
+struct KPlan {
+  int zw = 0;      // z pass (fused convolution): columns per tile
+  int cw = 0;      // y passes: columns per tile
+  int rp = 0;      // inverse x pass: rows per block
+  int ypb = 0;     // anterpolation + forward x pass: grid rows per block
+  int source = 0;  // AIM_PLAN_DEFAULT, AIM_PLAN_MEASURED or AIM_PLAN_CACHED
+};
+
 // per-kernel event timing (aim_profile / aim_get_profile); ids match AIM_K_* in aim.h
 struct ProfState {
   bool on = false;
@@ -222,6 +233,7 @@ struct aim_ctx {
   int precond = 0;             // AIM_PRECOND_*
   double precond_radius = 0;   // SAI pattern radius (m)
   bool zero_start = false;     // GMRES initial guess 0 instead of the previous currents
+  KPlan plan;                   // launch shapes of the grid passes
   int refine = 0;              // complex64 path: FP64-operator refinement sweeps per step (0: off)
   int ref_nb = 0;              // right-hand sides per FP64 residual product (its buffers' batch)
   void* d_A64 = nullptr;       // FP64 grid work buffers of the refinement residual ([ref_nb] x the

@@ -174,6 +174,8 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
     AIM_CUDA(cudaMallocHost(&c->h_rn, 2 * (size_t)B * sizeof(double)));
   }
   gmres_alloc(c);
+  if (opts->autotune < 0 || opts->autotune > 2) throw AimError{AIM_ERR_ARG, "aim_setup: autotune must be 0, 1 or 2"};
+  op_autotune(c, opts->autotune);
   // run every operator kernel once outside any stream capture: sets the shared-memory
   // attributes of each instantiation and surfaces launch errors at setup
   AIM_CUDA(cudaMemsetAsync(c->d_x, 0, vec, c->stream));
@@ -389,6 +391,11 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   info->preconditioner = c->precond;
   info->precond_nnz = c->d_sai ? c->snnz : c->ns;
   info->refine = c->refine;
+  info->plan_zw = c->plan.zw;
+  info->plan_cw = c->plan.cw;
+  info->plan_rp = c->plan.rp;
+  info->plan_ypb = c->plan.ypb;
+  info->plan_source = c->plan.source;
   return AIM_OK;
 }
 

@@ -1,5 +1,12 @@
 // Precision dispatch of the operator and the excitation kernel (Eq. 1).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+#include <string>
+
+#include <sys/stat.h>
 
 #include "aim_internal.h"
 #include "operator.h"
@@ -11,6 +18,10 @@ template <class C>
 void body_forward_slab(aim_ctx*, int, const double2*, void*);
 template <class C>
 void body_apply_rhs(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double, double2*);
+template <class C>
+void body_tune(aim_ctx*);
+template <class C>
+void body_plan_fill(aim_ctx*);
 
 void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
               const int* active, double2* y, VecSel vin, VecSel yout) {
@@ -64,6 +75,88 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
     body_apply_rhs<float2>(c, nb, sl, nl, base, sign, y);
   else
     body_apply_rhs<double2>(c, nb, sl, nl, base, sign, y);
+}
+
+// ---------------------------------------------------------------- launch plans
+// The plan cache: one JSON object per line,
+//   {"key": "<gpu name>|L=<L>|prec=<c64|c128>|nb=<batch>", "zw": .., "cw": .., "rp": .., "ypb": ..}
+// in the file named by AIM_GB300_PLAN_CACHE, else $HOME/.cache/aim_gb300_plans.jsonl.
+namespace {
+std::string plan_cache_path() {
+  if (const char* e = std::getenv("AIM_GB300_PLAN_CACHE")) return e;
+  if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/aim_gb300_plans.jsonl";
+  return "";
+}
+
+std::string plan_key(const aim_ctx* c) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  cudaGetLastError();
+  for (char& ch : name)
+    if (ch == '"' || ch == '|') ch = '_';
+  return name + "|L=" + std::to_string(c->L) + "|prec=" + (c->precision == AIM_C64 ? "c64" : "c128") +
+         "|nb=" + std::to_string(c->batch_max);
+}
+
+int json_int(const std::string& line, const char* field) {
+  const std::string f = std::string("\"") + field + "\":";
+  const size_t p = line.find(f);
+  return p == std::string::npos ? 0 : std::atoi(line.c_str() + p + f.size());
+}
+
+bool read_plan(const std::string& path, const std::string& key, KPlan& plan) {
+  std::ifstream in(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(in, line)) {  // the last line with the key wins
+    if (line.find("\"key\": \"" + key + "\"") == std::string::npos) continue;
+    KPlan p;
+    p.zw = json_int(line, "zw");
+    p.cw = json_int(line, "cw");
+    p.rp = json_int(line, "rp");
+    p.ypb = json_int(line, "ypb");
+    if (p.zw > 0 && p.cw > 0 && p.rp > 0 && p.ypb > 0) {
+      plan = p;
+      found = true;
+    }
+  }
+  return found;
+}
+
+void append_plan(const std::string& path, const std::string& key, const KPlan& p) {
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);  // may exist
+  std::ofstream out(path, std::ios::app);
+  if (!out) return;  // the cache is an optimisation: an unwritable path is not an error
+  out << "{\"key\": \"" << key << "\", \"zw\": " << p.zw << ", \"cw\": " << p.cw << ", \"rp\": " << p.rp
+      << ", \"ypb\": " << p.ypb << "}\n";
+}
+}  // namespace
+
+void op_autotune(aim_ctx* c, int mode) {
+  c->plan = KPlan();
+  if (mode > 0) {
+    const std::string path = plan_cache_path(), key = plan_key(c);
+    KPlan p;
+    if (mode == 1 && !path.empty() && read_plan(path, key, p)) {
+      p.source = AIM_PLAN_CACHED;
+      c->plan = p;
+    } else {
+      if (c->precision == AIM_C64)
+        body_tune<float2>(c);
+      else
+        body_tune<double2>(c);
+      c->plan.source = AIM_PLAN_MEASURED;
+      if (!path.empty()) append_plan(path, key, c->plan);
+    }
+  }
+  // the shapes in use, defaults included (reported by aim_get_info)
+  if (c->precision == AIM_C64)
+    body_plan_fill<float2>(c);
+  else
+    body_plan_fill<double2>(c);
 }
 
 // kernels one operator application launches: prep, anterp + x, y, z, y^-1, x^-1, interp

@@ -51,4 +51,7 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
 // V_l for the plane waves in exc (device parameter block [nb][6]: khat, phat)
 void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double t_d, int step_l, double2* out);
 int op_kernel_count(const aim_ctx* c);
+// choose the launch shapes of the grid passes (aim_opts.autotune: 1 tune or reuse the
+// cached plan, 2 tune and refresh the cache); leaves the defaults on mode 0
+void op_autotune(aim_ctx* c, int mode);
 size_t op_slab_bytes(const aim_ctx* c, int nb);

@@ -60,7 +60,25 @@ void body_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, 
   });
 }
 
+template <class C>
+void body_tune(aim_ctx* c) {
+  AIM_DISPATCH_L(c->L, GridOps<LL, C>::tune(c));
+}
+
+template <class C>
+void body_plan_fill(aim_ctx* c) {
+  AIM_DISPATCH_L(c->L, {
+    KPlan& p = c->plan;
+    p.zw = GridOps<LL, C>::zw(c);
+    p.cw = GridOps<LL, C>::cw(c);
+    p.rp = GridOps<LL, C>::rp(c);
+    p.ypb = GridOps<LL, C>::ypb(c);
+  });
+}
+
 #define AIM_INSTANTIATE_OPS(C)                                                                                   \
+  template void body_tune<C>(aim_ctx*);                                                                         \
+  template void body_plan_fill<C>(aim_ctx*);                                                                    \
   template void body_apply<C>(aim_ctx*, int, int, const double2*, const double2*, const double2*, double,       \
                               const int*, double2*, VecSel, VecSel);                                             \
   template void body_forward_slab<C>(aim_ctx*, int, const double2*, void*);                                     \

@@ -11,7 +11,9 @@
 // non-zero inputs, inverse passes write only the N needed outputs.
 #pragma once
 #include <algorithm>
+#include <functional>
 #include <type_traits>
+#include <vector>
 
 #include "aim_internal.h"
 #include "fft_kernels.cuh"
@@ -29,7 +31,9 @@ template <> __device__ __forceinline__ double2 cvt<double2>(double2 a) { return 
 // ---------------------------------------------------------------- stage i + x pass
 // S_c[n] = sum_k L_c[n,k] x_k gathered node by node (the transpose of the
 // interpolation rows), then the forward x-FFT of each grid row.  One block holds
-// the 4 components of ypb consecutive rows (z, y).
+// the 4 components of ypb consecutive rows (z, y); grid (nb, rows / ypb, N) with the
+// right-hand side fastest, so the CSR rows a block gathers serve the other right-hand
+// sides from L2.
 template <int L, class C>
 __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ nptr, const int* __restrict__ nidx,
                                                      const typename Real<C>::F4* __restrict__ ncoef,
@@ -38,13 +42,13 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
                                                      const C* __restrict__ twg) {
   pdl_wait();
   using R = typename Real<C>::T;
-  const int b = blockIdx.z;
+  const int b = blockIdx.x;
   if (active && !active[b]) return;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* b0 = tw + L;
   C* b1 = b0 + 4 * ypb * L;
   load_twiddles(tw, twg, L);
-  const int z = blockIdx.y, y0 = blockIdx.x * ypb;
+  const int z = blockIdx.z, y0 = blockIdx.y * ypb;
   const C* vb = xs + (size_t)b * ns;
   // gather the N nodes of each row (all threads busy), zero the padding half
   for (int t = threadIdx.x; t < ypb * N; t += blockDim.x) {
@@ -276,22 +280,34 @@ __device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restri
   (void)tw;
 }
 
+// Grid order of the z-pass blocks: (right-hand side, component) fastest, then the x
+// tile, then the row y taken in mirror pairs (0, N, 1, L-1, 2, L-2, ...).  Every block
+// reads the kernel-spectrum octant at (fold(z), fold(y), fold(x)); the octant of a large
+// grid does not fit in L2, and this order keeps the blocks that read the same entries
+// (all right-hand sides and components of one kernel kind, the rows y and L-y) close in
+// time, so the octant comes from DRAM about once per launch.
+__device__ __forceinline__ int zpass_row(int j, int N) {
+  if (j < 2) return j * N;
+  const int k = ((j - 2) >> 1) + 1;
+  return (j & 1) ? 2 * N - k : k;
+}
+
 // Forward z-FFT of the slab column, product with the kernel spectrum of delay m
 // (G^A for c = x,y,z; G^phi for c = div; even-symmetric octant), inverse z-FFT,
-// first N outputs written back in place.
+// first N outputs written back in place.  Grid (nb * 4, L / W, L) in the order above.
 template <int L, int W, class C>
 __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
                                                         const int* __restrict__ active,
                                                         const C* __restrict__ twg) {
   pdl_wait();
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
-  const int bc = blockIdx.z;
+  const int bc = blockIdx.x;
   if (active && !active[bc >> 2]) return;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
   load_twiddles(tw, twg, L);
   __syncthreads();
-  const int y = blockIdx.y, x0 = blockIdx.x * W;
+  const int y = zpass_row(blockIdx.z, N), x0 = blockIdx.y * W;
   const long long es = (long long)L * L;
   C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
   const int n1 = N + 1;
@@ -513,7 +529,7 @@ __global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __r
   C* t = tw + L;
   load_twiddles(tw, twg, L);
   __syncthreads();
-  const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
+  const int bc = blockIdx.x, y = zpass_row(blockIdx.z, N), x0 = blockIdx.y * W;  // z-pass grid order
   const long long es = (long long)L * L;
   const int n1 = N + 1;
   const size_t oct = (size_t)n1 * n1 * n1;
@@ -713,9 +729,54 @@ inline const float2* sel_sai(aim_ctx* c, float2*) { return c->d_saif; }
 inline const double2* sel_sai(aim_ctx* c, double2*) { return c->d_sai; }
 inline const double* sel_lam(aim_ctx* c, double2*) { return c->d_lam; }
 
+// Tile widths the z and y passes are instantiated for (the autotuner picks among them).
+template <class F>
+inline void with_width(int w, F&& f) {
+  switch (w) {
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 32: f(std::integral_constant<int, 32>{}); break;
+    default: throw AimError{AIM_ERR_ARG, "launch plan: unsupported tile width"};
+  }
+}
+constexpr size_t kPlanSmemMax = 220 * 1024;  // dynamic shared memory a plan may ask for
+
 template <int L, class C>
 struct GridOps {
-  static int ypb() { return std::max(1, 256 / (L / 2)); }
+  // ------------------------------------------------------------ launch shapes
+  static int def_zw() { return zcol_width<L, C>(); }
+  static int def_cw() { return col_width_p2<L, C>(); }
+  static int def_rp() { return pow2_len(L) ? std::max(1, 4096 / L) : std::max(1, 256 / split_r1(L)); }
+  static int def_ypb() { return std::max(1, 256 / (L / 2)); }
+  static size_t smem_z(int w) { return (size_t)(L + L * w) * sizeof(C); }
+  static size_t smem_x(int rp) { return (size_t)(L + rp * row_tmp_pitch<L>()) * sizeof(C); }
+  static size_t smem_anterp(int yp) { return (size_t)(L + 4 * yp * L + row_scratch<L>(4 * yp)) * sizeof(C); }
+  // the plan holds the shapes of the context's own precision (the FP64 residual of the
+  // refinement on the complex64 path runs with the defaults)
+  static bool own(const aim_ctx* c) { return (c->precision == AIM_C64) == (sizeof(C) == sizeof(float2)); }
+  static int zw(const aim_ctx* c) { return own(c) && c->plan.zw ? c->plan.zw : def_zw(); }
+  static int cw(const aim_ctx* c) { return own(c) && c->plan.cw ? c->plan.cw : def_cw(); }
+  static int rp(const aim_ctx* c) { return own(c) && c->plan.rp ? c->plan.rp : def_rp(); }
+  static int ypb(const aim_ctx* c) { return own(c) && c->plan.ypb ? c->plan.ypb : def_ypb(); }
+  // candidates the autotuner times
+  static std::vector<int> widths() {
+    std::vector<int> v;
+    for (int w : {8, 16, 32})
+      if (w <= L && L % w == 0 && smem_z(w) <= kPlanSmemMax) v.push_back(w);
+    return v;
+  }
+  static std::vector<int> rps() {
+    std::vector<int> v;
+    for (int r : {2, 4, 8, 16, 32, 64})
+      if (smem_x(r) <= 100 * 1024) v.push_back(r);
+    return v;
+  }
+  static std::vector<int> ypbs(int N) {
+    std::vector<int> v;
+    for (int y : {1, 2, 4, 8})
+      if (y <= N && smem_anterp(y) <= 100 * 1024) v.push_back(y);
+    return v;
+  }
 
   // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
   // dinv non-null asks for the context's right preconditioner: the diagonal dinv, or the
@@ -734,70 +795,78 @@ struct GridOps {
                  nb, reinterpret_cast<C*>(c->d_xs), want_fp64 ? c->d_xd : (double2*)nullptr);
   }
 
+  // anterpolation gather + forward x pass: d_xs -> A
+  static void anterp_x(aim_ctx* c, int nb, const int* active) {
+    const int N = c->N, yp = ypb(c);
+    const size_t sm = smem_anterp(yp);
+    smem_opt_in(k_anterp_rows<L, C>, sm);
+    KScope ks(c, AIM_K_ANTERP_XFFT);
+    launch_pdl(c->stream, dim3(nb, (N + yp - 1) / yp, N), dim3(256), sm, k_anterp_rows<L, C>, (const int*)c->d_nptr,
+               (const int*)c->d_nidx, ncoef(c), reinterpret_cast<const C*>(c->d_xs), active, c->ns, N, yp,
+               reinterpret_cast<C*>(c->d_A), twiddles(c));
+  }
+
+  // forward y pass (pruned input): A -> slab
+  static void y_fwd(aim_ctx* c, int nb, C* slab) {
+    static_assert(two_step_len(L), "every supported padded length has a two-step plan");
+    const int N = c->N;
+    const C* A = reinterpret_cast<const C*>(c->d_A);
+    KScope ks(c, AIM_K_YFFT_FWD);
+    with_width(cw(c), [&](auto wt) {
+      constexpr int CW = decltype(wt)::value;
+      if constexpr (CW <= L) {
+        const size_t sm = smem_z(CW);
+        smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
+        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>, A, slab, N,
+                   L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L, (long long)N * N * L,
+                   (long long)N * L * L, twiddles(c));
+      } else {
+        throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
+      }
+    });
+  }
+
+  // inverse y pass (pruned output): Bf -> A
+  static void y_inv(aim_ctx* c, int nb) {
+    const int N = c->N;
+    KScope ks(c, AIM_K_YFFT_INV);
+    with_width(cw(c), [&](auto wt) {
+      constexpr int CW = decltype(wt)::value;
+      if constexpr (CW <= L) {
+        const size_t sm = smem_z(CW);
+        smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
+        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>,
+                   (const C*)c->d_Bf, reinterpret_cast<C*>(c->d_A), L, N, (long long)L, (long long)L, L,
+                   (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, twiddles(c));
+      } else {
+        throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
+      }
+    });
+  }
+
+  // inverse x pass (pruned output): A -> P
+  static void x_inv(aim_ctx* c, int nb) {
+    const int N = c->N, r = rp(c), nrows = nb * 4 * N * N;
+    const size_t sm = smem_x(r);
+    smem_opt_in(k_rows_p2<L, true, C>, sm);
+    KScope ks(c, AIM_K_XFFT_INV);
+    launch_pdl(c->stream, dim3((nrows + r - 1) / r), dim3(256), sm, k_rows_p2<L, true, C>, (const C*)c->d_A,
+               reinterpret_cast<C*>(c->d_P), nrows, L, N, (long long)L, (long long)N, twiddles(c), r);
+  }
+
   static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab,
                            VecSel vs = VecSel(), bool want_fp64 = false) {
-    const int N = c->N;
-    const C* tw = twiddles(c);
-    C* A = reinterpret_cast<C*>(c->d_A);
     prep(c, nb, v, dinv, vs, active, want_fp64);
-    {
-      const int yp = ypb();
-      size_t sm = (L + 4 * yp * L + row_scratch<L>(4 * yp)) * sizeof(C);
-      smem_opt_in(k_anterp_rows<L, C>, sm);
-      dim3 grid((N + yp - 1) / yp, N, nb);
-      KScope ks(c, AIM_K_ANTERP_XFFT);
-      launch_pdl(c->stream, grid, dim3(256), sm, k_anterp_rows<L, C>, (const int*)c->d_nptr, (const int*)c->d_nidx,
-                 ncoef(c), reinterpret_cast<const C*>(c->d_xs), active, c->ns, N, yp, A, tw);
-    }
-    {
-      KScope ks(c, AIM_K_YFFT_FWD);
-      static_assert(two_step_len(L), "every supported padded length has a two-step plan");
-      {
-        constexpr int CW = col_width_p2<L, C>();
-        const size_t sm = (L + L * CW) * sizeof(C);
-        smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
-        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>,
-                   (const C*)A, slab, N, L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L,
-                   (long long)N * N * L, (long long)N * L * L, tw);
-      }
-      AIM_CHECK_LAUNCH();
-    }
+    anterp_x(c, nb, active);
+    y_fwd(c, nb, slab);
   }
 
   // inverse y and x passes: Bf slab -> P, then interpolation + near terms
   static void backward(aim_ctx* c, int nb, const NearList& nl, const double2* base, double sign, const int* active,
                        double2* y, VecSel ys = VecSel()) {
-    const int N = c->N;
-    const C* tw = twiddles(c);
-    C* A = reinterpret_cast<C*>(c->d_A);
-    C* Bf = reinterpret_cast<C*>(c->d_Bf);
-    C* P = reinterpret_cast<C*>(c->d_P);
-    {
-      KScope ks(c, AIM_K_YFFT_INV);
-      static_assert(two_step_len(L), "every supported padded length has a two-step plan");
-      {
-        constexpr int CW = col_width_p2<L, C>();
-        const size_t sm = (L + L * CW) * sizeof(C);
-        smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
-        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>, (const C*)Bf, A, L,
-                   N, (long long)L, (long long)L, L, (long long)L * L, (long long)N * L, (long long)N * L * L,
-                   (long long)N * N * L, tw);
-      }
-      AIM_CHECK_LAUNCH();
-    }
-    {
-      const int nrows = nb * 4 * N * N;
-      KScope ks(c, AIM_K_XFFT_INV);
-      {
-        const int rp = pow2_len(L) ? std::max(1, 4096 / L) : std::max(1, 256 / split_r1(L));
-        const size_t sm = (L + rp * row_tmp_pitch<L>()) * sizeof(C);
-        smem_opt_in(k_rows_p2<L, true, C>, sm);
-        launch_pdl(c->stream, dim3((nrows + rp - 1) / rp), dim3(256), sm, k_rows_p2<L, true, C>, (const C*)A, P, nrows,
-                   L, N, (long long)L, (long long)N, tw, rp);
-      }
-      AIM_CHECK_LAUNCH();
-    }
-    interp(c, nb, P, nl, base, sign, active, y, ys);
+    y_inv(c, nb);
+    x_inv(c, nb);
+    interp(c, nb, reinterpret_cast<const C*>(c->d_P), nl, base, sign, active, y, ys);
   }
 
   static void interp(aim_ctx* c, int nb, const C* P, const NearList& nl, const double2* base, double sign,
@@ -814,12 +883,65 @@ struct GridOps {
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     const C* G = kspec(c) + (size_t)m * 2 * oct;
     KScope ks(c, AIM_K_ZCONV);
-    constexpr int ZW = zcol_width<L, C>();
-    const size_t sm = (L + L * ZW) * sizeof(C);
-    smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
-    launch_pdl(c->stream, dim3(L / ZW, L, nb * 4), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
-               twiddles(c));
+    with_width(zw(c), [&](auto wt) {
+      constexpr int ZW = decltype(wt)::value;
+      if constexpr (ZW <= L) {
+        const size_t sm = smem_z(ZW);
+        smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
+        launch_pdl(c->stream, dim3(nb * 4, L / ZW, L), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
+                   twiddles(c));
+      } else {
+        throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
+      }
+    });
     AIM_CHECK_LAUNCH();
+  }
+
+  // Autotuner: time every candidate launch shape of each pass on this context's buffers
+  // (nb = batch_max right-hand sides, the contents are irrelevant to the timing) and keep
+  // the fastest.  Each pass's arithmetic per line is the same for every shape.
+  static void tune(aim_ctx* c) {
+    const int nb = c->batch_max;
+    cudaEvent_t e0, e1;
+    AIM_CUDA(cudaEventCreate(&e0));
+    AIM_CUDA(cudaEventCreate(&e1));
+    auto time_ms = [&](const std::function<void()>& launch) {
+      launch();  // first launch: shared-memory attribute and warm-up
+      float best = 1e30f;
+      for (int r = 0; r < 3; ++r) {
+        AIM_CUDA(cudaEventRecord(e0, c->stream));
+        launch();
+        AIM_CUDA(cudaEventRecord(e1, c->stream));
+        AIM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        AIM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+      }
+      return best;
+    };
+    KPlan& p = c->plan;
+    auto pick = [&](int& field, const std::vector<int>& cand, const std::function<void()>& launch) {
+      float best = 1e30f;
+      int arg = cand.empty() ? 0 : cand[0];
+      for (int v : cand) {
+        field = v;
+        const float t = time_ms(launch);
+        if (t < best) {
+          best = t;
+          arg = v;
+        }
+      }
+      field = arg;
+    };
+    pick(p.zw, widths(), [&] { zconv(c, nb, 0, nullptr); });
+    pick(p.cw, widths(), [&] {
+      y_fwd(c, nb, reinterpret_cast<C*>(c->d_Bf));
+      y_inv(c, nb);
+    });
+    pick(p.rp, rps(), [&] { x_inv(c, nb); });
+    pick(p.ypb, ypbs(c->N), [&] { anterp_x(c, nb, nullptr); });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
   }
 
   // forward z-FFT of the slab in Bf into the z-spectral history layout at dst
@@ -874,7 +996,7 @@ struct GridOps {
       constexpr int ZW = L < 8 ? L : 8;
       const size_t sm = (L + L * ZW) * sizeof(C);
       smem_opt_in(k_zrhs_2s<L, ZW, C>, sm);
-      k_zrhs_2s<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+      k_zrhs_2s<L, ZW, C><<<dim3(nb * 4, L / ZW, L), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
     }
     AIM_CHECK_LAUNCH();
   }
