@@ -83,17 +83,22 @@ def kernel_digest(kind):
 TRAFFIC = {}
 
 
-def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
-    """Algorithmic HBM bytes of one launch of each kernel (each byte counted once)."""
+def kernel_bytes(kind, N, ns, nnz, ng, nb, box=None, esz=8):
+    """Algorithmic HBM bytes of one launch of each kernel (each byte counted once), for the
+    grid lines each pass touches: with the active box (nx, ny, nz nodes per axis) the
+    anterpolation writes the box rows of A, the forward y pass reads them and writes the
+    box-z rows of the slab, the z pass reads and writes those rows, the inverse y pass
+    writes the box rows of A and the inverse x pass the box of P."""
     L = 2 * N
-    slab = 4 * N * L * L * esz * nb           # [nb][4][N][L][L]
+    bx, by, bz = box if box else (N, N, N)
+    slab = 4 * bz * L * L * esz * nb          # [nb][4][z in box][L][L]
     spec = 4 * L * L * L * esz * nb           # [nb][4][L][L][L]: z-spectrum of a slab (power-of-two L)
     pow2 = (L & (L - 1)) == 0
-    A = 4 * N * N * L * esz * nb              # [nb][4][N][N][L]
-    P = 4 * N * N * N * esz * nb              # [nb][4][N][N][N]
+    A = 4 * bz * by * L * esz * nb            # [nb][4][z, y in box][L]
+    P = 4 * bz * by * bx * esz * nb           # [nb][4][box]
     oct_ = (N + 1) ** 3 * esz                 # one kernel spectrum octant
     lam = ns * 256 * (esz // 2)               # interpolation rows
-    csrT = 64 * ns * (4 + 2 * esz) + (N ** 3 + 1) * 4
+    csrT = 64 * ns * (4 + 2 * esz) + (bz * by * N + 1) * 4
     near = nnz * (4 + 16) + (ns + 1) * 4
     vec = ns * 16 * nb
     return {
@@ -107,6 +112,27 @@ def kernel_bytes(kind, N, ns, nnz, ng, nb, esz=8):
         "xfft_inv": A + P,
         "interp_near": P + lam + ns * 12 + near + 2 * vec,
     }.get(kind)
+
+
+# FP32 arithmetic peak of the z pass's roofline (it is bound by FP32 instruction issue,
+# not by DRAM): 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+ALU_KERNELS = ("zconv", "zrhs")
+
+
+def kernel_flops(kind, N, nb, ng):
+    """Algorithmic FP32 flops of one launch of the z-pass kernels: per z column the
+    conventional 5 L log2 L of a length-L complex FFT forward and inverse, and 6 L for the
+    product with the kernel spectrum (the delay sum: N_g forward transforms and products,
+    one inverse); 4 nb L^2 columns per launch."""
+    L = 2 * N
+    fft = 5 * L * math.log2(L)
+    cols = 4 * nb * L * L
+    if kind == "zconv":
+        return cols * (2 * fft + 6 * L)
+    if kind == "zrhs":
+        return cols * ((ng + 1) * fft + 8 * ng * L)
+    return None
 
 
 class ClockSampler:
@@ -319,7 +345,8 @@ def run_aim(args):
 
     # roofline of the dominant operator kernel (algorithmic bytes / event time)
     hbm, src = load_peaks()
-    kb = lambda kind: kernel_bytes(kind, w.grid_n, ns, info["near_nnz"], info["n_delays"], prof_nb)
+    box = tuple(hi - lo + 1 for lo, hi in zip(info["box_lo"], info["box_hi"]))
+    kb = lambda kind: kernel_bytes(kind, w.grid_n, ns, info["near_nnz"], info["n_delays"], prof_nb, box)
     tot_ms = sum(v[1] for v in prof.values()) or 1e-12
     kernels = {}
     for kind, (n_l, ms_l) in prof.items():
@@ -329,6 +356,12 @@ def run_aim(args):
         kernels[kind] = {"launches": n_l, "ms": round(ms_l, 4), "share": round(ms_l / tot_ms, 4),
                          "gbs": round(b / (ms_l / n_l * 1e-3) / 1e9, 1) if b and ms_l > 0 else None,
                          "frac": round(b / (ms_l / n_l * 1e-3) / 1e9 / hbm, 4) if b and ms_l > 0 else None}
+    for kind in ALU_KERNELS:
+        if kind in kernels and kernels[kind]["ms"] > 0:
+            fl = kernel_flops(kind, w.grid_n, prof_nb, info["n_delays"])
+            tf = fl / (kernels[kind]["ms"] / kernels[kind]["launches"] * 1e-3) / 1e12
+            kernels[kind]["tflops"] = round(tf, 2)
+            kernels[kind]["alu_frac"] = round(tf / FP32_PEAK_TFLOPS, 4)
     dom = max((kd for kd in kernels if kb(kd)), key=lambda kd: kernels[kd]["ms"])
     n_l, ms_l = prof[dom]
     per_launch_ms = ms_l / n_l
@@ -343,6 +376,7 @@ def run_aim(args):
                    "waves_per_context": chunk, "chunks": len(chunks), "tol": w.tol, "chi": round(w.chi, 3),
                    "precond": w.precond, "precond_radius_m": round(w.precond_radius, 6),
                    "precond_nnz": info["precond_nnz"], "fp64_refinement": w.refine,
+                   "active_box": {"lo": list(info["box_lo"]), "hi": list(info["box_hi"])},
                    "launch_plan": {k: info["plan_" + k] for k in ("zw", "cw", "rp", "ypb")} |
                    {"source": ["default", "measured", "cached"][info["plan_source"]]},
                    "gmres_start": "previous step",
@@ -353,11 +387,8 @@ def run_aim(args):
         "refine_corrections_per_step": round(corr / (K * len(chunks)), 2),
         "split_ms_per_step": {"rhs": round(float(np.mean([s[0] for s in split])) * len(chunks), 3),
                               "solve": round(float(np.mean([s[1] for s in split])) * len(chunks), 3)},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                     "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                     "traffic": TRAFFIC.get((dom, w.name, kernel_digest(dom))),
-                     "bytes_per_launch": kb(dom), "ms_per_launch": round(per_launch_ms, 5),
-                     "waves_per_launch": prof_nb},
+        "roofline": roofline_entry(dom, kb(dom), kernel_flops(dom, w.grid_n, prof_nb, info["n_delays"]),
+                                   per_launch_ms, hbm, src, w.name, prof_nb),
         "kernels": kernels,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nw * 6 * 8, "d2h_bytes_per_step": nw * ns * 16},
         "gpu_launches": int(launches),
@@ -370,6 +401,7 @@ def run_aim(args):
     torch.cuda.empty_cache()
     if not args.no_compare:
         line["plain_c128"] = compare_march(w, k0, p0, wave0, stream, dict(precision="c128", refine=0), W, keep)
+        line["no_refine"] = compare_march(w, k0, p0, wave0, stream, dict(refine=0), W, keep)
         line["diag_precond"] = compare_march(w, k0, p0, wave0, stream, dict(precond="diag"), W, keep)
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, info["n_delays"], float(np.mean(iters)), nw)
@@ -379,6 +411,26 @@ def run_aim(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def roofline_entry(kind, nbytes, nflops, per_launch_ms, hbm, src, workload, nb):
+    """The dominant kernel against its bound: the z-pass kernels against the FP32 peak
+    (instruction-bound, DRAM a few per cent busy in the ncu profile), the other passes
+    against the measured HBM copy bandwidth."""
+    t = per_launch_ms * 1e-3
+    traffic = TRAFFIC.get((kind, workload, kernel_digest(kind)))
+    if kind in ALU_KERNELS and nflops:
+        achieved = nflops / t / 1e12
+        return {"bound": "alu", "kernel": kind, "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz", "unit": "TFLOP/s",
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
+                "hbm_gbs": round(nbytes / t / 1e9, 1), "hbm_frac": round(nbytes / t / 1e9 / hbm, 4),
+                "flops_per_launch": nflops, "bytes_per_launch": nbytes, "ms_per_launch": round(per_launch_ms, 5),
+                "waves_per_launch": nb}
+    achieved = nbytes / t / 1e9
+    return {"bound": "hbm", "kernel": kind, "achieved": round(achieved, 1), "peak": hbm, "peak_source": src,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic, "bytes_per_launch": nbytes,
+            "ms_per_launch": round(per_launch_ms, 5), "waves_per_launch": nb}
 
 
 def oracle_rows_error(w, ctx):

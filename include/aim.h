@@ -148,6 +148,11 @@ typedef struct {
   int32_t refine;        /* aim_opts.refine as set up (0 on the complex128 path)       */
   int32_t plan_zw, plan_cw, plan_rp, plan_ypb; /* launch shapes in use (see aim_opts.autotune) */
   int32_t plan_source;   /* AIM_PLAN_*                                                  */
+  int32_t box_lo[3], box_hi[3]; /* active box: grid nodes (x, y, z) touched by some stencil
+                            lie in [box_lo, box_hi] (inclusive).  Sources vanish outside it
+                            and potentials are needed only inside it, so every FFT pass but
+                            the z pass (all lines, reading and writing only z in the box)
+                            runs on the box's lines only.                               */
 } aim_info;
 
 enum { AIM_PLAN_DEFAULT = 0, AIM_PLAN_MEASURED = 1, AIM_PLAN_CACHED = 2 };

@@ -66,7 +66,8 @@ class aim_info(ct.Structure):
                 ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
                 ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64),
                 ("refine", ct.c_int32), ("plan_zw", ct.c_int32), ("plan_cw", ct.c_int32), ("plan_rp", ct.c_int32),
-                ("plan_ypb", ct.c_int32), ("plan_source", ct.c_int32)]
+                ("plan_ypb", ct.c_int32), ("plan_source", ct.c_int32), ("box_lo", ct.c_int32 * 3),
+                ("box_hi", ct.c_int32 * 3)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
@@ -220,7 +221,9 @@ def aim_get_info(ctx) -> dict:
     lib = load()
     info = aim_info()
     _check(lib, ctx, lib.aim_get_info(ctx, ct.byref(info)), "aim_get_info")
-    return {f: getattr(info, f) for f, _ in aim_info._fields_}
+    out = {f: getattr(info, f) for f, _ in aim_info._fields_}
+    out["box_lo"], out["box_hi"] = tuple(info.box_lo), tuple(info.box_hi)
+    return out
 
 
 def aim_num_unknowns(ctx):

@@ -181,6 +181,8 @@ struct aim_ctx {
   // problem
   int ns = 0, nt = 0, nv = 0;
   int N = 0, L = 0;            // grid nodes per axis, padded length 2N
+  int box_lo[3] = {0, 0, 0};   // active box: the nodes (x, y, z) some stencil touches lie in
+  int box_hi[3] = {0, 0, 0};   // [box_lo, box_hi] per axis (inclusive); the FFT passes prune to it
   double h = 0, origin[3] = {0, 0, 0};
   double dt = 0, f_c = 0, wc = 0, kc = 0, near_radius = 0;
   TBasis tb{};

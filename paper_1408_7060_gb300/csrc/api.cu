@@ -118,6 +118,15 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->h_free = hm.rfree;
   std::vector<int> anchor;
   host_anchors(hm, c->N, c->origin, c->h, anchor);
+  for (int d = 0; d < 3; ++d) {  // the active box: every stencil spans anchor .. anchor + 3
+    c->box_lo[d] = c->N - 4;
+    c->box_hi[d] = 3;
+  }
+  for (int k = 0; k < hm.ns; ++k)
+    for (int d = 0; d < 3; ++d) {
+      c->box_lo[d] = std::min(c->box_lo[d], anchor[3 * k + d]);
+      c->box_hi[d] = std::max(c->box_hi[d], anchor[3 * k + d] + 3);
+    }
 
   c->d_v = upload(c, hm.V);
   c->d_tri = upload(c, hm.F);
@@ -396,6 +405,10 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   info->plan_rp = c->plan.rp;
   info->plan_ypb = c->plan.ypb;
   info->plan_source = c->plan.source;
+  for (int d = 0; d < 3; ++d) {
+    info->box_lo[d] = c->box_lo[d];
+    info->box_hi[d] = c->box_hi[d];
+  }
   return AIM_OK;
 }
 

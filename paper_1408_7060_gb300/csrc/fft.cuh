@@ -189,10 +189,96 @@ template <bool INV, class C> struct DFT<16, INV, C> {
 // The two-step transforms of the lengths with a factor 3 (768 = 32 x 24, 192 = 16 x 12,
 // 96 = 8 x 12) need radices 12, 24, 48 and 32.  A radix R = RA RB is split once more in
 // registers, with n = RB na + nb and k = ka + RA kb:
-//   X[ka + RA kb] = sum_nb W_RB^{nb kb} [W_R^{nb ka} sum_na x[RB na + nb] W_RA^{na ka}],
-// and its twiddles W_R^q = W_L^{q L/R} are read from the FP64-computed table of the
-// padded length L (in shared memory), so no constants beyond those of the radix-3, 4, 8
-// and 16 butterflies are needed.
+//   X[ka + RA kb] = sum_nb W_RB^{nb kb} [W_R^{nb ka} sum_na x[RB na + nb] W_RA^{na ka}].
+// Its twiddles W_R^q = cos(2 pi q/R) - i sin(2 pi q/R) are compile-time constants: the
+// loops are unrolled, q is known, and qcos<R> holds cos(2 pi r/R) for r = 0..R/4 (the
+// exact values to 21 digits, from a 30-digit evaluation); the other quadrants follow by
+// symmetry.  (The table argument tw is unused by these radices.)
+template <int R> __device__ __forceinline__ double qcos(int r);
+template <> __device__ __forceinline__ double qcos<4>(int r) { return r == 0 ? 1.0 : 0.0; }
+template <> __device__ __forceinline__ double qcos<8>(int r) {
+  return r == 0 ? 1.0 : r == 1 ? 0.707106781186547524401 : 0.0;
+}
+template <> __device__ __forceinline__ double qcos<16>(int r) {
+  switch (r) {
+    case 0: return 1.0;
+    case 1: return 0.923879532511286756128;
+    case 2: return 0.707106781186547524401;
+    case 3: return 0.382683432365089771728;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double qcos<12>(int r) {
+  switch (r) {
+    case 0: return 1.0;
+    case 1: return 0.866025403784438646764;
+    case 2: return 0.5;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double qcos<24>(int r) {
+  switch (r) {
+    case 0: return 1.0;
+    case 1: return 0.96592582628906828675;
+    case 2: return 0.866025403784438646764;
+    case 3: return 0.707106781186547524401;
+    case 4: return 0.5;
+    case 5: return 0.258819045102520762349;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double qcos<32>(int r) {
+  switch (r) {
+    case 0: return 1.0;
+    case 1: return 0.980785280403230449126;
+    case 2: return 0.923879532511286756128;
+    case 3: return 0.831469612302545237079;
+    case 4: return 0.707106781186547524401;
+    case 5: return 0.555570233019602224743;
+    case 6: return 0.382683432365089771728;
+    case 7: return 0.195090322016128267848;
+    default: return 0.0;
+  }
+}
+template <> __device__ __forceinline__ double qcos<48>(int r) {
+  switch (r) {
+    case 0: return 1.0;
+    case 1: return 0.991444861373810411145;
+    case 2: return 0.96592582628906828675;
+    case 3: return 0.923879532511286756128;
+    case 4: return 0.866025403784438646764;
+    case 5: return 0.79335334029123516458;
+    case 6: return 0.707106781186547524401;
+    case 7: return 0.608761429008720639416;
+    case 8: return 0.5;
+    case 9: return 0.382683432365089771728;
+    case 10: return 0.258819045102520762349;
+    case 11: return 0.130526192220051591548;
+    default: return 0.0;
+  }
+}
+
+// a * W_R^q (forward) or a * conj(W_R^q) (inverse), W_R^q = exp(-2 pi i q / R)
+template <int R, bool INV, class C>
+__device__ __forceinline__ C mul_root(C a, int q) {
+  using Rl = decltype(a.x);
+  double c, s;  // cos, sin of 2 pi q / R
+  if constexpr (R == 6) {
+    const double h = 0.866025403784438646764;
+    const int m = q % 6;
+    c = m == 0 ? 1.0 : m == 3 ? -1.0 : (m == 1 || m == 5) ? 0.5 : -0.5;
+    s = (m == 1 || m == 2) ? h : (m == 4 || m == 5) ? -h : 0.0;
+  } else {
+    constexpr int Q = R / 4;
+    const int m = q % R, j = m / Q, r = m % Q;
+    const double c0 = qcos<R>(r), s0 = qcos<R>(Q - r);
+    c = j == 0 ? c0 : j == 1 ? -s0 : j == 2 ? -c0 : s0;
+    s = j == 0 ? s0 : j == 1 ? c0 : j == 2 ? -s0 : -c0;
+  }
+  if (INV) s = -s;
+  const Rl cr = (Rl)c, sr = (Rl)s;  // a (c - i s)
+  return mkc(a.x * cr + a.y * sr, a.y * cr - a.x * sr);
+}
 template <int R> struct RadixSplit { static constexpr int A = 0, B = 0; };
 template <> struct RadixSplit<6> { static constexpr int A = 2, B = 3; };
 template <> struct RadixSplit<12> { static constexpr int A = 4, B = 3; };
@@ -220,10 +306,7 @@ struct DFTL {
 #pragma unroll
         for (int ka = 0; ka < RA; ++ka) {
           C x = a[ka];
-          if (ka && nb) {
-            const C w = tw[(nb * ka) * (L / R)];
-            x = x * (INV ? conjc(w) : w);
-          }
+          if (ka && nb) x = mul_root<R, INV, C>(x, nb * ka);
           t[ka * RB + nb] = x;
         }
       }
@@ -239,6 +322,46 @@ struct DFTL {
     }
   }
 };
+
+// Even radix R with only the first R/2 inputs non-zero (the pruned zero padding):
+//   X[2k] = DFT_{R/2}(x)[k],  X[2k+1] = DFT_{R/2}(x[n] W_R^n)[k],
+// two half-length butterflies instead of a full one fed with zeros.  v[0..R/2) in,
+// v[0..R) out in natural order.
+template <int R, int L, bool INV, class C>
+__device__ __forceinline__ void dft_half_in(C* v, const C* tw) {
+  constexpr int H = R / 2;
+  C e[H], o[H];
+#pragma unroll
+  for (int n = 0; n < H; ++n) {
+    e[n] = v[n];
+    o[n] = n ? mul_root<R, INV, C>(v[n], n) : v[n];
+  }
+  DFTL<H, L, INV, C>::run(e, tw);
+  DFTL<H, L, INV, C>::run(o, tw);
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    v[2 * k] = e[k];
+    v[2 * k + 1] = o[k];
+  }
+}
+
+// Even radix R when only the first R/2 outputs are needed (the pruned inverse):
+//   x[n] = A[n] + W_R^{+-n} B[n],  A, B the half-length transforms of the even and odd
+// inputs.  v[0..R) in, v[0..R/2) out.
+template <int R, int L, bool INV, class C>
+__device__ __forceinline__ void dft_half_out(C* v, const C* tw) {
+  constexpr int H = R / 2;
+  C e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = v[2 * j];
+    o[j] = v[2 * j + 1];
+  }
+  DFTL<H, L, INV, C>::run(e, tw);
+  DFTL<H, L, INV, C>::run(o, tw);
+#pragma unroll
+  for (int n = 0; n < H; ++n) v[n] = e[n] + (n ? mul_root<R, INV, C>(o[n], n) : o[n]);
+}
 
 // ---------------------------------------------------------------- two-step transform
 // For L = R1 R2 (two_step_len): with n = R2 n1 + n2 and k = k1 + R1 k2,
@@ -264,7 +387,10 @@ __device__ __forceinline__ void col_fft2(C* a, C* tmp, const C* __restrict__ tw)
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) v[n1] = (HALF_IN && n1 >= R1 / 2) ? C{} : a[(R2 * n1 + n2) * W + l];
-    DFTL<R1, L, INV, C>::run(v, tw);
+    if constexpr (HALF_IN && R1 % 2 == 0)
+      dft_half_in<R1, L, INV, C>(v, tw);
+    else
+      DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -301,7 +427,10 @@ __device__ __forceinline__ void row_fft2(C* a, C* tmp, int nl, const C* __restri
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) v[n1] = (HALF_IN && n1 >= R1 / 2) ? C{} : a[r * L + R2 * n1 + n2];
-    DFTL<R1, L, INV, C>::run(v, tw);
+    if constexpr (HALF_IN && R1 % 2 == 0)
+      dft_half_in<R1, L, INV, C>(v, tw);
+    else
+      DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];

@@ -68,14 +68,26 @@ __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __res
   }
 }
 
+// Rows of a box of the grid: row r (0 <= r < nbc * nz * ny) is grid row
+// ((bc * N + z0 + zz) * N + y0 + yy) with (bc, zz, yy) its coordinates in the box; the
+// whole grid is the box nz = ny = N, z0 = y0 = 0.
+struct RowBox {
+  int nz, ny, z0, y0, N;
+  __device__ __forceinline__ long long row(int r) const {
+    const int yy = r % ny, q = r / ny, zz = q % nz, bc = q / nz;
+    return ((long long)bc * N + z0 + zz) * N + y0 + yy;
+  }
+};
+
 // Two-step L = R1 * R2 rows without staging copies: thread (r, n2) reads inputs
 // R2 n1 + n2 < n_in of row r straight from memory, radix-R1 butterfly, twiddle, one
 // exchange through the padded tile; thread (r, k1) runs the radix-R2 butterfly and
-// stores outputs k1 + R1 k2 < n_out straight to memory.  256 threads, rpb rows.
+// stores outputs out_lo <= k1 + R1 k2 < n_out straight to memory.  256 threads, rpb
+// rows of the box.
 template <int L, bool INV, class C>
 __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __restrict__ out, int nrows,
                                                  int n_in, int n_out, long long rs_in, long long rs_out,
-                                                 const C* __restrict__ twg, int rpb) {
+                                                 const C* __restrict__ twg, int rpb, RowBox box, int out_lo) {
   pdl_wait();
   constexpr int R1 = split_r1(L), R2 = L / R1, P = row_tmp_pitch<L>();
   C* tw = reinterpret_cast<C*>(aim_smem);
@@ -86,7 +98,7 @@ __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __
   const int nr = min(rpb, nrows - r0);
   for (int u = threadIdx.x; u < nr * R2; u += 256) {
     const int n2 = u % R2, r = u / R2;
-    const C* src = in + (long long)(r0 + r) * rs_in;
+    const C* src = in + box.row(r0 + r) * rs_in;
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
@@ -107,7 +119,7 @@ __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __
   __syncthreads();
   for (int u = threadIdx.x; u < nr * R1; u += 256) {
     const int k1 = u % R1, r = u / R1;
-    C* dst = out + (long long)(r0 + r) * rs_out;
+    C* dst = out + box.row(r0 + r) * rs_out;
     C v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[r * P + k1 * (R2 + 1) + n2];
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(256) k_rows_p2(const C* __restrict__ in, C* __
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
       const int k = k1 + R1 * k2;
-      if (k < n_out) dst[k] = v[k2];
+      if (k >= out_lo && k < n_out) dst[k] = v[k2];
     }
   }
   pdl_trigger();
@@ -159,15 +171,17 @@ __global__ void __launch_bounds__(256) k_cols(const C* __restrict__ in, C* __res
 }
 
 // Two-step L = R1 * R2 without staging copies: thread (l, n2) reads its R1 inputs
-// i = R2 n1 + n2 straight from memory (HALF: n1 < R1/2 only), radix-R1 butterfly,
-// twiddle, one exchange through t[(k1 R2 + n2) W + l]; thread (l, k1) runs the
-// radix-R2 butterfly and stores the outputs k1 + R1 k2 < n_out straight to memory.
+// i = R2 n1 + n2, in_lo <= i < n_in, straight from memory (HALF: n1 < R1/2 only; the
+// others are zero), radix-R1 butterfly, twiddle, one exchange through
+// t[(k1 R2 + n2) W + l]; thread (l, k1) runs the radix-R2 butterfly and stores the
+// outputs out_lo <= k1 + R1 k2 < n_out straight to memory.  Line p1 = blockIdx.y + p1_off.
 // 256 threads; tile t of L x W elements after the L twiddles.
 template <int L, int W, bool INV, class C, bool HALF = false>
 __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __restrict__ out, int n_in,
                                                  int n_out, long long es_in, long long es_out, int nx,
                                                  long long ps1_in, long long ps1_out, long long ps2_in,
-                                                 long long ps2_out, const C* __restrict__ twg) {
+                                                 long long ps2_out, const C* __restrict__ twg, int in_lo,
+                                                 int out_lo, int p1_off) {
   pdl_wait();
   constexpr int R1 = split_r1(L), R2 = L / R1;
   C* tw = reinterpret_cast<C*>(aim_smem);
@@ -176,17 +190,21 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
   __syncthreads();
   const int x0 = blockIdx.x * W;
   const int nw = min(W, nx - x0);
-  const C* src = in + blockIdx.z * ps2_in + blockIdx.y * ps1_in + x0;
-  C* dst = out + blockIdx.z * ps2_out + blockIdx.y * ps1_out + x0;
+  const long long p1 = (long long)blockIdx.y + p1_off;
+  const C* src = in + blockIdx.z * ps2_in + p1 * ps1_in + x0;
+  C* dst = out + blockIdx.z * ps2_out + p1 * ps1_out + x0;
   for (int u = threadIdx.x; u < W * R2; u += 256) {
     const int l = u % W, n2 = u / W;
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       const int i = R2 * n1 + n2;
-      v[n1] = ((!HALF || n1 < R1 / 2) && i < n_in && l < nw) ? src[(long long)i * es_in + l] : C{};
+      v[n1] = ((!HALF || n1 < R1 / 2) && i >= in_lo && i < n_in && l < nw) ? src[(long long)i * es_in + l] : C{};
     }
-    DFTL<R1, L, INV, C>::run(v, tw);
+    if constexpr (HALF && R1 % 2 == 0)
+      dft_half_in<R1, L, INV, C>(v, tw);
+    else
+      DFTL<R1, L, INV, C>::run(v, tw);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(256) k_cols_p2(const C* __restrict__ in, C* __
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) {
       const int k = k1 + R1 * k2;
-      if (k < n_out && l < nw) dst[(long long)k * es_out + l] = v[k2];
+      if (k >= out_lo && k < n_out && l < nw) dst[(long long)k * es_out + l] = v[k2];
     }
   }
   pdl_trigger();

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
                                                      const typename Real<C>::F4* __restrict__ ncoef,
                                                      const C* __restrict__ xs, const int* __restrict__ active,
                                                      int ns, int N, int ypb, C* __restrict__ A,
-                                                     const C* __restrict__ twg) {
+                                                     const C* __restrict__ twg, int ylo, int yhi, int zlo) {
   pdl_wait();
   using R = typename Real<C>::T;
   const int b = blockIdx.x;
@@ -48,13 +48,13 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
   C* b0 = tw + L;
   C* b1 = b0 + 4 * ypb * L;
   load_twiddles(tw, twg, L);
-  const int z = blockIdx.z, y0 = blockIdx.y * ypb;
+  const int z = zlo + blockIdx.z, y0 = ylo + blockIdx.y * ypb;  // rows of the active box
   const C* vb = xs + (size_t)b * ns;
   // gather the N nodes of each row (all threads busy), zero the padding half
   for (int t = threadIdx.x; t < ypb * N; t += blockDim.x) {
     const int yy = t / N, x = t % N, y = y0 + yy;
     C a0{}, a1{}, a2{}, a3{};
-    if (y < N) {
+    if (y <= yhi) {
       const size_t n = ((size_t)z * N + y) * N + x;
       const int e1 = nptr[n + 1];
       for (int e = nptr[n]; e < e1; ++e) {
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
   }
   for (int t = threadIdx.x; t < 4 * ypb * L; t += blockDim.x) {
     const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
-    if (y < N) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
+    if (y <= yhi) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
   }
   pdl_trigger();
 }
@@ -223,15 +223,25 @@ constexpr int zcol_width() {
 }
 constexpr int kZThreads = 256;
 
+// z rows of the active box: the z pass reads and writes only lo <= z <= hi (the slab rows
+// outside it are zero on input and not needed on output)
+struct ZRange {
+  int lo, hi;
+  __device__ __forceinline__ bool in(int z) const { return z >= lo && z <= hi; }
+};
+
 template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long es, C* t, const C* tw) {
+__device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long es, C* t, const C* tw, ZRange zr) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
   for (int u = threadIdx.x; u < W * R2; u += kZThreads) {
     const int l = u % W, n2 = u / W;
     C v[R1];
 #pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = n1 < R1 / 2 ? col[(long long)(R2 * n1 + n2) * es + l] : C{};
-    DFTL<R1, L, false, C>::run(v, tw);
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int z = R2 * n1 + n2;
+      v[n1] = n1 < R1 / 2 && zr.in(z) ? col[(long long)z * es + l] : C{};
+    }
+    dft_half_in<R1, L, false, C>(v, tw);  // samples z >= N are the zero padding
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -266,18 +276,20 @@ __device__ __forceinline__ void zcol_step_b_inv(C* t, const C* tw, int k1, int l
 }
 
 template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restrict__ col, long long es) {
+__device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restrict__ col, long long es, ZRange zr) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
   for (int u = threadIdx.x; u < W * R2; u += kZThreads) {
     const int l = u % W, n2 = u / W;
     C v[R1];
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) v[k1] = t[(k1 * R2 + n2) * W + l];
-    DFTL<R1, L, true, C>::run(v, tw);
+    dft_half_out<R1, L, true, C>(v, tw);  // only the outputs z < N are kept
 #pragma unroll
-    for (int n1 = 0; n1 < R1 / 2; ++n1) col[(long long)(n2 + R2 * n1) * es + l] = v[n1];
+    for (int n1 = 0; n1 < R1 / 2; ++n1) {
+      const int z = n2 + R2 * n1;
+      if (zr.in(z)) col[(long long)z * es + l] = v[n1];
+    }
   }
-  (void)tw;
 }
 
 // Grid order of the z-pass blocks: (right-hand side, component) fastest, then the x
@@ -298,7 +310,7 @@ __device__ __forceinline__ int zpass_row(int j, int N) {
 template <int L, int W, class C>
 __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
                                                         const int* __restrict__ active,
-                                                        const C* __restrict__ twg) {
+                                                        const C* __restrict__ twg, ZRange zr) {
   pdl_wait();
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
   const int bc = blockIdx.x;
@@ -312,7 +324,7 @@ __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, cons
   C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
   const int n1 = N + 1;
   const C* Gy = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1 + (size_t)fold(y, N) * n1;
-  zcol_step_a<L, W, C>(col, es, t, tw);
+  zcol_step_a<L, W, C>(col, es, t, tw, zr);
   __syncthreads();
   for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
     const int l = u % W, k1 = u / W;
@@ -326,7 +338,7 @@ __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, cons
     zcol_step_b_inv<L, W, C>(t, tw, k1, l, v);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, col, es);
+  zcol_step_c<L, W, C>(t, tw, col, es, zr);
   pdl_trigger();
 }
 
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, cons
 // spectral layout; thread (l, k1) of step B stores X[k1 + R1 k2] for all k2.
 template <int L, int W, class C>
 __global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ Bf, C* __restrict__ S, int N,
-                                                         const C* __restrict__ twg) {
+                                                         const C* __restrict__ twg, ZRange zr) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ B
   __syncthreads();
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
   const long long es = (long long)L * L;
-  zcol_step_a<L, W, C>(Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, t, tw);
+  zcol_step_a<L, W, C>(Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, t, tw, zr);
   __syncthreads();
   C* out = S + (size_t)bc * L * L * L + (size_t)y * L + x0;
   for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ B
 // frequencies k1 + R1 k2).
 template <int L, int W, class C>
 __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec(SlabList sl, const C* __restrict__ kspec_all, int N,
-                                                         C* __restrict__ Bf, const C* __restrict__ twg) {
+                                                         C* __restrict__ Bf, const C* __restrict__ twg, ZRange zr) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
@@ -410,7 +422,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec(SlabList sl, const C
     if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
+  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, zr);
 }
 
 // The same with the spectra streamed by TMA (complex64): the L x W tile of each spectrum
@@ -425,7 +437,8 @@ template <int L, int W>
 __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_constant__ CUtensorMap ring,
                                                                 SlabRing sr, const float2* __restrict__ kspec_all,
                                                                 int N, float2* __restrict__ Bf,
-                                                                const float2* __restrict__ twg, int* __restrict__ err) {
+                                                                const float2* __restrict__ twg, int* __restrict__ err,
+                                                                ZRange zr) {
   using C = float2;
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   __shared__ __align__(8) uint64_t bar[2];
@@ -513,7 +526,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
     if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
+  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, zr);
 }
 
 // Lengths with a factor 3 keep x/y-transformed history slabs (a z-spectral ring would
@@ -523,7 +536,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
 // B^-1 and C), the N outputs written to Bf.
 template <int L, int W, class C>
 __global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __restrict__ kspec_all, int N,
-                                                       C* __restrict__ Bf, const C* __restrict__ twg) {
+                                                       C* __restrict__ Bf, const C* __restrict__ twg, ZRange zr) {
   constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
   C* t = tw + L;
@@ -544,7 +557,7 @@ __global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __r
     const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
     const C* Gy = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct + (size_t)fy * n1;
     if (s) __syncthreads();  // the previous delay's step B has read t
-    zcol_step_a<L, W, C>(col, es, t, tw);
+    zcol_step_a<L, W, C>(col, es, t, tw, zr);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < U; ++j) {
@@ -566,7 +579,7 @@ __global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __r
     if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es);
+  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, zr);
 }
 
 // ---------------------------------------------------------------- stage iii + iv
@@ -795,15 +808,20 @@ struct GridOps {
                  nb, reinterpret_cast<C*>(c->d_xs), want_fp64 ? c->d_xd : (double2*)nullptr);
   }
 
-  // anterpolation gather + forward x pass: d_xs -> A
+  // the active box (x, y, z node ranges): every pass outside the z pass touches only the
+  // grid lines that are non-zero on input or needed on output
+  static ZRange zr(const aim_ctx* c) { return ZRange{c->box_lo[2], c->box_hi[2]}; }
+  static int nbox(const aim_ctx* c, int d) { return c->box_hi[d] - c->box_lo[d] + 1; }
+
+  // anterpolation gather + forward x pass: d_xs -> A (rows of the active box)
   static void anterp_x(aim_ctx* c, int nb, const int* active) {
     const int N = c->N, yp = ypb(c);
     const size_t sm = smem_anterp(yp);
     smem_opt_in(k_anterp_rows<L, C>, sm);
     KScope ks(c, AIM_K_ANTERP_XFFT);
-    launch_pdl(c->stream, dim3(nb, (N + yp - 1) / yp, N), dim3(256), sm, k_anterp_rows<L, C>, (const int*)c->d_nptr,
-               (const int*)c->d_nidx, ncoef(c), reinterpret_cast<const C*>(c->d_xs), active, c->ns, N, yp,
-               reinterpret_cast<C*>(c->d_A), twiddles(c));
+    launch_pdl(c->stream, dim3(nb, (nbox(c, 1) + yp - 1) / yp, nbox(c, 2)), dim3(256), sm, k_anterp_rows<L, C>,
+               (const int*)c->d_nptr, (const int*)c->d_nidx, ncoef(c), reinterpret_cast<const C*>(c->d_xs), active,
+               c->ns, N, yp, reinterpret_cast<C*>(c->d_A), twiddles(c), c->box_lo[1], c->box_hi[1], c->box_lo[2]);
   }
 
   // forward y pass (pruned input): A -> slab
@@ -817,9 +835,10 @@ struct GridOps {
       if constexpr (CW <= L) {
         const size_t sm = smem_z(CW);
         smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
-        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>, A, slab, N,
-                   L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L, (long long)N * N * L,
-                   (long long)N * L * L, twiddles(c));
+        // lines (z in the box, x): inputs y in the box, all L outputs
+        launch_pdl(c->stream, dim3(L / CW, nbox(c, 2), nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>, A,
+                   slab, c->box_hi[1] + 1, L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L,
+                   (long long)N * N * L, (long long)N * L * L, twiddles(c), c->box_lo[1], 0, c->box_lo[2]);
       } else {
         throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
       }
@@ -835,23 +854,26 @@ struct GridOps {
       if constexpr (CW <= L) {
         const size_t sm = smem_z(CW);
         smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
-        launch_pdl(c->stream, dim3(L / CW, N, nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>,
-                   (const C*)c->d_Bf, reinterpret_cast<C*>(c->d_A), L, N, (long long)L, (long long)L, L,
-                   (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, twiddles(c));
+        // lines (z in the box, x): all L inputs, outputs y in the box
+        launch_pdl(c->stream, dim3(L / CW, nbox(c, 2), nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>,
+                   (const C*)c->d_Bf, reinterpret_cast<C*>(c->d_A), L, c->box_hi[1] + 1, (long long)L, (long long)L, L,
+                   (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, twiddles(c), 0,
+                   c->box_lo[1], c->box_lo[2]);
       } else {
         throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
       }
     });
   }
 
-  // inverse x pass (pruned output): A -> P
+  // inverse x pass (pruned output): A -> P, the rows of the active box, outputs x in the box
   static void x_inv(aim_ctx* c, int nb) {
-    const int N = c->N, r = rp(c), nrows = nb * 4 * N * N;
+    const int N = c->N, r = rp(c), nz = nbox(c, 2), ny = nbox(c, 1), nrows = nb * 4 * nz * ny;
     const size_t sm = smem_x(r);
     smem_opt_in(k_rows_p2<L, true, C>, sm);
     KScope ks(c, AIM_K_XFFT_INV);
     launch_pdl(c->stream, dim3((nrows + r - 1) / r), dim3(256), sm, k_rows_p2<L, true, C>, (const C*)c->d_A,
-               reinterpret_cast<C*>(c->d_P), nrows, L, N, (long long)L, (long long)N, twiddles(c), r);
+               reinterpret_cast<C*>(c->d_P), nrows, L, c->box_hi[0] + 1, (long long)L, (long long)N, twiddles(c), r,
+               RowBox{nz, ny, c->box_lo[2], c->box_lo[1], N}, c->box_lo[0]);
   }
 
   static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab,
@@ -889,7 +911,7 @@ struct GridOps {
         const size_t sm = smem_z(ZW);
         smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
         launch_pdl(c->stream, dim3(nb * 4, L / ZW, L), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
-                   twiddles(c));
+                   twiddles(c), zr(c));
       } else {
         throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
       }
@@ -953,7 +975,7 @@ struct GridOps {
       KScope ks(c, AIM_K_ZFWD);
       smem_opt_in(k_zfwd_spec<L, ZW, C>, sm);
       k_zfwd_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
-          reinterpret_cast<const C*>(c->d_Bf), dst, c->N, twiddles(c));
+          reinterpret_cast<const C*>(c->d_Bf), dst, c->N, twiddles(c), zr(c));
       AIM_CHECK_LAUNCH();
     }
   }
@@ -979,7 +1001,7 @@ struct GridOps {
         const size_t sm = 128 + (2 * L * ZW + L + L * ZW) * sizeof(C);
         smem_opt_in(k_zrhs_spec_tma<L, ZW>, sm);
         k_zrhs_spec_tma<L, ZW><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
-            c->ring_map, sr, kspec(c), N, Bf, twiddles(c), c->d_err);
+            c->ring_map, sr, kspec(c), N, Bf, twiddles(c), c->d_err, zr(c));
         AIM_CHECK_LAUNCH();
         return;
       }
@@ -990,13 +1012,15 @@ struct GridOps {
       constexpr int ZW = L < 16 ? L : 16;
       const size_t sm = (L + L * ZW) * sizeof(C);
       smem_opt_in(k_zrhs_spec<L, ZW, C>, sm);
-      k_zrhs_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+      k_zrhs_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c),
+                                                                                  zr(c));
     } else {
       // 8 columns per tile: one step-B item per thread, the delay sum held in registers
       constexpr int ZW = L < 8 ? L : 8;
       const size_t sm = (L + L * ZW) * sizeof(C);
       smem_opt_in(k_zrhs_2s<L, ZW, C>, sm);
-      k_zrhs_2s<L, ZW, C><<<dim3(nb * 4, L / ZW, L), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c));
+      k_zrhs_2s<L, ZW, C><<<dim3(nb * 4, L / ZW, L), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c),
+                                                                                zr(c));
     }
     AIM_CHECK_LAUNCH();
   }
