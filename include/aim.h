@@ -106,6 +106,9 @@ typedef struct {
                             Z_0 d = r (complex64 operator, from zero, to 1e-2) update
                             x += d.  The march's tolerance then holds for the FP64
                             operator (AIM_ERR_NOCONV if k corrections do not reach it).  */
+  int32_t refine_every;  /* with refine: check (and correct) the FP64 residual at every k-th
+                            step only (k <= 1: every step); the other steps keep the complex64
+                            solve                                                            */
   int32_t autotune;      /* launch shapes of the grid passes (the tile widths of the z and y
                             passes, rows per block of the x passes): 0 built-in defaults;
                             1 time every candidate on this context's buffers at setup and
@@ -133,6 +136,7 @@ typedef struct {
                             FP64 refinement)                                          */
   int32_t* iters;        /* optional caller array [n_steps][nb] of iteration counts */
   int32_t refine_corrections; /* correction solves of the FP64 refinement (all steps)  */
+  int32_t refine_checks; /* steps whose FP64 residual was formed (aim_opts.refine_every) */
 } aim_stats;
 
 typedef struct {
@@ -146,6 +150,7 @@ typedef struct {
   int32_t preconditioner;/* AIM_PRECOND_*                                           */
   int64_t precond_nnz;   /* entries of the preconditioner's sparsity pattern          */
   int32_t refine;        /* aim_opts.refine as set up (0 on the complex128 path)       */
+  int32_t refine_every;  /* aim_opts.refine_every as set up (>= 1)                       */
   int32_t plan_zw, plan_cw, plan_rp, plan_ypb; /* launch shapes in use (see aim_opts.autotune) */
   int32_t plan_source;   /* AIM_PLAN_*                                                  */
   int32_t box_lo[3], box_hi[3]; /* active box: grid nodes (x, y, z) touched by some stencil
@@ -274,8 +279,9 @@ int aim_excitation_vector(aim_ctx* ctx, const aim_excitation* exc, int32_t step_
  * immediate system to relative residual tol, warm-started from I_{l-1}.
  *   currents: [n_steps][nb][ns] aim_c128, host or device (written step by step).
  *   stats: optional.  Returns AIM_ERR_NOCONV if a solve hits gmres_max_iter, or the
- *   FP64 refinement (aim_opts.refine) does not reach tol (steps up to stats->last_step
- *   are valid), AIM_WARN_UNSTABLE if the march completed with late-time growth.
+ *   FP64 refinement (aim_opts.refine) does not reach tol at a checked step (steps up to
+ *   stats->last_step are valid), AIM_WARN_UNSTABLE if the march completed with late-time
+ *   growth.
  */
 int aim_march(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double tol,
               aim_c128* currents, aim_stats* stats);

@@ -47,7 +47,7 @@ class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32),
-                ("refine", ct.c_int32), ("autotune", ct.c_int32)]
+                ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("autotune", ct.c_int32)]
 
 
 class aim_excitation(ct.Structure):
@@ -58,14 +58,14 @@ class aim_excitation(ct.Structure):
 class aim_stats(ct.Structure):
     _fields_ = [("last_step", ct.c_int32), ("total_iters", ct.c_int32), ("max_iters", ct.c_int32),
                 ("max_rel_res", ct.c_double), ("rhs_ms", ct.c_double), ("solve_ms", ct.c_double),
-                ("iters", ct.c_void_p), ("refine_corrections", ct.c_int32)]
+                ("iters", ct.c_void_p), ("refine_corrections", ct.c_int32), ("refine_checks", ct.c_int32)]
 
 
 class aim_info(ct.Structure):
     _fields_ = [("ns", ct.c_int32), ("n_delays", ct.c_int32), ("n_active", ct.c_int32),
                 ("near_nnz", ct.c_int64), ("grid_n", ct.c_int32), ("precision", ct.c_int32),
                 ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64),
-                ("refine", ct.c_int32), ("plan_zw", ct.c_int32), ("plan_cw", ct.c_int32), ("plan_rp", ct.c_int32),
+                ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("plan_zw", ct.c_int32), ("plan_cw", ct.c_int32), ("plan_rp", ct.c_int32),
                 ("plan_ypb", ct.c_int32), ("plan_source", ct.c_int32), ("box_lo", ct.c_int32 * 3),
                 ("box_hi", ct.c_int32 * 3)]
 
@@ -189,13 +189,14 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
               restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False,
-              refine=0, autotune=0):
+              refine=0, autotune=0, refine_every=1):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
     precond_radius, default the near radius).  zero_start: GMRES from zero instead of
     the previous step's currents.  refine (complex64 only): up to this many FP64
-    refinement corrections per step (0: off).  autotune: 0 default launch shapes, 1 tuned
-    at setup (cached plan reused), 2 tuned and cache refreshed."""
+    refinement corrections per step (0: off), checked every refine_every-th step.
+    autotune: 0 default launch shapes, 1 tuned at setup (cached plan reused), 2 tuned and
+    cache refreshed."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -205,7 +206,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
                     stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
-                    int(bool(zero_start)), int(refine), int(autotune))
+                    int(bool(zero_start)), int(refine), int(refine_every), int(autotune))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -288,7 +289,7 @@ def aim_march(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
     e, keep = _exc(khat, phat, sigma, t_d)
     cur = np.empty((n_steps, e.nb, ns), dtype=np.complex128) if out is None else out
     iters = np.zeros((n_steps, e.nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
     rc = lib.aim_march(ctx, ct.byref(e), int(n_steps), float(tol), _ptr(cur), ct.byref(st))
     stats = _stats(st, iters)
     _check(lib, ctx, rc, "aim_march", stats)
@@ -302,7 +303,7 @@ def aim_march_continue(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
     e, keep = _exc(khat, phat, sigma, t_d)
     cur = np.empty((n_steps, e.nb, ns), dtype=np.complex128) if out is None else out
     iters = np.zeros((n_steps, e.nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
     rc = lib.aim_march_continue(ctx, ct.byref(e), int(n_steps), float(tol), _ptr(cur), ct.byref(st))
     stats = _stats(st, iters)
     _check(lib, ctx, rc, "aim_march_continue", stats)
@@ -336,7 +337,7 @@ def aim_march_source(ctx, src, tol, transpose=False, out=None):
     n_steps, nb, ns = src.shape
     cur = _like(src, tuple(src.shape)) if out is None else out
     iters = np.zeros((n_steps, nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
     rc = lib.aim_march_source(ctx, int(bool(transpose)), int(nb), int(n_steps), _ptr(src), float(tol), _ptr(cur),
                               ct.byref(st))
     stats = _stats(st, iters)
@@ -350,7 +351,7 @@ def aim_march_adjoint(ctx, G, tol, out=None):
     n_steps, nb, ns = G.shape
     lam = _like(G, tuple(G.shape)) if out is None else out
     iters = np.zeros((n_steps, nb), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
     rc = lib.aim_march_adjoint(ctx, int(nb), int(n_steps), _ptr(G), float(tol), _ptr(lam), ct.byref(st))
     stats = _stats(st, iters)
     _check(lib, ctx, rc, "aim_march_adjoint", stats)
@@ -365,7 +366,7 @@ def aim_march_farfield(ctx, khat, phat, i0, a, n_steps, tol, rhat, e1, e2, n0, n
     r, u, v = _vec3(rhat), _vec3(e1), _vec3(e2)
     F = _like(a, (int(n_out), len(r), 2)) if out is None else out
     iters = np.zeros((int(n_steps), 1), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
     rc = lib.aim_march_farfield(ctx, k.ctypes.data, p.ctypes.data, int(i0), int(a.shape[0]), _ptr(a), int(n_steps),
                                 float(tol), len(r), r.ctypes.data, u.ctypes.data, v.ctypes.data, int(n0),
                                 int(n_out), _ptr(F), ct.byref(st))
@@ -381,7 +382,7 @@ def aim_march_adjoint_farfield(ctx, khat, phat, i0, n_samp, n_steps, tol, rhat, 
     r, u, v = _vec3(rhat), _vec3(e1), _vec3(e2)
     g = _like(F, (int(n_samp),)) if out is None else out
     iters = np.zeros((int(n_steps), 1), dtype=np.int32)
-    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
     rc = lib.aim_march_adjoint_farfield(ctx, k.ctypes.data, p.ctypes.data, int(i0), int(n_samp), int(n_steps),
                                         float(tol), len(r), r.ctypes.data, u.ctypes.data, v.ctypes.data, int(n0),
                                         int(F.shape[0]), _ptr(F), _ptr(g), ct.byref(st))
@@ -486,7 +487,7 @@ class AimContext:
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
                   precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine,
-                  autotune=w.autotune)
+                  refine_every=w.refine_every, autotune=w.autotune)
         kw.update(over)
         return cls(**kw)
 

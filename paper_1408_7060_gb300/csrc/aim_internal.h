@@ -237,6 +237,7 @@ struct aim_ctx {
   bool zero_start = false;     // GMRES initial guess 0 instead of the previous currents
   KPlan plan;                   // launch shapes of the grid passes
   int refine = 0;              // complex64 path: FP64-operator refinement sweeps per step (0: off)
+  int refine_every = 1;        // FP64 residual checked at every k-th step
   int ref_nb = 0;              // right-hand sides per FP64 residual product (its buffers' batch)
   void* d_A64 = nullptr;       // FP64 grid work buffers of the refinement residual ([ref_nb] x the
   void* d_Bf64 = nullptr;      // layouts of d_A, d_Bf, d_P), and its FP64 operator input

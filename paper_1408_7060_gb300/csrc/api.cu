@@ -89,6 +89,7 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->zero_start = opts->zero_start != 0;
   if (opts->refine < 0 || opts->refine > 64) throw AimError{AIM_ERR_ARG, "aim_setup: refine out of range"};
   c->refine = opts->precision == AIM_C64 ? opts->refine : 0;
+  c->refine_every = std::max(1, opts->refine_every);
   c->precond_radius = opts->precond_radius > 0 ? opts->precond_radius : near_radius;
   if (c->precond == AIM_PRECOND_NEAR_SAI && c->precond_radius < 0)
     throw AimError{AIM_ERR_ARG, "aim_setup: the SAI preconditioner needs a pattern radius or a near zone"};
@@ -400,6 +401,7 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   info->preconditioner = c->precond;
   info->precond_nnz = c->d_sai ? c->snnz : c->ns;
   info->refine = c->refine;
+  info->refine_every = c->refine_every;
   info->plan_zw = c->plan.zw;
   info->plan_cw = c->plan.cw;
   info->plan_rp = c->plan.rp;
@@ -887,6 +889,7 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
     stats->rhs_ms = 0;
     stats->solve_ms = 0;
     stats->refine_corrections = 0;
+    stats->refine_checks = 0;
   }
   int rc = AIM_OK;
   const int l0 = c->l_done;
@@ -924,7 +927,8 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
     int r_ref = AIM_OK, n_corr = 0;
     std::vector<int> its_ref(nb, 0);
     std::vector<double> res_ref;
-    if (c->refine > 0) {
+    const bool refining = c->refine > 0 && l % c->refine_every == 0;
+    if (refining) {
       AIM_CUDA(cudaStreamSynchronize(st));
       r_ref = refine_solution(c, nb, tol, its_ref, res_ref, n_corr);
     }
@@ -954,7 +958,7 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
       throw AimError{AIM_ERR_TIMEOUT, "a bounded wait of the delayed-sum kernel gave up at step " + std::to_string(l)};
     }
     int r;
-    if (c->refine > 0) {  // statistics gathered by the refinement (solves and FP64 residuals)
+    if (refining) {  // statistics gathered by the refinement (solves and FP64 residuals)
       r = r_ref;
       its = its_ref;
       res = res_ref;
@@ -978,12 +982,13 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
       }
       stats->last_step = l;
       stats->refine_corrections += n_corr;
+      stats->refine_checks += refining ? 1 : 0;
     }
     c->l_done = l;
     prof_flush(c);
     if (r != AIM_OK) {
       if (stats) stats->last_step = l - 1;
-      c->err = (c->refine > 0 ? "GMRES reached its iteration cap or the FP64 refinement did not reach tol at step "
+      c->err = (refining ? "GMRES reached its iteration cap or the FP64 refinement did not reach tol at step "
                                : "GMRES reached its iteration cap at step ") +
                std::to_string(l);
       rc = r;

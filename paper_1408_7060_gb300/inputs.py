@@ -247,6 +247,7 @@ class Workload:
     precond_radius: float = 0.0  # SAI pattern radius (m); 0: the near radius
     zero_start: bool = False  # GMRES from zero instead of the previous step's currents
     refine: int = 0        # complex64 path: FP64 refinement corrections per step (0: off)
+    refine_every: int = 1  # the FP64 residual checked at every k-th step
     autotune: int = 0      # launch shapes: 0 defaults, 1 tuned at setup (cache reused), 2 re-tuned
 
     @property

@@ -75,3 +75,23 @@ def test_refinement_with_batch_and_sai():
     assert st["max_rel_res"] <= tol
     for b in range(3):
         assert rel(i64r[:, b], i128[:, b]) < 1e-5, b
+
+
+@pytest.mark.parametrize("every", [1, 4])
+def test_refine_every_kth_step(every):
+    """aim_opts.refine_every = k forms the FP64 residual (and corrects) at every k-th step
+    only; the other steps keep the complex64 solve.  On the 480-RWG sphere (40 steps,
+    tol 1e-6): the number of checked steps is 40 / k, every reported residual meets tol
+    and the march agrees with the complex128 march within the 1e-4 bound."""
+    from paper_1408_7060_gb300 import AimContext
+
+    w = make_workload("sphere480")
+    nt, tol = 40, 1e-6
+    with AimContext.from_workload(w, precision="c128") as c:
+        i128, _, _ = c.march(w.khat, w.phat, w.sigma, w.t_d, nt, tol)
+    with AimContext.from_workload(w, precision="c64", refine=6, refine_every=every) as c:
+        assert c.info["refine_every"] == every
+        i64r, st, rc = c.march(w.khat, w.phat, w.sigma, w.t_d, nt, tol)
+    assert st["last_step"] == nt and st["max_rel_res"] <= tol
+    assert st["refine_checks"] == nt // every
+    assert rel(i64r, i128) < 1e-4
