@@ -83,20 +83,22 @@ def kernel_digest(kind):
 TRAFFIC = {}
 
 
-def kernel_bytes(kind, N, ns, nnz, ng, nb, box=None, esz=8):
+def kernel_bytes(kind, N, ns, nnz, ng, nb, box=None, esz=8, lz=None):
     """Algorithmic HBM bytes of one launch of each kernel (each byte counted once), for the
     grid lines each pass touches: with the active box (nx, ny, nz nodes per axis) the
     anterpolation writes the box rows of A, the forward y pass reads them and writes the
     box-z rows of the slab, the z pass reads and writes those rows, the inverse y pass
-    writes the box rows of A and the inverse x pass the box of P."""
+    writes the box rows of A and the inverse x pass the box of P.  lz: the length of the
+    z transform (2N without a shorter one)."""
     L = 2 * N
+    lz = lz or L
     bx, by, bz = box if box else (N, N, N)
     slab = 4 * bz * L * L * esz * nb          # [nb][4][z in box][L][L]
-    spec = 4 * L * L * L * esz * nb           # [nb][4][L][L][L]: z-spectrum of a slab (power-of-two L)
-    pow2 = (L & (L - 1)) == 0
+    spec = 4 * lz * L * L * esz * nb          # [nb][4][lz][L][L]: z-spectrum of a slab (power-of-two lz)
+    pow2 = (lz & (lz - 1)) == 0
     A = 4 * bz * by * L * esz * nb            # [nb][4][z, y in box][L]
     P = 4 * bz * by * bx * esz * nb           # [nb][4][box]
-    oct_ = (N + 1) ** 3 * esz                 # one kernel spectrum octant
+    oct_ = (N + 1) ** 2 * (lz // 2 + 1) * esz  # one kernel spectrum octant
     lam = ns * 256 * (esz // 2)               # interpolation rows
     csrT = 64 * ns * (4 + 2 * esz) + (bz * by * N + 1) * 4
     near = nnz * (4 + 16) + (ns + 1) * 4
@@ -120,18 +122,19 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 ALU_KERNELS = ("zconv", "zrhs")
 
 
-def kernel_flops(kind, N, nb, ng):
+def kernel_flops(kind, N, nb, ng, lz=None):
     """Algorithmic FP32 flops of one launch of the z-pass kernels: per z column the
-    conventional 5 L log2 L of a length-L complex FFT forward and inverse, and 6 L for the
-    product with the kernel spectrum (the delay sum: N_g forward transforms and products,
-    one inverse); 4 nb L^2 columns per launch."""
+    conventional 5 n log2 n of a length-n complex FFT (n = lz, the z transform length)
+    forward and inverse, and 6 n for the product with the kernel spectrum (the delay sum:
+    N_g forward transforms and products, one inverse); 4 nb L^2 columns per launch."""
     L = 2 * N
-    fft = 5 * L * math.log2(L)
+    n = lz or L
+    fft = 5 * n * math.log2(n)
     cols = 4 * nb * L * L
     if kind == "zconv":
-        return cols * (2 * fft + 6 * L)
+        return cols * (2 * fft + 6 * n)
     if kind == "zrhs":
-        return cols * ((ng + 1) * fft + 8 * ng * L)
+        return cols * ((ng + 1) * fft + 8 * ng * n)
     return None
 
 
@@ -206,22 +209,38 @@ def log(*a):
 
 # --------------------------------------------------------------------------- memory plan
 
+Z_LENGTHS = (16, 32, 64, 128, 192, 256, 768)   # z transform lengths the library is built for
+
+
+def box_depth(w):
+    """Estimated z-planes of the active box (the stencils of edges between the mesh's
+    lowest and highest vertices, 4 nodes each) and the z transform length the context
+    picks for it (the shortest built length >= 2 nz)."""
+    V = w.mesh[0]
+    N, L = w.grid_n, 2 * w.grid_n
+    nz = min(N, int((V[:, 2].max() - V[:, 2].min()) / w.h) + 5)
+    lz = next((n for n in Z_LENGTHS if 2 * nz <= n <= L), L)
+    return nz, lz
+
+
 def chunk_size(w, ng_est, refine, total_bytes, restart=50):
     """Right-hand sides per context that fit in device memory: per-RHS work buffers and
-    history ring (x/y-transformed slabs for lengths with a factor 3, z-spectra for
-    powers of two) against the tables (kernel octants in both precisions, anterpolation,
-    near zone and preconditioner estimated at 80 entries per row, FP64 refinement
-    buffers for one RHS) and a 6 GB margin."""
+    history ring over the box's z-planes (x/y-transformed slabs for z lengths with a
+    factor 3, z-spectra for powers of two) against the tables (kernel octants in both
+    precisions, anterpolation, near zone and preconditioner estimated at 80 entries per
+    row, FP64 refinement buffers of up to 8 GiB) and a 6 GB margin."""
     N, L = w.grid_n, 2 * w.grid_n
+    nz, lz = box_depth(w)
     V, F = w.mesh
     ns = len(F) * 3 // 2
     es = 8
-    Z = L if (L & (L - 1)) == 0 else N
-    per = es * 4 * (N * N * L + N * L * L + N ** 3) + ng_est * es * 4 * Z * L * L + ns * 16 * (restart + 2 * ng_est + 10)
-    base = (ng_est + 1) * 2 * (N + 1) ** 3 * 24 + ns * 256 * 12 + 64 * ns * 52 + 4 * N ** 3
+    Z = lz if (lz & (lz - 1)) == 0 else nz
+    grid = 4 * nz * (N * L + L * L + N * N)
+    per = es * grid + ng_est * es * 4 * Z * L * L + ns * 16 * (restart + 2 * ng_est + 10)
+    base = (ng_est + 1) * 2 * (N + 1) ** 2 * (lz // 2 + 1) * 24 + ns * 256 * 12 + 64 * ns * 52 + 4 * N ** 3
     base += ns * 80 * (16 * (ng_est + 1) + 8 + 24)
     if refine:
-        base += 16 * 4 * (N * N * L + N * L * L + N ** 3)
+        base += min(16 * grid * 16, 8 << 30)
     return max(1, int((total_bytes - base - 6e9) // per))
 
 
@@ -347,7 +366,8 @@ def run_aim(args):
     # roofline of the dominant operator kernel (algorithmic bytes / event time)
     hbm, src = load_peaks()
     box = tuple(hi - lo + 1 for lo, hi in zip(info["box_lo"], info["box_hi"]))
-    kb = lambda kind: kernel_bytes(kind, w.grid_n, ns, info["near_nnz"], info["n_delays"], prof_nb, box)
+    lz = info["z_len"]
+    kb = lambda kind: kernel_bytes(kind, w.grid_n, ns, info["near_nnz"], info["n_delays"], prof_nb, box, lz=lz)
     tot_ms = sum(v[1] for v in prof.values()) or 1e-12
     kernels = {}
     for kind, (n_l, ms_l) in prof.items():
@@ -359,7 +379,7 @@ def run_aim(args):
                          "frac": round(b / (ms_l / n_l * 1e-3) / 1e9 / hbm, 4) if b and ms_l > 0 else None}
     for kind in ALU_KERNELS:
         if kind in kernels and kernels[kind]["ms"] > 0:
-            fl = kernel_flops(kind, w.grid_n, prof_nb, info["n_delays"])
+            fl = kernel_flops(kind, w.grid_n, prof_nb, info["n_delays"], lz)
             tf = fl / (kernels[kind]["ms"] / kernels[kind]["launches"] * 1e-3) / 1e12
             kernels[kind]["tflops"] = round(tf, 2)
             kernels[kind]["alu_frac"] = round(tf / FP32_PEAK_TFLOPS, 4)
@@ -372,7 +392,8 @@ def run_aim(args):
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 grid / f64 solve + f64 refinement" if w.refine else "c64 grid / f64 solve",
         "data": "synthetic",
-        "config": {"workload": w.name, "ns": ns, "grid": f"{w.grid_n}^3 -> {2 * w.grid_n}^3 FFT",
+        "config": {"workload": w.name, "ns": ns, "grid": f"{w.grid_n}^3",
+                   "fft": f"{2 * w.grid_n} x {2 * w.grid_n} x {lz} (z: {box[2]} box planes)",
                    "n_delays": info["n_delays"], "near_nnz": info["near_nnz"], "plane_waves": nw,
                    "waves_per_context": chunk, "chunks": len(chunks), "tol": w.tol, "chi": round(w.chi, 3),
                    "precond": w.precond, "precond_radius_m": round(w.precond_radius, 6),
@@ -389,7 +410,7 @@ def run_aim(args):
         "refine_corrections_per_step": round(corr / (K * len(chunks)), 2),
         "split_ms_per_step": {"rhs": round(float(np.mean([s[0] for s in split])) * len(chunks), 3),
                               "solve": round(float(np.mean([s[1] for s in split])) * len(chunks), 3)},
-        "roofline": roofline_entry(dom, kb(dom), kernel_flops(dom, w.grid_n, prof_nb, info["n_delays"]),
+        "roofline": roofline_entry(dom, kb(dom), kernel_flops(dom, w.grid_n, prof_nb, info["n_delays"], lz),
                                    per_launch_ms, hbm, src, w.name, prof_nb),
         "kernels": kernels,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nw * 6 * 8, "d2h_bytes_per_step": nw * ns * 16},

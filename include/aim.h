@@ -157,7 +157,13 @@ typedef struct {
                             lie in [box_lo, box_hi] (inclusive).  Sources vanish outside it
                             and potentials are needed only inside it, so every FFT pass but
                             the z pass (all lines, reading and writing only z in the box)
-                            runs on the box's lines only.                               */
+                            runs on the box's lines only, and the grid buffers hold the
+                            box's z-planes only.                                          */
+  int32_t z_len;         /* length of the z transform: the shortest supported length
+                            >= 2 (box_hi[2] - box_lo[2] + 1) (at most 2N).  The linear
+                            convolution over the box's z-planes needs z offsets below the
+                            box depth only, so this circular length gives the values of
+                            the 2N padding on them.                                       */
 } aim_info;
 
 enum { AIM_PLAN_DEFAULT = 0, AIM_PLAN_MEASURED = 1, AIM_PLAN_CACHED = 2 };
@@ -244,9 +250,10 @@ int aim_matvec(aim_ctx* ctx, int32_t delay_m, int32_t nb, const aim_c128* x, aim
  *   Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).  The
  *   grid work space comes from one fixed 16 MiB device array in the library, held by
  *   every GPU that loads it until process exit; the context's other tables are used
- *   as set up by aim_setup.  nb * 4 * (N*N*2N + N*2N*2N + N^3) elements (complex64 or
- *   complex128 by precision) must fit in 16 MiB, else AIM_ERR_ARG (e.g. N <= 32 in
- *   complex64 for one right-hand side).  The first call on a device looks up the
+ *   as set up by aim_setup.  nb * 4 * nz * (N*2N + 2N*2N + N^2) elements (complex64 or
+ *   complex128 by precision; nz = the active box's z-planes, aim_info.box_lo/box_hi)
+ *   must fit in 16 MiB, else AIM_ERR_ARG (e.g. N <= 32 in complex64 for one
+ *   right-hand side).  The first call on a device looks up the
  *   array's device address (cudaGetSymbolAddress) with that device current and keeps
  *   it for the process; the kept address does not survive cudaDeviceReset, so do not
  *   call this entry point on a device after resetting it.  All calls share the array,
@@ -378,9 +385,11 @@ int aim_farfield_adjoint(aim_ctx* ctx, int32_t nd, const double* rhat, const dou
  *     stencil node t = (dz*4 + dy)*4 + dx).
  *   aim_get_near: rowptr [ns+1], col [nnz], val [(N_g+1)][nnz] aim_c128 (the
  *     pre-corrected Z~near_m).
- *   aim_get_kernel_spectrum: the stored octant [(N+1)^3] of the padded-grid
- *     spectrum of G^A_m (kind 0) or G^phi_m (kind 1), including the folded constants
- *     mu/(4 pi) or 1/(4 pi eps) and 1/(2N)^3.
+ *   aim_get_kernel_spectrum: the stored octant [z_len/2 + 1][N+1][N+1] (kz, ky, kx) of
+ *     the spectrum of G^A_m (kind 0) or G^phi_m (kind 1) on the (2N, 2N, z_len) padded
+ *     grid (offsets |d| < N in x and y, |dz| < z_len/2 in z, even-symmetric
+ *     embedding), including the folded constants mu/(4 pi) or 1/(4 pi eps) and
+ *     1/(4 N^2 z_len).
  *   aim_get_preconditioner: the right preconditioner M in CSR form: rowptr [ns+1],
  *     col [precond_nnz], val [precond_nnz] aim_c128 with val[e] = M[row, col[e]]
  *     (AIM_PRECOND_DIAG: one diagonal entry per row).

@@ -67,7 +67,7 @@ class aim_info(ct.Structure):
                 ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64),
                 ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("plan_zw", ct.c_int32), ("plan_cw", ct.c_int32), ("plan_rp", ct.c_int32),
                 ("plan_ypb", ct.c_int32), ("plan_source", ct.c_int32), ("box_lo", ct.c_int32 * 3),
-                ("box_hi", ct.c_int32 * 3)]
+                ("box_hi", ct.c_int32 * 3), ("z_len", ct.c_int32)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
@@ -466,8 +466,9 @@ def aim_get_preconditioner(ctx):
 
 def aim_get_kernel_spectrum(ctx, m, kind):
     lib = load()
-    n = aim_get_info(ctx)["grid_n"] + 1
-    out = np.empty((n, n, n), dtype=np.complex128)
+    info = aim_get_info(ctx)
+    n = info["grid_n"] + 1
+    out = np.empty((info["z_len"] // 2 + 1, n, n), dtype=np.complex128)
     _check(lib, ctx, lib.aim_get_kernel_spectrum(ctx, int(m), int(kind), out.ctypes.data), "aim_get_kernel_spectrum")
     return out
 

@@ -177,12 +177,20 @@ struct ProfState {
   long long launches = 0;
 };
 
+struct aim_ctx;
+// elements of the grid work buffers for nb right-hand sides (layouts above d_A, d_Bf, d_P)
+size_t grid_a_elems(const aim_ctx* c, int nb);
+size_t grid_bf_elems(const aim_ctx* c, int nb);
+size_t grid_p_elems(const aim_ctx* c, int nb);
+
 struct aim_ctx {
   // problem
   int ns = 0, nt = 0, nv = 0;
   int N = 0, L = 0;            // grid nodes per axis, padded length 2N
   int box_lo[3] = {0, 0, 0};   // active box: the nodes (x, y, z) some stencil touches lie in
   int box_hi[3] = {0, 0, 0};   // [box_lo, box_hi] per axis (inclusive); the FFT passes prune to it
+  int NZ = 0;                  // z-planes held by the grid buffers: the box's, box_lo[2] .. box_hi[2]
+  int LZ = 0;                  // z transform length: the shortest supported length >= 2 NZ
   double h = 0, origin[3] = {0, 0, 0};
   double dt = 0, f_c = 0, wc = 0, kc = 0, near_radius = 0;
   TBasis tb{};
@@ -223,10 +231,12 @@ struct aim_ctx {
   double4_32a* d_ncoef = nullptr;  // [64 ns]  (x, y, z, div) coefficients
   float4* d_ncoeff = nullptr;  // [64 ns]  FP32 copy
 
-  double2* d_kspec = nullptr;  // [(N_g+1)][2][(N+1)^3] kernel spectra octant (FP64)
+  double2* d_kspec = nullptr;  // [(N_g+1)][2][LZ/2+1][N+1][N+1] kernel spectra octant (FP64)
   float2* d_kspecf = nullptr;  // FP32 copy
   double2* d_tw = nullptr;     // [L] twiddles W_L^t (FP64)
   float2* d_twf = nullptr;     // [L] FP32
+  double2* d_twz = nullptr;    // [LZ] twiddles W_LZ^t of the z transform (FP64)
+  float2* d_twzf = nullptr;    // [LZ] FP32
 
   int* d_rowptr = nullptr;     // [ns+1] near CSR
   int* d_col = nullptr;        // [nnz]
@@ -255,12 +265,12 @@ struct aim_ctx {
   double2* d_nearT = nullptr;  // [(N_g+1)][nnz] values of the transposed near matrices (lazy)
 
   // ---- work buffers (sized for batch_max) ----
-  void* d_A = nullptr;         // [B][4][N][N][L]   after the x pass
-  void* d_Bf = nullptr;        // [B][4][N][L][L]   after the y pass (z<N slab)
-  void* d_P = nullptr;         // [B][4][N][N][N]   potentials on the grid
-  void* d_ring = nullptr;      // [N_g][B][4][Z][L][L] history slabs: z-spectra (Z = L, power-of-two L)
-                               // or x/y-transformed grids (Z = N)
-  CUtensorMap ring_map;        // TMA view of the ring [slot][B*4*N][L][L] (complex64, power-of-two L)
+  void* d_A = nullptr;         // [B][4][NZ][N][L]  after the x pass
+  void* d_Bf = nullptr;        // [B][4][NZ][L][L]  after the y pass (the slab)
+  void* d_P = nullptr;         // [B][4][NZ][N][N]  potentials on the grid
+  void* d_ring = nullptr;      // [N_g][B][4][Z][L][L] history slabs: z-spectra (Z = LZ, power-of-two
+                               // LZ) or x/y-transformed grids (Z = NZ)
+  CUtensorMap ring_map;        // TMA view of the ring [slot][B*4*LZ][L][L] (complex64, power-of-two LZ)
   bool ring_tma = false;
   int* d_err = nullptr;        // device error flag (a bounded wait gave up)
   void* d_xs = nullptr;        // [B][ns] prepared operator input, grid precision

@@ -62,6 +62,14 @@ T* upload(aim_ctx* c, const std::vector<T>& v) {
 
 size_t grid_elem(const aim_ctx* c) { return c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2); }
 
+// z transform length for nz box planes: the shortest length of the z pass >= 2 nz (at most
+// the padded length L = 2N >= 2 nz)
+static int z_length(int nz, int L) {
+  for (int lz : {16, 32, 64, 128, 192, 256, 768})
+    if (lz >= 2 * nz && lz <= L) return lz;
+  return L;
+}
+
 void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double near_radius, double dt,
                 aim_tbasis tb, const aim_opts* opts) {
   if (!mesh || !grid || !opts) throw AimError{AIM_ERR_ARG, "null argument"};
@@ -128,6 +136,8 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
       c->box_lo[d] = std::min(c->box_lo[d], anchor[3 * k + d]);
       c->box_hi[d] = std::max(c->box_hi[d], anchor[3 * k + d] + 3);
     }
+  c->NZ = c->box_hi[2] - c->box_lo[2] + 1;
+  c->LZ = z_length(c->NZ, c->L);
 
   c->d_v = upload(c, hm.V);
   c->d_tri = upload(c, hm.F);
@@ -149,11 +159,11 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   setup_device_tables(c, hm, anchor);
 
   // work buffers
-  const int B = c->batch_max, N = c->N, L = c->L, ns = c->ns, ng = c->n_delays;
+  const int B = c->batch_max, ns = c->ns, ng = c->n_delays;
   const size_t es = grid_elem(c);
-  c->d_A = aim_alloc(c, (size_t)B * 4 * N * N * L * es);
-  c->d_Bf = aim_alloc(c, (size_t)B * 4 * N * L * L * es);
-  c->d_P = aim_alloc(c, (size_t)B * 4 * N * N * N * es);
+  c->d_A = aim_alloc(c, grid_a_elems(c, B) * es);
+  c->d_Bf = aim_alloc(c, grid_bf_elems(c, B) * es);
+  c->d_P = aim_alloc(c, grid_p_elems(c, B) * es);
   c->d_xs = aim_alloc(c, (size_t)B * ns * es);
   c->d_xd = (double2*)aim_alloc(c, (size_t)B * ns * sizeof(double2));
   c->d_vf = (float2*)aim_alloc(c, (size_t)B * ns * sizeof(float2));
@@ -173,13 +183,13 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   if (c->refine > 0) {
     // FP64 grid buffers for the refinement residual, for as many right-hand sides at a
     // time as fit in 8 GiB (at least one)
-    const size_t per = (size_t)4 * ((size_t)N * N * L + (size_t)N * L * L + (size_t)N * N * N) * sizeof(double2);
+    const size_t per = (grid_a_elems(c, 1) + grid_bf_elems(c, 1) + grid_p_elems(c, 1)) * sizeof(double2);
     c->ref_nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, (size_t(8) << 30) / per));
-    const size_t rb = (size_t)c->ref_nb;
-    c->d_A64 = aim_alloc(c, rb * 4 * N * N * L * sizeof(double2));
-    c->d_Bf64 = aim_alloc(c, rb * 4 * N * L * L * sizeof(double2));
-    c->d_P64 = aim_alloc(c, rb * 4 * N * N * N * sizeof(double2));
-    c->d_xs64 = aim_alloc(c, rb * ns * sizeof(double2));
+    const int rb = c->ref_nb;
+    c->d_A64 = aim_alloc(c, grid_a_elems(c, rb) * sizeof(double2));
+    c->d_Bf64 = aim_alloc(c, grid_bf_elems(c, rb) * sizeof(double2));
+    c->d_P64 = aim_alloc(c, grid_p_elems(c, rb) * sizeof(double2));
+    c->d_xs64 = aim_alloc(c, (size_t)rb * ns * sizeof(double2));
     c->d_rn = (double*)aim_alloc(c, 2 * (size_t)B * sizeof(double));
     AIM_CUDA(cudaMallocHost(&c->h_rn, 2 * (size_t)B * sizeof(double)));
   }
@@ -211,14 +221,14 @@ void ensure_ring(aim_ctx* c) {
   if (c->d_ring) return;
   const size_t slab = op_slab_bytes(c, c->batch_max);
   c->d_ring = aim_alloc(c, (size_t)c->n_delays * slab);
-  // TMA view for the complex64 delayed sum over the z-spectra: [slot][B*4*L][L][L],
-  // boxes of 16 x 1 x L x 1
-  const int L = c->L;
-  if (c->precision == AIM_C64 && (L & (L - 1)) == 0 && L <= 256) {
-    const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)c->batch_max * 4 * L,
+  // TMA view for the complex64 delayed sum over the z-spectra: [slot][B*4*LZ][L][L],
+  // boxes of 16 x 1 x LZ x 1
+  const int L = c->L, LZ = c->LZ;
+  if (c->precision == AIM_C64 && (LZ & (LZ - 1)) == 0 && LZ <= 256 && L <= 256) {
+    const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)c->batch_max * 4 * LZ,
                                 (cuuint64_t)c->n_delays};
     const cuuint64_t strides[3] = {(cuuint64_t)L * 8, (cuuint64_t)L * L * 8, (cuuint64_t)slab};
-    const cuuint32_t box[4] = {(cuuint32_t)(L < 16 ? L : 16), 1, (cuuint32_t)L, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)(L < 16 ? L : 16), 1, (cuuint32_t)LZ, 1};
     c->ring_tma = encode_tiled_map(&c->ring_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c->d_ring, dims, strides, box);
   }
 }
@@ -411,6 +421,7 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
     info->box_lo[d] = c->box_lo[d];
     info->box_hi[d] = c->box_hi[d];
   }
+  info->z_len = c->LZ;
   return AIM_OK;
 }
 
@@ -813,7 +824,7 @@ int aim_get_kernel_spectrum(const aim_ctx* c, int32_t m, int32_t kind, aim_c128*
   return guard(const_cast<aim_ctx*>(c), [&] {
     if (!out || m < 0 || m > c->n_delays || kind < 0 || kind > 1)
       throw AimError{AIM_ERR_ARG, "aim_get_kernel_spectrum: bad delay or kind"};
-    const size_t oct = (size_t)(c->N + 1) * (c->N + 1) * (c->N + 1);
+    const size_t oct = (size_t)(c->N + 1) * (c->N + 1) * (c->LZ / 2 + 1);
     AIM_CUDA(cudaMemcpy(out, c->d_kspec + ((size_t)m * 2 + kind) * oct, oct * sizeof(double2),
                         cudaMemcpyDeviceToHost));
     return AIM_OK;

@@ -68,14 +68,14 @@ __global__ void __launch_bounds__(256) k_rows(const C* __restrict__ in, C* __res
   }
 }
 
-// Rows of a box of the grid: row r (0 <= r < nbc * nz * ny) is grid row
-// ((bc * N + z0 + zz) * N + y0 + yy) with (bc, zz, yy) its coordinates in the box; the
-// whole grid is the box nz = ny = N, z0 = y0 = 0.
+// Rows of a box of a buffer of np planes of N rows per (right-hand side, component):
+// row r (0 <= r < nbc * nz * ny) is buffer row ((bc * np + z0 + zz) * N + y0 + yy) with
+// (bc, zz, yy) its coordinates in the box.
 struct RowBox {
-  int nz, ny, z0, y0, N;
+  int nz, ny, z0, y0, np, N;
   __device__ __forceinline__ long long row(int r) const {
     const int yy = r % ny, q = r / ny, zz = q % nz, bc = q / nz;
-    return ((long long)bc * N + z0 + zz) * N + y0 + yy;
+    return ((long long)bc * np + z0 + zz) * N + y0 + yy;
   }
 };
 

@@ -71,10 +71,9 @@ extern "C" int aim_matvec_noalloc(aim_ctx* c, int32_t m, int32_t nb, const aim_c
     if (!x || !y || nb < 1 || nb > c->batch_max || m < 0 || m > c->n_delays)
       throw AimError{AIM_ERR_ARG, "aim_matvec_noalloc: bad delay, batch or pointer"};
     const size_t es = c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2);
-    const size_t N = c->N, L = c->L;
-    const size_t a = round256((size_t)nb * 4 * N * N * L * es);
-    const size_t bf = round256((size_t)nb * 4 * N * L * L * es);
-    const size_t p = round256((size_t)nb * 4 * N * N * N * es);
+    const size_t a = round256(grid_a_elems(c, nb) * es);
+    const size_t bf = round256(grid_bf_elems(c, nb) * es);
+    const size_t p = round256(grid_p_elems(c, nb) * es);
     if (a + bf + p > kNoAllocScratchBytes)
       throw AimError{AIM_ERR_ARG, "aim_matvec_noalloc: grid work space of " + std::to_string(a + bf + p) +
                                       " bytes exceeds the fixed 16 MiB array (use aim_matvec)"};

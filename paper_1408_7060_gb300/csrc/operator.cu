@@ -79,7 +79,7 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
 
 // ---------------------------------------------------------------- launch plans
 // The plan cache: one JSON object per line,
-//   {"key": "<gpu name>|L=<L>|prec=<c64|c128>|nb=<batch>", "zw": .., "cw": .., "rp": .., "ypb": ..}
+//   {"key": "<gpu name>|L=<L>|LZ=<LZ>|prec=<c64|c128>|nb=<batch>", "zw": .., "cw": .., "rp": .., "ypb": ..}
 // in the file named by AIM_GB300_PLAN_CACHE, else $HOME/.cache/aim_gb300_plans.jsonl.
 namespace {
 std::string plan_cache_path() {
@@ -96,7 +96,7 @@ std::string plan_key(const aim_ctx* c) {
   cudaGetLastError();
   for (char& ch : name)
     if (ch == '"' || ch == '|') ch = '_';
-  return name + "|L=" + std::to_string(c->L) + "|prec=" + (c->precision == AIM_C64 ? "c64" : "c128") +
+  return name + "|L=" + std::to_string(c->L) + "|LZ=" + std::to_string(c->LZ) + "|prec=" + (c->precision == AIM_C64 ? "c64" : "c128") +
          "|nb=" + std::to_string(c->batch_max);
 }
 
@@ -162,10 +162,14 @@ void op_autotune(aim_ctx* c, int mode) {
 // kernels one operator application launches: prep, anterp + x, y, z, y^-1, x^-1, interp
 int op_kernel_count(const aim_ctx*) { return 7; }
 
-// bytes of one history slab: [nb][4][Z][L][L] with Z = L (z-transformed, power-of-two L)
-// or N (x/y-transformed only)
+size_t grid_a_elems(const aim_ctx* c, int nb) { return (size_t)nb * 4 * c->NZ * c->N * c->L; }
+size_t grid_bf_elems(const aim_ctx* c, int nb) { return (size_t)nb * 4 * c->NZ * c->L * c->L; }
+size_t grid_p_elems(const aim_ctx* c, int nb) { return (size_t)nb * 4 * c->NZ * c->N * c->N; }
+
+// bytes of one history slab: [nb][4][Z][L][L] with Z = LZ (z-transformed, power-of-two
+// LZ) or NZ (x/y-transformed only)
 size_t op_slab_bytes(const aim_ctx* c, int nb) {
-  const int L = c->L, Z = (L & (L - 1)) == 0 ? L : c->N;
+  const int L = c->L, Z = (c->LZ & (c->LZ - 1)) == 0 ? c->LZ : c->NZ;
   return (size_t)nb * 4 * Z * (size_t)L * L * (c->precision == AIM_C64 ? sizeof(float2) : sizeof(double2));
 }
 

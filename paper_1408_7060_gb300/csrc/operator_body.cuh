@@ -33,12 +33,12 @@ void body_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv
   });
 }
 
-// a history slab: x/y-transformed (factor-3 lengths) or, for power-of-two lengths, also
-// z-transformed (through Bf, which must not be dst)
+// a history slab: x/y-transformed (factor-3 z lengths) or, for power-of-two z lengths,
+// also z-transformed (through Bf, which must not be dst)
 template <class C>
 void body_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst) {
   AIM_DISPATCH_L(c->L, {
-    if constexpr (pow2_len(LL)) {
+    if (pow2_len(c->LZ)) {
       GridOps<LL, C>::forward_slab(c, nb, v, nullptr, nullptr, reinterpret_cast<C*>(c->d_Bf));
       GridOps<LL, C>::zfwd(c, nb, reinterpret_cast<C*>(dst));
     } else {

@@ -1,14 +1,15 @@
 // The ET-AIM operator on the device (Eq. 5, Sec. 4 stages i-iv), templated on the
 // complex type of the grid stages (float2: complex64 path, double2: plain path).
 //
-// Data layout per right-hand side b and component c (x, y, z, div), with L = 2N:
-//   A  [b][c][z<N][y<N][x<L]   after anterpolation + forward x-FFT
-//   Bf [b][c][z<N][y<L][x<L]   after the forward y-FFT (the z<N slab)
-//   P  [b][c][z<N][y<N][x<N]   potentials after the inverse passes
-// The forward z-FFT, the pointwise kernel product and the inverse z-FFT are one
-// kernel per column (k_zconv / k_zrhs), so the full (2N)^3 spectrum never reaches
-// memory.  Zero padding is pruned in every pass: forward passes read only the N
-// non-zero inputs, inverse passes write only the N needed outputs.
+// Data layout per right-hand side b and component c (x, y, z, div), with L = 2N and the
+// nz z-planes z0 .. z0 + nz - 1 of the active box (the nodes some stencil touches):
+//   A  [b][c][nz][y<N][x<L]   after anterpolation + forward x-FFT
+//   Bf [b][c][nz][y<L][x<L]   after the forward y-FFT (the slab)
+//   P  [b][c][nz][y<N][x<N]   potentials after the inverse passes
+// The forward z-FFT (length LZ >= 2 nz), the pointwise kernel product and the inverse
+// z-FFT are one kernel per column (k_zconv / k_zrhs), so no 3-D spectrum reaches
+// memory.  Zero padding is pruned in every pass: forward passes read only the non-zero
+// inputs, inverse passes write only the needed outputs.
 #pragma once
 #include <algorithm>
 #include <functional>
@@ -31,7 +32,7 @@ template <> __device__ __forceinline__ double2 cvt<double2>(double2 a) { return 
 // ---------------------------------------------------------------- stage i + x pass
 // S_c[n] = sum_k L_c[n,k] x_k gathered node by node (the transpose of the
 // interpolation rows), then the forward x-FFT of each grid row.  One block holds
-// the 4 components of ypb consecutive rows (z, y); grid (nb, rows / ypb, N) with the
+// the 4 components of ypb consecutive rows (z, y); grid (nb, rows / ypb, nz) with the
 // right-hand side fastest, so the CSR rows a block gathers serve the other right-hand
 // sides from L2.
 template <int L, class C>
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
                                                      const typename Real<C>::F4* __restrict__ ncoef,
                                                      const C* __restrict__ xs, const int* __restrict__ active,
                                                      int ns, int N, int ypb, C* __restrict__ A,
-                                                     const C* __restrict__ twg, int ylo, int yhi, int zlo) {
+                                                     const C* __restrict__ twg, int ylo, int yhi, int zlo, int nz) {
   pdl_wait();
   using R = typename Real<C>::T;
   const int b = blockIdx.x;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
   }
   for (int t = threadIdx.x; t < 4 * ypb * L; t += blockDim.x) {
     const int row = t / L, x = t % L, c = row / ypb, y = y0 + row % ypb;
-    if (y <= yhi) A[((((size_t)b * 4 + c) * N + z) * N + y) * L + x] = res[t];
+    if (y <= yhi) A[((((size_t)b * 4 + c) * nz + blockIdx.z) * N + y) * L + x] = res[t];
   }
   pdl_trigger();
 }
@@ -200,48 +201,53 @@ __global__ void __launch_bounds__(256) k_prep_sai(const double2* __restrict__ v,
 // ---------------------------------------------------------------- z pass with the kernel
 __device__ __forceinline__ int fold(int k, int N) { return k <= N ? k : 2 * N - k; }
 
-// Two-step L = R1 * R2, one tile of W adjacent z-columns per block, a single
+// Geometry of a z pass.  The slab holds the nz z-planes of the active box (plane p is grid
+// z = box_lo + p), each an L x L plane of x/y spectra.  The z transform length LZ (a
+// template parameter) is at least 2 nz: the linear convolution of nz planes with the
+// kernel needs offsets |dz| < nz only, so a circular convolution of any length >= 2 nz - 1
+// gives the same values on the nz output planes as the 2N-point padding.  The kernel
+// spectrum octant is [LZ/2 + 1][N + 1][N + 1] (z, y, x).
+struct ZGeom {
+  int L;   // x/y padded length 2N
+  int N;   // L / 2 (x/y fold of the kernel octant)
+  int nz;  // z planes of the slab: input samples 0 .. nz-1, outputs kept 0 .. nz-1
+};
+
+// Two-step LZ = R1 * R2, one tile of W adjacent z-columns per block, a single
 // shared exchange tile t[(k1 R2 + n2) W + l]:
-//   A  thread (l, n2): the N = L/2 nonzero samples z = R2 n1 + n2 (n1 < R1/2) come
-//      straight from memory, radix-R1 butterfly, twiddle W_L^{n2 k1}, into t;
+//   A  thread (l, n2): the nz <= LZ/2 nonzero samples p = R2 n1 + n2 (n1 < R1/2) come
+//      straight from memory, radix-R1 butterfly, twiddle W_LZ^{n2 k1}, into t;
 //   B  thread (l, k1): its R2 values of t, radix-R2 butterfly -> X[k1 + R1 k2] in
 //      registers; product with the kernel spectrum; inverse radix-R2 butterfly,
-//      twiddle W_L^{-k1 n2}, back into the same slots of t (a thread reads and writes
+//      twiddle W_LZ^{-k1 n2}, back into the same slots of t (a thread reads and writes
 //      only its own (k1, l) slice, so B needs no barrier inside);
 //   C  thread (l, n2): inverse radix-R1 butterfly over k1, the outputs
-//      z = n2 + R2 n1 < N stored straight to memory.
+//      p = n2 + R2 n1 < nz stored straight to memory.
 // A column's data cross shared memory twice instead of once per pass.
-// radix split of the z pass: for L = 128 the 16 x 8 split keeps the step-B registers
+// radix split of the z pass: for LZ = 128 the 16 x 8 split keeps the step-B registers
 // (operands and spectrum slice) at 8 complex values each
-template <int L>
+template <int LZ>
 constexpr int zsplit_r1() {
-  return L == 128 ? 16 : split_r1(L);
+  return LZ == 128 ? 16 : split_r1(LZ);
 }
-template <int L, class C>
+template <int LZ, class C>
 constexpr int zcol_width() {
-  return (int)sizeof(C) == 8 ? (L < 32 ? L : L >= 512 ? 16 : 32) : (L < 16 ? L : L >= 512 ? 8 : 16);
+  return (int)sizeof(C) == 8 ? (LZ < 32 ? LZ : LZ >= 512 ? 16 : 32) : (LZ < 16 ? LZ : LZ >= 512 ? 8 : 16);
 }
 constexpr int kZThreads = 256;
 
-// z rows of the active box: the z pass reads and writes only lo <= z <= hi (the slab rows
-// outside it are zero on input and not needed on output)
-struct ZRange {
-  int lo, hi;
-  __device__ __forceinline__ bool in(int z) const { return z >= lo && z <= hi; }
-};
-
-template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long es, C* t, const C* tw, ZRange zr) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+template <int LZ, int W, class C>
+__device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long es, C* t, const C* tw, int nz) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
   for (int u = threadIdx.x; u < W * R2; u += kZThreads) {
     const int l = u % W, n2 = u / W;
     C v[R1];
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
-      const int z = R2 * n1 + n2;
-      v[n1] = n1 < R1 / 2 && zr.in(z) ? col[(long long)z * es + l] : C{};
+      const int p = R2 * n1 + n2;
+      v[n1] = n1 < R1 / 2 && p < nz ? col[(long long)p * es + l] : C{};
     }
-    dft_half_in<R1, L, false, C>(v, tw);  // samples z >= N are the zero padding
+    dft_half_in<R1, LZ, false, C>(v, tw);  // samples p >= LZ/2 are the zero padding
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       C x = v[k1];
@@ -252,20 +258,21 @@ __device__ __forceinline__ void zcol_step_a(const C* __restrict__ col, long long
 }
 
 // the spectrum X[k1 + R1 k2] of column l from t (after step A and a barrier)
-template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_b_fwd(const C* t, const C* tw, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+template <int LZ, int W, class C>
+__device__ __forceinline__ void zcol_step_b_fwd(const C* t, const C* tw, int k1, int l,
+                                                C (&v)[LZ / zsplit_r1<LZ>()]) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) v[n2] = t[(k1 * R2 + n2) * W + l];
-  DFTL<R2, L, false, C>::run(v, tw);
+  DFTL<R2, LZ, false, C>::run(v, tw);
   (void)R1;
 }
 
 // inverse radix-R2 butterfly of a spectrum slice, twiddled back into t
-template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_b_inv(C* t, const C* tw, int k1, int l, C (&v)[L / zsplit_r1<L>()]) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
-  DFTL<R2, L, true, C>::run(v, tw);
+template <int LZ, int W, class C>
+__device__ __forceinline__ void zcol_step_b_inv(C* t, const C* tw, int k1, int l, C (&v)[LZ / zsplit_r1<LZ>()]) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
+  DFTL<R2, LZ, true, C>::run(v, tw);
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) {
     C x = v[n2];
@@ -275,26 +282,26 @@ __device__ __forceinline__ void zcol_step_b_inv(C* t, const C* tw, int k1, int l
   (void)R1;
 }
 
-template <int L, int W, class C>
-__device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restrict__ col, long long es, ZRange zr) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+template <int LZ, int W, class C>
+__device__ __forceinline__ void zcol_step_c(const C* t, const C* tw, C* __restrict__ col, long long es, int nz) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
   for (int u = threadIdx.x; u < W * R2; u += kZThreads) {
     const int l = u % W, n2 = u / W;
     C v[R1];
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) v[k1] = t[(k1 * R2 + n2) * W + l];
-    dft_half_out<R1, L, true, C>(v, tw);  // only the outputs z < N are kept
+    dft_half_out<R1, LZ, true, C>(v, tw);  // only the outputs p < LZ/2 are formed
 #pragma unroll
     for (int n1 = 0; n1 < R1 / 2; ++n1) {
-      const int z = n2 + R2 * n1;
-      if (zr.in(z)) col[(long long)z * es + l] = v[n1];
+      const int p = n2 + R2 * n1;
+      if (p < nz) col[(long long)p * es + l] = v[n1];
     }
   }
 }
 
 // Grid order of the z-pass blocks: (right-hand side, component) fastest, then the x
 // tile, then the row y taken in mirror pairs (0, N, 1, L-1, 2, L-2, ...).  Every block
-// reads the kernel-spectrum octant at (fold(z), fold(y), fold(x)); the octant of a large
+// reads the kernel-spectrum octant at (fold(kz), fold(y), fold(x)); the octant of a large
 // grid does not fit in L2, and this order keeps the blocks that read the same entries
 // (all right-hand sides and components of one kernel kind, the rows y and L-y) close in
 // time, so the octant comes from DRAM about once per launch.
@@ -304,69 +311,75 @@ __device__ __forceinline__ int zpass_row(int j, int N) {
   return (j & 1) ? 2 * N - k : k;
 }
 
+// the kernel-spectrum column of kind `kind` at (x, y): entry kz at [fold(kz, LZ/2) * n1^2]
+template <int LZ, class C>
+__device__ __forceinline__ const C* kcol(const C* kspec, const ZGeom& g, int kind, int x, int y) {
+  const size_t n1 = (size_t)g.N + 1;
+  return kspec + (size_t)kind * n1 * n1 * (LZ / 2 + 1) + (size_t)fold(y, g.N) * n1 + fold(x, g.N);
+}
+
 // Forward z-FFT of the slab column, product with the kernel spectrum of delay m
 // (G^A for c = x,y,z; G^phi for c = div; even-symmetric octant), inverse z-FFT,
-// first N outputs written back in place.  Grid (nb * 4, L / W, L) in the order above.
-template <int L, int W, class C>
-__global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, const C* __restrict__ kspec, int N,
+// the nz outputs written back in place.  Grid (nb * 4, L / W, L) in the order above.
+template <int LZ, int W, class C>
+__global__ void __launch_bounds__(kZThreads) k_zconv_p2(C* __restrict__ Bf, const C* __restrict__ kspec, ZGeom g,
                                                         const int* __restrict__ active,
-                                                        const C* __restrict__ twg, ZRange zr) {
+                                                        const C* __restrict__ twg) {
   pdl_wait();
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
   const int bc = blockIdx.x;
   if (active && !active[bc >> 2]) return;
   C* tw = reinterpret_cast<C*>(aim_smem);
-  C* t = tw + L;
-  load_twiddles(tw, twg, L);
+  C* t = tw + LZ;
+  load_twiddles(tw, twg, LZ);
   __syncthreads();
-  const int y = zpass_row(blockIdx.z, N), x0 = blockIdx.y * W;
-  const long long es = (long long)L * L;
-  C* col = Bf + (size_t)bc * N * L * L + (size_t)y * L + x0;
-  const int n1 = N + 1;
-  const C* Gy = kspec + (size_t)((bc & 3) == 3 ? 1 : 0) * n1 * n1 * n1 + (size_t)fold(y, N) * n1;
-  zcol_step_a<L, W, C>(col, es, t, tw, zr);
+  const int y = zpass_row(blockIdx.z, g.N), x0 = blockIdx.y * W;
+  const long long es = (long long)g.L * g.L;
+  C* col = Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0;
+  const size_t nn = (size_t)(g.N + 1) * (g.N + 1);
+  zcol_step_a<LZ, W, C>(col, es, t, tw, g.nz);
   __syncthreads();
   for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
     const int l = u % W, k1 = u / W;
-    const C* G = Gy + fold(x0 + l, N);
-    C g[R2], v[R2];
+    const C* G = kcol<LZ>(kspec, g, (bc & 3) == 3 ? 1 : 0, x0 + l, y);
+    C gk[R2], v[R2];
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) g[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
-    zcol_step_b_fwd<L, W, C>(t, tw, k1, l, v);
+    for (int k2 = 0; k2 < R2; ++k2) gk[k2] = __ldg(G + (size_t)fold(k1 + R1 * k2, LZ / 2) * nn);
+    zcol_step_b_fwd<LZ, W, C>(t, tw, k1, l, v);
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) v[k2] = v[k2] * g[k2];
-    zcol_step_b_inv<L, W, C>(t, tw, k1, l, v);
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = v[k2] * gk[k2];
+    zcol_step_b_inv<LZ, W, C>(t, tw, k1, l, v);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, col, es, zr);
+  zcol_step_c<LZ, W, C>(t, tw, col, es, g.nz);
   pdl_trigger();
 }
 
-// History slabs of power-of-two length are kept z-transformed: S[bc][kz][y][x], all L
-// frequencies kz of every (x, y) line (twice the bytes of the x/y-transformed slab, whose
-// z holds only the N nonzero samples).  The delay sum of the right-hand side is then a
-// multiply-accumulate streamed over the N_g spectra and one inverse z-FFT, instead of N_g
-// forward z-FFTs recomputed at every step.
+// History slabs of power-of-two z length are kept z-transformed: S[bc][kz][y][x], all LZ
+// frequencies kz of every (x, y) line (LZ / nz times the bytes of the x/y-transformed
+// slab).  The delay sum of the right-hand side is then a multiply-accumulate streamed
+// over the N_g spectra and one inverse z-FFT, instead of N_g forward z-FFTs recomputed
+// at every step.
 //
 // k_zfwd_spec: the forward z-FFT (steps A and B of the z pass) of the slab in Bf into the
 // spectral layout; thread (l, k1) of step B stores X[k1 + R1 k2] for all k2.
-template <int L, int W, class C>
-__global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ Bf, C* __restrict__ S, int N,
-                                                         const C* __restrict__ twg, ZRange zr) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1;
+template <int LZ, int W, class C>
+__global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ Bf, C* __restrict__ S, ZGeom g,
+                                                         const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
   C* tw = reinterpret_cast<C*>(aim_smem);
-  C* t = tw + L;
-  load_twiddles(tw, twg, L);
+  C* t = tw + LZ;
+  load_twiddles(tw, twg, LZ);
   __syncthreads();
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
-  const long long es = (long long)L * L;
-  zcol_step_a<L, W, C>(Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, t, tw, zr);
+  const long long es = (long long)g.L * g.L;
+  zcol_step_a<LZ, W, C>(Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0, es, t, tw, g.nz);
   __syncthreads();
-  C* out = S + (size_t)bc * L * L * L + (size_t)y * L + x0;
+  C* out = S + (size_t)bc * LZ * es + (size_t)y * g.L + x0;
   for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
     const int l = u % W, k1 = u / W;
     C v[R2];
-    zcol_step_b_fwd<L, W, C>(t, tw, k1, l, v);
+    zcol_step_b_fwd<LZ, W, C>(t, tw, k1, l, v);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) out[(long long)(k1 + R1 * k2) * es + l] = v[k2];
   }
@@ -376,99 +389,94 @@ __global__ void __launch_bounds__(kZThreads) k_zfwd_spec(const C* __restrict__ B
 //   P^_col = sum_i G^_{m_i} . S_i(col), then one inverse z-FFT (steps B inverse and C),
 // the sum kept in the registers of the step-B threads (thread (l, k1) owns the
 // frequencies k1 + R1 k2).
-template <int L, int W, class C>
-__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec(SlabList sl, const C* __restrict__ kspec_all, int N,
-                                                         C* __restrict__ Bf, const C* __restrict__ twg, ZRange zr) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
+template <int LZ, int W, class C>
+__global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec(SlabList sl, const C* __restrict__ kspec_all, ZGeom g,
+                                                         C* __restrict__ Bf, const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
-  C* t = tw + L;
-  load_twiddles(tw, twg, L);
+  C* t = tw + LZ;
+  load_twiddles(tw, twg, LZ);
   __syncthreads();
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
-  const long long es = (long long)L * L;
-  const int n1 = N + 1;
-  const size_t oct = (size_t)n1 * n1 * n1;
+  const long long es = (long long)g.L * g.L;
+  const size_t nn = (size_t)(g.N + 1) * (g.N + 1), oct = nn * (LZ / 2 + 1);
   const int kind = (bc & 3) == 3 ? 1 : 0;
-  const int fy = fold(y, N);
   C acc[U][R2];
 #pragma unroll
   for (int j = 0; j < U; ++j)
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
   for (int s = 0; s < sl.n; ++s) {
-    const C* Sc = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * L * L * L + (size_t)y * L + x0;
-    const C* Gy = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct + (size_t)fy * n1;
+    const C* Sc = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * LZ * es + (size_t)y * g.L + x0;
+    const C* Gm = kspec_all + (size_t)sl.m[s] * 2 * oct;
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kZThreads;
       if (u < W * R1) {
         const int l = u % W, k1 = u / W;
-        const C* G = Gy + fold(x0 + l, N);
-        C g[R2], v[R2];
+        const C* G = kcol<LZ>(Gm, g, kind, x0 + l, y);
+        C gk[R2], v[R2];
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) {
           const int kz = k1 + R1 * k2;
           v[k2] = Sc[(long long)kz * es + l];
-          g[k2] = __ldg(G + (size_t)fold(kz, N) * n1 * n1);
+          gk[k2] = __ldg(G + (size_t)fold(kz, LZ / 2) * nn);
         }
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * g[k2];
+        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * gk[k2];
       }
     }
   }
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const int u = threadIdx.x + j * kZThreads;
-    if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
+    if (u < W * R1) zcol_step_b_inv<LZ, W, C>(t, tw, u / W, u % W, acc[j]);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, zr);
+  zcol_step_c<LZ, W, C>(t, tw, Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0, es, g.nz);
 }
 
-// The same with the spectra streamed by TMA (complex64): the L x W tile of each spectrum
-// is a 4-D box of the ring tensor [slot][B*4*L][L][L], loaded into one of two 128-byte
+// The same with the spectra streamed by TMA (complex64): the LZ x W tile of each spectrum
+// is a 4-D box of the ring tensor [slot][B*4*LZ][L][L], loaded into one of two 128-byte
 // aligned shared buffers by cp.async.bulk.tensor and signalled on an mbarrier, so
 // spectrum s + 2 streams in while spectrum s + 1 is accumulated.  Waits are bounded.  A
 // wait that gives up sets *err (the host reports AIM_ERR_TIMEOUT) and a block-wide flag;
 // the block then issues no further load, drains the loads it has in flight with one more
 // bounded wait each and returns without writing its output (which is undefined whenever
 // *err is set).
-template <int L, int W>
+template <int LZ, int W>
 __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_constant__ CUtensorMap ring,
                                                                 SlabRing sr, const float2* __restrict__ kspec_all,
-                                                                int N, float2* __restrict__ Bf,
-                                                                const float2* __restrict__ twg, int* __restrict__ err,
-                                                                ZRange zr) {
+                                                                ZGeom g, float2* __restrict__ Bf,
+                                                                const float2* __restrict__ twg, int* __restrict__ err) {
   using C = float2;
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int gave_up[2];  // by iteration parity: a write in iteration s + 1 cannot reach a
                               // thread still reading the flag of iteration s
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(aim_smem) + 127) & ~static_cast<uintptr_t>(127));
-  C* in0 = reinterpret_cast<C*>(base);  // [2][L][W]
-  C* tw = in0 + 2 * L * W;
-  C* t = tw + L;
+  C* in0 = reinterpret_cast<C*>(base);  // [2][LZ][W]
+  C* tw = in0 + 2 * LZ * W;
+  C* t = tw + LZ;
   const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
-  const unsigned bytes = (unsigned)(L * W * sizeof(C));
+  const unsigned bytes = (unsigned)(LZ * W * sizeof(C));
   if (threadIdx.x == 0) {
     gave_up[0] = gave_up[1] = 0;
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
-  load_twiddles(tw, twg, L);
+  load_twiddles(tw, twg, LZ);
   __syncthreads();
   if (threadIdx.x == 0)
     for (int s = 0; s < 2 && s < sr.n; ++s) {
       mbar_arrive_expect_tx(&bar[s], bytes);
-      tma_load_4d(in0 + s * L * W, &ring, &bar[s], x0, y, bc * L, sr.slot[s]);
+      tma_load_4d(in0 + s * LZ * W, &ring, &bar[s], x0, y, bc * LZ, sr.slot[s]);
     }
-  const long long es = (long long)L * L;
-  const int n1 = N + 1;
-  const size_t oct = (size_t)n1 * n1 * n1;
+  const long long es = (long long)g.L * g.L;
+  const size_t nn = (size_t)(g.N + 1) * (g.N + 1), oct = nn * (LZ / 2 + 1);
   const int kind = (bc & 3) == 3 ? 1 : 0;
-  const int fy = fold(y, N);
   C acc[U][R2];
 #pragma unroll
   for (int j = 0; j < U; ++j)
@@ -476,15 +484,15 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
     for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
   for (int s = 0; s < sr.n; ++s) {
     const int buf = s & 1;
-    const C* Gy = kspec_all + ((size_t)sr.m[s] * 2 + kind) * oct + (size_t)fy * n1;
-    C g[U][R2];
+    const C* Gm = kspec_all + (size_t)sr.m[s] * 2 * oct;
+    C gk[U][R2];
 #pragma unroll
     for (int j = 0; j < U; ++j) {  // the kernel spectrum while the tile streams in
       const int u = threadIdx.x + j * kZThreads;
       if (u < W * R1) {
-        const C* G = Gy + fold(x0 + u % W, N);
+        const C* G = kcol<LZ>(Gm, g, kind, x0 + u % W, y);
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) g[j][k2] = __ldg(G + (size_t)fold(u / W + R1 * k2, N) * n1 * n1);
+        for (int k2 = 0; k2 < R2; ++k2) gk[j][k2] = __ldg(G + (size_t)fold(u / W + R1 * k2, LZ / 2) * nn);
       }
     }
     const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)((s >> 1) & 1));
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
       atomicExch(err, 1);
       gave_up[s & 1] = 1;
     }
-    const C* tile = in0 + buf * L * W;  // [kz][l]
+    const C* tile = in0 + buf * LZ * W;  // [kz][l]
     if (ok) {
 #pragma unroll
       for (int j = 0; j < U; ++j) {
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
         if (u < W * R1) {
           const int l = u % W, k1 = u / W;
 #pragma unroll
-          for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += tile[(k1 + R1 * k2) * W + l] * g[j][k2];
+          for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += tile[(k1 + R1 * k2) * W + l] * gk[j][k2];
         }
       }
     }
@@ -517,58 +525,55 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
     if (threadIdx.x == 0 && s + 2 < sr.n) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bar[buf], bytes);
-      tma_load_4d(in0 + buf * L * W, &ring, &bar[buf], x0, y, bc * L, sr.slot[s + 2]);
+      tma_load_4d(in0 + buf * LZ * W, &ring, &bar[buf], x0, y, bc * LZ, sr.slot[s + 2]);
     }
   }
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const int u = threadIdx.x + j * kZThreads;
-    if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
+    if (u < W * R1) zcol_step_b_inv<LZ, W, C>(t, tw, u / W, u % W, acc[j]);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, zr);
+  zcol_step_c<LZ, W, C>(t, tw, Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0, es, g.nz);
 }
 
-// Lengths with a factor 3 keep x/y-transformed history slabs (a z-spectral ring would
-// double the largest buffer): the delay sum recomputes each slab's forward z-transform
-// (steps A and B of the z pass), multiplies it by its delay's kernel spectrum and
-// accumulates in the registers of the step-B threads; then one inverse z-FFT (steps
-// B^-1 and C), the N outputs written to Bf.
-template <int L, int W, class C>
-__global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __restrict__ kspec_all, int N,
-                                                       C* __restrict__ Bf, const C* __restrict__ twg, ZRange zr) {
-  constexpr int R1 = zsplit_r1<L>(), R2 = L / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
+// z lengths with a factor 3 keep x/y-transformed history slabs: the delay sum recomputes
+// each slab's forward z-transform (steps A and B of the z pass), multiplies it by its
+// delay's kernel spectrum and accumulates in the registers of the step-B threads; then one
+// inverse z-FFT (steps B^-1 and C), the nz outputs written to Bf.
+template <int LZ, int W, class C>
+__global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __restrict__ kspec_all, ZGeom g,
+                                                       C* __restrict__ Bf, const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1, U = (W * R1 + kZThreads - 1) / kZThreads;
   C* tw = reinterpret_cast<C*>(aim_smem);
-  C* t = tw + L;
-  load_twiddles(tw, twg, L);
+  C* t = tw + LZ;
+  load_twiddles(tw, twg, LZ);
   __syncthreads();
-  const int bc = blockIdx.x, y = zpass_row(blockIdx.z, N), x0 = blockIdx.y * W;  // z-pass grid order
-  const long long es = (long long)L * L;
-  const int n1 = N + 1;
-  const size_t oct = (size_t)n1 * n1 * n1;
+  const int bc = blockIdx.x, y = zpass_row(blockIdx.z, g.N), x0 = blockIdx.y * W;  // z-pass grid order
+  const long long es = (long long)g.L * g.L;
+  const size_t nn = (size_t)(g.N + 1) * (g.N + 1), oct = nn * (LZ / 2 + 1);
   const int kind = (bc & 3) == 3 ? 1 : 0;
-  const int fy = fold(y, N);
   C acc[U][R2];
 #pragma unroll
   for (int j = 0; j < U; ++j)
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] = C{};
   for (int s = 0; s < sl.n; ++s) {
-    const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * N * L * L + (size_t)y * L + x0;
-    const C* Gy = kspec_all + ((size_t)sl.m[s] * 2 + kind) * oct + (size_t)fy * n1;
+    const C* col = reinterpret_cast<const C*>(sl.p[s]) + (size_t)bc * g.nz * es + (size_t)y * g.L + x0;
+    const C* Gm = kspec_all + (size_t)sl.m[s] * 2 * oct;
     if (s) __syncthreads();  // the previous delay's step B has read t
-    zcol_step_a<L, W, C>(col, es, t, tw, zr);
+    zcol_step_a<LZ, W, C>(col, es, t, tw, g.nz);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kZThreads;
       if (u < W * R1) {
         const int l = u % W, k1 = u / W;
-        const C* G = Gy + fold(x0 + l, N);
+        const C* G = kcol<LZ>(Gm, g, kind, x0 + l, y);
         C v[R2];
-        zcol_step_b_fwd<L, W, C>(t, tw, k1, l, v);
+        zcol_step_b_fwd<LZ, W, C>(t, tw, k1, l, v);
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * __ldg(G + (size_t)fold(k1 + R1 * k2, N) * n1 * n1);
+        for (int k2 = 0; k2 < R2; ++k2) acc[j][k2] += v[k2] * __ldg(G + (size_t)fold(k1 + R1 * k2, LZ / 2) * nn);
       }
     }
   }
@@ -576,10 +581,10 @@ __global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __r
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const int u = threadIdx.x + j * kZThreads;
-    if (u < W * R1) zcol_step_b_inv<L, W, C>(t, tw, u / W, u % W, acc[j]);
+    if (u < W * R1) zcol_step_b_inv<LZ, W, C>(t, tw, u / W, u % W, acc[j]);
   }
   __syncthreads();
-  zcol_step_c<L, W, C>(t, tw, Bf + (size_t)bc * N * L * L + (size_t)y * L + x0, es, zr);
+  zcol_step_c<LZ, W, C>(t, tw, Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0, es, g.nz);
 }
 
 // ---------------------------------------------------------------- stage iii + iv
@@ -596,7 +601,8 @@ constexpr int kInterpBlockRows = 8 * kInterpRows;  // 256 threads
 
 template <class C>
 __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P, const int* __restrict__ anchor,
-                                                     const typename Real<C>::T* __restrict__ lam, int N, int ns,
+                                                     const typename Real<C>::T* __restrict__ lam, int N, int nz,
+                                                     int zlo, int ns,
                                                      int nb, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col, NearList nl,
                                                      const double2* __restrict__ base, double sign,
@@ -610,7 +616,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
   // grid part, row by row; lane group r (lanes 8r .. 8r+7) keeps row r's sum
   C mine{};
   if (P) {
-    const size_t N3 = (size_t)N * N * N;
+    const size_t N3 = (size_t)nz * N * N;  // the box planes z0 .. z0 + nz - 1
 #pragma unroll
     for (int r = 0; r < kInterpRows; ++r) {
       const int k = k0 + r;
@@ -618,7 +624,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
       if (k < ns) {
         // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node)
         // terms of an RWG take 8 warp loads of 8 rows x 32 B each
-        const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2];
+        const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2] - zlo;
         const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
         const R* lk = lam + (size_t)k * 256 + lane;
 #pragma unroll
@@ -733,6 +739,8 @@ static void smem_opt_in(K kernel, size_t bytes) {
 // precision selectors for the context tables
 inline const float2* sel_tw(aim_ctx* c, float2*) { return c->d_twf; }
 inline const double2* sel_tw(aim_ctx* c, double2*) { return c->d_tw; }
+inline const float2* sel_twz(aim_ctx* c, float2*) { return c->d_twzf; }
+inline const double2* sel_twz(aim_ctx* c, double2*) { return c->d_twz; }
 inline const float2* sel_kspec(aim_ctx* c, float2*) { return c->d_kspecf; }
 inline const double2* sel_kspec(aim_ctx* c, double2*) { return c->d_kspec; }
 inline const float4* sel_ncoef(aim_ctx* c, float2*) { return c->d_ncoeff; }
@@ -752,30 +760,55 @@ inline void with_width(int w, F&& f) {
     default: throw AimError{AIM_ERR_ARG, "launch plan: unsupported tile width"};
   }
 }
+// z transform lengths the z pass is instantiated for (aim_ctx::LZ is one of them)
+template <class F>
+inline void with_zlen(int lz, F&& f) {
+  switch (lz) {
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 32: f(std::integral_constant<int, 32>{}); break;
+    case 64: f(std::integral_constant<int, 64>{}); break;
+    case 128: f(std::integral_constant<int, 128>{}); break;
+    case 192: f(std::integral_constant<int, 192>{}); break;
+    case 256: f(std::integral_constant<int, 256>{}); break;
+    case 768: f(std::integral_constant<int, 768>{}); break;
+    default: throw AimError{AIM_ERR_ARG, "unsupported z transform length"};
+  }
+}
 constexpr size_t kPlanSmemMax = 220 * 1024;  // dynamic shared memory a plan may ask for
 
 template <int L, class C>
 struct GridOps {
   // ------------------------------------------------------------ launch shapes
-  static int def_zw() { return zcol_width<L, C>(); }
+  static int def_zw(const aim_ctx* c) {
+    int w = 0;
+    with_zlen(c->LZ, [&](auto lz) { w = zcol_width<decltype(lz)::value, C>(); });
+    return w;
+  }
   static int def_cw() { return col_width_p2<L, C>(); }
   static int def_rp() { return pow2_len(L) ? std::max(1, 4096 / L) : std::max(1, 256 / split_r1(L)); }
   static int def_ypb() { return std::max(1, 256 / (L / 2)); }
-  static size_t smem_z(int w) { return (size_t)(L + L * w) * sizeof(C); }
+  static size_t smem_z(int lz, int w) { return (size_t)(lz + lz * w) * sizeof(C); }
+  static size_t smem_y(int w) { return (size_t)(L + L * w) * sizeof(C); }
   static size_t smem_x(int rp) { return (size_t)(L + rp * row_tmp_pitch<L>()) * sizeof(C); }
   static size_t smem_anterp(int yp) { return (size_t)(L + 4 * yp * L + row_scratch<L>(4 * yp)) * sizeof(C); }
   // the plan holds the shapes of the context's own precision (the FP64 residual of the
   // refinement on the complex64 path runs with the defaults)
   static bool own(const aim_ctx* c) { return (c->precision == AIM_C64) == (sizeof(C) == sizeof(float2)); }
-  static int zw(const aim_ctx* c) { return own(c) && c->plan.zw ? c->plan.zw : def_zw(); }
+  static int zw(const aim_ctx* c) { return own(c) && c->plan.zw ? c->plan.zw : def_zw(c); }
   static int cw(const aim_ctx* c) { return own(c) && c->plan.cw ? c->plan.cw : def_cw(); }
   static int rp(const aim_ctx* c) { return own(c) && c->plan.rp ? c->plan.rp : def_rp(); }
   static int ypb(const aim_ctx* c) { return own(c) && c->plan.ypb ? c->plan.ypb : def_ypb(); }
-  // candidates the autotuner times
-  static std::vector<int> widths() {
+  // candidates the autotuner times: z tiles of x-adjacent columns (w divides L), y tiles
+  static std::vector<int> zwidths(const aim_ctx* c) {
     std::vector<int> v;
     for (int w : {8, 16, 32})
-      if (w <= L && L % w == 0 && smem_z(w) <= kPlanSmemMax) v.push_back(w);
+      if (w <= L && L % w == 0 && smem_z(c->LZ, w) <= kPlanSmemMax) v.push_back(w);
+    return v;
+  }
+  static std::vector<int> ywidths() {
+    std::vector<int> v;
+    for (int w : {8, 16, 32})
+      if (w <= L && L % w == 0 && smem_y(w) <= kPlanSmemMax) v.push_back(w);
     return v;
   }
   static std::vector<int> rps() {
@@ -791,7 +824,7 @@ struct GridOps {
     return v;
   }
 
-  // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][N][L][L]
+  // stage i + forward x and y passes: v[nb][ns] (optionally times dinv) -> slab [nb][4][nz][L][L]
   // dinv non-null asks for the context's right preconditioner: the diagonal dinv, or the
   // near-zone SAI when the context built one
   static void prep(aim_ctx* c, int nb, const double2* v, const double2* dinv, VecSel vs, const int* active,
@@ -808,10 +841,10 @@ struct GridOps {
                  nb, reinterpret_cast<C*>(c->d_xs), want_fp64 ? c->d_xd : (double2*)nullptr);
   }
 
-  // the active box (x, y, z node ranges): every pass outside the z pass touches only the
-  // grid lines that are non-zero on input or needed on output
-  static ZRange zr(const aim_ctx* c) { return ZRange{c->box_lo[2], c->box_hi[2]}; }
+  // the active box (x, y, z node ranges): every pass touches only the grid lines that are
+  // non-zero on input or needed on output; the buffers hold the box's nz z-planes only
   static int nbox(const aim_ctx* c, int d) { return c->box_hi[d] - c->box_lo[d] + 1; }
+  static ZGeom zgeom(const aim_ctx* c) { return ZGeom{L, c->N, c->NZ}; }
 
   // anterpolation gather + forward x pass: d_xs -> A (rows of the active box)
   static void anterp_x(aim_ctx* c, int nb, const int* active) {
@@ -819,26 +852,27 @@ struct GridOps {
     const size_t sm = smem_anterp(yp);
     smem_opt_in(k_anterp_rows<L, C>, sm);
     KScope ks(c, AIM_K_ANTERP_XFFT);
-    launch_pdl(c->stream, dim3(nb, (nbox(c, 1) + yp - 1) / yp, nbox(c, 2)), dim3(256), sm, k_anterp_rows<L, C>,
+    launch_pdl(c->stream, dim3(nb, (nbox(c, 1) + yp - 1) / yp, c->NZ), dim3(256), sm, k_anterp_rows<L, C>,
                (const int*)c->d_nptr, (const int*)c->d_nidx, ncoef(c), reinterpret_cast<const C*>(c->d_xs), active,
-               c->ns, N, yp, reinterpret_cast<C*>(c->d_A), twiddles(c), c->box_lo[1], c->box_hi[1], c->box_lo[2]);
+               c->ns, N, yp, reinterpret_cast<C*>(c->d_A), twiddles(c), c->box_lo[1], c->box_hi[1], c->box_lo[2],
+               c->NZ);
   }
 
   // forward y pass (pruned input): A -> slab
   static void y_fwd(aim_ctx* c, int nb, C* slab) {
     static_assert(two_step_len(L), "every supported padded length has a two-step plan");
-    const int N = c->N;
+    const int N = c->N, nz = c->NZ;
     const C* A = reinterpret_cast<const C*>(c->d_A);
     KScope ks(c, AIM_K_YFFT_FWD);
     with_width(cw(c), [&](auto wt) {
       constexpr int CW = decltype(wt)::value;
       if constexpr (CW <= L) {
-        const size_t sm = smem_z(CW);
+        const size_t sm = smem_y(CW);
         smem_opt_in(k_cols_p2<L, CW, false, C, true>, sm);
-        // lines (z in the box, x): inputs y in the box, all L outputs
-        launch_pdl(c->stream, dim3(L / CW, nbox(c, 2), nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>, A,
-                   slab, c->box_hi[1] + 1, L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L,
-                   (long long)N * N * L, (long long)N * L * L, twiddles(c), c->box_lo[1], 0, c->box_lo[2]);
+        // lines (plane, x): inputs y in the box, all L outputs
+        launch_pdl(c->stream, dim3(L / CW, nz, nb * 4), dim3(256), sm, k_cols_p2<L, CW, false, C, true>, A, slab,
+                   c->box_hi[1] + 1, L, (long long)L, (long long)L, L, (long long)N * L, (long long)L * L,
+                   (long long)nz * N * L, (long long)nz * L * L, twiddles(c), c->box_lo[1], 0, 0);
       } else {
         throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
       }
@@ -847,18 +881,18 @@ struct GridOps {
 
   // inverse y pass (pruned output): Bf -> A
   static void y_inv(aim_ctx* c, int nb) {
-    const int N = c->N;
+    const int N = c->N, nz = c->NZ;
     KScope ks(c, AIM_K_YFFT_INV);
     with_width(cw(c), [&](auto wt) {
       constexpr int CW = decltype(wt)::value;
       if constexpr (CW <= L) {
-        const size_t sm = smem_z(CW);
+        const size_t sm = smem_y(CW);
         smem_opt_in(k_cols_p2<L, CW, true, C>, sm);
-        // lines (z in the box, x): all L inputs, outputs y in the box
-        launch_pdl(c->stream, dim3(L / CW, nbox(c, 2), nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>,
+        // lines (plane, x): all L inputs, outputs y in the box
+        launch_pdl(c->stream, dim3(L / CW, nz, nb * 4), dim3(256), sm, k_cols_p2<L, CW, true, C>,
                    (const C*)c->d_Bf, reinterpret_cast<C*>(c->d_A), L, c->box_hi[1] + 1, (long long)L, (long long)L, L,
-                   (long long)L * L, (long long)N * L, (long long)N * L * L, (long long)N * N * L, twiddles(c), 0,
-                   c->box_lo[1], c->box_lo[2]);
+                   (long long)L * L, (long long)N * L, (long long)nz * L * L, (long long)nz * N * L, twiddles(c), 0,
+                   c->box_lo[1], 0);
       } else {
         throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
       }
@@ -867,13 +901,13 @@ struct GridOps {
 
   // inverse x pass (pruned output): A -> P, the rows of the active box, outputs x in the box
   static void x_inv(aim_ctx* c, int nb) {
-    const int N = c->N, r = rp(c), nz = nbox(c, 2), ny = nbox(c, 1), nrows = nb * 4 * nz * ny;
+    const int N = c->N, r = rp(c), nz = c->NZ, ny = nbox(c, 1), nrows = nb * 4 * nz * ny;
     const size_t sm = smem_x(r);
     smem_opt_in(k_rows_p2<L, true, C>, sm);
     KScope ks(c, AIM_K_XFFT_INV);
     launch_pdl(c->stream, dim3((nrows + r - 1) / r), dim3(256), sm, k_rows_p2<L, true, C>, (const C*)c->d_A,
                reinterpret_cast<C*>(c->d_P), nrows, L, c->box_hi[0] + 1, (long long)L, (long long)N, twiddles(c), r,
-               RowBox{nz, ny, c->box_lo[2], c->box_lo[1], N}, c->box_lo[0]);
+               RowBox{nz, ny, 0, c->box_lo[1], nz, N}, c->box_lo[0]);
   }
 
   static void forward_slab(aim_ctx* c, int nb, const double2* v, const double2* dinv, const int* active, C* slab,
@@ -895,25 +929,33 @@ struct GridOps {
                      const int* active, double2* y, VecSel ys = VecSel()) {
     KScope ks(c, AIM_K_INTERP_NEAR);
     launch_pdl(c->stream, dim3((unsigned)((c->ns + kInterpBlockRows - 1) / kInterpBlockRows), (unsigned)nb), dim3(256),
-               0, k_interp_near<C>, P, (const int*)c->d_anchor, lam(c), c->N, c->ns, nb, (const int*)c->d_rowptr,
-               (const int*)c->d_col, nl, base, sign, active, y, ys, c->dotfuse);
+               0, k_interp_near<C>, P, (const int*)c->d_anchor, lam(c), c->N, c->NZ, c->box_lo[2], c->ns, nb,
+               (const int*)c->d_rowptr, (const int*)c->d_col, nl, base, sign, active, y, ys, c->dotfuse);
   }
 
+  // size of one kernel-spectrum octant [LZ/2 + 1][N + 1][N + 1]
+  static size_t octant(const aim_ctx* c) { return (size_t)(c->N + 1) * (c->N + 1) * (c->LZ / 2 + 1); }
+
   static void zconv(aim_ctx* c, int nb, int m, const int* active) {
-    const int N = c->N;
-    const size_t oct = (size_t)(N + 1) * (N + 1) * (N + 1);
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
-    const C* G = kspec(c) + (size_t)m * 2 * oct;
+    const C* G = kspec(c) + (size_t)m * 2 * octant(c);
     KScope ks(c, AIM_K_ZCONV);
-    with_width(zw(c), [&](auto wt) {
-      constexpr int ZW = decltype(wt)::value;
-      if constexpr (ZW <= L) {
-        const size_t sm = smem_z(ZW);
-        smem_opt_in(k_zconv_p2<L, ZW, C>, sm);
-        launch_pdl(c->stream, dim3(nb * 4, L / ZW, L), dim3(kZThreads), sm, k_zconv_p2<L, ZW, C>, Bf, G, N, active,
-                   twiddles(c), zr(c));
+    with_zlen(c->LZ, [&](auto lz) {
+      constexpr int LZ = decltype(lz)::value;
+      if constexpr (LZ <= L) {
+        with_width(zw(c), [&](auto wt) {
+          constexpr int ZW = decltype(wt)::value;
+          if constexpr (ZW <= L) {
+            const size_t sm = smem_z(LZ, ZW);
+            smem_opt_in(k_zconv_p2<LZ, ZW, C>, sm);
+            launch_pdl(c->stream, dim3(nb * 4, L / ZW, L), dim3(kZThreads), sm, k_zconv_p2<LZ, ZW, C>, Bf, G,
+                       zgeom(c), active, ztwiddles(c));
+          } else {
+            throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
+          }
+        });
       } else {
-        throw AimError{AIM_ERR_ARG, "launch plan: tile wider than the line"};
+        throw AimError{AIM_ERR_ARG, "z transform longer than the padded length"};
       }
     });
     AIM_CHECK_LAUNCH();
@@ -955,8 +997,8 @@ struct GridOps {
       }
       field = arg;
     };
-    pick(p.zw, widths(), [&] { zconv(c, nb, 0, nullptr); });
-    pick(p.cw, widths(), [&] {
+    pick(p.zw, zwidths(c), [&] { zconv(c, nb, 0, nullptr); });
+    pick(p.cw, ywidths(), [&] {
       y_fwd(c, nb, reinterpret_cast<C*>(c->d_Bf));
       y_inv(c, nb);
     });
@@ -967,65 +1009,77 @@ struct GridOps {
   }
 
   // forward z-FFT of the slab in Bf into the z-spectral history layout at dst
-  // (power-of-two lengths only)
+  // (power-of-two z lengths only)
   static void zfwd(aim_ctx* c, int nb, C* dst) {
-    if constexpr (pow2_len(L)) {
-      constexpr int ZW = zcol_width<L, C>();
-      const size_t sm = (L + L * ZW) * sizeof(C);
-      KScope ks(c, AIM_K_ZFWD);
-      smem_opt_in(k_zfwd_spec<L, ZW, C>, sm);
-      k_zfwd_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
-          reinterpret_cast<const C*>(c->d_Bf), dst, c->N, twiddles(c), zr(c));
-      AIM_CHECK_LAUNCH();
-    }
+    with_zlen(c->LZ, [&](auto lz) {
+      constexpr int LZ = decltype(lz)::value;
+      if constexpr (pow2_len(LZ) && LZ <= L) {
+        constexpr int ZW = zcol_width<LZ, C>();
+        const size_t sm = smem_z(LZ, ZW);
+        KScope ks(c, AIM_K_ZFWD);
+        smem_opt_in(k_zfwd_spec<LZ, ZW, C>, sm);
+        k_zfwd_spec<LZ, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
+            reinterpret_cast<const C*>(c->d_Bf), dst, zgeom(c), ztwiddles(c));
+        AIM_CHECK_LAUNCH();
+      } else {
+        throw AimError{AIM_ERR_ARG, "z-spectral history needs a power-of-two z length"};
+      }
+    });
   }
 
   static void zrhs(aim_ctx* c, int nb, const SlabList& sl) {
-    const int N = c->N;
     C* Bf = reinterpret_cast<C*>(c->d_Bf);
     KScope ks(c, AIM_K_ZRHS);
-    if constexpr (pow2_len(L) && L <= 256 && std::is_same<C, float2>::value) {
-      // the spectra's ring slots (the march and aim_rhs keep every history slab in the ring)
-      const size_t slab = op_slab_bytes(c, c->batch_max);
-      SlabRing sr{};
-      sr.n = sl.n;
-      bool in_ring = c->ring_tma && sl.n > 0;
-      for (int i = 0; i < sl.n && in_ring; ++i) {
-        const long long off = (const char*)sl.p[i] - (const char*)c->d_ring;
-        in_ring = off >= 0 && off % (long long)slab == 0 && off / (long long)slab < c->n_delays;
-        sr.slot[i] = in_ring ? (int)(off / (long long)slab) : 0;
-        sr.m[i] = sl.m[i];
-      }
-      if (in_ring) {
-        constexpr int ZW = L < 16 ? L : 16;
-        const size_t sm = 128 + (2 * L * ZW + L + L * ZW) * sizeof(C);
-        smem_opt_in(k_zrhs_spec_tma<L, ZW>, sm);
-        k_zrhs_spec_tma<L, ZW><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
-            c->ring_map, sr, kspec(c), N, Bf, twiddles(c), c->d_err, zr(c));
+    with_zlen(c->LZ, [&](auto lz) {
+      constexpr int LZ = decltype(lz)::value;
+      if constexpr (LZ <= L) {
+        if constexpr (pow2_len(LZ) && LZ <= 256 && L <= 256 && std::is_same<C, float2>::value) {
+          // the spectra's ring slots (the march and aim_rhs keep every history slab in the ring)
+          const size_t slab = op_slab_bytes(c, c->batch_max);
+          SlabRing sr{};
+          sr.n = sl.n;
+          bool in_ring = c->ring_tma && sl.n > 0;
+          for (int i = 0; i < sl.n && in_ring; ++i) {
+            const long long off = (const char*)sl.p[i] - (const char*)c->d_ring;
+            in_ring = off >= 0 && off % (long long)slab == 0 && off / (long long)slab < c->n_delays;
+            sr.slot[i] = in_ring ? (int)(off / (long long)slab) : 0;
+            sr.m[i] = sl.m[i];
+          }
+          if (in_ring) {
+            constexpr int ZW = L < 16 ? L : 16;
+            const size_t sm = 128 + (2 * LZ * ZW + LZ + LZ * ZW) * sizeof(C);
+            smem_opt_in(k_zrhs_spec_tma<LZ, ZW>, sm);
+            k_zrhs_spec_tma<LZ, ZW><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
+                c->ring_map, sr, kspec(c), zgeom(c), Bf, ztwiddles(c), c->d_err);
+            AIM_CHECK_LAUNCH();
+            return;
+          }
+        }
+        if constexpr (pow2_len(LZ)) {
+          // 16 columns per tile: one step-B item per thread, so the delay sum held in
+          // registers stays at one radix-R2 slice
+          constexpr int ZW = L < 16 ? L : 16;
+          const size_t sm = smem_z(LZ, ZW);
+          smem_opt_in(k_zrhs_spec<LZ, ZW, C>, sm);
+          k_zrhs_spec<LZ, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), zgeom(c), Bf,
+                                                                                      ztwiddles(c));
+        } else {
+          // 8 columns per tile: one step-B item per thread, the delay sum held in registers
+          constexpr int ZW = L < 8 ? L : 8;
+          const size_t sm = smem_z(LZ, ZW);
+          smem_opt_in(k_zrhs_2s<LZ, ZW, C>, sm);
+          k_zrhs_2s<LZ, ZW, C><<<dim3(nb * 4, L / ZW, L), kZThreads, sm, c->stream>>>(sl, kspec(c), zgeom(c), Bf,
+                                                                                    ztwiddles(c));
+        }
         AIM_CHECK_LAUNCH();
-        return;
+      } else {
+        throw AimError{AIM_ERR_ARG, "z transform longer than the padded length"};
       }
-    }
-    if constexpr (pow2_len(L)) {
-      // 16 columns per tile: one step-B item per thread, so the delay sum held in
-      // registers stays at one radix-R2 slice
-      constexpr int ZW = L < 16 ? L : 16;
-      const size_t sm = (L + L * ZW) * sizeof(C);
-      smem_opt_in(k_zrhs_spec<L, ZW, C>, sm);
-      k_zrhs_spec<L, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c),
-                                                                                  zr(c));
-    } else {
-      // 8 columns per tile: one step-B item per thread, the delay sum held in registers
-      constexpr int ZW = L < 8 ? L : 8;
-      const size_t sm = (L + L * ZW) * sizeof(C);
-      smem_opt_in(k_zrhs_2s<L, ZW, C>, sm);
-      k_zrhs_2s<L, ZW, C><<<dim3(nb * 4, L / ZW, L), kZThreads, sm, c->stream>>>(sl, kspec(c), N, Bf, twiddles(c),
-                                                                                zr(c));
-    }
-    AIM_CHECK_LAUNCH();
+    });
   }
 
   static const C* twiddles(aim_ctx* c) { return sel_tw(c, (C*)nullptr); }
+  static const C* ztwiddles(aim_ctx* c) { return sel_twz(c, (C*)nullptr); }
   static const C* kspec(aim_ctx* c) { return sel_kspec(c, (C*)nullptr); }
   static const typename Real<C>::F4* ncoef(aim_ctx* c) { return sel_ncoef(c, (C*)nullptr); }
   static const typename Real<C>::T* lam(aim_ctx* c) { return sel_lam(c, (C*)nullptr); }

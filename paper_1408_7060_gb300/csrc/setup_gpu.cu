@@ -172,16 +172,19 @@ __global__ void k_max_dist2(const int* __restrict__ cand, int nc, int N, int* __
 
 // ------------------------------------------------------------------ grid kernels
 
-// G_m on the padded grid: offset i for i < N, i - 2N for i > N, plane N unused (0)
-__global__ void k_kernel_grid(TimeK p, int m, int N, double h, double2* __restrict__ GA, double2* __restrict__ GP) {
+// G_m on the (2N, 2N, LZ) padded grid [z][y][x]: offset i for i < H, i - length for
+// i > H, plane H unused (0), with H = N in x and y and H = LZ/2 in z
+__global__ void k_kernel_grid(TimeK p, int m, int N, int LZ, double h, double2* __restrict__ GA,
+                              double2* __restrict__ GP) {
   const long long L = 2 * N;
-  const long long M = L * L * L;
+  const long long M = L * L * LZ;
+  const int HZ = LZ / 2;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < M;
        idx += (long long)gridDim.x * blockDim.x) {
     int ix = (int)(idx % L), iy = (int)((idx / L) % L), iz = (int)(idx / (L * L));
     double2 a = make_double2(0, 0), b = make_double2(0, 0);
-    if (ix != N && iy != N && iz != N) {
-      int dx = ix < N ? ix : ix - (int)L, dy = iy < N ? iy : iy - (int)L, dz = iz < N ? iz : iz - (int)L;
+    if (ix != N && iy != N && iz != HZ) {
+      int dx = ix < N ? ix : ix - (int)L, dy = iy < N ? iy : iy - (int)L, dz = iz < HZ ? iz : iz - LZ;
       grid_kernel(p, m, h, dx, dy, dz, a, b);
     }
     GA[idx] = a;
@@ -189,11 +192,13 @@ __global__ void k_kernel_grid(TimeK p, int m, int N, double h, double2* __restri
   }
 }
 
-__global__ void k_extract_octant(const double2* __restrict__ G, int N, double scale, double2* __restrict__ o64,
-                                 float2* __restrict__ o32) {
+// the octant [LZ/2 + 1][N + 1][N + 1] of the (2N, 2N, LZ) spectrum
+__global__ void k_extract_octant(const double2* __restrict__ G, int N, int LZ, double scale,
+                                 double2* __restrict__ o64, float2* __restrict__ o32) {
   const int n1 = N + 1;
   const long long L = 2 * N;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n1 * n1 * n1; idx += gridDim.x * blockDim.x) {
+  const int noct = n1 * n1 * (LZ / 2 + 1);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < noct; idx += gridDim.x * blockDim.x) {
     int x = idx % n1, y = (idx / n1) % n1, z = idx / (n1 * n1);
     double2 v = G[((long long)z * L + y) * L + x];
     v = make_double2(scale * v.x, scale * v.y);
@@ -632,28 +637,33 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
     if (c->n_delays + 1 > aimc::kMaxDelays) throw AimError{AIM_ERR_ARG, "too many delays (N_g + 1 > 32)"};
   }
   const int nm = c->n_delays + 1;
-  // ---- twiddles W_L^t = exp(-2 pi i t / L)
+  // ---- twiddles W_n^t = exp(-2 pi i t / n) of the x/y (n = L) and z (n = LZ) transforms
   {
-    std::vector<double2> tw(L);
-    std::vector<float2> twf(L);
-    for (int t = 0; t < L; ++t) {
-      double a = 2.0 * aimc::kPi * (double)t / (double)L;
-      tw[t] = make_double2(std::cos(a), -std::sin(a));
-      twf[t] = make_float2((float)tw[t].x, (float)tw[t].y);
-    }
-    c->d_tw = (double2*)aim_alloc(c, L * sizeof(double2));
-    c->d_twf = (float2*)aim_alloc(c, L * sizeof(float2));
-    AIM_CUDA(cudaMemcpyAsync(c->d_tw, tw.data(), L * sizeof(double2), cudaMemcpyHostToDevice, st));
-    AIM_CUDA(cudaMemcpyAsync(c->d_twf, twf.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st));
-    AIM_CUDA(cudaStreamSynchronize(st));
+    auto table = [&](int n, double2*& d64, float2*& d32) {
+      std::vector<double2> tw(n);
+      std::vector<float2> twf(n);
+      for (int t = 0; t < n; ++t) {
+        double a = 2.0 * aimc::kPi * (double)t / (double)n;
+        tw[t] = make_double2(std::cos(a), -std::sin(a));
+        twf[t] = make_float2((float)tw[t].x, (float)tw[t].y);
+      }
+      d64 = (double2*)aim_alloc(c, n * sizeof(double2));
+      d32 = (float2*)aim_alloc(c, n * sizeof(float2));
+      AIM_CUDA(cudaMemcpyAsync(d64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st));
+      AIM_CUDA(cudaMemcpyAsync(d32, twf.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st));
+      AIM_CUDA(cudaStreamSynchronize(st));
+    };
+    table(L, c->d_tw, c->d_twf);
+    table(c->LZ, c->d_twz, c->d_twzf);
   }
-  // ---- kernel spectra: tabulate on the padded grid, full 3-D FFT (FP64), keep the octant
+  // ---- kernel spectra: tabulate on the (L, L, LZ) padded grid, full 3-D FFT (FP64),
+  //      keep the octant
   {
     const size_t n1 = (size_t)(N + 1);
-    const size_t oct = n1 * n1 * n1;
+    const size_t oct = n1 * n1 * (size_t)(c->LZ / 2 + 1);
     c->d_kspec = (double2*)aim_alloc(c, (size_t)nm * 2 * oct * sizeof(double2));
     c->d_kspecf = (float2*)aim_alloc(c, (size_t)nm * 2 * oct * sizeof(float2));
-    const size_t M = (size_t)L * L * L;
+    const size_t M = (size_t)L * L * c->LZ;
     double2* GA = nullptr;
     double2* GP = nullptr;
     AIM_CUDA(cudaMalloc(&GA, M * sizeof(double2)));
@@ -665,13 +675,13 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
     try {
       const double cA = aimc::kMu0 / (4.0 * aimc::kPi), cP = 1.0 / (4.0 * aimc::kPi * aimc::kEps0);
       for (int m = 0; m < nm; ++m) {
-        k_kernel_grid<<<launch_blocks((long long)M, 256), 256, 0, st>>>(tk, m, N, c->h, GA, GP);
+        k_kernel_grid<<<launch_blocks((long long)M, 256), 256, 0, st>>>(tk, m, N, c->LZ, c->h, GA, GP);
         AIM_CHECK_LAUNCH();
         for (int kind = 0; kind < 2; ++kind) {
           double2* G = kind == 0 ? GA : GP;
           fft3d_full_c128(c, G);
           k_extract_octant<<<launch_blocks((long long)oct, 256), 256, 0, st>>>(
-              G, N, (kind == 0 ? cA : cP) / (double)M, c->d_kspec + ((size_t)m * 2 + kind) * oct,
+              G, N, c->LZ, (kind == 0 ? cA : cP) / (double)M, c->d_kspec + ((size_t)m * 2 + kind) * oct,
               c->d_kspecf + ((size_t)m * 2 + kind) * oct);
           AIM_CHECK_LAUNCH();
         }
@@ -809,25 +819,38 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
 // ------------------------------------------------------------------ full 3-D FFT (setup)
 #include "operator_body.cuh"
 
+// the full FFT of a [LZ][L][L] grid (z, y, x)
 template <int L>
 static void fft3d_full_L(aim_ctx* c, double2* G) {
   constexpr int W = col_width<L, double2>();
   cudaStream_t st = c->stream;
   const double2* tw = c->d_tw;
+  const int LZ = c->LZ;
   const int rp = std::max(1, 2048 / L);
   size_t sm = (L + rp * L + row_scratch<L>(rp)) * sizeof(double2);
   smem_opt_in(k_rows<L, false, double2>, sm);
-  k_rows<L, false, double2><<<(L * L + rp - 1) / rp, 256, sm, st>>>(G, G, L * L, L, L, L, L, tw, rp);
+  k_rows<L, false, double2><<<(L * LZ + rp - 1) / rp, 256, sm, st>>>(G, G, L * LZ, L, L, L, L, tw, rp);
   AIM_CHECK_LAUNCH();
   sm = (L + 2 * L * W) * sizeof(double2);
   smem_opt_in(k_cols<L, W, false, double2>, sm);
   const long long LL2 = (long long)L * L;
   // y lines: planes z (stride L^2), element stride L
-  k_cols<L, W, false, double2><<<dim3(L / W, L, 1), 256, sm, st>>>(G, G, L, L, L, L, L, LL2, LL2, 0, 0, tw);
+  k_cols<L, W, false, double2><<<dim3(L / W, LZ, 1), 256, sm, st>>>(G, G, L, L, L, L, L, LL2, LL2, 0, 0, tw);
   AIM_CHECK_LAUNCH();
   // z lines: rows y (stride L), element stride L^2
-  k_cols<L, W, false, double2><<<dim3(L / W, L, 1), 256, sm, st>>>(G, G, L, L, LL2, LL2, L, L, L, 0, 0, tw);
-  AIM_CHECK_LAUNCH();
+  with_zlen(LZ, [&](auto lz) {
+    constexpr int Z = decltype(lz)::value;
+    if constexpr (Z <= L) {
+      constexpr int WZ = col_width<Z, double2>();
+      const size_t smz = (Z + 2 * Z * WZ) * sizeof(double2);
+      smem_opt_in(k_cols<Z, WZ, false, double2>, smz);
+      k_cols<Z, WZ, false, double2><<<dim3(L / WZ, L, 1), 256, smz, st>>>(G, G, Z, Z, LL2, LL2, L, L, L, 0, 0,
+                                                                         c->d_twz);
+      AIM_CHECK_LAUNCH();
+    } else {
+      throw AimError{AIM_ERR_ARG, "z transform longer than the padded length"};
+    }
+  });
 }
 
 void fft3d_full_c128(aim_ctx* c, double2* G) { AIM_DISPATCH_L(c->L, fft3d_full_L<LL>(c, G)); }

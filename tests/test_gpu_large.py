@@ -44,6 +44,10 @@ def test_array_384_sampled_rows():
     xd = torch.tensor(x, device="cuda")
     with AimContext.from_workload(w, precision="c128") as c:
         assert c.n_delays == A.n_delays
+        # the flat array spans about a fifth of the grid in z: its z transforms are
+        # shorter than the 768-point padding (same values on the box's planes)
+        nz = c.info["box_hi"][2] - c.info["box_lo"][2] + 1
+        assert 2 * nz <= c.info["z_len"] < 2 * w.grid_n
         y128 = c.matvec(0, xd).cpu().numpy()[0]
     with AimContext.from_workload(w, precision="c64") as c:
         y64 = c.matvec(0, xd).cpu().numpy()[0]

@@ -95,13 +95,26 @@ def test_near_zone(s480, s480_ctx):
         assert np.abs(val[m] - ref[m]).max() < 1e-9 * sc, m
 
 
+def z_embedded(G2, lz):
+    """The (2N)^3 kernel grid [z][y][x] re-embedded with z period lz: offsets |dz| < lz/2
+    taken from the 2N grid, plane lz/2 zero (the layout the context's z transform uses)."""
+    n2 = G2.shape[0]
+    iz = np.arange(lz)
+    dz = np.where(iz < lz // 2, iz, iz - lz)
+    out = G2[dz % n2].copy()
+    out[lz // 2] = 0
+    return out
+
+
 def test_kernel_spectra(s480, s480_ctx):
     w, rwg, p, A = s480
     n = A.n
-    M = (2 * n) ** 3
+    lz = s480_ctx.info["z_len"]
+    assert lz % 16 == 0 and 2 * (s480_ctx.info["box_hi"][2] - s480_ctx.info["box_lo"][2] + 1) <= lz <= 2 * n
+    M = (2 * n) ** 2 * lz
     for m in range(A.n_delays + 1):
         for kind in (0, 1):
-            G = np.fft.fftn(A.kernel_grid(m, kind))[: n + 1, : n + 1, : n + 1]
+            G = np.fft.fftn(z_embedded(A.kernel_grid(m, kind), lz))[: lz // 2 + 1, : n + 1, : n + 1]
             G *= (oaim.CA if kind == 0 else oaim.CP) / M
             got = s480_ctx.kernel_spectrum(m, kind)
             assert np.abs(got - G).max() < 1e-12 * np.abs(G).max(), (m, kind)
