@@ -20,7 +20,11 @@ What it computes (each module cites the passage it follows):
                  grid Green-function envelopes, brute-force and FFT grid sums, and
                  the pre-corrected near-zone matrices (Sec. 4, stages i-iv).
 * ``march``      time marching of Eq. 4 (direct ET-MOT) and Eq. 5 (ET-AIM).
-* ``mie``        Mie series for a PEC sphere (Sec. 5, reference [18]).
+* ``mie``        Mie series for a PEC sphere (Sec. 5, reference [18]) and the dB-error
+                 norm of Eq. 2.
+* ``rcs``        bistatic RCS of a marched current envelope at one frequency
+                 (Sec. 2.4): the CPPIF spectrum, the envelope and incident-pulse
+                 transforms, and the directions and weights of the Eq. 2 integrals.
 
 Readings of passages the paper leaves open are listed in the design notes; the
 code states each one where it is used.

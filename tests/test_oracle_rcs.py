@@ -1,0 +1,81 @@
+"""Pins of the oracle's time-domain RCS pipeline (Sec. 2.4, Eq. 2).
+
+* the CPPIF spectrum That(w) (Eq. 3): the closed form sinc^2(w/2) of the linear
+  interpolant (Q = 1); That(2 pi n) = delta_n0 and That'(2 pi n) = 0 for n != 0 (the
+  basis reproduces constants and linear functions); That(w) = 1 + O(w^{Q+1}) near 0;
+* the RCS of an ET-MOT march at the centre frequency equals the frequency-domain EFIE
+  RCS on the same mesh: summing the march over all steps with the CPPIF partition of
+  unity gives (sum_m Z_m) (sum_l I_l) = sum_l V_l, the frequency-domain system at f_c,
+  so the two agree to rounding -- a check of every normalisation in the conversion
+  (dt, the incident spectrum, the 1/2 of the envelope convention);
+* off the centre frequency, inside the pulse's band, the two agree to the temporal
+  discretisation error, and both agree with the Mie series in the dB norm of Eq. 2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import efie, march, mie, rcs
+from oracle.rwg import build_rwg
+from paper_1408_7060_gb300.inputs import icosphere
+
+
+def test_cppif_spectrum_closed_form_and_strang_fix():
+    w = np.linspace(-7.0, 7.0, 29)
+    assert np.abs(rcs.cppif_spectrum(w, 1) - np.sinc(w / (2 * np.pi)) ** 2).max() < 1e-14
+    for Q in (1, 2, 3):
+        That = rcs.cppif_spectrum(2 * np.pi * np.arange(-3, 4), Q)
+        assert abs(That[3] - 1) < 1e-14 and np.abs(np.delete(That, 3)).max() < 1e-14, Q
+        h = 1e-4
+        for n in (1, 2, -1):
+            d = (rcs.cppif_spectrum(2 * np.pi * n + h, Q) - rcs.cppif_spectrum(2 * np.pi * n - h, Q)) / (2 * h)
+            assert abs(d[0]) < 1e-7, (Q, n)
+        # That(w) - 1 = O(w^{Q+1}): halving w divides the defect by 2^{Q+1}
+        a, b = rcs.cppif_spectrum(0.02, Q)[0] - 1, rcs.cppif_spectrum(0.01, Q)[0] - 1
+        assert abs(abs(a / b) - 2 ** (Q + 1)) < 0.05 * 2 ** (Q + 1), Q
+
+
+@pytest.fixture(scope="module")
+def sphere_march():
+    """480-RWG sphere, 150 MHz +-5 % (chi = 20), ET-MOT march by dense LU."""
+    V, F = icosphere(2, 1.0)
+    rwg = build_rwg(V, F)
+    f_c, fb = 150e6, 0.05 * 150e6
+    sigma, dt = 3 / (2 * math.pi * fb), 1 / (4 * fb)
+    t_d = 8 * sigma
+    p = efie.Params(dt=dt, f_c=f_c, Q=2)
+    Z = efie.fill_dense(rwg, p)
+    n_t = int(2 * t_d / dt) + 30
+    Vx = efie.excitation(rwg, p, [0, 0, 1], [1, 0, 0], sigma, t_d, np.arange(1, n_t + 1))
+    I = march.march_dense(Z, Vx)[:, 0]
+    return rwg, p, I, sigma, t_d, fb
+
+
+def fd_rcs(rwg, p, f, rh, pol):
+    pf = efie.Params(dt=p.dt, f_c=f, Q=p.Q)
+    ZF = efie.fill_dense(rwg, pf, freq=True)
+    VF = efie.excitation_fd(rwg, pf, [0, 0, 1], [1, 0, 0])[0]
+    return efie.rcs_fd(rwg, pf, np.linalg.solve(ZF, VF), rh, pol)
+
+
+def test_march_rcs_at_centre_frequency_is_the_fd_rcs(sphere_march):
+    rwg, p, I, sigma, t_d, fb = sphere_march
+    assert np.abs(I[-1]).max() < 1e-8 * np.abs(I).max()  # the march has rung down
+    rh, eth, w, T, P = rcs.sphere_directions(12, 12)
+    s_td = rcs.rcs_td(rwg, p, I, sigma, t_d, p.f_c, rh, eth)
+    s_fd = fd_rcs(rwg, p, p.f_c, rh, eth)
+    assert np.abs(s_td - s_fd).max() < 1e-10 * s_fd.max()
+    assert mie.db_error(s_td, s_fd, w) < 1e-12
+
+
+def test_march_rcs_in_band_vs_fd_and_mie(sphere_march):
+    rwg, p, I, sigma, t_d, fb = sphere_march
+    rh, eth, w, T, P = rcs.sphere_directions(12, 12)
+    for f in (p.f_c + 0.5 * fb, p.f_c - 0.5 * fb):
+        s_td = rcs.rcs_td(rwg, p, I, sigma, t_d, f, rh, eth)
+        s_fd = fd_rcs(rwg, p, f, rh, eth)
+        k = 2 * math.pi * f / 299792458.0
+        s_mie = mie.rcs(k, k, T, "E") * np.cos(P) ** 2
+        assert mie.db_error(s_td, s_fd, w) < 1e-4, f
+        assert mie.db_error(s_td, s_mie, w) < 1e-3, f
