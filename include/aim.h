@@ -370,6 +370,35 @@ int aim_march_adjoint_farfield(aim_ctx* ctx, const double* khat, const double* p
                                int32_t n_steps, double tol, int32_t nd, const double* rhat, const double* e1,
                                const double* e2, int32_t n0, int32_t n_out, const aim_c128* F, aim_c128* grad,
                                aim_stats* stats);
+
+/*
+ * aim_march_spectrum -- the frequency-domain currents of a march (Sec. 2.4): march Eq. 5
+ * from rest for the plane waves of exc (as aim_march) and, instead of the current
+ * history, return for each frequency f the current for a unit incident plane wave
+ *   I_f[b][k] = dt That(Omega dt) sum_l I_l[b][k] e^{-j Omega l dt} / E~(Omega),
+ *   Omega = 2 pi (f - f_c),  That(w) = int T(u) e^{-j w u} du  (the CPPIF of Eq. 3),
+ *   E~(Omega) = sigma sqrt(2 pi) exp(-sigma^2 Omega^2 / 2) exp(-j (w_c + Omega) t_d),
+ * E~ being the transform of the incident envelope of Eq. 1 at the origin (envelope
+ * convention x(t) = Re{x~(t) e^{j w_c t}}).  Each committed I_l is added at once; no
+ * current history is kept.  The march cannot be continued (aim_march_continue).
+ *   freqs: host [n_freq] (Hz, > 0), 1 <= n_freq <= 64; spec: [n_freq][nb][ns], host or
+ *   device.  stats and errors as aim_march.
+ *
+ * aim_rcs -- bistatic RCS (m^2) of frequency-domain currents for a unit incident field:
+ *   sigma[f][b][d] = 4 pi (w mu0 / (4 pi))^2 |pol_d . (I - r_d r_d) sum_k I_f[b][k]
+ *                    int S_k(r') e^{+j k r_d.r'} dS'|^2,   w = 2 pi f_f,  k = w / c
+ * (the 7-point cubature of every face).  With the currents of aim_march_spectrum this
+ * is the co- or cross-polarised RCS of the march at f, the quantity the dB-error norm
+ * of Eq. 2 compares over all directions.
+ *   freqs: host [n_freq]; spec: [n_freq][nb][ns] host or device; rhat, pol: host
+ *   [nd][3] unit vectors; sigma: [n_freq][nb][nd] host or device.  AIM_ERR_ARG on null
+ *   pointers or sizes outside 1..65535.
+ */
+int aim_march_spectrum(aim_ctx* ctx, const aim_excitation* exc, int32_t n_steps, double tol, int32_t n_freq,
+                       const double* freqs, aim_c128* spec, aim_stats* stats);
+int aim_rcs(aim_ctx* ctx, int32_t n_freq, const double* freqs, int32_t nb, const aim_c128* spec, int32_t nd,
+            const double* rhat, const double* pol, double* sigma);
+
 int aim_excitation_samples(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0, int32_t n_samp,
                            const aim_c128* a, int32_t n_steps, aim_c128* V);
 int aim_excitation_samples_adjoint(aim_ctx* ctx, const double* khat, const double* phat, int32_t i0,

@@ -75,7 +75,7 @@ EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_nu
            "aim_get_near", "aim_get_preconditioner", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
            "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
            "aim_farfield", "aim_farfield_adjoint", "aim_march_adjoint", "aim_march_farfield",
-           "aim_march_adjoint_farfield"]
+           "aim_march_adjoint_farfield", "aim_march_spectrum", "aim_rcs"]
 AIM_K_COUNT = 13
 
 _LIB = None
@@ -123,6 +123,8 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
                                           ct.POINTER(aim_stats)]),
         "aim_march_adjoint_farfield": (ct.c_int, [P, P, P, I32, I32, I32, D, I32, P, P, P, I32, I32, P, P,
                                                   ct.POINTER(aim_stats)]),
+        "aim_march_spectrum": (ct.c_int, [P, ct.POINTER(aim_excitation), I32, D, I32, P, P, ct.POINTER(aim_stats)]),
+        "aim_rcs": (ct.c_int, [P, I32, P, I32, P, I32, P, P, P]),
         "aim_get_anterp": (ct.c_int, [P, P, P]),
         "aim_get_near": (ct.c_int, [P, P, P, P]),
         "aim_get_preconditioner": (ct.c_int, [P, P, P, P]),
@@ -294,6 +296,37 @@ def aim_march(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
     stats = _stats(st, iters)
     _check(lib, ctx, rc, "aim_march", stats)
     return cur, stats, rc
+
+
+def aim_march_spectrum(ctx, khat, phat, sigma, t_d, n_steps, tol, freqs, out=None):
+    """March Eq. 5 from rest and return the frequency-domain currents for a unit incident
+    field at ``freqs`` (Hz): (spec[n_freq, nb, ns], stats dict, status)."""
+    lib = load()
+    ns, _ = aim_num_unknowns(ctx)
+    e, keep = _exc(khat, phat, sigma, t_d)
+    fr = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+    spec = np.empty((len(fr), e.nb, ns), dtype=np.complex128) if out is None else out
+    iters = np.zeros((n_steps, e.nb), dtype=np.int32)
+    st = aim_stats(0, 0, 0, 0.0, 0.0, 0.0, iters.ctypes.data, 0, 0)
+    rc = lib.aim_march_spectrum(ctx, ct.byref(e), int(n_steps), float(tol), len(fr), fr.ctypes.data, _ptr(spec),
+                                ct.byref(st))
+    stats = _stats(st, iters)
+    _check(lib, ctx, rc, "aim_march_spectrum", stats)
+    return spec, stats, rc
+
+
+def aim_rcs(ctx, freqs, spec, rhat, pol, out=None):
+    """Bistatic RCS (m^2) of frequency-domain currents spec[n_freq, nb, ns] in the
+    directions rhat[nd, 3] for receive polarisations pol[nd, 3]: [n_freq, nb, nd]."""
+    lib = load()
+    fr = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+    rh = np.ascontiguousarray(rhat, dtype=np.float64).reshape(-1, 3)
+    po = np.ascontiguousarray(pol, dtype=np.float64).reshape(-1, 3)
+    nb = spec.shape[1]
+    sig = np.empty((len(fr), nb, len(rh))) if out is None else out
+    _check(lib, ctx, lib.aim_rcs(ctx, len(fr), fr.ctypes.data, nb, _ptr(spec), len(rh), rh.ctypes.data,
+                                 po.ctypes.data, _ptr(sig)), "aim_rcs")
+    return sig
 
 
 def aim_march_continue(ctx, khat, phat, sigma, t_d, n_steps, tol, out=None):
@@ -503,6 +536,12 @@ class AimContext:
 
     def march(self, khat, phat, sigma, t_d, n_steps, tol, out=None):
         return aim_march(self.handle, khat, phat, sigma, t_d, n_steps, tol, out)
+
+    def march_spectrum(self, khat, phat, sigma, t_d, n_steps, tol, freqs, out=None):
+        return aim_march_spectrum(self.handle, khat, phat, sigma, t_d, n_steps, tol, freqs, out)
+
+    def rcs(self, freqs, spec, rhat, pol, out=None):
+        return aim_rcs(self.handle, freqs, spec, rhat, pol, out)
 
     def march_continue(self, khat, phat, sigma, t_d, n_steps, tol, out=None):
         return aim_march_continue(self.handle, khat, phat, sigma, t_d, n_steps, tol, out)

@@ -1,6 +1,7 @@
 // extern "C" entry points of the ET-AIM library (declared in include/aim.h).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
@@ -13,6 +14,7 @@
 #include "gmres.h"
 #include "tma.cuh"
 #include "operator.h"
+#include "rcs.h"
 #include "setup_gpu.h"
 #include "setup_host.h"
 
@@ -741,6 +743,80 @@ int aim_march_farfield(aim_ctx* c, const double* khat, const double* phat, int32
     const int rc = march_steps(c, io, n_steps, tol, stats);
     finish_out(c, F, Fd, nf, dev);
     return rc;
+  });
+}
+
+int aim_march_spectrum(aim_ctx* c, const aim_excitation* exc, int32_t n_steps, double tol, int32_t n_freq,
+                       const double* freqs, aim_c128* spec, aim_stats* stats) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!spec || !freqs || n_steps < 1 || !(tol > 0) || n_freq < 1 || n_freq > kMaxRcsFreq)
+      throw AimError{AIM_ERR_ARG, "aim_march_spectrum: bad arguments (1 <= n_freq <= 64)"};
+    for (int f = 0; f < n_freq; ++f)
+      if (!(freqs[f] > 0)) throw AimError{AIM_ERR_ARG, "aim_march_spectrum: frequencies must be > 0"};
+    upload_waves(c, exc);
+    const int nb = exc->nb;
+    const size_t n = (size_t)n_freq * nb * c->ns;
+    std::vector<double> omega(n_freq);
+    for (int f = 0; f < n_freq; ++f) omega[f] = 2.0 * aimc::kPi * (freqs[f] - c->f_c);
+    const bool dev = is_device_ptr(spec);
+    double2* acc = dev ? reinterpret_cast<double2*>(spec) : scratch(c, n, 3);
+    AIM_CUDA(cudaMemsetAsync(acc, 0, n * sizeof(double2), c->stream));
+    AIM_CUDA(cudaMemsetAsync(c->d_x, 0, (size_t)nb * c->ns * sizeof(double2), c->stream));
+    c->l_done = 0;
+    c->march_nb = 0;  // no current history to continue from
+    StepIO io;
+    io.exc = exc;
+    io.nb = nb;
+    io.commit = [&](int j, const double2* x) { rcs_dft_accum(c, nb, j, n_freq, omega.data(), x, acc); };
+    const int rc = march_steps(c, io, n_steps, tol, stats);
+    // dt That(Omega dt) / E~(Omega): the interpolated envelope over the unit incident pulse
+    RcsPhases sc{};
+    sc.n = n_freq;
+    for (int f = 0; f < n_freq; ++f) {
+      const double W = omega[f];
+      const std::complex<double> E = exc->sigma * std::sqrt(2.0 * aimc::kPi) *
+                                     std::exp(-0.5 * exc->sigma * exc->sigma * W * W) *
+                                     std::exp(std::complex<double>(0.0, -(c->wc + W) * exc->t_d));
+      const std::complex<double> v = c->dt * cppif_spectrum(c->tb, W * c->dt) / E;
+      sc.w[f] = make_double2(v.real(), v.imag());
+    }
+    rcs_scale(c, nb, sc, acc);
+    finish_out(c, spec, acc, n, dev);
+    return rc;
+  });
+}
+
+int aim_rcs(aim_ctx* c, int32_t n_freq, const double* freqs, int32_t nb, const aim_c128* spec, int32_t nd,
+            const double* rhat, const double* pol, double* sigma) {
+  if (!c) return AIM_ERR_ARG;
+  return guard(c, [&] {
+    if (!freqs || !spec || !rhat || !pol || !sigma || n_freq < 1 || nb < 1 || nd < 1 || nd > 65535 || nb > 65535 ||
+        n_freq > 65535)
+      throw AimError{AIM_ERR_ARG, "aim_rcs: bad arguments"};
+    const size_t n = (size_t)n_freq * nb * c->ns, no = (size_t)n_freq * nb * nd;
+    std::vector<double> h((size_t)6 * nd + 2 * n_freq);
+    for (int d = 0; d < nd; ++d)
+      for (int x = 0; x < 3; ++x) {
+        h[6 * d + x] = rhat[3 * d + x];
+        h[6 * d + 3 + x] = pol[3 * d + x];
+      }
+    for (int f = 0; f < n_freq; ++f) {
+      if (!(freqs[f] > 0)) throw AimError{AIM_ERR_ARG, "aim_rcs: frequencies must be > 0"};
+      const double w = 2.0 * aimc::kPi * freqs[f];
+      const double a = w * aimc::kMu0 / (4.0 * aimc::kPi);
+      h[6 * nd + 2 * f] = w / aimc::kC0;
+      h[6 * nd + 2 * f + 1] = 4.0 * aimc::kPi * a * a;
+    }
+    double* dd = reinterpret_cast<double*>(scratch(c, h.size() / 2 + 1, 4));
+    AIM_CUDA(cudaMemcpyAsync(dd, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const double2* ds = dev_in(c, spec, n, scratch(c, n, 1));
+    const bool dev = is_device_ptr(sigma);
+    double* out = dev ? sigma : reinterpret_cast<double*>(scratch(c, no / 2 + 1, 2));
+    rcs_farfield(c, n_freq, nb, ds, nd, dd, dd + 6 * nd, out);
+    if (!dev) AIM_CUDA(cudaMemcpyAsync(sigma, out, no * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    AIM_CUDA(cudaStreamSynchronize(c->stream));
+    return AIM_OK;
   });
 }
 
