@@ -23,9 +23,11 @@
  *    passes; the context owns all device memory it allocates.
  *  - A context is bound to one CUDA device and one stream (aim_opts.cuda_stream,
  *    or a stream it creates).  It is not thread-safe.
- *  - RWG ordering: edges sorted by (lower vertex, higher vertex); T+ is the face
- *    whose counter-clockwise cycle runs along the edge from the lower to the
- *    higher vertex.  aim_rwg_table() exports it.
+ *  - RWG ordering: interior edges sorted by (lower vertex, higher vertex); T+ is the
+ *    face whose counter-clockwise cycle runs along the edge from the lower to the
+ *    higher vertex.  aim_rwg_table() exports it.  Open surfaces (the plates of
+ *    Sec. 5.1) are accepted: an edge of a single face is a boundary edge and carries
+ *    no basis function.
  *  - Grid nodes are indexed n = (iz * N + iy) * N + ix; each RWG owns the 4x4x4
  *    stencil anchored at floor((x_e - origin)/h) - 1 (clamped to [0, N-4]) per
  *    axis, x_e the midpoint of its edge.
@@ -42,7 +44,8 @@ extern "C" {
 enum {
   AIM_OK = 0,
   AIM_ERR_ARG = -1,      /* invalid argument (null pointer, size out of range)     */
-  AIM_ERR_MESH = -2,     /* boundary or non-manifold edge, inconsistent orientation */
+  AIM_ERR_MESH = -2,     /* non-manifold edge, inconsistent orientation, degenerate
+                            face, or no interior edge                                 */
   AIM_ERR_CUDA = -3,     /* a CUDA runtime call failed (message in aim_last_error)  */
   AIM_ERR_OOM = -4,      /* device allocation failed                               */
   AIM_ERR_NOCONV = -5,   /* GMRES hit its iteration cap; stats->last_step is valid  */

@@ -1,7 +1,9 @@
-"""RWG (Rao-Wilton-Glisson) spatial basis on a closed triangle mesh, Sec. 3 (Eq. 3).
+"""RWG (Rao-Wilton-Glisson) spatial basis on a triangle mesh, Sec. 3 (Eq. 3).
 
-One basis per interior edge.  Ordering and orientation (a reading; the paper
-defers the basis to its reference [14]):
+One basis per interior edge (an edge shared by two faces); an edge of one face only
+lies on the boundary of an open surface (the plates of Sec. 5.1) and carries none, its
+face slot left empty.  Ordering and orientation (a reading; the paper defers the basis
+to its reference [14]):
 
 * edges are sorted by (lower vertex index, higher vertex index);
 * T+ is the face whose counter-clockwise vertex cycle runs along the edge from
@@ -37,7 +39,8 @@ class RWG:
     def tri_bases(self):
         """For every face, the (rwg, sign, free vertex) of its three edges.
 
-        Returns ``k[nt,3], s[nt,3], vfree[nt,3]`` (vertex indices).
+        Returns ``k[nt,3], s[nt,3], vfree[nt,3]`` (vertex indices); a slot of a
+        boundary edge keeps k = -1, s = 0, vfree = -1 (its coefficient s l / 2A is 0).
         """
         nt = len(self.F)
         k = np.full((nt, 3), -1, dtype=np.int64)
@@ -67,6 +70,8 @@ def build_rwg(V: np.ndarray, F: np.ndarray) -> RWG:
     edge, tri, free = [], [], []
     for key in keys:
         own = owners[key]
+        if len(own) == 1:
+            continue  # boundary edge of an open surface: no basis
         if len(own) != 2 or own[0][1] == own[1][1]:
             raise ValueError(f"edge {key} is not a consistently oriented manifold edge")
         plus = own[0] if own[0][1] > 0 else own[1]

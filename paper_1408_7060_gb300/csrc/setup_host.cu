@@ -52,8 +52,12 @@ void host_build_rwg(const aim_mesh* m, HostMesh& hm) {
   for (size_t i = 0; i < own.size();) {
     size_t j = i;
     while (j < own.size() && own[j].key == own[i].key) ++j;
+    if (j - i == 1) {  // boundary edge of an open surface: no basis function
+      i = j;
+      continue;
+    }
     if (j - i != 2 || own[i].dir == own[i + 1].dir)
-      throw AimError{AIM_ERR_MESH, "boundary, non-manifold or inconsistently oriented edge"};
+      throw AimError{AIM_ERR_MESH, "non-manifold or inconsistently oriented edge"};
     const Own& pl = own[i].dir > 0 ? own[i] : own[i + 1];
     const Own& mi = own[i].dir > 0 ? own[i + 1] : own[i];
     int lo = (int)(own[i].key / hm.nv), hi = (int)(own[i].key % hm.nv);
@@ -66,6 +70,7 @@ void host_build_rwg(const aim_mesh* m, HostMesh& hm) {
     i = j;
   }
   hm.ns = (int)hm.edge.size() / 2;
+  if (hm.ns < 1) throw AimError{AIM_ERR_MESH, "no interior edge"};
   hm.len.resize(hm.ns);
   double sum = 0.0;
   for (int k = 0; k < hm.ns; ++k) {

@@ -84,6 +84,21 @@ def sphere_array(sub: int, radius: float, pitch: float, nx: int = 4, ny: int = 4
     return np.concatenate(Vs), np.concatenate(Fs).astype(np.int32)
 
 
+def plate_mesh(side: float, n: int):
+    """Square plate of side ``side`` in the z = 0 plane, centred on the origin: n x n
+    square cells, each split by its (+x, +y) diagonal, faces counter-clockwise about +z.
+    The open surface has 3 n^2 - 2 n interior edges (RWG functions): 280, 1160, 4720 and
+    19 040 for the 0.1 m cells of the 1, 2, 4 and 8 m plates of Table II."""
+    x = (np.arange(n + 1) / n - 0.5) * side
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    V = np.stack([X.ravel(), Y.ravel(), np.zeros((n + 1) ** 2)], axis=1)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    a = (j * (n + 1) + i).ravel()          # cell corners a (x, y), b (x+1, y), c (x+1, y+1), d (x, y+1)
+    b, c, d = a + 1, a + n + 2, a + n + 1
+    F = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, d], 1)])
+    return V, F.astype(np.int32)
+
+
 def ellipsoid_mesh(semi_axes=(1.0, 0.5, 0.25), n_points: int = 6668, seed: int = 3,
                    relax_iters: int = 150):
     """Closed ellipsoid surface with nearly uniform point spacing.
@@ -290,7 +305,8 @@ def place_grid(V: np.ndarray, n: int, h: float | None = None):
 
 
 def make_workload(name: str, **over) -> Workload:
-    """The named benchmark shapes (PEC spheres/ellipsoid/sphere array, EFIE, CPPIF Q=2)."""
+    """The named benchmark shapes (PEC spheres/ellipsoid/sphere array, CPPIF Q=2; square
+    plates, CPPIF Q=3; EFIE throughout)."""
     if name == "sphere480":
         V, F = icosphere(2, 1.0)
         h, o = place_grid(V, 16, 0.15)
@@ -328,6 +344,18 @@ def make_workload(name: str, **over) -> Workload:
         w = dict(mesh=(V, F), f_c=1e9, band_frac=0.05, n_t=50, grid_n=int(n), h=h, origin=o,
                  near_radius=3 * h, tol=1e-5, khat=np.array([[0.0, 0.0, 1.0]]),
                  phat=np.array([[1.0, 0.0, 0.0]]), precision="c64")
+    elif name.startswith("plate"):
+        # square PEC plates of Table II (0.1 m cells, 3 n^2 - 2 n RWG), EFIE (alpha = 1,
+        # Sec. 5.1), the chi ~ 20 pulse of Table I (f_c = 285 MHz, sigma = 1/(10 pi) us,
+        # so f_c + 3/(2 pi sigma) = 300 MHz) and CPPIF Q = 3 (Table III), at normal incidence
+        side, grid = {"plate280": (1.0, 16), "plate1160": (2.0, 32), "plate4720": (4.0, 64),
+                      "plate19k": (8.0, 96), "plate306k": (32.0, 384)}[name]
+        V, F = plate_mesh(side, int(round(side / 0.1)))
+        h, o = place_grid(V, grid)
+        f_bw = 3.0 / (2.0 * math.pi * (1e-6 / (10.0 * math.pi)))
+        w = dict(mesh=(V, F), f_c=285e6, band_frac=f_bw / 285e6, n_t=80, grid_n=grid, h=h, origin=o,
+                 near_radius=3 * h, tol=1e-6, khat=np.array([[0.0, 0.0, -1.0]]),
+                 phat=np.array([[1.0, 0.0, 0.0]]), order=3, precision="c64")
     elif name.startswith("sphere_sub"):
         # small parity cases: sphere_sub<s>_n<N>  (radius 1 m, 600 MHz +-30 %)
         s, n = name[len("sphere_sub"):].split("_n")

@@ -52,3 +52,29 @@ def test_sphere_meshes_closed_outward():
     g = (np.arange(4) - 1.5) * 1.5
     centres = np.array([(x, y, 0.0) for y in g for x in g])
     _check_closed_outward(V, F, centres)
+
+
+def test_plate_meshes_match_table_ii():
+    """Square plates: open, every interior edge shared by two faces of opposite
+    traversal, boundary edges on the outline only, faces counter-clockwise about +z, and
+    the RWG counts 3 n^2 - 2 n of Table II (280, 1160, 4720, 19 040 for 1, 2, 4, 8 m)."""
+    from oracle.rwg import build_rwg
+    from paper_1408_7060_gb300.inputs import plate_mesh
+
+    for side, ns in ((1.0, 280), (2.0, 1160), (4.0, 4720), (8.0, 19040)):
+        n = int(round(side / 0.1))
+        V, F = plate_mesh(side, n)
+        P = V[F]
+        nz = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])[:, 2]
+        assert (nz > 0).all() and np.allclose(V[:, 2], 0.0)
+        count = {}
+        for f in F:
+            for j in range(3):
+                a, b = int(f[j]), int(f[(j + 1) % 3])
+                count[(a, b)] = count.get((a, b), 0) + 1
+        assert max(count.values()) == 1                       # no half-edge twice
+        boundary = [(a, b) for (a, b) in count if (b, a) not in count]
+        mid = np.array([(V[a] + V[b]) / 2 for a, b in boundary])
+        assert np.all(np.isclose(np.abs(mid[:, :2]).max(axis=1), side / 2))
+        assert len(boundary) == 4 * n
+        assert build_rwg(V, F).ns == ns == 3 * n * n - 2 * n
