@@ -20,6 +20,8 @@ What it computes (each module cites the passage it follows):
                  grid Green-function envelopes, brute-force and FFT grid sums, and
                  the pre-corrected near-zone matrices (Sec. 4, stages i-iv).
 * ``march``      time marching of Eq. 4 (direct ET-MOT) and Eq. 5 (ET-AIM).
+* ``blocked``    the delayed sums of the right-hand side by the multilevel blocked
+                 schedule with temporal FFTs (Sec. 4, stage ii), and directly.
 * ``mie``        Mie series for a PEC sphere (Sec. 5, reference [18]) and the dB-error
                  norm of Eq. 2.
 * ``rcs``        bistatic RCS of a marched current envelope at one frequency
