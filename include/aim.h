@@ -120,6 +120,13 @@ typedef struct {
                             Cache: the file named by AIM_GB300_PLAN_CACHE, else
                             $HOME/.cache/aim_gb300_plans.jsonl (one JSON object per line).
                             The results do not depend on the plan (same arithmetic per line). */
+  int32_t rhs_blocked;   /* 1: the march forms the delayed grid sums of Eq. 5 by the
+                            multilevel blocked schedule of Sec. 4 stage ii: after step l
+                            the z-spectra of its last b = 2^min(ctz(l), P) steps are
+                            radiated at once to the next b steps' pending sums (2^P >= N_g),
+                            so each step reads O(log N_g) spectra instead of N_g.  Needs a
+                            power-of-two z transform (aim_info.z_len); holds 2^P source and
+                            2^(P+1) pending z-spectra per right-hand side.  0: direct sums. */
 } aim_opts;
 
 typedef struct {
@@ -162,6 +169,7 @@ typedef struct {
                             the z pass (all lines, reading and writing only z in the box)
                             runs on the box's lines only, and the grid buffers hold the
                             box's z-planes only.                                          */
+  int32_t rhs_blocked;   /* aim_opts.rhs_blocked as set up                                 */
   int32_t z_len;         /* length of the z transform: the shortest supported length
                             >= 2 (box_hi[2] - box_lo[2] + 1) (at most 2N).  The linear
                             convolution over the box's z-planes needs z offsets below the
@@ -211,6 +219,8 @@ enum {
   AIM_K_GMRES_SMALL,     /* cycle start, rotations + back substitution, solution update    */
   AIM_K_PREP,            /* operator input: selection, Krylov scale, preconditioner, cast  */
   AIM_K_ZFWD,            /* z-spectrum of a committed history slab (power-of-two lengths)  */
+  AIM_K_BLOCK_SQUARE,    /* blocked right-hand side: one square of source/observer steps   */
+  AIM_K_ZINV_PENDING,    /* blocked right-hand side: pending z-spectra -> potentials slab  */
   AIM_K_COUNT
 };
 

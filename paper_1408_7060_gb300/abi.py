@@ -47,7 +47,8 @@ class aim_opts(ct.Structure):
     _fields_ = [("f_c", ct.c_double), ("precision", ct.c_int32), ("batch_max", ct.c_int32),
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32),
-                ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("autotune", ct.c_int32)]
+                ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("autotune", ct.c_int32),
+                ("rhs_blocked", ct.c_int32)]
 
 
 class aim_excitation(ct.Structure):
@@ -67,7 +68,7 @@ class aim_info(ct.Structure):
                 ("device_bytes", ct.c_int64), ("preconditioner", ct.c_int32), ("precond_nnz", ct.c_int64),
                 ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("plan_zw", ct.c_int32), ("plan_cw", ct.c_int32), ("plan_rp", ct.c_int32),
                 ("plan_ypb", ct.c_int32), ("plan_source", ct.c_int32), ("box_lo", ct.c_int32 * 3),
-                ("box_hi", ct.c_int32 * 3), ("z_len", ct.c_int32)]
+                ("box_hi", ct.c_int32 * 3), ("rhs_blocked", ct.c_int32), ("z_len", ct.c_int32)]
 
 
 EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
@@ -76,7 +77,7 @@ EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_nu
            "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
            "aim_farfield", "aim_farfield_adjoint", "aim_march_adjoint", "aim_march_farfield",
            "aim_march_adjoint_farfield", "aim_march_spectrum", "aim_rcs"]
-AIM_K_COUNT = 13
+AIM_K_COUNT = 15
 
 _LIB = None
 
@@ -191,14 +192,15 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
               restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False,
-              refine=0, autotune=0, refine_every=1):
+              refine=0, autotune=0, refine_every=1, rhs_blocked=0):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
     precond_radius, default the near radius).  zero_start: GMRES from zero instead of
     the previous step's currents.  refine (complex64 only): up to this many FP64
     refinement corrections per step (0: off), checked every refine_every-th step.
     autotune: 0 default launch shapes, 1 tuned at setup (cached plan reused), 2 tuned and
-    cache refreshed."""
+    cache refreshed.  rhs_blocked: delayed grid sums by the multilevel blocked schedule
+    (power-of-two z transforms)."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -208,7 +210,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
                     stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
-                    int(bool(zero_start)), int(refine), int(refine_every), int(autotune))
+                    int(bool(zero_start)), int(refine), int(refine_every), int(autotune), int(bool(rhs_blocked)))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -521,7 +523,7 @@ class AimContext:
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
                   precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine,
-                  refine_every=w.refine_every, autotune=w.autotune)
+                  refine_every=w.refine_every, autotune=w.autotune, rhs_blocked=w.rhs_blocked)
         kw.update(over)
         return cls(**kw)
 

@@ -248,6 +248,9 @@ struct aim_ctx {
   KPlan plan;                   // launch shapes of the grid passes
   int refine = 0;              // complex64 path: FP64-operator refinement sweeps per step (0: off)
   int refine_every = 1;        // FP64 residual checked at every k-th step
+  bool rhs_blocked = false;    // multilevel blocked delayed sums (Sec. 4 stage ii)
+  int blk_P = 0;               // top level: 2^P >= N_g source steps held
+  void* d_pend = nullptr;      // [2^(P+1)] pending z-spectra of future steps (blocked sums)
   int ref_nb = 0;              // right-hand sides per FP64 residual product (its buffers' batch)
   void* d_A64 = nullptr;       // FP64 grid work buffers of the refinement residual ([ref_nb] x the
   void* d_Bf64 = nullptr;      // layouts of d_A, d_Bf, d_P), and its FP64 operator input

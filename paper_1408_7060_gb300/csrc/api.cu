@@ -100,6 +100,7 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   if (opts->refine < 0 || opts->refine > 64) throw AimError{AIM_ERR_ARG, "aim_setup: refine out of range"};
   c->refine = opts->precision == AIM_C64 ? opts->refine : 0;
   c->refine_every = std::max(1, opts->refine_every);
+  c->rhs_blocked = opts->rhs_blocked != 0;
   c->precond_radius = opts->precond_radius > 0 ? opts->precond_radius : near_radius;
   if (c->precond == AIM_PRECOND_NEAR_SAI && c->precond_radius < 0)
     throw AimError{AIM_ERR_ARG, "aim_setup: the SAI preconditioner needs a pattern radius or a near zone"};
@@ -159,6 +160,11 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   AIM_CUDA(cudaStreamSynchronize(c->stream));
 
   setup_device_tables(c, hm, anchor);
+  if (c->rhs_blocked) {
+    if ((c->LZ & (c->LZ - 1)) != 0)
+      throw AimError{AIM_ERR_ARG, "aim_setup: the blocked right-hand side needs a power-of-two z transform"};
+    while ((1 << c->blk_P) < c->n_delays) ++c->blk_P;  // 2^P >= N_g (<= 32)
+  }
 
   // work buffers
   const int B = c->batch_max, ns = c->ns, ng = c->n_delays;
@@ -222,7 +228,13 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
 void ensure_ring(aim_ctx* c) {
   if (c->d_ring) return;
   const size_t slab = op_slab_bytes(c, c->batch_max);
-  c->d_ring = aim_alloc(c, (size_t)c->n_delays * slab);
+  // blocked sums: 2^P >= N_g source slots and 2^(P+1) pending slots
+  const int nslots = c->rhs_blocked ? 1 << c->blk_P : c->n_delays;
+  c->d_ring = aim_alloc(c, (size_t)nslots * slab);
+  if (c->rhs_blocked) {
+    c->d_pend = aim_alloc(c, ((size_t)2 << c->blk_P) * slab);
+    AIM_CUDA(cudaMemsetAsync(c->d_pend, 0, ((size_t)2 << c->blk_P) * slab, c->stream));
+  }
   // TMA view for the complex64 delayed sum over the z-spectra: [slot][B*4*LZ][L][L],
   // boxes of 16 x 1 x LZ x 1
   const int L = c->L, LZ = c->LZ;
@@ -424,6 +436,7 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
     info->box_hi[d] = c->box_hi[d];
   }
   info->z_len = c->LZ;
+  info->rhs_blocked = c->rhs_blocked ? 1 : 0;
   return AIM_OK;
 }
 
@@ -580,7 +593,7 @@ int aim_get_profile(aim_ctx* c, int64_t* launches, double* ms, int64_t* total) {
 const char* aim_kernel_name(int32_t id) {
   static const char* names[AIM_K_COUNT] = {"anterp_xfft", "yfft_fwd", "zconv", "zrhs", "yfft_inv", "xfft_inv",
                                           "interp_near", "excitation", "gmres_dot", "gmres_update", "gmres_small", "prep",
-                                          "zfwd"};
+                                          "zfwd", "block_square", "zinv_pending"};
   return id >= 0 && id < AIM_K_COUNT ? names[id] : "?";
 }
 
@@ -980,6 +993,9 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
   }
   int rc = AIM_OK;
   const int l0 = c->l_done;
+  const int nsrc = c->rhs_blocked ? 1 << c->blk_P : ng;  // source slots of the ring
+  if (c->rhs_blocked && l0 == 0)  // a march from rest: nothing pending
+    AIM_CUDA(cudaMemsetAsync(c->d_pend, 0, ((size_t)2 << c->blk_P) * slab, st));
   for (int l = l0 + 1; l <= l0 + n_steps; ++l) {
     AIM_CUDA(cudaEventRecord(ev[0], st));
     const int j = l - l0;                                       // step within this call
@@ -998,16 +1014,21 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
     for (int m = 1; m <= ng; ++m) {
       if (l - m < 1) continue;
       const int s = (l - m) % ng;
-      sl.p[sl.n] = (char*)c->d_ring + (size_t)s * slab;
-      sl.m[sl.n] = m;
-      sl.n++;
+      if (!c->rhs_blocked) {
+        sl.p[sl.n] = (char*)c->d_ring + (size_t)s * slab;
+        sl.m[sl.n] = m;
+        sl.n++;
+      }
       if (c->nnz > 0) {
         nl.val[nl.n] = c->d_near + (size_t)m * c->nnz;
         nl.x[nl.n] = c->d_iring + (size_t)s * B * ns;
         nl.n++;
       }
     }
-    op_apply_rhs(c, nb, sl, nl, c->d_b, -1.0, c->d_b);  // b = V_l - sum_m Z_m I_{l-m}
+    if (c->rhs_blocked && l > 1)  // the grid part was gathered by the squares of earlier steps
+      op_apply_rhs_pending(c, nb, (char*)c->d_pend + (size_t)(l % (2 * nsrc)) * slab, nl, c->d_b, -1.0, c->d_b);
+    else
+      op_apply_rhs(c, nb, sl, nl, c->d_b, -1.0, c->d_b);  // b = V_l - sum_m Z_m I_{l-m}
     AIM_CUDA(cudaEventRecord(ev[1], st));
     if (c->zero_start) AIM_CUDA(cudaMemsetAsync(c->d_x, 0, n * sizeof(double2), st));
     gmres_solve_async(c, nb, c->d_b, c->d_x, tol);
@@ -1024,7 +1045,27 @@ static int march_steps(aim_ctx* c, const StepIO& io, int n_steps, double tol, ai
     const int s = l % ng;
     AIM_CUDA(cudaMemcpyAsync(c->d_iring + (size_t)s * B * ns, c->d_x, n * sizeof(double2),
                              cudaMemcpyDeviceToDevice, st));
-    op_forward_slab(c, nb, c->d_x, (char*)c->d_ring + (size_t)s * slab);
+    op_forward_slab(c, nb, c->d_x, (char*)c->d_ring + (size_t)(l % nsrc) * slab);
+    if (c->rhs_blocked) {
+      // the square of the last b = 2^min(ctz(l), P) steps radiated to the next b steps,
+      // as sub-squares of at most 16 steps (source block u, observer block v: delays
+      // from 1 + bs (v - u - 1) + 1 ... ; blocks whose delays all exceed N_g are skipped)
+      int p = 0;
+      while (p < c->blk_P && ((l >> p) & 1) == 0) ++p;
+      const int b = 1 << p, bs = std::min(b, 16), nblk = b / bs;
+      for (int u = 0; u < nblk; ++u)
+        for (int v = 0; v < nblk; ++v) {
+          BlockSquare sq{};
+          sq.b = bs;
+          sq.toff = b + (v - u) * bs;  // delay of (observer i, source j) = toff + i - j
+          if (sq.toff - bs + 1 > ng || sq.toff + bs - 1 < 1) continue;
+          for (int j = 0; j < bs; ++j) {
+            sq.src[j] = (char*)c->d_ring + (size_t)((l - b + 1 + u * bs + j) % nsrc) * slab;
+            sq.dst[j] = (char*)c->d_pend + (size_t)((l + 1 + v * bs + j) % (2 * nsrc)) * slab;
+          }
+          op_block_square(c, nb, sq);
+        }
+    }
     if (currents) {
       const double2* xo = c->d_x;
       if (io.rev) {

@@ -19,6 +19,10 @@ void body_forward_slab(aim_ctx*, int, const double2*, void*);
 template <class C>
 void body_apply_rhs(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double, double2*);
 template <class C>
+void body_apply_rhs_pending(aim_ctx*, int, void*, const NearList&, const double2*, double, double2*);
+template <class C>
+void body_block_square(aim_ctx*, int, const BlockSquare&);
+template <class C>
 void body_tune(aim_ctx*);
 template <class C>
 void body_plan_fill(aim_ctx*);
@@ -75,6 +79,21 @@ void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, co
     body_apply_rhs<float2>(c, nb, sl, nl, base, sign, y);
   else
     body_apply_rhs<double2>(c, nb, sl, nl, base, sign, y);
+}
+
+void op_apply_rhs_pending(aim_ctx* c, int nb, void* P, const NearList& nl, const double2* base, double sign,
+                          double2* y) {
+  if (c->precision == AIM_C64)
+    body_apply_rhs_pending<float2>(c, nb, P, nl, base, sign, y);
+  else
+    body_apply_rhs_pending<double2>(c, nb, P, nl, base, sign, y);
+}
+
+void op_block_square(aim_ctx* c, int nb, const BlockSquare& sq) {
+  if (c->precision == AIM_C64)
+    body_block_square<float2>(c, nb, sq);
+  else
+    body_block_square<double2>(c, nb, sq);
 }
 
 // ---------------------------------------------------------------- launch plans

@@ -36,6 +36,18 @@ struct SlabList {
   int n;
 };
 
+// One square of the multilevel blocked delay sums (Sec. 4 stage ii): the z-spectra of b
+// consecutive steps (src[j], j = 0..b-1 oldest first) radiated to the pending
+// accumulators of b consecutive steps (dst[i]): dst[i] += sum_j G^_{toff+i-j} . src[j],
+// delays outside 1..N_g contributing nothing.  b a power of two <= 16 (a larger square
+// is launched as sub-squares with their own toff).
+struct BlockSquare {
+  const void* src[16];
+  void* dst[16];
+  int b;
+  int toff;
+};
+
 // y = base + sign * Z~AIM_m (dinv .* v)     (dinv, base optional; m = delay)
 void op_apply(aim_ctx* c, int m, int nb, const double2* v, const double2* dinv, const double2* base, double sign,
               const int* active, double2* y, VecSel vin = VecSel(), VecSel yout = VecSel());
@@ -48,6 +60,11 @@ void op_forward_slab(aim_ctx* c, int nb, const double2* v, void* dst);
 // y = base + sign * [ sum_s Z~FFT_{m_s} (slab_s) + near terms ]
 void op_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, const double2* base, double sign,
                   double2* y);
+// blocked right-hand side: y = base + sign * [ grid part from the pending z-spectra P
+// (which are read and cleared) + near terms ]
+void op_apply_rhs_pending(aim_ctx* c, int nb, void* P, const NearList& nl, const double2* base, double sign,
+                          double2* y);
+void op_block_square(aim_ctx* c, int nb, const BlockSquare& sq);
 // V_l for the plane waves in exc (device parameter block [nb][6]: khat, phat)
 void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double t_d, int step_l, double2* out);
 int op_kernel_count(const aim_ctx* c);

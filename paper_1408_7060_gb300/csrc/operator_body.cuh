@@ -61,6 +61,20 @@ void body_apply_rhs(aim_ctx* c, int nb, const SlabList& sl, const NearList& nl, 
 }
 
 template <class C>
+void body_apply_rhs_pending(aim_ctx* c, int nb, void* P, const NearList& nl, const double2* base, double sign,
+                            double2* y) {
+  AIM_DISPATCH_L(c->L, {
+    GridOps<LL, C>::zinv_pending(c, nb, reinterpret_cast<C*>(P));
+    GridOps<LL, C>::backward(c, nb, nl, base, sign, nullptr, y);
+  });
+}
+
+template <class C>
+void body_block_square(aim_ctx* c, int nb, const BlockSquare& sq) {
+  AIM_DISPATCH_L(c->L, GridOps<LL, C>::block_square(c, nb, sq));
+}
+
+template <class C>
 void body_tune(aim_ctx* c) {
   AIM_DISPATCH_L(c->L, GridOps<LL, C>::tune(c));
 }
@@ -83,4 +97,7 @@ void body_plan_fill(aim_ctx* c) {
                               const int*, double2*, VecSel, VecSel);                                             \
   template void body_forward_slab<C>(aim_ctx*, int, const double2*, void*);                                     \
   template void body_apply_rhs<C>(aim_ctx*, int, const SlabList&, const NearList&, const double2*, double,      \
-                                  double2*);
+                                  double2*);                                                                   \
+  template void body_apply_rhs_pending<C>(aim_ctx*, int, void*, const NearList&, const double2*, double,        \
+                                          double2*);                                                           \
+  template void body_block_square<C>(aim_ctx*, int, const BlockSquare&);

@@ -537,6 +537,73 @@ __global__ void __launch_bounds__(kZThreads, 3) k_zrhs_spec_tma(const __grid_con
   zcol_step_c<LZ, W, C>(t, tw, Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0, es, g.nz);
 }
 
+// Blocked right-hand side (Sec. 4 stage ii), power-of-two z lengths.  The pending
+// accumulator of a step holds the z-spectra P^ of its delayed grid sum, built by the
+// squares of earlier steps; k_zinv_pending turns it into the slab of potentials (inverse
+// z-FFT, steps B^-1 and C) and clears it for reuse.
+template <int LZ, int W, class C>
+__global__ void __launch_bounds__(kZThreads) k_zinv_pending(C* __restrict__ S, ZGeom g, C* __restrict__ Bf,
+                                                            const C* __restrict__ twg) {
+  constexpr int R1 = zsplit_r1<LZ>(), R2 = LZ / R1;
+  C* tw = reinterpret_cast<C*>(aim_smem);
+  C* t = tw + LZ;
+  load_twiddles(tw, twg, LZ);
+  __syncthreads();
+  const int bc = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * W;
+  const long long es = (long long)g.L * g.L;
+  C* Sc = S + (size_t)bc * LZ * es + (size_t)y * g.L + x0;
+  for (int u = threadIdx.x; u < W * R1; u += kZThreads) {
+    const int l = u % W, k1 = u / W;
+    C v[R2];
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      C* e = Sc + (long long)(k1 + R1 * k2) * es + l;
+      v[k2] = *e;
+      *e = C{};
+    }
+    zcol_step_b_inv<LZ, W, C>(t, tw, k1, l, v);
+  }
+  __syncthreads();
+  zcol_step_c<LZ, W, C>(t, tw, Bf + (size_t)bc * g.nz * es + (size_t)y * g.L + x0, es, g.nz);
+}
+
+// One square: every element q of the z-spectra ([bc][kz][y][x], nb * 4 * LZ * L * L of
+// them) gathers its kernel taps G^_m, m = toff - B + 1 .. toff + B - 1 within 1 .. N_g,
+// from the octant, its B sources, and adds the B Toeplitz products into the pending
+// accumulators.  Each source and accumulator element is read (and written) once per
+// square; at B <= 16 the direct product (8 B^2 flops per element) costs no more than
+// temporal FFTs of length 2B would.
+template <int B, class C>
+__global__ void __launch_bounds__(256) k_block_square(BlockSquare sq, const C* __restrict__ kspec, ZGeom g, int LZ,
+                                                      int ng, long long n) {
+  const size_t nn = (size_t)(g.N + 1) * (g.N + 1), oct = nn * (LZ / 2 + 1);
+  const long long plane = (long long)g.L * g.L, per_bc = plane * LZ;
+  const int m0 = sq.toff - B + 1;  // tap[t] = G^_{m0 + t}
+  for (long long q = blockIdx.x * 256LL + threadIdx.x; q < n; q += (long long)gridDim.x * 256) {
+    const int x = (int)(q % g.L), y = (int)((q / g.L) % g.L), kz = (int)((q / plane) % LZ);
+    const int bc = (int)(q / per_bc), kind = (bc & 3) == 3 ? 1 : 0;
+    const size_t go = (size_t)kind * oct + ((size_t)fold(kz, LZ / 2) * (g.N + 1) + fold(y, g.N)) * (g.N + 1) +
+                      fold(x, g.N);
+    C tap[2 * B - 1];
+#pragma unroll
+    for (int t = 0; t < 2 * B - 1; ++t) {
+      const int m = m0 + t;
+      tap[t] = (m >= 1 && m <= ng) ? __ldg(kspec + (size_t)m * 2 * oct + go) : C{};
+    }
+    C s[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) s[j] = reinterpret_cast<const C*>(sq.src[j])[q];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      C acc{};
+#pragma unroll
+      for (int j = 0; j < B; ++j) acc += tap[B - 1 + i - j] * s[j];
+      C* d = reinterpret_cast<C*>(sq.dst[i]) + q;
+      *d = *d + acc;
+    }
+  }
+}
+
 // z lengths with a factor 3 keep x/y-transformed history slabs: the delay sum recomputes
 // each slab's forward z-transform (steps A and B of the z pass), multiplies it by its
 // delay's kernel spectrum and accumulates in the registers of the step-B threads; then one
@@ -1076,6 +1143,43 @@ struct GridOps {
         throw AimError{AIM_ERR_ARG, "z transform longer than the padded length"};
       }
     });
+  }
+
+  // blocked right-hand side: pending z-spectra -> slab of potentials in Bf (cleared)
+  static void zinv_pending(aim_ctx* c, int nb, C* S) {
+    with_zlen(c->LZ, [&](auto lz) {
+      constexpr int LZ = decltype(lz)::value;
+      if constexpr (pow2_len(LZ) && LZ <= L) {
+        constexpr int ZW = L < 16 ? L : 16;
+        const size_t sm = smem_z(LZ, ZW);
+        KScope ks(c, AIM_K_ZINV_PENDING);
+        smem_opt_in(k_zinv_pending<LZ, ZW, C>, sm);
+        k_zinv_pending<LZ, ZW, C><<<dim3(L / ZW, L, nb * 4), kZThreads, sm, c->stream>>>(
+            S, zgeom(c), reinterpret_cast<C*>(c->d_Bf), ztwiddles(c));
+        AIM_CHECK_LAUNCH();
+      } else {
+        throw AimError{AIM_ERR_ARG, "the blocked right-hand side needs a power-of-two z length"};
+      }
+    });
+  }
+
+  static void block_square(aim_ctx* c, int nb, const BlockSquare& sq) {
+    const long long n = (long long)nb * 4 * c->LZ * L * L;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    KScope ks(c, AIM_K_BLOCK_SQUARE);
+    auto go = [&](auto bt) {
+      constexpr int B = decltype(bt)::value;
+      k_block_square<B, C><<<grid, 256, 0, c->stream>>>(sq, kspec(c), zgeom(c), c->LZ, c->n_delays, n);
+    };
+    switch (sq.b) {
+      case 1: go(std::integral_constant<int, 1>{}); break;
+      case 2: go(std::integral_constant<int, 2>{}); break;
+      case 4: go(std::integral_constant<int, 4>{}); break;
+      case 8: go(std::integral_constant<int, 8>{}); break;
+      case 16: go(std::integral_constant<int, 16>{}); break;
+      default: throw AimError{AIM_ERR_ARG, "blocked right-hand side: square size"};
+    }
+    AIM_CHECK_LAUNCH();
   }
 
   static const C* twiddles(aim_ctx* c) { return sel_tw(c, (C*)nullptr); }

@@ -264,6 +264,7 @@ class Workload:
     refine: int = 0        # complex64 path: FP64 refinement corrections per step (0: off)
     refine_every: int = 1  # the FP64 residual checked at every k-th step
     autotune: int = 0      # launch shapes: 0 defaults, 1 tuned at setup (cache reused), 2 re-tuned
+    rhs_blocked: int = 0   # delayed grid sums by the multilevel blocked schedule (Sec. 4 stage ii)
 
     @property
     def f_bw(self) -> float:
