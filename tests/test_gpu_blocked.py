@@ -1,10 +1,9 @@
 """The multilevel blocked delayed sums of the right-hand side (aim_opts.rhs_blocked,
 Sec. 4 stage ii) on the GPU.
 
-* 480-RWG sphere at 150 MHz +-20 % (N_g <= 4, squares of 1, 2 and 4 steps): the blocked
-  complex128 march
-  agrees with the oracle's LU march of the AIM operator (1e-6) and with the direct-sum
-  march to rounding (1e-12);
+* 480-RWG sphere at 150 MHz +-20 % (N_g <= 4, squares of 1, 2 and 4 steps): the
+  blocked complex128 march agrees with the oracle's LU march of the AIM operator (1e-6)
+  and with the direct-sum march to rounding (1e-12);
 * the same sphere at 600 MHz +-50 % (N_g > 16: 32-step top squares, launched as
   16-step sub-squares): blocked and direct marches agree to rounding in complex128 and
   to the complex64 tolerance (1e-5) in complex64;
