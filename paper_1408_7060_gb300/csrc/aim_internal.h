@@ -224,6 +224,7 @@ struct aim_ctx {
                                // r.u / (c dt) of every cubature point)
 
   int* d_anchor = nullptr;     // [ns][3]
+  int* d_order = nullptr;      // [ns] RWGs in Morton order of their anchors (interpolation visit order)
   double* d_lam = nullptr;     // [ns][4][64]  FP64 anterpolation rows
   float* d_lamf = nullptr;     // [ns][4][64]  FP32 copy (C64 path)
   int* d_nptr = nullptr;       // [N^3 + 1]    node-major CSR of the transpose

@@ -155,6 +155,28 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->d_tbs = upload(c, hm.tbs);
   c->d_tbf = upload(c, hm.tbf);
   c->d_anchor = upload(c, anchor);
+  {
+    // interpolation visit order: RWGs sorted by the Morton code of their stencil anchors,
+    // so that the warps of one block gather from neighbouring grid rows (L2 reuse)
+    auto spread = [](uint64_t v) {  // 21 bits -> every third bit
+      v &= 0x1fffff;
+      v = (v | v << 32) & 0x1f00000000ffffULL;
+      v = (v | v << 16) & 0x1f0000ff0000ffULL;
+      v = (v | v << 8) & 0x100f00f00f00f00fULL;
+      v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+      v = (v | v << 2) & 0x1249249249249249ULL;
+      return v;
+    };
+    std::vector<uint64_t> key(hm.ns);
+    std::vector<int> order(hm.ns);
+    for (int k = 0; k < hm.ns; ++k) {
+      key[k] = spread((uint64_t)anchor[3 * k]) | spread((uint64_t)anchor[3 * k + 1]) << 1 |
+               spread((uint64_t)anchor[3 * k + 2]) << 2;
+      order[k] = k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+    c->d_order = upload(c, order);
+  }
   c->d_lam = (double*)aim_alloc(c, (size_t)c->ns * 256 * sizeof(double));
   c->d_lamf = (float*)aim_alloc(c, (size_t)c->ns * 256 * sizeof(float));
   AIM_CUDA(cudaStreamSynchronize(c->stream));

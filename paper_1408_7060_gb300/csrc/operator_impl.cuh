@@ -57,8 +57,30 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
     C a0{}, a1{}, a2{}, a3{};
     if (y <= yhi) {
       const size_t n = ((size_t)z * N + y) * N + x;
+      int e = nptr[n];
       const int e1 = nptr[n + 1];
-      for (int e = nptr[n]; e < e1; ++e) {
+      // four entries at a time: their index and coefficient loads, then their gathers of
+      // x, are independent and in flight together (the sums keep the entry order)
+      for (; e + 4 <= e1; e += 4) {
+        int k[4];
+        typename Real<C>::F4 w[4];
+        C xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          k[u] = nidx[e + u];
+          w[u] = ncoef[e + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = vb[k[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a0 += (R)w[u].x * xv[u];
+          a1 += (R)w[u].y * xv[u];
+          a2 += (R)w[u].z * xv[u];
+          a3 += (R)w[u].w * xv[u];
+        }
+      }
+      for (; e < e1; ++e) {
         const int k = nidx[e];
         const typename Real<C>::F4 w = ncoef[e];
         const C xv = vb[k];
@@ -668,6 +690,7 @@ constexpr int kInterpBlockRows = 8 * kInterpRows;  // 256 threads
 
 template <class C>
 __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P, const int* __restrict__ anchor,
+                                                     const int* __restrict__ order,
                                                      const typename Real<C>::T* __restrict__ lam, int N, int nz,
                                                      int zlo, int ns,
                                                      int nb, const int* __restrict__ rowptr,
@@ -679,16 +702,17 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
   using R = typename Real<C>::T;
   const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (active && !active[b]) return;
-  const int k0 = blockIdx.x * kInterpBlockRows + warp * kInterpRows;  // the warp's first row
+  const int k0 = blockIdx.x * kInterpBlockRows + warp * kInterpRows;  // the warp's first position
   // grid part, row by row; lane group r (lanes 8r .. 8r+7) keeps row r's sum
   C mine{};
   if (P) {
     const size_t N3 = (size_t)nz * N * N;  // the box planes z0 .. z0 + nz - 1
 #pragma unroll
     for (int r = 0; r < kInterpRows; ++r) {
-      const int k = k0 + r;
+      const int pos = k0 + r;
       C g{};
-      if (k < ns) {
+      if (pos < ns) {
+        const int k = order[pos];
         // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node)
         // terms of an RWG take 8 warp loads of 8 rows x 32 B each
         const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2] - zlo;
@@ -711,8 +735,8 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
   }
   // near part: lane group r, sub-lane sl
   const int r = lane >> 3, sl = lane & 7;
-  const int k = k0 + r;
-  const bool on = k < ns;
+  const bool on = k0 + r < ns;
+  const int k = on ? order[k0 + r] : 0;
   long long xoff = 0;
   double xscale = 1.0;
   if (nl.xsel.sel) {
@@ -761,11 +785,12 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
     if (sl == 0) wsm[warp * kInterpRows + r] = out;  // zero for rows past ns
     __syncthreads();
     const int J = *df.jdev + 1;
-    const int kb = blockIdx.x * kInterpBlockRows + lane;
+    const int pb = blockIdx.x * kInterpBlockRows + lane;
+    const int kb = pb < ns ? order[pb] : 0;
     const double2* Vb = df.V + (size_t)b * ns;
     for (int i = warp; i < J; i += 8) {
       double2 t = make_double2(0, 0);
-      if (kb < ns) {
+      if (pb < ns) {
         const double2 v = Vb[i * df.vstride + kb], w = wsm[lane];
         t = make_double2(v.x * w.x + v.y * w.y, v.x * w.y - v.y * w.x);  // conj(v) w
       }
@@ -996,7 +1021,8 @@ struct GridOps {
                      const int* active, double2* y, VecSel ys = VecSel()) {
     KScope ks(c, AIM_K_INTERP_NEAR);
     launch_pdl(c->stream, dim3((unsigned)((c->ns + kInterpBlockRows - 1) / kInterpBlockRows), (unsigned)nb), dim3(256),
-               0, k_interp_near<C>, P, (const int*)c->d_anchor, lam(c), c->N, c->NZ, c->box_lo[2], c->ns, nb,
+               0, k_interp_near<C>, P, (const int*)c->d_anchor, (const int*)c->d_order, lam(c), c->N, c->NZ,
+               c->box_lo[2], c->ns, nb,
                (const int*)c->d_rowptr, (const int*)c->d_col, nl, base, sign, active, y, ys, c->dotfuse);
   }
 
