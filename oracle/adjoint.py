@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import efie, tbasis
-from .constants import C0, MU0
+from .constants import MU0
 
 
 def _half_bases(rwg):
@@ -35,7 +35,7 @@ def incident_taps(rwg, p: efie.Params, khat, phat, s_range):
     """B_s[k] for s in s_range (list of ints): [len(s_range), ns]."""
     g, S = _half_bases(rwg)
     khat, phat = np.asarray(khat, float), np.asarray(phat, float)
-    u = (g.P @ khat) / (C0 * p.dt)                                     # [nt,7]
+    u = (g.P @ khat) / p.cdt                                           # [nt,7]
     ph = np.exp(-1j * p.kc * (g.P @ khat))
     sp = np.einsum("tpqx,x->tpq", S, phat)                            # [nt,3,7]
     out = np.zeros((len(s_range), rwg.ns), dtype=complex)
@@ -55,7 +55,7 @@ def farfield_taps(rwg, p: efie.Params, rhat, e1, e2, s_range):
     E = np.stack([np.atleast_2d(e1), np.atleast_2d(e2)], axis=1)     # [nd,2,3]
     out = np.zeros((len(s_range), len(rhat), 2, rwg.ns), dtype=complex)
     for d in range(len(rhat)):
-        w = (g.P @ rhat[d]) / (C0 * p.dt)
+        w = (g.P @ rhat[d]) / p.cdt
         ph = np.exp(1j * p.kc * (g.P @ rhat[d]))
         for q in range(2):
             sp = np.einsum("tpqx,x->tpq", S, E[d, q])
@@ -79,8 +79,9 @@ def excitation_from_samples(B, s_range, a, i0, n_steps):
     return V
 
 
-def farfield(A, s_range, I, n_range):
-    """F(n)[d][q] = -mu/4pi sum_l sum_k A_{n-l}[d][q][k] I_l[k]; I is [n_steps, ns] (l from 1)."""
+def farfield(A, s_range, I, n_range, mu: float = MU0):
+    """F(n)[d][q] = -mu/4pi sum_l sum_k A_{n-l}[d][q][k] I_l[k]; I is [n_steps, ns] (l from 1);
+    mu the background permeability (vacuum by default)."""
     nd = A.shape[1]
     F = np.zeros((len(n_range), nd, 2), dtype=complex)
     for ni, n in enumerate(n_range):
@@ -88,14 +89,14 @@ def farfield(A, s_range, I, n_range):
             l = n - s
             if 1 <= l <= len(I):
                 F[ni] += np.einsum("dqk,k->dq", A[si], I[l - 1])
-    return -MU0 / (4 * np.pi) * F
+    return -mu / (4 * np.pi) * F
 
 
 def objective(F):
     return float(np.sum(np.abs(F) ** 2))
 
 
-def gradient(Z, B, sB, A, sA, a, i0, n_steps, n_range):
+def gradient(Z, B, sB, A, sA, a, i0, n_steps, n_range, mu: float = MU0):
     """(J, dJ/d conj(a)) with the march solved densely: Z[N_g+1, ns, ns]."""
     ns = Z.shape[1]
     ng = Z.shape[0] - 1
@@ -103,11 +104,11 @@ def gradient(Z, B, sB, A, sA, a, i0, n_steps, n_range):
     from .march import march_dense
 
     I = march_dense(Z, V[:, None, :])[:, 0, :]
-    F = farfield(A, sA, I, n_range)
+    F = farfield(A, sA, I, n_range, mu)
     J = objective(F)
     # G_l = dJ/d conj(I_l) = sum_n (-mu/4pi)^* A_{n-l}^H F(n)
     G = np.zeros((n_steps, ns), dtype=complex)
-    c = np.conj(-MU0 / (4 * np.pi))
+    c = np.conj(-mu / (4 * np.pi))
     for ni, n in enumerate(n_range):
         for si, s in enumerate(sA):
             l = n - s

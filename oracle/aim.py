@@ -31,13 +31,14 @@ from . import efie, quad, tbasis
 from .constants import EPS0, MU0
 from .rwg import RWG
 
-CA = MU0 / (4 * math.pi)
+CA = MU0 / (4 * math.pi)          # vacuum values of the two kernel constants
 CP = 1.0 / (4 * math.pi * EPS0)
 
 
 class AimOracle:
     def __init__(self, rwg: RWG, n: int, h: float, origin, near_radius: float, p: efie.Params):
         self.rwg, self.n, self.h, self.p = rwg, int(n), float(h), p
+        self.ca, self.cp = p.mu / (4 * math.pi), 1.0 / (4 * math.pi * p.eps)  # mu/4pi, 1/(4 pi eps)
         self.origin = np.asarray(origin, dtype=np.float64)
         self.near_radius = float(near_radius)
         self.anchor = self._anchors()
@@ -232,8 +233,8 @@ class AimOracle:
 
     def interpolate(self, P: np.ndarray) -> np.ndarray:
         """y[k] = mu/4pi sum_{c=x,y,z} L_c^T P_c + 1/(4 pi eps) L_div^T P_div."""
-        y = CA * sum(self.lam_sparse(c).T @ P[c] for c in range(3))
-        return y + CP * (self.lam_sparse(3).T @ P[3])
+        y = self.ca * sum(self.lam_sparse(c).T @ P[c] for c in range(3))
+        return y + self.cp * (self.lam_sparse(3).T @ P[3])
 
     def fft_part(self, m: int, x: np.ndarray, method: str = "fft") -> np.ndarray:
         S = self.anterpolate(x)
@@ -252,7 +253,7 @@ class AimOracle:
             tg = self.nodes[k]
             for c in range(4):
                 P = self.conv_direct(m, S[c], 0 if c < 3 else 1, targets=tg)
-                y[i] += (CA if c < 3 else CP) * (self.lam[c, k] @ P)
+                y[i] += (self.ca if c < 3 else self.cp) * (self.lam[c, k] @ P)
         return y
 
     def fft_dense(self, m: int) -> np.ndarray:
@@ -263,7 +264,7 @@ class AimOracle:
         out = 0
         for c in range(4):
             L = self.lam_sparse(c)[act].toarray()                 # [nact, ns]
-            out = out + (CA * (L.T @ GA @ L) if c < 3 else CP * (L.T @ GP @ L))
+            out = out + (self.ca * (L.T @ GA @ L) if c < 3 else self.cp * (L.T @ GP @ L))
         return out
 
     def fft_pairs(self, m: int, pairs: np.ndarray) -> np.ndarray:
@@ -285,7 +286,7 @@ class AimOracle:
             for c in range(4):
                 G = GA if c < 3 else GP
                 val = np.einsum("pa,pab,pb->p", self.lam[c, k[sl]], G, self.lam[c, kp[sl]])
-                out[sl] += (CA if c < 3 else CP) * val
+                out[sl] += (self.ca if c < 3 else self.cp) * val
         return out
 
     # ------------------------------------------------------------------ near zone

@@ -32,21 +32,37 @@ from .rwg import RWG
 
 @dataclasses.dataclass
 class Params:
+    """Time step, carrier, CPPIF order and the homogeneous background medium (Sec. 2.1:
+    relative permittivity and permeability; vacuum by default)."""
     dt: float
     f_c: float
     Q: int = 2
+    eps_r: float = 1.0
+    mu_r: float = 1.0
 
     @property
     def wc(self) -> float:
         return 2.0 * math.pi * self.f_c
 
     @property
+    def c(self) -> float:
+        return C0 / math.sqrt(self.eps_r * self.mu_r)
+
+    @property
+    def mu(self) -> float:
+        return MU0 * self.mu_r
+
+    @property
+    def eps(self) -> float:
+        return EPS0 * self.eps_r
+
+    @property
     def kc(self) -> float:
-        return self.wc / C0
+        return self.wc / self.c
 
     @property
     def cdt(self) -> float:
-        return C0 * self.dt
+        return self.c * self.dt
 
 
 # ----------------------------------------------------------------------------
@@ -124,10 +140,10 @@ class Geometry:
 
 
 def tri_pair_blocks(g: Geometry, t: np.ndarray, tp: np.ndarray, m: np.ndarray, p: Params,
-                    kern=time_kernels, kern0=time_kernels_at0, scale=(MU0 / (4 * np.pi), 1 / (4 * np.pi * EPS0))):
+                    kern=time_kernels, kern0=time_kernels_at0, scale=None):
     """Galerkin blocks between the three half-bases of test triangle ``t`` and
     source triangle ``tp``:  ``Z[nm, npair, 3, 3]``."""
-    cA, cP = scale
+    cA, cP = scale if scale is not None else (p.mu / (4 * np.pi), 1 / (4 * np.pi * p.eps))
     Pt, Ps = g.P[t], g.P[tp]                                         # [n,7,3]
     Wt, Ws = g.W[t], g.W[tp]
     dvec = Pt[:, :, None, :] - Ps[:, None, :, :]                     # [n,7,7,3]
@@ -261,7 +277,7 @@ def excitation(rwg: RWG, p: Params, khat, phat, sigma: float, t_d: float, steps)
     steps = np.asarray(steps, dtype=np.float64)
     out = np.zeros((len(steps), len(khat), rwg.ns), dtype=complex)
     for b in range(len(khat)):
-        delay = g.P @ khat[b] / C0                                     # [nt,7]
+        delay = g.P @ khat[b] / p.c                                    # [nt,7]
         tau = steps[:, None, None] * p.dt - delay[None] - t_d
         env = np.exp(-tau ** 2 / (2 * sigma ** 2))
         val = (-tau / sigma ** 2 + 1j * p.wc) * env * np.exp(-1j * p.wc * (delay + t_d))[None]
@@ -309,4 +325,4 @@ def rcs_fd(rwg: RWG, p: Params, I: np.ndarray, rhat: np.ndarray, pol: np.ndarray
     """RCS 4 pi (w mu / 4 pi)^2 |pol . F|^2 for a unit incident field."""
     F = far_field_fd(rwg, p, I, rhat)
     e = np.einsum("dx,dx->d", F, np.atleast_2d(pol))
-    return 4 * np.pi * (p.wc * MU0 / (4 * np.pi)) ** 2 * np.abs(e) ** 2
+    return 4 * np.pi * (p.wc * p.mu / (4 * np.pi)) ** 2 * np.abs(e) ** 2
