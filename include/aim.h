@@ -127,6 +127,10 @@ typedef struct {
                             so each step reads O(log N_g) spectra instead of N_g.  Needs a
                             power-of-two z transform (aim_info.z_len); holds 2^P source and
                             2^(P+1) pending z-spectra per right-hand side.  0: direct sums. */
+  double eps_r, mu_r;    /* homogeneous background medium (Sec. 2.1): relative permittivity
+                            and permeability; values <= 0 mean 1 (vacuum).  Light speed
+                            c0 / sqrt(eps_r mu_r), mu = mu0 mu_r, eps = eps0 eps_r in every
+                            kernel, excitation, far field and RCS.                          */
 } aim_opts;
 
 typedef struct {

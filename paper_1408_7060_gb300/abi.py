@@ -48,7 +48,7 @@ class aim_opts(ct.Structure):
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32),
                 ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("autotune", ct.c_int32),
-                ("rhs_blocked", ct.c_int32)]
+                ("rhs_blocked", ct.c_int32), ("eps_r", ct.c_double), ("mu_r", ct.c_double)]
 
 
 class aim_excitation(ct.Structure):
@@ -192,7 +192,7 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
               restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False,
-              refine=0, autotune=0, refine_every=1, rhs_blocked=0):
+              refine=0, autotune=0, refine_every=1, rhs_blocked=0, eps_r=1.0, mu_r=1.0):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
     precond_radius, default the near radius).  zero_start: GMRES from zero instead of
@@ -200,7 +200,7 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     refinement corrections per step (0: off), checked every refine_every-th step.
     autotune: 0 default launch shapes, 1 tuned at setup (cached plan reused), 2 tuned and
     cache refreshed.  rhs_blocked: delayed grid sums by the multilevel blocked schedule
-    (power-of-two z transforms)."""
+    (power-of-two z transforms).  eps_r, mu_r: the homogeneous background medium."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -210,7 +210,8 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
                     stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
-                    int(bool(zero_start)), int(refine), int(refine_every), int(autotune), int(bool(rhs_blocked)))
+                    int(bool(zero_start)), int(refine), int(refine_every), int(autotune), int(bool(rhs_blocked)),
+                    float(eps_r), float(mu_r))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -523,7 +524,8 @@ class AimContext:
         kw = dict(V=V, F=F, grid_n=w.grid_n, origin=w.origin, h=w.h, near_radius=w.near_radius, dt=w.dt,
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
                   precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine,
-                  refine_every=w.refine_every, autotune=w.autotune, rhs_blocked=w.rhs_blocked)
+                  refine_every=w.refine_every, autotune=w.autotune, rhs_blocked=w.rhs_blocked, eps_r=w.eps_r,
+                  mu_r=w.mu_r)
         kw.update(over)
         return cls(**kw)
 

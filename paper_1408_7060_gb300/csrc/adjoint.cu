@@ -45,6 +45,7 @@ struct MeshArgs {
   const double* qw;
   int ns;
   double dt, wc, kc, cdt;
+  double mu;  // permeability of the background medium
   TBasis tb;
 };
 
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kT) k_farfield(MeshArgs m, DirArgs d, int l0, 
       }
     }
   }
-  const double cf = -aimc::kMu0 / (4.0 * aimc::kPi);
+  const double cf = -m.mu / (4.0 * aimc::kPi);
   const double2 s1 = block_sum(a1);
   const double2 s2 = block_sum(a2);
   if (threadIdx.x == 0) {
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kT) k_farfield_adj(MeshArgs m, DirArgs d, int 
       }
     }
   }
-  const double cf = -aimc::kMu0 / (4.0 * aimc::kPi);  // real: conj(cf) = cf
+  const double cf = -m.mu / (4.0 * aimc::kPi);  // real: conj(cf) = cf
   G[(size_t)(l - l0) * m.ns + k] = make_double2(cf * acc.x, conj_out ? -cf * acc.y : cf * acc.y);
 }
 
@@ -284,7 +285,8 @@ MeshArgs mesh_args(aim_ctx* c) {
   m.dt = c->dt;
   m.wc = c->wc;
   m.kc = c->kc;
-  m.cdt = aimc::kC0 * c->dt;
+  m.cdt = c->c_med * c->dt;
+  m.mu = c->mu_med;
   m.tb = c->tb;
   return m;
 }
@@ -293,7 +295,7 @@ MeshArgs mesh_args(aim_ctx* c) {
 
 // time reach of the cubature points in units of dt: every point r has |r.u| / (c dt) <= this
 // for any unit u (the largest vertex distance from the origin bounds the points)
-static double reach(aim_ctx* c) { return c->rmax / (aimc::kC0 * c->dt); }
+static double reach(aim_ctx* c) { return c->rmax / (c->c_med * c->dt); }
 
 void adj_excitation_samples(aim_ctx* c, const double* khat, const double* phat, int i0, int n_samp,
                             const double2* a, int l0, int n_steps, double2* V) {

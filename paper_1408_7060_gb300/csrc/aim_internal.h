@@ -193,6 +193,7 @@ struct aim_ctx {
   int LZ = 0;                  // z transform length: the shortest supported length >= 2 NZ
   double h = 0, origin[3] = {0, 0, 0};
   double dt = 0, f_c = 0, wc = 0, kc = 0, near_radius = 0;
+  double c_med = 0, mu_med = 0, eps_med = 0;  // light speed, permeability, permittivity of the medium
   TBasis tb{};
   int precision = AIM_C64;
   int batch_max = 1, restart = 50, max_iter = 500;

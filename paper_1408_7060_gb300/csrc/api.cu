@@ -87,7 +87,13 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   c->dt = dt;
   c->f_c = opts->f_c;
   c->wc = 2.0 * aimc::kPi * opts->f_c;
-  c->kc = c->wc / aimc::kC0;
+  {
+    const double er = opts->eps_r > 0 ? opts->eps_r : 1.0, mr = opts->mu_r > 0 ? opts->mu_r : 1.0;
+    c->c_med = aimc::kC0 / std::sqrt(er * mr);
+    c->mu_med = aimc::kMu0 * mr;
+    c->eps_med = aimc::kEps0 * er;
+  }
+  c->kc = c->wc / c->c_med;
   c->near_radius = near_radius;
   c->precision = opts->precision;
   c->batch_max = opts->batch_max;
@@ -839,8 +845,8 @@ int aim_rcs(aim_ctx* c, int32_t n_freq, const double* freqs, int32_t nb, const a
     for (int f = 0; f < n_freq; ++f) {
       if (!(freqs[f] > 0)) throw AimError{AIM_ERR_ARG, "aim_rcs: frequencies must be > 0"};
       const double w = 2.0 * aimc::kPi * freqs[f];
-      const double a = w * aimc::kMu0 / (4.0 * aimc::kPi);
-      h[6 * nd + 2 * f] = w / aimc::kC0;
+      const double a = w * c->mu_med / (4.0 * aimc::kPi);
+      h[6 * nd + 2 * f] = w / c->c_med;
       h[6 * nd + 2 * f + 1] = 4.0 * aimc::kPi * a * a;
     }
     double* dd = reinterpret_cast<double*>(scratch(c, h.size() / 2 + 1, 4));

@@ -238,6 +238,6 @@ void op_excitation(aim_ctx* c, int nb, const double* d_kp, double sigma, double 
   KScope ks(c, AIM_K_EXCITATION);
   k_excitation<<<(int)((n + 127) / 128), 128, 0, c->stream>>>(c->ns, nb, c->d_rtri, c->d_rfree, c->d_len, c->d_area,
                                                       c->d_v, c->d_qp, c->d_qw, d_kp, sigma, t_d,
-                                                      step_l * c->dt, c->wc, aimc::kC0, out);
+                                                      step_l * c->dt, c->wc, c->c_med, out);
   AIM_CHECK_LAUNCH();
 }

@@ -244,7 +244,7 @@ __global__ void k_near_direct(SetupGeom g, TimeK p, int nnz, int nm, const int* 
   if (idx >= (long long)nnz * nm) return;
   const int e = (int)(idx % nnz), m = (int)(idx / nnz);
   const int k = prow[e], kp = pcol[e];
-  const double cA = aimc::kMu0 / (4.0 * aimc::kPi), cP = 1.0 / (4.0 * aimc::kPi * aimc::kEps0);
+  const double cA = p.cA, cP = p.cP;
   double2 Z = make_double2(0, 0);
   double2 fA0, fP0, dA0, dP0;
   time_kernels_at0(p, m, fA0, fP0, dA0, dP0);
@@ -315,7 +315,8 @@ __global__ void k_near_direct(SetupGeom g, TimeK p, int nnz, int nm, const int* 
 // subtract the grid approximation sum_c coef_c L_c[.,k]^T G_m L_c[.,k'] (one warp per (e, m))
 __global__ void k_precorrect(int nnz, int nm, const int* __restrict__ prow, const int* __restrict__ pcol,
                              const int* __restrict__ anchor, const double* __restrict__ lam,
-                             const double2* __restrict__ tab, int D, double2* __restrict__ zout) {
+                             const double2* __restrict__ tab, int D, double cA, double cP,
+                             double2* __restrict__ zout) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= (long long)nnz * nm) return;
@@ -324,7 +325,6 @@ __global__ void k_precorrect(int nnz, int nm, const int* __restrict__ prow, cons
   const int D1 = D + 1, V3 = D1 * D1 * D1;
   const double2* tA = tab + (size_t)(2 * m) * V3;
   const double2* tP = tab + (size_t)(2 * m + 1) * V3;
-  const double cA = aimc::kMu0 / (4.0 * aimc::kPi), cP = 1.0 / (4.0 * aimc::kPi * aimc::kEps0);
   const int bx = anchor[3 * k] - anchor[3 * kp], by = anchor[3 * k + 1] - anchor[3 * kp + 1],
             bz = anchor[3 * k + 2] - anchor[3 * kp + 2];
   const double* lk = lam + (size_t)k * 256;
@@ -560,7 +560,9 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
   tk.dt = c->dt;
   tk.wc = c->wc;
   tk.kc = c->kc;
-  tk.cdt = aimc::kC0 * c->dt;
+  tk.cdt = c->c_med * c->dt;
+  tk.cA = c->mu_med / (4.0 * aimc::kPi);
+  tk.cP = 1.0 / (4.0 * aimc::kPi * c->eps_med);
   tk.tb = c->tb;
 
   SetupGeom g;
@@ -633,7 +635,7 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
     AIM_CUDA(cudaMemcpyAsync(&best, d_best, sizeof(int), cudaMemcpyDeviceToHost, st));
     AIM_CUDA(cudaStreamSynchronize(st));
     double rmax = c->h * std::sqrt((double)best);
-    c->n_delays = (int)std::floor(rmax / (aimc::kC0 * c->dt) + c->tb.Q);
+    c->n_delays = (int)std::floor(rmax / (c->c_med * c->dt) + c->tb.Q);
     if (c->n_delays + 1 > aimc::kMaxDelays) throw AimError{AIM_ERR_ARG, "too many delays (N_g + 1 > 32)"};
   }
   const int nm = c->n_delays + 1;
@@ -673,7 +675,7 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
       throw AimError{AIM_ERR_OOM, "kernel tabulation scratch"};
     }
     try {
-      const double cA = aimc::kMu0 / (4.0 * aimc::kPi), cP = 1.0 / (4.0 * aimc::kPi * aimc::kEps0);
+      const double cA = c->mu_med / (4.0 * aimc::kPi), cP = 1.0 / (4.0 * aimc::kPi * c->eps_med);
       for (int m = 0; m < nm; ++m) {
         k_kernel_grid<<<launch_blocks((long long)M, 256), 256, 0, st>>>(tk, m, N, c->LZ, c->h, GA, GP);
         AIM_CHECK_LAUNCH();
@@ -755,7 +757,7 @@ void setup_device_tables(aim_ctx* c, HostMesh& hm, const std::vector<int>& ancho
       AIM_CHECK_LAUNCH();
       long long warps = (long long)nnz * nm;
       k_precorrect<<<(int)((warps * 32 + 255) / 256), 256, 0, st>>>(nnz, nm, d_prow, d_pcol, c->d_anchor, c->d_lam,
-                                                                   tab, D, c->d_near);
+                                                                   tab, D, tk.cA, tk.cP, c->d_near);
       AIM_CHECK_LAUNCH();
     }
     // SAI from the direct immediate entries Z_0 on its pattern: the near pairs, or the

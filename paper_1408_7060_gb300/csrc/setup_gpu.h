@@ -7,6 +7,7 @@
 
 struct TimeK {
   double dt, wc, kc, cdt;
+  double cA, cP;  // mu / (4 pi) and 1 / (4 pi eps) of the background medium
   TBasis tb;
 };
 

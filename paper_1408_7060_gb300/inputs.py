@@ -265,6 +265,8 @@ class Workload:
     refine_every: int = 1  # the FP64 residual checked at every k-th step
     autotune: int = 0      # launch shapes: 0 defaults, 1 tuned at setup (cache reused), 2 re-tuned
     rhs_blocked: int = 0   # delayed grid sums by the multilevel blocked schedule (Sec. 4 stage ii)
+    eps_r: float = 1.0     # homogeneous background medium (Sec. 2.1); vacuum by default
+    mu_r: float = 1.0
 
     @property
     def f_bw(self) -> float:
