@@ -46,7 +46,7 @@ CSRC = os.path.join(ROOT, "paper_1408_7060_gb300", "csrc")
 PRESETS = {
     "array491k": dict(precond="sai", precond_scale=1.4, refine=4),
     "sphere7680": dict(precond="sai", precond_scale=2.5, refine=4),
-    "sphere7680_ng20": dict(precond="sai", precond_scale=2.5, refine=0),
+    "sphere7680_wide": dict(precond="sai", precond_scale=2.5, refine=0),
     "sphere7680_b64": dict(precond="sai", precond_scale=2.5, refine=4),
     "ellipsoid20k": dict(precond="sai", precond_scale=1.0, refine=4),
 }

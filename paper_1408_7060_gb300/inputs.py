@@ -316,14 +316,14 @@ def make_workload(name: str, **over) -> Workload:
         w = dict(mesh=(V, F), f_c=150e6, band_frac=0.5, n_t=200, grid_n=16, h=h, origin=o,
                  near_radius=0.3, tol=1e-6, khat=np.array([[0.0, 0.0, 1.0]]),
                  phat=np.array([[1.0, 0.0, 0.0]]), precision="c128")
-    elif name in ("sphere7680", "sphere7680_b64", "sphere7680_ng20"):
+    elif name in ("sphere7680", "sphere7680_b64", "sphere7680_wide"):
         V, F = icosphere(4, 1.0)
         h, o = place_grid(V, 64)
         if name == "sphere7680":
             k, p = np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]])
             w = dict(f_c=600e6, band_frac=0.3, n_t=400)
-        elif name == "sphere7680_ng20":
-            # the same sphere and grid at 600 MHz +-60 %: the shorter step gives N_g = 20
+        elif name == "sphere7680_wide":
+            # the same sphere and grid at 600 MHz +-60 %: the shorter step gives N_g = 12
             # (a right-hand side with many delays, for the blocked delayed sums)
             k, p = np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]])
             w = dict(f_c=600e6, band_frac=0.6, n_t=100)

@@ -3,10 +3,11 @@ Sec. 4 stage ii) on the GPU.
 
 * 480-RWG sphere at 150 MHz +-20 % (N_g <= 4, squares of 1, 2 and 4 steps): the
   blocked complex128 march agrees with the oracle's LU march of the AIM operator (1e-6)
-  and with the direct-sum march to rounding (1e-12);
-* the same sphere at 600 MHz +-50 % (N_g > 16: 32-step top squares, launched as
-  16-step sub-squares): blocked and direct marches agree to rounding in complex128 and
-  to the complex64 tolerance (1e-5) in complex64;
+  and with the direct-sum march within the solves' tolerance (both solved to 1e-10: the
+  sums differ in rounding order only, measured 3.7e-11 over 60 steps; bound 1e-9);
+* the same sphere at 1.2 GHz +-50 % (N_g = 24 > 16: 32-step top squares, launched as
+  16-step sub-squares, the one whose delays all exceed N_g skipped): blocked and direct
+  marches agree within 1e-9 in complex128 and 1e-5 in complex64;
 * 7680-RWG sphere (complex64, N_g = 7): blocked and direct marches agree within 1e-5 and
   the blocked march keeps matching across aim_march_continue calls (its pending sums
   carry over).
@@ -43,20 +44,20 @@ def test_blocked_march_vs_oracle_and_direct():
         dirc, _, _ = c.march(w.khat, w.phat, w.sigma, w.t_d, w.n_t, 1e-10)
     assert st["last_step"] == w.n_t
     assert rel(blk, ref) < 1e-6
-    assert rel(blk, dirc) < 1e-12
+    assert rel(blk, dirc) < 1e-9
 
 
 def test_blocked_sub_squares_large_ng():
     from paper_1408_7060_gb300 import AimContext
 
-    w = make_workload("sphere480", f_c=600e6, band_frac=0.5, n_t=80)
+    w = make_workload("sphere480", f_c=1.2e9, band_frac=0.5, n_t=80)
     got = {}
     for prec in ("c128", "c64"):
         for blocked in (0, 1):
             with AimContext.from_workload(w, precision=prec, rhs_blocked=blocked) as c:
                 assert c.n_delays > 16
                 got[prec, blocked] = c.march(w.khat, w.phat, w.sigma, w.t_d, w.n_t, 1e-10 if prec == "c128" else 1e-6)[0]
-    assert rel(got["c128", 1], got["c128", 0]) < 1e-12
+    assert rel(got["c128", 1], got["c128", 0]) < 1e-9
     assert rel(got["c64", 1], got["c64", 0]) < 1e-5
 
 
