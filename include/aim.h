@@ -80,7 +80,8 @@ typedef struct {
 } aim_mesh;
 
 typedef struct {
-  int32_t n;             /* nodes per axis (cubic grid N^3); padded FFT size 2N     */
+  int32_t n;             /* nodes per axis (cubic grid N^3); x and y transforms of 2N
+                            points, z transforms of aim_info.z_len points             */
   double origin[3];      /* position of node (0,0,0) (m)                            */
   double h;              /* node spacing (m)                                        */
 } aim_grid;
@@ -116,7 +117,7 @@ typedef struct {
                             passes, rows per block of the x passes): 0 built-in defaults;
                             1 time every candidate on this context's buffers at setup and
                             keep the fastest, reusing a plan cached for the same GPU model,
-                            padded length, precision and batch; 2 time and refresh the cache.
+                            padded lengths, precision and batch; 2 time and refresh the cache.
                             Cache: the file named by AIM_GB300_PLAN_CACHE, else
                             $HOME/.cache/aim_gb300_plans.jsonl (one JSON object per line).
                             The results do not depend on the plan (same arithmetic per line). */
@@ -188,7 +189,8 @@ enum { AIM_PLAN_DEFAULT = 0, AIM_PLAN_MEASURED = 1, AIM_PLAN_CACHED = 2 };
  * RWG table, anterpolation coefficients by moment matching up to order 3 per
  * axis (Sec. 5.1), grid kernels G^A_m = (D^2 T)(m - R/c dt) e^{-j k_c R}/R and
  * G^phi_m = T(m - R/c dt) e^{-j k_c R}/R for m = 0..N_g (G(0) = 0) and their
- * zero-padded FFT spectra, near-zone pairs (edge-midpoint distance <= near_radius;
+ * zero-padded FFT spectra (2N x 2N x z_len: the z padding follows the depth of the
+ * active box, aim_info), near-zone pairs (edge-midpoint distance <= near_radius;
  * negative: none), the Galerkin near-zone entries Z_m (FP64, singularity
  * extraction) minus their grid approximation, and the diagonal preconditioner.
  *   mesh, grid, opts: host structs;  dt: time step (s);  out: receives the context.
