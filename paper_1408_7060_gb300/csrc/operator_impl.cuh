@@ -849,6 +849,7 @@ inline void with_width(int w, F&& f) {
     case 8: f(std::integral_constant<int, 8>{}); break;
     case 16: f(std::integral_constant<int, 16>{}); break;
     case 32: f(std::integral_constant<int, 32>{}); break;
+    case 64: f(std::integral_constant<int, 64>{}); break;
     default: throw AimError{AIM_ERR_ARG, "launch plan: unsupported tile width"};
   }
 }
@@ -893,13 +894,13 @@ struct GridOps {
   // candidates the autotuner times: z tiles of x-adjacent columns (w divides L), y tiles
   static std::vector<int> zwidths(const aim_ctx* c) {
     std::vector<int> v;
-    for (int w : {8, 16, 32})
+    for (int w : {8, 16, 32, 64})
       if (w <= L && L % w == 0 && smem_z(c->LZ, w) <= kPlanSmemMax) v.push_back(w);
     return v;
   }
   static std::vector<int> ywidths() {
     std::vector<int> v;
-    for (int w : {8, 16, 32})
+    for (int w : {8, 16, 32, 64})
       if (w <= L && L % w == 0 && smem_y(w) <= kPlanSmemMax) v.push_back(w);
     return v;
   }
