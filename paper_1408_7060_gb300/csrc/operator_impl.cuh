@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kZThreads) k_zrhs_2s(SlabList sl, const C* __r
 
 // ---------------------------------------------------------------- stage iii + iv
 // y_k = sign * ( sum_c sum_{n in stencil(k)} L_c[n,k] P_c[n]  +  sum_terms Z~near_m x_m ) + base_k
-// Grid (ceil(ns / 32), nb): a block takes 32 rows of one RHS, one warp per kInterpRows
+// Grid (nb, ceil(ns / 32)): a block takes 32 rows of one RHS, one warp per kInterpRows
 // consecutive rows.  Grid part: the whole warp per row, accumulated in the grid precision.
 // Near part: 8 lanes per row, all rows at once, in FP64 -- the warp's FP64 instructions
 // (each holds the sub-partition's FP64 pipe for the whole warp) serve kInterpRows rows
@@ -700,9 +700,11 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
                                                      VecSel ys, DotFuse df) {
   pdl_wait();
   using R = typename Real<C>::T;
-  const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the right-hand side is the fastest grid index: the blocks of all right-hand sides
+  // for one set of rows run together and share that set's near-zone rows through L2
+  const int b = blockIdx.x, rb = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (active && !active[b]) return;
-  const int k0 = blockIdx.x * kInterpBlockRows + warp * kInterpRows;  // the warp's first position
+  const int k0 = rb * kInterpBlockRows + warp * kInterpRows;  // the warp's first position
   // grid part, row by row; lane group r (lanes 8r .. 8r+7) keeps row r's sum
   C mine{};
   if (P) {
@@ -785,7 +787,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
     if (sl == 0) wsm[warp * kInterpRows + r] = out;  // zero for rows past ns
     __syncthreads();
     const int J = *df.jdev + 1;
-    const int pb = blockIdx.x * kInterpBlockRows + lane;
+    const int pb = rb * kInterpBlockRows + lane;
     const int kb = pb < ns ? order[pb] : 0;
     const double2* Vb = df.V + (size_t)b * ns;
     for (int i = warp; i < J; i += 8) {
@@ -795,7 +797,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
         t = make_double2(v.x * w.x + v.y * w.y, v.x * w.y - v.y * w.x);  // conj(v) w
       }
       t = warp_sum_c(t);
-      if (lane == 0) df.pd[((size_t)b * 64 + i) * df.P + blockIdx.x] = t;
+      if (lane == 0) df.pd[((size_t)b * 64 + i) * df.P + rb] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1021,7 +1023,9 @@ struct GridOps {
   static void interp(aim_ctx* c, int nb, const C* P, const NearList& nl, const double2* base, double sign,
                      const int* active, double2* y, VecSel ys = VecSel()) {
     KScope ks(c, AIM_K_INTERP_NEAR);
-    launch_pdl(c->stream, dim3((unsigned)((c->ns + kInterpBlockRows - 1) / kInterpBlockRows), (unsigned)nb), dim3(256),
+    const unsigned nrb = (unsigned)((c->ns + kInterpBlockRows - 1) / kInterpBlockRows);
+    if (nrb > 65535u) throw AimError{AIM_ERR_ARG, "interpolation: more than 2 097 120 RWGs"};
+    launch_pdl(c->stream, dim3((unsigned)nb, nrb), dim3(256),
                0, k_interp_near<C>, P, (const int*)c->d_anchor, (const int*)c->d_order, lam(c), c->N, c->NZ,
                c->box_lo[2], c->ns, nb,
                (const int*)c->d_rowptr, (const int*)c->d_col, nl, base, sign, active, y, ys, c->dotfuse);
