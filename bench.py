@@ -7,12 +7,12 @@ every iteration, then FP64 refinement of the residual (FP64 grid stages) until i
 meets the tolerance.
 
 Default workload (the largest configuration that fits one GPU): 4 x 4 array of PEC
-spheres, icosphere subdivision 5 each (491 520 RWG), 1 GHz +-5 %, 384^3 grid (768^3
-padded FFT), 16 seeded plane waves, tol 1e-5, near-zone SAI preconditioner.  Inputs
-are synthetic (seeded meshes and pulses).  The 16 waves march in chunks of as many
-as fit in device memory next to their history rings (the factor-3 padded length keeps
-N_g x/y-transformed slabs per wave): every chunk marches W untimed steps from rest,
-then K timed steps; the step time is the sum over chunks.
+spheres, icosphere subdivision 5 each (491 520 RWG), 1 GHz +-5 %, 384^3 grid (768 x 768
+x 192 transforms: the z transform follows the 72-plane depth of the active box), 16
+seeded plane waves, tol 1e-5, near-zone SAI preconditioner.  Inputs are synthetic
+(seeded meshes and pulses).  The waves march in chunks of as many as fit in device
+memory next to their history rings (all 16 in one at this workload): every chunk marches
+W untimed steps from rest, then K timed steps; the step time is the sum over chunks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl aim|reference]
                     [--workload NAME]

@@ -171,7 +171,7 @@ typedef struct {
   int32_t box_lo[3], box_hi[3]; /* active box: grid nodes (x, y, z) touched by some stencil
                             lie in [box_lo, box_hi] (inclusive).  Sources vanish outside it
                             and potentials are needed only inside it, so every FFT pass but
-                            the z pass (all lines, reading and writing only z in the box)
+                            the z pass (all lines, reading and writing only the box planes)
                             runs on the box's lines only, and the grid buffers hold the
                             box's z-planes only.                                          */
   int32_t rhs_blocked;   /* aim_opts.rhs_blocked as set up                                 */

@@ -6,8 +6,9 @@
 //    integral is evaluated with a 6x6 Gauss-Legendre rule on the collapsed triangle
 //    (exact for the degree-10 integrand);
 //  * N_g from the largest node-to-node distance of the active grid (after Eq. 4);
-//  * the delayed grid kernels G^A_m, G^phi_m on the zero-padded (2N)^3 grid and
-//    their spectra (stage ii), stored as the even-symmetric octant;
+//  * the delayed grid kernels G^A_m, G^phi_m on the zero-padded (2N, 2N, LZ) grid
+//    (LZ: the z transform length of the active box) and their spectra (stage ii),
+//    stored as the even-symmetric octant;
 //  * the near-zone Galerkin entries Z_m[k,k'] (Eq. 4 entries, EFIE, singularity
 //    extraction) minus their grid approximation L^T G_m L (stage iv).
 #include <algorithm>
