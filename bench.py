@@ -186,15 +186,22 @@ def dist_setup():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def reduce_max(x, ws):
+def reduce_max(x, ws, device="cuda"):
+    """The largest of the ranks' values (the slowest rank's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def wave_share(n_waves, ws, rank):
+    """Indices of the plane waves rank marches: contiguous, disjoint, covering all waves
+    (independent right-hand sides; no data-path exchange between ranks)."""
+    return np.array_split(np.arange(n_waves), ws)[rank]
 
 
 def barrier(ws):
@@ -275,7 +282,7 @@ def run_aim(args):
     if args.max_waves:
         waves_k, waves_p = waves_k[:args.max_waves], waves_p[:args.max_waves]
     if ws > 1:  # every rank its own share of the plane waves (independent right-hand sides)
-        share = np.array_split(np.arange(len(waves_k)), ws)[rank]
+        share = wave_share(len(waves_k), ws, rank)
         waves_k, waves_p = waves_k[share], waves_p[share]
     nw = len(waves_k)
     total = torch.cuda.get_device_properties(local).total_memory
