@@ -59,9 +59,28 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
       const size_t n = ((size_t)z * N + y) * N + x;
       int e = nptr[n];
       const int e1 = nptr[n + 1];
-      // four entries at a time: their index and coefficient loads, then their gathers of
+      // eight entries at a time: their index and coefficient loads, then their gathers of
       // x, are independent and in flight together (the sums keep the entry order)
-      for (; e + 4 <= e1; e += 4) {
+      for (; e + 8 <= e1; e += 8) {
+        int k[8];
+        typename Real<C>::F4 w[8];
+        C xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          k[u] = nidx[e + u];
+          w[u] = ncoef[e + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xv[u] = vb[k[u]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a0 += (R)w[u].x * xv[u];
+          a1 += (R)w[u].y * xv[u];
+          a2 += (R)w[u].z * xv[u];
+          a3 += (R)w[u].w * xv[u];
+        }
+      }
+      if (e + 4 <= e1) {  // then four
         int k[4];
         typename Real<C>::F4 w[4];
         C xv[4];
@@ -79,6 +98,7 @@ __global__ void __launch_bounds__(256) k_anterp_rows(const int* __restrict__ npt
           a2 += (R)w[u].z * xv[u];
           a3 += (R)w[u].w * xv[u];
         }
+        e += 4;
       }
       for (; e < e1; ++e) {
         const int k = nidx[e];
@@ -709,23 +729,32 @@ __global__ void __launch_bounds__(256, 3) k_interp_near(const C* __restrict__ P,
   C mine{};
   if (P) {
     const size_t N3 = (size_t)nz * N * N;  // the box planes z0 .. z0 + nz - 1
+    // the warp's RWGs and their stencil origins first, so that the potential gathers of
+    // all kInterpRows RWGs depend on no further load and can be in flight together
+    int kr[kInterpRows];
+    size_t org[kInterpRows];
+#pragma unroll
+    for (int r = 0; r < kInterpRows; ++r) kr[r] = k0 + r < ns ? order[k0 + r] : -1;
 #pragma unroll
     for (int r = 0; r < kInterpRows; ++r) {
-      const int pos = k0 + r;
+      const int k = kr[r] < 0 ? 0 : kr[r];
+      org[r] = ((size_t)(anchor[3 * k + 2] - zlo) * N + anchor[3 * k + 1]) * N + anchor[3 * k];
+    }
+#pragma unroll
+    for (int r = 0; r < kInterpRows; ++r) {
       C g{};
-      if (pos < ns) {
-        const int k = order[pos];
+      if (kr[r] >= 0) {
+        const int k = kr[r];
         // 4 lanes per stencil row: lane -> (row of 8, dx); the 256 (component, node)
         // terms of an RWG take 8 warp loads of 8 rows x 32 B each
-        const int ax = anchor[3 * k], ay = anchor[3 * k + 1], az = anchor[3 * k + 2] - zlo;
-        const C* Pb = P + (size_t)b * 4 * N3 + ax + (lane & 3);
+        const C* Pb = P + (size_t)b * 4 * N3 + org[r] + (lane & 3);
         const R* lk = lam + (size_t)k * 256 + lane;
 #pragma unroll
         for (int it = 0; it < 8; ++it) {
           const int q = it * 8 + (lane >> 2);  // (component, row) pair, 0..63
           const int c = q >> 4, row = q & 15;
           const int dz = row >> 2, dy = row & 3;
-          g += lk[it * 32] * Pb[c * N3 + ((size_t)(az + dz) * N + (ay + dy)) * N];
+          g += lk[it * 32] * Pb[c * N3 + ((size_t)dz * N + dy) * N];
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
