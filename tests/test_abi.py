@@ -54,3 +54,37 @@ def test_kernel_classes_match_header():
     got = [lib.aim_kernel_name(i).decode() for i in range(abi.AIM_K_COUNT + 1)]
     assert "?" not in got[:-1] and len(set(got[:-1])) == abi.AIM_K_COUNT
     assert got[-1] == "?"
+
+
+def test_struct_layouts_match_header():
+    """The binding's ctypes structs list the header's fields in order (a field added to
+    one side only would shift every later field)."""
+    from paper_1408_7060_gb300 import abi
+
+    src = open(os.path.join(ROOT, "include", "aim.h")).read()
+    for name, cls in (("aim_opts", abi.aim_opts), ("aim_stats", abi.aim_stats), ("aim_info", abi.aim_info)):
+        end = src.index("} " + name + ";")
+        body = src[src.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            names = decl.split(None, 1)[1] if not decl.startswith("const ") else decl.split(None, 2)[2]
+            for n in names.split(","):
+                fields.append(re.sub(r"[\s*]|\[\d+\]", "", n))
+        assert [f for f, _ in cls._fields_] == fields, name
+
+
+def test_z_lengths_agree():
+    """The z transform lengths the library chooses from (api.cu), dispatches
+    (operator_impl.cuh) and the bench's memory plan assumes are the same list."""
+    import bench
+
+    api = open(os.path.join(ROOT, "paper_1408_7060_gb300", "csrc", "api.cu")).read()
+    impl = open(os.path.join(ROOT, "paper_1408_7060_gb300", "csrc", "operator_impl.cuh")).read()
+    chosen = [int(x) for x in re.search(r"for \(int lz : \{([\d, ]+)\}\)", api).group(1).split(",")]
+    body = re.search(r"inline void with_zlen\(int lz, F&& f\) \{(.*?)default:", impl, re.S).group(1)
+    dispatched = [int(x) for x in re.findall(r"case (\d+):", body)]
+    assert chosen == dispatched == list(bench.Z_LENGTHS)
