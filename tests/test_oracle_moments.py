@@ -35,13 +35,14 @@ CA = MU0 / (4 * math.pi)
 CP = 1.0 / (4 * math.pi * EPS0)
 
 
-@pytest.fixture(scope="module")
-def small():
-    """80-triangle sphere (120 RWG), the 150 MHz +-50 % pulse of the 480-RWG workload."""
+@pytest.fixture(scope="module", params=[2, 3], ids=["Q2", "Q3"])
+def small(request):
+    """80-triangle sphere (120 RWG), the 150 MHz +-50 % pulse of the 480-RWG workload, CPPIF
+    of order Q = 2 (the sphere workloads) and Q = 3 (the plates)."""
     w = make_workload("sphere480")
     V, F = icosphere(1, 1.0)
     rwg = build_rwg(V, F)
-    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=2)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=request.param)
     return w, rwg, p
 
 

@@ -199,6 +199,18 @@ def test_dc_identity_operator(s480_Z, s480):
     assert np.abs(S - 1j * p.wc * ZF).max() < 1e-13 * np.abs(S).max()
 
 
+def test_dc_identity_operator_open_plate():
+    """The same identity on an open surface (the 1 m plate of Table II, its boundary edges
+    carrying no basis), with the plates' CPPIF of order 3."""
+    w = make_workload("plate280")
+    rwg = build_rwg(*w.mesh)
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=w.order)
+    S = efie.fill_dense(rwg, p).sum(0)
+    ZF = efie.fill_dense(rwg, p, freq=True)
+    assert rwg.ns == 280
+    assert np.abs(S - 1j * p.wc * ZF).max() < 1e-13 * np.abs(S).max()
+
+
 def test_dc_identity_excitation(s480):
     """dt sum_l V_l = j w sigma sqrt(2 pi) e^{-j w t_d} V^FD (Gaussian sample sum)."""
     w, rwg, p = s480
