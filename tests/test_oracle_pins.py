@@ -335,6 +335,31 @@ def test_grid_convolution_fft_equals_direct(s480_aim):
             assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(a)
 
 
+def test_box_deep_z_period_gives_the_linear_convolution(s480_aim):
+    """Sources confined to n_z consecutive z-planes: a circular convolution of z period
+    L_z >= 2 n_z (kernel offsets |dz| < L_z/2 taken from the 2N embedding, the plane L_z/2
+    zero) gives on those planes the values of the 2N-padded linear convolution -- the
+    reading behind the library's box-deep z transforms."""
+    A = s480_aim
+    n = A.n
+    z0, nz = 5, 6
+    rng = np.random.default_rng(41)
+    src = np.zeros((n, n, n), dtype=complex)  # [z][y][x]
+    src[z0:z0 + nz] = rng.standard_normal((nz, n, n)) + 1j * rng.standard_normal((nz, n, n))
+    for m, kind in ((0, 0), (1, 1)):
+        ref = A.conv_fft(m, src.ravel(), kind).reshape(n, n, n)[z0:z0 + nz]
+        G2 = A.kernel_grid(m, kind)  # [z][y][x], period 2N
+        for lz in (2 * nz, 16):
+            iz = np.arange(lz)
+            dz = np.where(iz < lz // 2, iz, iz - lz)
+            G = G2[dz % (2 * n)].copy()
+            G[lz // 2] = 0
+            a = np.zeros((lz, 2 * n, 2 * n), dtype=complex)
+            a[:nz, :n, :n] = src[z0:z0 + nz]
+            out = np.fft.ifftn(np.fft.fftn(a) * np.fft.fftn(G))[:nz, :n, :n]
+            assert np.abs(out - ref).max() < 1e-12 * np.abs(ref).max(), (m, kind, lz)
+
+
 def test_grid_convolution_point_source(s480_aim):
     """A unit source at one node radiates the kernel itself: P[n] = G_m(n - n0)."""
     A = s480_aim
