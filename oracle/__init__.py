@@ -19,6 +19,8 @@ What it computes (each module cites the passage it follows):
 * ``aim``        the ET-AIM operator of Eq. 5: moment-matching anter/interpolation,
                  grid Green-function envelopes, brute-force and FFT grid sums, and
                  the pre-corrected near-zone matrices (Sec. 4, stages i-iv).
+* ``mfie``       the time-differentiated envelope MFIE and its frequency-domain form, for
+                 the combined-field equation of Sec. 2.1 (CFIE).
 * ``march``      time marching of Eq. 4 (direct ET-MOT) and Eq. 5 (ET-AIM).
 * ``blocked``    the delayed sums of the right-hand side by the multilevel blocked
                  schedule with temporal FFTs (Sec. 4, stage ii), and directly.
