@@ -9,6 +9,8 @@ What it computes (each module cites the passage it follows):
 * ``rwg``        RWG spatial basis on a triangle mesh (Sec. 3, Eq. 3).
 * ``tbasis``     causal piecewise-polynomial interpolatory temporal basis, CPPIF
                  (Sec. 3, Eq. 3).
+* ``blif``       band-limited interpolatory temporal basis (approximate prolate
+                 spheroidal) and its causal extrapolation (Sec. 3, 3.1.2).
 * ``quad``       triangle cubature rules.
 * ``singular``   closed-form integrals of 1/R and (r'-r)/R over a triangle, used
                  for singularity extraction (Sec. 3.1 mentions singularity
@@ -27,7 +29,7 @@ What it computes (each module cites the passage it follows):
 * ``mie``        Mie series for a PEC sphere (Sec. 5, reference [18]) and the dB-error
                  norm of Eq. 2.
 * ``rcs``        bistatic RCS of a marched current envelope at one frequency
-                 (Sec. 2.4): the CPPIF spectrum, the envelope and incident-pulse
+                 (Sec. 2.4): the CPPIF and BLIF spectra, the envelope and incident-pulse
                  transforms, and the directions and weights of the Eq. 2 integrals.
 
 Readings of passages the paper leaves open are listed in the design notes; the

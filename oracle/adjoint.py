@@ -33,6 +33,8 @@ def _half_bases(rwg):
 
 def incident_taps(rwg, p: efie.Params, khat, phat, s_range):
     """B_s[k] for s in s_range (list of ints): [len(s_range), ns]."""
+    if p.basis != "cppif":
+        raise NotImplementedError("the adjoint taps interpolate with the CPPIF")
     g, S = _half_bases(rwg)
     khat, phat = np.asarray(khat, float), np.asarray(phat, float)
     u = (g.P @ khat) / p.cdt                                           # [nt,7]
@@ -50,6 +52,8 @@ def incident_taps(rwg, p: efie.Params, khat, phat, s_range):
 
 def farfield_taps(rwg, p: efie.Params, rhat, e1, e2, s_range):
     """A_s[d][q][k] for directions d, transverse components q: [len(s_range), nd, 2, ns]."""
+    if p.basis != "cppif":
+        raise NotImplementedError("the adjoint taps interpolate with the CPPIF")
     g, S = _half_bases(rwg)
     rhat = np.atleast_2d(rhat)
     E = np.stack([np.atleast_2d(e1), np.atleast_2d(e2)], axis=1)     # [nd,2,3]

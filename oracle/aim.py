@@ -27,7 +27,7 @@ import math
 import numpy as np
 import scipy.sparse as sp
 
-from . import efie, quad, tbasis
+from . import efie, quad
 from .constants import EPS0, MU0
 from .rwg import RWG
 
@@ -142,7 +142,7 @@ class AimOracle:
             d2 = sq[i:i + 4096, None] + sq[None, :] - 2.0 * (ijk[i:i + 4096] @ ijk.T)
             best = max(best, float(d2.max()))
         rmax = self.h * math.sqrt(int(round(best)))
-        return int(math.floor(rmax / self.p.cdt + self.p.Q))
+        return int(math.floor(rmax / self.p.cdt + self.p.support))
 
     def kernel_values(self, m: int, dijk: np.ndarray):
         """(G^A_m, G^phi_m) at integer offsets ``dijk[...,3]`` (G(0) = 0)."""
@@ -151,11 +151,10 @@ class AimOracle:
         v = m - R / self.p.cdt
         ph = np.exp(-1j * self.p.kc * R)
         p = self.p
-        D2T = (tbasis.T(v, p.Q, 2) / p.dt ** 2 + 2j * p.wc * tbasis.T(v, p.Q, 1) / p.dt
-               - p.wc ** 2 * tbasis.T(v, p.Q, 0))
+        D2T = p.T(v, 2, m) / p.dt ** 2 + 2j * p.wc * p.T(v, 1, m) / p.dt - p.wc ** 2 * p.T(v, 0, m)
         with np.errstate(divide="ignore", invalid="ignore"):
             GA = np.where(R > 0, D2T * ph / R, 0.0)
-            GP = np.where(R > 0, tbasis.T(v, p.Q, 0) * ph / R, 0.0)
+            GP = np.where(R > 0, p.T(v, 0, m) * ph / R, 0.0)
         return GA, GP
 
     # ------------------------------------------------------------------ grid sums

@@ -25,20 +25,44 @@ import math
 
 import numpy as np
 
-from . import quad, singular, tbasis
+from . import blif, quad, singular, tbasis
 from .constants import C0, EPS0, MU0
 from .rwg import RWG
 
 
 @dataclasses.dataclass
 class Params:
-    """Time step, carrier, CPPIF order and the homogeneous background medium (Sec. 2.1:
-    relative permittivity and permeability; vacuum by default)."""
+    """Time step, carrier, temporal basis and the homogeneous background medium (Sec. 2.1:
+    relative permittivity and permeability; vacuum by default).  The basis is the CPPIF of
+    order Q (Eq. 3), or with ``basis="blif"`` the BLIF of half-width M for the band fraction
+    beta = f_bw dt with its causal extrapolation (``blif``)."""
     dt: float
     f_c: float
     Q: int = 2
     eps_r: float = 1.0
     mu_r: float = 1.0
+    basis: str = "cppif"
+    M: int = 3
+    beta: float = 0.25
+
+    def __post_init__(self):
+        if self.basis not in ("cppif", "blif"):
+            raise ValueError("basis is 'cppif' or 'blif'")
+        self._E = blif.extrapolation(self.M, self.beta) if self.basis == "blif" else None
+
+    @property
+    def support(self) -> int:
+        """Upper end of the basis' support in steps: Q (CPPIF, (-1, Q]) or M (BLIF, (-M, M))."""
+        return self.Q if self.basis == "cppif" else self.M
+
+    def T(self, v, deriv: int = 0, m=None) -> np.ndarray:
+        """T^(deriv)(v); with the delay ``m`` (broadcast against v) the causal time factor
+        of that delay, which for the BLIF adds the extrapolated samples."""
+        if self.basis == "cppif":
+            return tbasis.T(v, self.Q, deriv)
+        if m is None:
+            return blif.T(v, self.M, self.beta, deriv)
+        return blif.T_eff(m, v, self.M, self.beta, self._E, deriv)
 
     @property
     def wc(self) -> float:
@@ -70,11 +94,12 @@ class Params:
 # ----------------------------------------------------------------------------
 
 
-def _d2T(v, p: Params, extra_deriv: int = 0):
-    """(D^2 T)^(extra_deriv)(v) in physical units of the T argument."""
-    T0 = tbasis.T(v, p.Q, 0 + extra_deriv)
-    T1 = tbasis.T(v, p.Q, 1 + extra_deriv)
-    T2 = tbasis.T(v, p.Q, 2 + extra_deriv)
+def _d2T(v, p: Params, extra_deriv: int = 0, m=None):
+    """(D^2 T)^(extra_deriv)(v) in physical units of the T argument (the time factor of
+    delay ``m`` where given)."""
+    T0 = p.T(v, 0 + extra_deriv, m)
+    T1 = p.T(v, 1 + extra_deriv, m)
+    T2 = p.T(v, 2 + extra_deriv, m)
     return T2 / p.dt ** 2 + 2j * p.wc * T1 / p.dt - p.wc ** 2 * T0
 
 
@@ -83,17 +108,18 @@ def time_kernels(m: np.ndarray, R: np.ndarray, p: Params):
 
     ``m`` has shape [nm]; the result has shape [nm, *R.shape].
     """
-    v = m.reshape((-1,) + (1,) * R.ndim) - R[None] / p.cdt
+    mb = m.reshape((-1,) + (1,) * R.ndim)
+    v = mb - R[None] / p.cdt
     ph = np.exp(-1j * p.kc * R)[None]
-    return _d2T(v, p) * ph, tbasis.T(v, p.Q) * ph
+    return _d2T(v, p, 0, mb) * ph, p.T(v, 0, mb) * ph
 
 
 def time_kernels_at0(m: np.ndarray, p: Params):
     """Values and one-sided R-derivatives at R = 0+ of both time kernels."""
     v = m.astype(np.float64)
-    fA0, fP0 = _d2T(v, p), tbasis.T(v, p.Q).astype(complex)
-    dA0 = -_d2T(v, p, 1) / p.cdt - 1j * p.kc * fA0
-    dP0 = -tbasis.T(v, p.Q, 1) / p.cdt - 1j * p.kc * fP0
+    fA0, fP0 = _d2T(v, p, 0, v), p.T(v, 0, v).astype(complex)
+    dA0 = -_d2T(v, p, 1, v) / p.cdt - 1j * p.kc * fA0
+    dP0 = -p.T(v, 1, v) / p.cdt - 1j * p.kc * fP0
     return fA0, fP0, dA0, dP0
 
 
@@ -214,8 +240,9 @@ def max_point_distance(g: Geometry) -> float:
 
 def n_delays_mot(g: Geometry, p: Params) -> int:
     """N_g = floor(R_max / (c dt) + Q): last delay with a non-zero entry (Sec. 3,
-    after Eq. 4, with l_max read as the CPPIF order Q), R_max over cubature points."""
-    return int(math.floor(max_point_distance(g) / p.cdt + p.Q))
+    after Eq. 4, with l_max read as the upper end of the basis' support: the CPPIF order Q,
+    or the BLIF half-width M), R_max over cubature points."""
+    return int(math.floor(max_point_distance(g) / p.cdt + p.support))
 
 
 def fill_dense(rwg: RWG, p: Params, n_delays: int | None = None, chunk: int = 4096,

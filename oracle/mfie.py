@@ -32,7 +32,7 @@ import math
 
 import numpy as np
 
-from . import efie, quad, tbasis
+from . import efie, quad
 
 
 def normals(rwg) -> np.ndarray:
@@ -59,15 +59,16 @@ def subdivided_rule(levels: int):
     return pts, w
 
 
-def _dT(v, p: efie.Params):
-    return tbasis.T(v, p.Q, 1) / p.dt + 1j * p.wc * tbasis.T(v, p.Q, 0)
+def _dT(v, p: efie.Params, m=None):
+    return p.T(v, 1, m) / p.dt + 1j * p.wc * p.T(v, 0, m)
 
 
 def _kernel_td(m: np.ndarray, R: np.ndarray, p: efie.Params):
     """[nm, *R.shape]: [(DT)(v)/R^2 + (D^2 T)(v)/(c R)] e^{-j k_c R} / (4 pi)."""
-    v = m.reshape((-1,) + (1,) * R.ndim) - R[None] / p.cdt
+    mb = m.reshape((-1,) + (1,) * R.ndim)
+    v = mb - R[None] / p.cdt
     ph = np.exp(-1j * p.kc * R)[None] / (4 * math.pi)
-    return (_dT(v, p) / R[None] ** 2 + efie._d2T(v, p) / (p.c * R[None])) * ph
+    return (_dT(v, p, mb) / R[None] ** 2 + efie._d2T(v, p, 0, mb) / (p.c * R[None])) * ph
 
 
 def _kernel_fd(m: np.ndarray, R: np.ndarray, p: efie.Params):
@@ -114,7 +115,7 @@ def fill_dense(rwg, p: efie.Params, n_delays: int | None = None, freq: bool = Fa
             n_delays = efie.n_delays_mot(g, p)
         m = np.arange(n_delays + 1, dtype=np.float64)
         kern = _kernel_td
-        gram = 0.5 * _dT(m, p)
+        gram = 0.5 * _dT(m, p, m)
     out = np.zeros((len(m), ns, ns), dtype=complex)
     T_, TP_ = np.meshgrid(np.arange(ntri), np.arange(ntri), indexing="ij")
     T_, TP_ = T_.ravel(), TP_.ravel()

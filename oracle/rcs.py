@@ -27,7 +27,9 @@ import math
 
 import numpy as np
 
-from . import efie, tbasis
+from scipy import integrate
+
+from . import blif, efie, tbasis
 
 
 def cppif_spectrum(w, Q: int = 2, npts: int = 24) -> np.ndarray:
@@ -41,6 +43,33 @@ def cppif_spectrum(w, Q: int = 2, npts: int = 24) -> np.ndarray:
         Tu = tbasis.T(u, Q)
         out += 0.5 * np.sum(wt * Tu * np.exp(-1j * np.outer(w, u)), axis=1)
     return out
+
+
+def blif_spectrum(w: float, M: int, beta: float) -> complex:
+    """That(w) = int T(u) e^{-j w u} du of the BLIF over (-M, M) (scipy's adaptive quadrature on
+    each unit interval).  The extrapolation only changes how the samples are solved for: the
+    envelope between them is still sum_l I_l T(t/dt - l)."""
+    re = im = 0.0
+    for j in range(-M, M):
+        re += integrate.quad(lambda u: blif.T(np.array([u]), M, beta)[0] * math.cos(w * u), j, j + 1,
+                             epsabs=1e-15, epsrel=1e-13)[0]
+        im -= integrate.quad(lambda u: blif.T(np.array([u]), M, beta)[0] * math.sin(w * u), j, j + 1,
+                             epsabs=1e-15, epsrel=1e-13)[0]
+    return complex(re, im)
+
+
+def basis_spectrum(w: float, p: efie.Params) -> complex:
+    """That(w) of the temporal basis of ``p`` (CPPIF or BLIF)."""
+    if p.basis == "blif":
+        return blif_spectrum(w, p.M, p.beta)
+    return complex(cppif_spectrum(w, p.Q)[0])
+
+
+def envelope_spectrum_p(I: np.ndarray, p: efie.Params, Omega: float, l0: int = 1) -> np.ndarray:
+    """``envelope_spectrum`` for the basis of ``p``."""
+    l = np.arange(l0, l0 + len(I))
+    s = np.tensordot(np.exp(-1j * Omega * l * p.dt), np.asarray(I), axes=(0, 0))
+    return p.dt * basis_spectrum(Omega * p.dt, p) * s
 
 
 def envelope_spectrum(I: np.ndarray, dt: float, Q: int, Omega: float, l0: int = 1) -> np.ndarray:
@@ -63,7 +92,7 @@ def rcs_td(rwg, p: efie.Params, I: np.ndarray, sigma: float, t_d: float, f: floa
     polarisations pol [nd, 3], of the marched envelope I [n_steps, ns] excited by the
     Gaussian plane wave of Eq. 1 (sigma, t_d; f_c = p.f_c)."""
     Omega = 2 * math.pi * (f - p.f_c)
-    Ifd = envelope_spectrum(I, p.dt, p.Q, Omega, l0) / incident_spectrum(sigma, t_d, p.f_c, Omega)
+    Ifd = envelope_spectrum_p(I, p, Omega, l0) / incident_spectrum(sigma, t_d, p.f_c, Omega)
     return efie.rcs_fd(rwg, efie.Params(dt=p.dt, f_c=f, Q=p.Q), Ifd, rhat, pol)
 
 

@@ -255,7 +255,7 @@ class Workload:
     tol: float             # GMRES relative-residual tolerance
     khat: np.ndarray       # [nb,3]
     phat: np.ndarray       # [nb,3]
-    order: int = 2         # CPPIF order Q
+    order: int = 2         # CPPIF order Q, or the BLIF half-width M
     precision: str = "c64"  # "c128" plain path, "c64" grid path with FP64 outer solve
     beta: float = 0.25
     precond: str = "diag"  # GMRES right preconditioner: "diag" (Sec. 5.1) or "sai"
@@ -267,6 +267,7 @@ class Workload:
     rhs_blocked: int = 0   # delayed grid sums by the multilevel blocked schedule (Sec. 4 stage ii)
     eps_r: float = 1.0     # homogeneous background medium (Sec. 2.1); vacuum by default
     mu_r: float = 1.0
+    basis: str = "cppif"   # temporal basis: "cppif" (Eq. 3) or "blif" (half-width = order, band = beta)
 
     @property
     def f_bw(self) -> float:
