@@ -59,7 +59,15 @@ enum { AIM_C128 = 0,     /* plain path: every stage in complex128               
                             interpolation) in complex64 with FP32 accumulation;
                             near zone, residual and Krylov basis in FP64            */
 
-enum { AIM_CPPIF = 0 };  /* causal piecewise-polynomial interpolatory basis        */
+enum { AIM_CPPIF = 0,    /* causal piecewise-polynomial interpolatory basis        */
+       AIM_BLIF = 1 };   /* band-limited interpolatory basis (Sec. 3, 3.1.2): the
+                            approximate prolate spheroidal interpolant
+                            T(u) = sinc(u) w(u), |u| < M, w(u) = G(M^2 - u^2)/G(M^2),
+                            G(s) = sinh(b sqrt s)/sqrt s, guard band
+                            b = pi (1 - 2 aim_opts.blif_band); made causal by
+                            extrapolating the samples l+1..l+M-1 from l..l-M+1
+                            (least squares over 2M frequencies spread evenly over the
+                            band, edges included), which folds them into Z_0..Z_{M-1} */
 
 /* Right preconditioner of the immediate system (x = M y, solve Z_0 M y = b). */
 enum { AIM_PRECOND_DIAG = 0,      /* M = diag(1 / Z_0[k,k]) (Sec. 5.1)                  */
@@ -87,8 +95,10 @@ typedef struct {
 } aim_grid;
 
 typedef struct {
-  int32_t kind;          /* AIM_CPPIF                                               */
-  int32_t order;         /* Q (1..4); support (-1, Q] in units of dt                */
+  int32_t kind;          /* AIM_CPPIF or AIM_BLIF                                   */
+  int32_t order;         /* CPPIF: Q (1..4), support (-1, Q] in units of dt;
+                            BLIF: the half-width M (2..5), support (-M, M); N_g is
+                            floor(R_max / (c dt) + order) in both cases             */
 } aim_tbasis;
 
 typedef struct {
@@ -132,6 +142,11 @@ typedef struct {
                             and permeability; values <= 0 mean 1 (vacuum).  Light speed
                             c0 / sqrt(eps_r mu_r), mu = mu0 mu_r, eps = eps0 eps_r in every
                             kernel, excitation, far field and RCS.                          */
+  double blif_band;      /* AIM_BLIF only: the envelope's half band times the time step,
+                            f_bw dt, in (0, 1/2) (AIM_ERR_ARG otherwise).  With AIM_BLIF the
+                            sampled-envelope excitation and far-field entry points
+                            (aim_excitation_samples*, aim_farfield*, aim_march_farfield,
+                            aim_march_adjoint_farfield) return AIM_ERR_ARG.                 */
 } aim_opts;
 
 typedef struct {
@@ -243,6 +258,15 @@ int aim_get_profile(aim_ctx* ctx, int64_t* launches, double* ms, int64_t* total_
 const char* aim_kernel_name(int32_t id);
 
 /* N_s and N_g of the context. */
+/* aim_time_factor -- the temporal basis on the host, no context or GPU needed (Sec. 3, Eq. 3
+ * and Sec. 3.1.2): out[i][d] = d-th derivative (d = 0..3, in units of the step) of the time
+ * factor of delay m at x[i] = R / (c dt), i = 0..n-1: T(m - x) for AIM_CPPIF; for AIM_BLIF
+ * T(m - x) plus, for m < M, the extrapolated samples sum_p E[p][m] T(-p - x) (the factor the
+ * context's Z_m is built with).  x and out are host arrays ([n], [n][4]), owned by the caller.
+ * AIM_ERR_ARG for a bad basis, order or blif_band (aim_last_error(NULL) says which), m < 0,
+ * n < 0 or null arrays. */
+int aim_time_factor(aim_tbasis tbasis, double blif_band, int32_t m, int32_t n, const double* x, double* out);
+
 int aim_num_unknowns(const aim_ctx* ctx, int32_t* ns, int32_t* n_delays);
 
 /*

@@ -19,6 +19,7 @@ AIM_OK, AIM_ERR_ARG, AIM_ERR_MESH, AIM_ERR_CUDA, AIM_ERR_OOM, AIM_ERR_NOCONV, AI
 AIM_WARN_UNSTABLE = 1
 AIM_C128, AIM_C64 = 0, 1
 AIM_CPPIF = 0
+AIM_BLIF = 1
 AIM_PLAN_DEFAULT, AIM_PLAN_MEASURED, AIM_PLAN_CACHED = 0, 1, 2
 
 _NAMES = {0: "AIM_OK", -1: "AIM_ERR_ARG", -2: "AIM_ERR_MESH", -3: "AIM_ERR_CUDA", -4: "AIM_ERR_OOM",
@@ -48,7 +49,8 @@ class aim_opts(ct.Structure):
                 ("gmres_restart", ct.c_int32), ("gmres_max_iter", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("preconditioner", ct.c_int32), ("precond_radius", ct.c_double), ("zero_start", ct.c_int32),
                 ("refine", ct.c_int32), ("refine_every", ct.c_int32), ("autotune", ct.c_int32),
-                ("rhs_blocked", ct.c_int32), ("eps_r", ct.c_double), ("mu_r", ct.c_double)]
+                ("rhs_blocked", ct.c_int32), ("eps_r", ct.c_double), ("mu_r", ct.c_double),
+                ("blif_band", ct.c_double)]
 
 
 class aim_excitation(ct.Structure):
@@ -71,7 +73,7 @@ class aim_info(ct.Structure):
                 ("box_hi", ct.c_int32 * 3), ("rhs_blocked", ct.c_int32), ("z_len", ct.c_int32)]
 
 
-EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_num_unknowns", "aim_rwg_table",
+EXPORTS = ["aim_setup", "aim_destroy", "aim_last_error", "aim_get_info", "aim_time_factor", "aim_num_unknowns", "aim_rwg_table",
            "aim_matvec", "aim_rhs", "aim_excitation_vector", "aim_march", "aim_march_continue", "aim_get_anterp",
            "aim_get_near", "aim_get_preconditioner", "aim_get_kernel_spectrum", "aim_profile", "aim_get_profile", "aim_kernel_name",
            "aim_matvec_noalloc", "aim_march_source", "aim_excitation_samples", "aim_excitation_samples_adjoint",
@@ -103,6 +105,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
         "aim_destroy": (None, [P]),
         "aim_last_error": (ct.c_char_p, [P]),
         "aim_get_info": (ct.c_int, [P, ct.POINTER(aim_info)]),
+        "aim_time_factor": (ct.c_int, [aim_tbasis, D, I32, I32, ct.c_void_p, ct.c_void_p]),
         "aim_num_unknowns": (ct.c_int, [P, ct.POINTER(I32), ct.POINTER(I32)]),
         "aim_rwg_table": (ct.c_int, [P, P, P, P]),
         "aim_matvec": (ct.c_int, [P, I32, I32, P, P]),
@@ -192,7 +195,8 @@ PRECOND = {"diag": 0, "sai": 1}  # AIM_PRECOND_DIAG, AIM_PRECOND_NEAR_SAI
 
 def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision="c64", batch_max=1,
               restart=50, max_iter=500, stream=None, precond="diag", precond_radius=0.0, zero_start=False,
-              refine=0, autotune=0, refine_every=1, rhs_blocked=0, eps_r=1.0, mu_r=1.0):
+              refine=0, autotune=0, refine_every=1, rhs_blocked=0, eps_r=1.0, mu_r=1.0, basis="cppif",
+              blif_band=0.25):
     """Build a context; returns an opaque handle (int).  precond: "diag" (the paper's
     diagonal preconditioner) or "sai" (sparse approximate inverse on the pairs within
     precond_radius, default the near radius).  zero_start: GMRES from zero instead of
@@ -200,18 +204,19 @@ def aim_setup(V, F, grid_n, origin, h, near_radius, dt, f_c, order=2, precision=
     refinement corrections per step (0: off), checked every refine_every-th step.
     autotune: 0 default launch shapes, 1 tuned at setup (cached plan reused), 2 tuned and
     cache refreshed.  rhs_blocked: delayed grid sums by the multilevel blocked schedule
-    (power-of-two z transforms).  eps_r, mu_r: the homogeneous background medium."""
+    (power-of-two z transforms).  eps_r, mu_r: the homogeneous background medium.  basis:
+    "cppif" (order = Q) or "blif" (order = the half-width M, blif_band = f_bw dt)."""
     lib = load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
     mesh = aim_mesh(len(V), len(F), V.ctypes.data, F.ctypes.data)
     grid = aim_grid(int(grid_n), (ct.c_double * 3)(*[float(o) for o in origin]), float(h))
-    tb = aim_tbasis(AIM_CPPIF, int(order))
+    tb = aim_tbasis({"cppif": AIM_CPPIF, "blif": AIM_BLIF}[basis], int(order))
     prec = {"c128": AIM_C128, "c64": AIM_C64}[precision]
     opts = aim_opts(float(f_c), prec, int(batch_max), int(restart), int(max_iter),
                     stream if stream is not None else _stream_handle(), PRECOND[precond], float(precond_radius),
                     int(bool(zero_start)), int(refine), int(refine_every), int(autotune), int(bool(rhs_blocked)),
-                    float(eps_r), float(mu_r))
+                    float(eps_r), float(mu_r), float(blif_band))
     out = ct.c_void_p()
     rc = lib.aim_setup(ct.byref(mesh), ct.byref(grid), float(near_radius), float(dt), tb, ct.byref(opts),
                        ct.byref(out))
@@ -229,6 +234,18 @@ def aim_get_info(ctx) -> dict:
     _check(lib, ctx, lib.aim_get_info(ctx, ct.byref(info)), "aim_get_info")
     out = {f: getattr(info, f) for f, _ in aim_info._fields_}
     out["box_lo"], out["box_hi"] = tuple(info.box_lo), tuple(info.box_hi)
+    return out
+
+
+def aim_time_factor(m, x, basis="cppif", order=2, blif_band=0.25):
+    """[len(x), 4]: the time factor of delay m and its first three derivatives at x = R/(c dt)
+    (host computation, no GPU)."""
+    lib = load()
+    x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
+    out = np.zeros((len(x), 4))
+    tb = aim_tbasis({"cppif": AIM_CPPIF, "blif": AIM_BLIF}[basis], int(order))
+    _check(lib, None, lib.aim_time_factor(tb, float(blif_band), int(m), len(x), x.ctypes.data, out.ctypes.data),
+           "aim_time_factor")
     return out
 
 
@@ -525,7 +542,7 @@ class AimContext:
                   f_c=w.f_c, order=w.order, precision=w.precision, batch_max=w.nb, precond=w.precond,
                   precond_radius=w.precond_radius, zero_start=w.zero_start, refine=w.refine,
                   refine_every=w.refine_every, autotune=w.autotune, rhs_blocked=w.rhs_blocked, eps_r=w.eps_r,
-                  mu_r=w.mu_r)
+                  mu_r=w.mu_r, basis=w.basis, blif_band=w.beta)
         kw.update(over)
         return cls(**kw)
 

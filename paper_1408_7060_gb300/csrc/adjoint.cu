@@ -287,6 +287,8 @@ MeshArgs mesh_args(aim_ctx* c) {
   m.kc = c->kc;
   m.cdt = c->c_med * c->dt;
   m.mu = c->mu_med;
+  if (c->tb.kind != AIM_CPPIF)
+    throw AimError{AIM_ERR_ARG, "the sampled-envelope excitation and far field interpolate with the CPPIF only"};
   m.tb = c->tb;
   return m;
 }

@@ -17,6 +17,7 @@ constexpr double kMu0 = 4.0e-7 * kPi;
 constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
 constexpr int kMaxDelays = 32;   // N_g + 1 <= kMaxDelays
 constexpr int kMaxOrder = 4;     // CPPIF order
+constexpr int kMaxHalfWidth = 5; // BLIF half-width M
 }  // namespace aimc
 
 struct AimError {
@@ -64,10 +65,16 @@ inline void launch_pdl(cudaStream_t st, dim3 grid, dim3 block, size_t smem, void
     AIM_CHECK_LAUNCH();              \
   } while (0)
 
-// CPPIF pieces: T on (j-1, j] is sum_p coef[j][p] u^p (Horner on device)
+// Temporal basis.  CPPIF (kind AIM_CPPIF): T on the piece (j-1, j] is sum_p coef[j][p] u^p
+// (Horner on device), support (-1, Q].  BLIF (kind AIM_BLIF): T(u) = sinc(u) w(u) on |u| < M,
+// w(u) = G(M^2 - u^2) / G(M^2), G(s) = sinh(b sqrt s) / sqrt s, b the guard band, and the
+// sample l+p (p = 1..M-1) extrapolated as sum_q ext[p][q] I_{l-q}, q = 0..M-1.
 struct TBasis {
-  int Q;
+  int kind;
+  int Q;         // upper end of the support in steps: the CPPIF order Q or the BLIF half-width M
   double coef[aimc::kMaxOrder + 1][aimc::kMaxOrder + 1];
+  double b, invG0;
+  double ext[aimc::kMaxHalfWidth][aimc::kMaxHalfWidth];
 };
 
 // Sum over the lanes of a warp of a complex value, in 5 FP64 additions instead of 10:

@@ -17,6 +17,7 @@
 #include "rcs.h"
 #include "setup_gpu.h"
 #include "setup_host.h"
+#include "tbasis.cuh"
 
 namespace {
 
@@ -77,7 +78,7 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
   if (!mesh || !grid || !opts) throw AimError{AIM_ERR_ARG, "null argument"};
   if (!supported_n(grid->n)) throw AimError{AIM_ERR_ARG, "grid n must be one of 8,16,32,64,96,128,384"};
   if (!(grid->h > 0) || !(dt > 0) || !(opts->f_c > 0)) throw AimError{AIM_ERR_ARG, "h, dt and f_c must be > 0"};
-  if (tb.kind != AIM_CPPIF) throw AimError{AIM_ERR_ARG, "only the CPPIF temporal basis is built"};
+  if (tb.kind != AIM_CPPIF && tb.kind != AIM_BLIF) throw AimError{AIM_ERR_ARG, "temporal basis: AIM_CPPIF or AIM_BLIF"};
   if (opts->precision != AIM_C64 && opts->precision != AIM_C128) throw AimError{AIM_ERR_ARG, "precision"};
   if (opts->batch_max < 1 || opts->batch_max > 4096) throw AimError{AIM_ERR_ARG, "batch_max out of range"};
   c->N = grid->n;
@@ -120,7 +121,10 @@ void setup_impl(aim_ctx* c, const aim_mesh* mesh, const aim_grid* grid, double n
     AIM_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     c->own_stream = true;
   }
-  host_cppif(tb.order, c->tb);
+  if (tb.kind == AIM_BLIF)
+    host_blif(tb.order, opts->blif_band, c->tb);
+  else
+    host_cppif(tb.order, c->tb);
 
   HostMesh hm;
   host_build_rwg(mesh, hm);
@@ -465,6 +469,24 @@ int aim_get_info(const aim_ctx* c, aim_info* info) {
   }
   info->z_len = c->LZ;
   info->rhs_blocked = c->rhs_blocked ? 1 : 0;
+  return AIM_OK;
+}
+
+int aim_time_factor(aim_tbasis tb, double blif_band, int32_t m, int32_t n, const double* x, double* out) {
+  if (m < 0 || n < 0 || (n > 0 && (!x || !out))) return AIM_ERR_ARG;
+  try {
+    TBasis b;
+    if (tb.kind == AIM_BLIF)
+      host_blif(tb.order, blif_band, b);
+    else if (tb.kind == AIM_CPPIF)
+      host_cppif(tb.order, b);
+    else
+      throw AimError{AIM_ERR_ARG, "temporal basis: AIM_CPPIF or AIM_BLIF"};
+    for (int32_t i = 0; i < n; ++i) tb_eval(b, m, x[i], out + 4 * (size_t)i);
+  } catch (const AimError& e) {
+    g_last_setup_error = e.msg;
+    return e.code;
+  }
   return AIM_OK;
 }
 
@@ -819,7 +841,7 @@ int aim_march_spectrum(aim_ctx* c, const aim_excitation* exc, int32_t n_steps, d
       const std::complex<double> E = exc->sigma * std::sqrt(2.0 * aimc::kPi) *
                                      std::exp(-0.5 * exc->sigma * exc->sigma * W * W) *
                                      std::exp(std::complex<double>(0.0, -(c->wc + W) * exc->t_d));
-      const std::complex<double> v = c->dt * cppif_spectrum(c->tb, W * c->dt) / E;
+      const std::complex<double> v = c->dt * basis_spectrum(c->tb, W * c->dt) / E;
       sc.w[f] = make_double2(v.real(), v.imag());
     }
     rcs_scale(c, nb, sc, acc);

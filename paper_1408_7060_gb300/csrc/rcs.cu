@@ -113,11 +113,19 @@ int blocks_for(long long n) { return (int)std::min<long long>((n + kT - 1) / kT,
 
 }  // namespace
 
-std::complex<double> cppif_spectrum(const TBasis& tb, double w) {
+std::complex<double> basis_spectrum(const TBasis& tb, double w) {
   std::vector<double> x, wt;
   host_gauss_legendre(24, x, wt);
   std::complex<double> s = 0.0;
-  for (int j = 0; j <= tb.Q; ++j) {  // piece (j-1, j]
+  if (tb.kind == AIM_BLIF) {  // smooth on (-M, M): 24 points on each unit interval
+    for (int j = -tb.Q; j < tb.Q; ++j)
+      for (size_t i = 0; i < x.size(); ++i) {
+        const double u = j + 0.5 + 0.5 * x[i];
+        s += 0.5 * wt[i] * host_blif_value(tb, u) * std::exp(std::complex<double>(0.0, -w * u));
+      }
+    return s;
+  }
+  for (int j = 0; j <= tb.Q; ++j) {  // CPPIF piece (j-1, j]
     for (size_t i = 0; i < x.size(); ++i) {
       const double u = j - 0.5 + 0.5 * x[i];
       double T = 0;

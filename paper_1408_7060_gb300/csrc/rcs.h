@@ -12,8 +12,9 @@ struct RcsPhases {  // one complex factor per frequency, passed by value
   double2 w[kMaxRcsFreq];
 };
 
-// That(w) = int T(u) e^{-j w u} du over the CPPIF support (Eq. 3), 24-point Gauss-Legendre per piece
-std::complex<double> cppif_spectrum(const TBasis& tb, double w);
+// That(w) = int T(u) e^{-j w u} du over the basis' support (Eq. 3): 24-point Gauss-Legendre
+// per CPPIF piece, or per unit interval of the BLIF's (-M, M)
+std::complex<double> basis_spectrum(const TBasis& tb, double w);
 // acc[f][b][k] += e^{-j omega_f l dt} x[b][k] (nb right-hand sides of the context's ns)
 void rcs_dft_accum(aim_ctx* c, int nb, int l, int n_freq, const double* omega, const double2* x, double2* acc);
 // acc[f] *= s.w[f]

@@ -27,7 +27,7 @@
 // with (D^2 T)(u) = T''/dt^2 + 2 j w T'/dt - w^2 T (envelope derivative D = d/dt + j w)
 __device__ __forceinline__ void time_kernels(const TimeK& p, int m, double R, double2& fA, double2& fP) {
   double T[4];
-  cppif_eval(p.tb, (double)m - R / p.cdt, T);
+  tb_eval(p.tb, m, R / p.cdt, T);
   double re = T[2] / (p.dt * p.dt) - p.wc * p.wc * T[0];
   double im = 2.0 * p.wc * T[1] / p.dt;
   double s, c;
@@ -40,7 +40,7 @@ __device__ __forceinline__ void time_kernels(const TimeK& p, int m, double R, do
 __device__ __forceinline__ void time_kernels_at0(const TimeK& p, int m, double2& fA0, double2& fP0,
                                                  double2& dA0, double2& dP0) {
   double T[4];
-  cppif_eval(p.tb, (double)m, T);
+  tb_eval(p.tb, m, 0.0, T);
   const double dt2 = p.dt * p.dt, w2 = p.wc * p.wc;
   fA0 = make_double2(T[2] / dt2 - w2 * T[0], 2.0 * p.wc * T[1] / p.dt);
   fP0 = make_double2(T[0], 0.0);

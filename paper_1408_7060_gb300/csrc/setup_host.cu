@@ -254,8 +254,9 @@ void host_extreme_candidates(int N, const std::vector<int>& nptr, std::vector<in
 // T(u) = prod_{k != j} (u - j + k)/(k - j), expanded in ascending powers of u.
 void host_cppif(int Q, TBasis& tb) {
   if (Q < 1 || Q > aimc::kMaxOrder) throw AimError{AIM_ERR_ARG, "CPPIF order must be 1..4"};
+  std::memset(&tb, 0, sizeof(tb));
+  tb.kind = AIM_CPPIF;
   tb.Q = Q;
-  std::memset(tb.coef, 0, sizeof(tb.coef));
   for (int j = 0; j <= Q; ++j) {
     double c[aimc::kMaxOrder + 1] = {1.0};
     int deg = 0;
@@ -275,6 +276,74 @@ void host_cppif(int Q, TBasis& tb) {
 }
 
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+// BLIF of half-width M for the band fraction beta = f_bw dt (Sec. 3.1.2): guard band
+// b = pi (1 - 2 beta), 1/G(M^2) = M / sinh(b M), and the extrapolation weights.  Each row
+// ext[p] (p = 1..M-1) is the least-squares fit of exp(j w_n p) by sum_q ext[p][q]
+// exp(-j w_n q), q = 0..M-1, over the 2M frequencies w_n = 2 pi beta (-1 + 2n/(2M-1)).  The
+// frequency set is symmetric, so the solution is real: it is the least-squares solution of
+// the real system [cos(w_n q); -sin(w_n q)] e = [cos(w_n p); sin(w_n p)] (4M rows), solved
+// here by Gram-Schmidt with one re-orthogonalisation and back substitution.
+void host_blif(int M, double beta, TBasis& tb) {
+  if (M < 2 || M > aimc::kMaxHalfWidth) throw AimError{AIM_ERR_ARG, "BLIF half-width must be 2..5"};
+  if (!(beta > 0.0 && beta < 0.5)) throw AimError{AIM_ERR_ARG, "blif_band (f_bw dt) must lie in (0, 1/2)"};
+  std::memset(&tb, 0, sizeof(tb));
+  tb.kind = AIM_BLIF;
+  tb.Q = M;
+  tb.b = aimc::kPi * (1.0 - 2.0 * beta);
+  tb.invG0 = (double)M / std::sinh(tb.b * M);
+  const int nw = 2 * M, rows = 2 * nw;
+  std::vector<double> A((size_t)rows * M), Q((size_t)rows * M), R((size_t)M * M, 0.0);
+  for (int n = 0; n < nw; ++n) {
+    const double w = 2.0 * aimc::kPi * beta * (-1.0 + 2.0 * n / (double)(nw - 1));
+    for (int q = 0; q < M; ++q) {
+      A[(size_t)n * M + q] = std::cos(w * q);
+      A[(size_t)(nw + n) * M + q] = -std::sin(w * q);
+    }
+  }
+  Q = A;
+  for (int j = 0; j < M; ++j) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < j; ++i) {
+        double d = 0.0;
+        for (int r = 0; r < rows; ++r) d += Q[(size_t)r * M + i] * Q[(size_t)r * M + j];
+        R[(size_t)i * M + j] += d;
+        for (int r = 0; r < rows; ++r) Q[(size_t)r * M + j] -= d * Q[(size_t)r * M + i];
+      }
+    double nrm = 0.0;
+    for (int r = 0; r < rows; ++r) nrm += Q[(size_t)r * M + j] * Q[(size_t)r * M + j];
+    nrm = std::sqrt(nrm);
+    R[(size_t)j * M + j] = nrm;
+    for (int r = 0; r < rows; ++r) Q[(size_t)r * M + j] /= nrm;
+  }
+  for (int p = 1; p < M; ++p) {
+    std::vector<double> rhs(rows), y(M, 0.0);
+    for (int n = 0; n < nw; ++n) {
+      const double w = 2.0 * aimc::kPi * beta * (-1.0 + 2.0 * n / (double)(nw - 1));
+      rhs[n] = std::cos(w * p);
+      rhs[nw + n] = std::sin(w * p);
+    }
+    for (int j = 0; j < M; ++j)
+      for (int r = 0; r < rows; ++r) y[j] += Q[(size_t)r * M + j] * rhs[r];
+    for (int j = M - 1; j >= 0; --j) {
+      double s = y[j];
+      for (int i = j + 1; i < M; ++i) s -= R[(size_t)j * M + i] * tb.ext[p][i];
+      tb.ext[p][j] = s / R[(size_t)j * M + j];
+    }
+  }
+}
+
+// T(u) of the BLIF on the host (values only): sinc(u) sinh(b sqrt(M^2 - u^2)) /
+// sqrt(M^2 - u^2) / G(M^2), the limit b / G(M^2) at |u| = M
+double host_blif_value(const TBasis& tb, double u) {
+  const double M = tb.Q;
+  if (!(std::fabs(u) < M)) return 0.0;
+  const double x = aimc::kPi * u;
+  const double sinc = std::fabs(x) < 1e-8 ? 1.0 - x * x / 6.0 : std::sin(x) / x;
+  const double r = std::sqrt(M * M - u * u);
+  const double g = r < 1e-12 ? tb.b : std::sinh(tb.b * r) / r;
+  return sinc * g * tb.invG0;
+}
+
 void host_gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.resize(n);
   w.resize(n);

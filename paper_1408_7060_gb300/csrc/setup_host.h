@@ -29,4 +29,6 @@ void host_transpose_pattern(int N, const std::vector<int>& anchor, int ns, std::
                             std::vector<int>& nidx, std::vector<int>& nslot);
 void host_extreme_candidates(int N, const std::vector<int>& nptr, std::vector<int>& cand, int& n_active);
 void host_cppif(int Q, TBasis& tb);
+void host_blif(int M, double beta, TBasis& tb);
+double host_blif_value(const TBasis& tb, double u);
 void host_gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);

@@ -1,0 +1,93 @@
+"""The BLIF temporal basis (aim_tbasis.kind = AIM_BLIF, half-width M = 3, band fraction 1/4;
+Sec. 3.1.2) on the GPU against the oracle.
+
+Expected values: ``tests/golden/blif_sphere480.txt``, written by the committed script
+``tests/golden/make_blif_sphere480.py`` from the oracle alone (its ET-AIM matrices with the
+extrapolated BLIF time factors, and their dense-LU march of Eq. 5), for the 480-RWG sphere at
+150 MHz +-20 %:
+
+* N_g = floor(R_max/(c dt) + M) equal;
+* products Z~_m x for every delay on 96 sampled rows, complex128: 1e-10;
+* the complex128 march (GMRES tolerance 1e-10) on 32 sampled rows over 50 steps: 1e-6; the
+  complex64 march (tolerance 1e-6): 1e-4;
+* aim_march_spectrum of the same march equals the oracle's transform of the library's own
+  currents, with the BLIF's spectrum from adaptive quadrature: 1e-10;
+* the CPPIF-only entry points (sampled-envelope excitation and far field) refuse a BLIF
+  context with AIM_ERR_ARG.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import efie, rcs
+from paper_1408_7060_gb300.inputs import make_workload
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "blif_sphere480.txt")
+
+
+def golden():
+    ng, prod, mar = None, {}, {}
+    for line in open(GOLD):
+        if line.startswith("#"):
+            continue
+        f = line.split()
+        if f[0] == "ng":
+            ng = int(f[1])
+        elif f[0] == "prod":
+            prod.setdefault(int(f[1]), []).append((int(f[2]), float(f[3]) + 1j * float(f[4])))
+        else:
+            mar.setdefault(int(f[1]), []).append((int(f[2]), float(f[3]) + 1j * float(f[4])))
+    prow = np.array([r for r, _ in prod[0]])
+    P = np.array([[v for _, v in prod[m]] for m in sorted(prod)])
+    mrow = np.array([r for r, _ in mar[1]])
+    I = np.array([[v for _, v in mar[l]] for l in sorted(mar)])
+    return ng, prow, P, mrow, I
+
+
+def workload():
+    return make_workload("sphere480", band_frac=0.2, n_t=50, basis="blif", order=3)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+def test_blif_products_and_march_vs_oracle():
+    from paper_1408_7060_gb300 import AimContext
+
+    ng, prow, P, mrow, I = golden()
+    w = workload()
+    rng = np.random.default_rng(41)
+    x = rng.standard_normal(480) + 1j * rng.standard_normal(480)
+    with AimContext.from_workload(w, precision="c128") as c:
+        assert c.n_delays == ng
+        for m in range(ng + 1):
+            assert rel(c.matvec(m, x[None])[0][prow], P[m]) < 1e-10, m
+        cur, st, rc = c.march(w.khat, w.phat, w.sigma, w.t_d, w.n_t, 1e-10)
+    assert st["last_step"] == w.n_t
+    assert rel(cur[:, 0][:, mrow], I) < 1e-6
+    with AimContext.from_workload(w, precision="c64") as c:
+        cur64, st, rc = c.march(w.khat, w.phat, w.sigma, w.t_d, w.n_t, 1e-6)
+    assert rel(cur64[:, 0][:, mrow], I) < 1e-4
+
+
+def test_blif_march_spectrum_and_refusals():
+    from paper_1408_7060_gb300 import AimContext, abi
+
+    w = workload()
+    p = efie.Params(dt=w.dt, f_c=w.f_c, basis="blif", M=3, beta=w.beta)
+    freqs = np.array([w.f_c, w.f_c + 0.5 * w.f_bw])
+    with AimContext.from_workload(w, precision="c128") as c:
+        spec, st, rc = c.march_spectrum(w.khat, w.phat, w.sigma, w.t_d, w.n_t, 1e-10, freqs)
+        cur, _, _ = c.march(w.khat, w.phat, w.sigma, w.t_d, w.n_t, 1e-10)
+        for f, s in zip(freqs, spec):
+            Om = 2 * math.pi * (f - w.f_c)
+            ref = rcs.envelope_spectrum_p(cur[:, 0], p, Om) / rcs.incident_spectrum(w.sigma, w.t_d, w.f_c, Om)
+            assert rel(s[0], ref) < 1e-10, f
+        with pytest.raises(abi.AimError):
+            abi.aim_farfield(c.handle, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]),
+                             np.array([[0.0, 1.0, 0.0]]), np.ascontiguousarray(cur[:4, 0]), 0, 2)
