@@ -6,7 +6,9 @@
 * sum_m m K_m = -(1/dt) K'  with K' the same fill for the kernel (1 + j k R + k^2 R^2)/R^2
   e^{-jkR}/(4 pi) and the Gram factor 1/2: the first time moment, which pins the T'/dt terms
   of (DT) and (D^2 T) that the partition of unity cancels;
-* dt sum_l W_l = j w_c sigma sqrt(2 pi) e^{-j w_c t_d} W_FD (the Gaussian sample sum).
+* dt sum_l W_l = j w_c sigma sqrt(2 pi) e^{-j w_c t_d} W_FD (the Gaussian sample sum);
+* at chi = 3 the CFIE march decays where the EFIE march grows (the EFIE's interior-resonance
+  growth on a closed surface; the CFIE is the paper's choice for spheres, Sec. 5.1).
 """
 import math
 
@@ -78,3 +80,24 @@ def test_excitation_dc(s120):
     lhs = w.dt * W.sum(0)
     rhs = 1j * p.wc * w.sigma * math.sqrt(2 * math.pi) * np.exp(-1j * p.wc * w.t_d) * WF
     assert np.linalg.norm(lhs - rhs) < 1e-12 * np.linalg.norm(rhs)
+
+
+def test_cfie_march_decays_where_efie_grows():
+    """chi = 3 on the 120-RWG sphere (CPPIF Q = 2, beta = 1/4): the EFIE march grows after the
+    pulse (the broadband growth of Sec. 3.1.1), the CFIE (alpha = 0.5, Sec. 5.1) march decays
+    by more than 15 orders of magnitude over 200 steps."""
+    w = make_workload("sphere480", band_frac=0.5)
+    rwg = build_rwg(*icosphere(1, 1.0))
+    p = efie.Params(dt=w.dt, f_c=w.f_c, Q=2)
+    Z = efie.fill_dense(rwg, p)
+    K = mfie.fill_dense(rwg, p, n_delays=Z.shape[0] - 1)
+    eta = math.sqrt(p.mu / p.eps)
+    steps = np.arange(1, 201)
+    V = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, steps)[:, 0]
+    W = mfie.excitation(rwg, p, w.khat[0], w.phat[0], w.sigma, w.t_d, steps)
+    from oracle import march
+
+    ne = np.linalg.norm(march.march_dense(Z, V[:, None])[:, 0], axis=1)
+    nc = np.linalg.norm(march.march_dense(0.5 * Z + 0.5 * eta * K, (0.5 * V + 0.5 * eta * W)[:, None])[:, 0], axis=1)
+    assert ne[-1] > ne[:60].max()
+    assert nc[-1] < 1e-15 * nc.max()
