@@ -13,7 +13,9 @@ Output: ``blif_sphere480.txt``:
   numpy's default_rng(41) (standard normal real and imaginary parts, in that order), on 96
   rows drawn with PCG64(8);
 * ``march step row re im``: the currents of Eq. 5 solved by dense LU on the oracle's AIM
-  matrices, steps 1..50, on 32 rows drawn with PCG64(9).
+  matrices, steps 1..50, on 32 rows drawn with PCG64(9);
+* ``mot step row re im``: the direct ET-MOT currents of Eq. 4 (the oracle's Galerkin fill of
+  the same envelope EFIE with the same time factors, dense LU), same steps and rows.
 
     python tests/golden/make_blif_sphere480.py      # a few minutes on one core
 """
@@ -49,14 +51,18 @@ def main():
     x = rng.standard_normal(rwg.ns) + 1j * rng.standard_normal(rwg.ns)
     V = efie.excitation(rwg, p, w.khat, w.phat, w.sigma, w.t_d, np.arange(1, w.n_t + 1))
     I = march.march_dense(ZA, V)[:, 0]
+    J = march.march_dense(efie.fill_dense(rwg, p), V)[:, 0]
     prow, mrow = seeded_rows(rwg.ns, 96, 8), seeded_rows(rwg.ns, 32, 9)
-    lines = ["# blif sphere480: ng N_g | prod m row re im | march step row re im (oracle ET-AIM, dense LU)",
+    lines = ["# blif sphere480: ng N_g | prod m row re im | march / mot step row re im (oracle ET-AIM / "
+             "direct ET-MOT, dense LU)",
              f"ng {A.n_delays}"]
     for m in range(A.n_delays + 1):
         y = ZA[m] @ x
         lines += [f"prod {m} {r} {y[r].real:.17e} {y[r].imag:.17e}" for r in prow]
     for l in range(w.n_t):
         lines += [f"march {l + 1} {r} {I[l, r].real:.17e} {I[l, r].imag:.17e}" for r in mrow]
+    for l in range(w.n_t):
+        lines += [f"mot {l + 1} {r} {J[l, r].real:.17e} {J[l, r].imag:.17e}" for r in mrow]
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
     print("wrote", OUT)
