@@ -23,6 +23,9 @@ What it computes (each module cites the passage it follows):
                  the pre-corrected near-zone matrices (Sec. 4, stages i-iv).
 * ``mfie``       the time-differentiated envelope MFIE and its frequency-domain form, for
                  the combined-field equation of Sec. 2.1 (CFIE).
+* ``mfie_aim``   the AIM form of the MFIE operator (Sec. 4 on the CFIE's MFIE term): curl
+                 test weights by moment matching, the grid kernel (DT) e^{-jkR}/R and the
+                 pre-corrected near zone.
 * ``march``      time marching of Eq. 4 (direct ET-MOT) and Eq. 5 (ET-AIM).
 * ``blocked``    the delayed sums of the right-hand side by the multilevel blocked
                  schedule with temporal FFTs (Sec. 4, stage ii), and directly.
