@@ -277,6 +277,10 @@ def run_aim(args):
     w = make_workload(args.workload, precond=pre["precond"], refine=pre["refine"], autotune=args.autotune)
     w.refine_every = max(1, args.refine_every)
     w.rhs_blocked = args.rhs_blocked
+    if args.basis:
+        w.basis = args.basis
+    if args.order:
+        w.order = args.order
     w.precond_radius = pre["precond_scale"] * w.near_radius if w.precond == "sai" else 0.0
     waves_k, waves_p = w.khat, w.phat
     if args.max_waves:
@@ -409,6 +413,7 @@ def run_aim(args):
                    "precond": w.precond, "precond_radius_m": round(w.precond_radius, 6),
                    "precond_nnz": info["precond_nnz"], "fp64_refinement": w.refine,
                    "fp64_check_every": w.refine_every, "rhs": "blocked" if w.rhs_blocked else "direct",
+                   "temporal_basis": f"{w.basis} {'Q' if w.basis == 'cppif' else 'M'}={w.order}",
                    "active_box": {"lo": list(info["box_lo"]), "hi": list(info["box_hi"])},
                    "launch_plan": {k: info["plan_" + k] for k in ("zw", "cw", "rp", "ypb")} |
                    {"source": ["default", "measured", "cached"][info["plan_source"]]},
@@ -617,6 +622,9 @@ def main():
     ap.add_argument("--rhs-blocked", type=int, default=0,
                     help="1: delayed grid sums by the multilevel blocked schedule (power-of-two z lengths)")
     ap.add_argument("--precond-scale", type=float, default=0.0, help="SAI pattern radius in near radii")
+    ap.add_argument("--basis", default=None, choices=["cppif", "blif"],
+                    help="temporal basis (default: the workload's); blif uses the workload's beta as its band")
+    ap.add_argument("--order", type=int, default=0, help="CPPIF order Q or BLIF half-width M (0: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1, 2],
                     help="launch plan: 0 defaults, 1 tuned at setup (cached plan reused), 2 re-tuned")
     ap.add_argument("--e2e-steps", type=int, default=3)
